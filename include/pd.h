@@ -1,0 +1,215 @@
+/*
+ * pd.h -- C ABI of the GB300 projective-dynamics library (libpdgb300.so).
+ *
+ * The library time-steps a tetrahedral mesh whose elements carry their own
+ * strain and volume stiffness, with the domain-decomposed projective
+ * dynamics of "Volumetric Homogenization for Knitwear Simulation"
+ * (arXiv 2405.12484), Sec. 7:
+ *   - implicit Euler, inertial target y = x* + dt v* + dt^2 g   (Sec. 7, eq. for a)
+ *   - PD local step: per tet F = Ds Dm^-1, SVD, rotation target R(F) and
+ *     volume target V(F)                                        (Sec. 7.1, Eq. pd_local, Eq. vol_pre)
+ *   - PD global step K x = b                                     (Sec. 7.1, K and b)
+ *     solved by the domain-decomposed subspace solve: per-domain internal
+ *     solves, boundary modes Psi = -Kii^-1 Kib, and the reduced (interface)
+ *     system                                                     (Sec. 7.2, Eq. cms_boundary,
+ *                                                                 Eq. global_subspace, Eq. dd)
+ *   - the elasticity of Eq. energy with per-element gamma_s, gamma_v >= 0
+ *                                                                (Sec. 6, Eq. energy, Eq. elasticity_fit)
+ *
+ * Conventions shared by every entry point
+ *   - Status: every function returns pd_status (0 = PD_OK, < 0 = error).
+ *     No function aborts, prints, or traps the device.  pd_last_error()
+ *     returns a text description of the most recent error of the calling
+ *     thread.
+ *   - Memory: arguments marked [host] are read or written on the host
+ *     before the call returns.  Arguments marked [device] are CUDA device
+ *     pointers on the current device, accessed in stream order on the
+ *     mesh's stream; the caller keeps them alive until that work is done.
+ *     The caller owns every buffer it passes; the library owns everything
+ *     it derives (matrices, factors, orderings, scratch).
+ *   - Vertex arrays are n_v x 3 float (x, y, z per vertex, row-major) in the
+ *     caller's vertex order.  Pinned-vertex arrays list the pinned vertices
+ *     in increasing vertex id.
+ *   - Calls on one mesh are stream-ordered and asynchronous; a device-side
+ *     error (non-finite state, failed factorisation) is reported by the next
+ *     pd_sync().
+ *   - A mesh object is not thread-safe: one host thread at a time.
+ */
+#ifndef PD_GB300_H
+#define PD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pd_status;
+
+enum {
+    PD_OK = 0,
+    PD_ERR_INVALID_ARG = -1,      /* null pointer, size out of range, bad option */
+    PD_ERR_BAD_MESH = -2,         /* index out of range, repeated corner, rest volume <= 0, isolated vertex */
+    PD_ERR_BAD_MATERIAL = -3,     /* gamma < 0 or non-finite (Sec. 6: gamma >= 0) */
+    PD_ERR_NOT_PREFACTORED = -4,  /* pd_step before pd_prefactor, or after pd_set_materials */
+    PD_ERR_NOT_SPD = -5,          /* a Cholesky pivot was <= 0 during pd_prefactor */
+    PD_ERR_NO_MEMORY = -6,        /* device or host allocation failed */
+    PD_ERR_NONFINITE = -7,        /* NaN/Inf found in the state (device flag) */
+    PD_ERR_TIMEOUT = -8,          /* a bounded wait expired */
+    PD_ERR_CUDA = -9,             /* any other CUDA runtime error */
+    PD_ERR_UNSUPPORTED = -10      /* option not available in this build */
+};
+
+/* Arithmetic of the per-iteration dense products of the subspace solve. */
+enum {
+    PD_PREC_FP32 = 0,   /* FP32 storage, FP32 accumulation */
+    PD_PREC_BF16 = 1,   /* BF16 storage, FP32 accumulation (FP64-residual refinement advised) */
+    PD_PREC_TF32 = 2    /* TF32-rounded storage, FP32 accumulation */
+};
+
+typedef struct pd_solver_opts {
+    int32_t precision;     /* PD_PREC_*; default PD_PREC_FP32 */
+    int32_t refine_steps;  /* 0..2 refinement steps per PD iteration with an FP64 residual r = b - K x */
+    int32_t use_graphs;    /* 1: replay each frame as a captured CUDA graph (default), 0: plain launches */
+    int32_t reserved;      /* must be 0 */
+} pd_solver_opts;
+
+typedef struct pd_mesh pd_mesh;   /* opaque, library-owned */
+
+typedef struct pd_mesh_info {
+    int32_t n_vertices, n_tets, n_domains, n_pinned;
+    int32_t n_interface;           /* vertices shared by two or more domains (not pinned) */
+    int32_t n_internal;            /* sum over domains of internal (non-interface, non-pinned) vertices */
+    int32_t max_domain_internal;   /* largest per-domain internal vertex count */
+    int32_t max_domain_boundary;   /* largest per-domain boundary-mode count */
+    int64_t device_bytes;          /* device memory held by the mesh */
+    double prefactor_seconds;      /* wall time of the last pd_prefactor */
+    int32_t launches_per_iter;     /* kernels launched per PD iteration (after pd_prefactor) */
+    int32_t launches_per_frame;    /* kernels launched per frame besides the iterations (pin copy, inertia, velocity) */
+    int64_t phase_bytes[16];       /* algorithmic bytes moved by one launch of each phase (pd_phase_name order) */
+} pd_mesh_info;
+
+/*
+ * pd_create_mesh -- build a mesh object from rest geometry (Sec. 4: tet mesh;
+ * Sec. 7.2: element-based partition into domains).
+ *   rest_xyz    [host]  n_v x 3 double rest positions.
+ *   tets        [host]  n_t x 4 int32 vertex ids (any orientation; the rest
+ *                       volume |det Dm|/6 must be > 0).
+ *   vertex_mass [host]  n_v double lumped masses, or NULL: then
+ *                       m_v = sum over incident tets of density * V_e / 4.
+ *   tet_domain  [host]  n_t int32 domain ids in [0, n_domains), or NULL:
+ *                       then tets are split into n_domains slabs along the
+ *                       longest axis of the rest bounding box.
+ *   pinned      [host]  n_v uint8, nonzero = Dirichlet vertex, or NULL.
+ *   cuda_stream         cudaStream_t used for all work on this mesh (NULL =
+ *                       legacy default stream).
+ *   out         [host]  receives the new mesh.
+ * Vertices touching tets of two or more domains become interface vertices;
+ * the others are internal to their domain.  Errors: INVALID_ARG, BAD_MESH,
+ * NO_MEMORY, CUDA.  On error *out is NULL and nothing is leaked.
+ */
+pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tets, int32_t n_t,
+                         const double* vertex_mass, double density, const int32_t* tet_domain,
+                         int32_t n_domains, const uint8_t* pinned, void* cuda_stream, pd_mesh** out);
+
+/* Release every resource of the mesh (synchronises its stream first).  NULL is ignored. */
+void pd_destroy_mesh(pd_mesh* mesh);
+
+/*
+ * pd_set_materials -- per-element parameters gamma_s (strain) and gamma_v
+ * (volume) of Eq. energy (Sec. 6); n_t floats each, in the caller's tet
+ * order; host or device pointers (detected).  Values must be finite and
+ * >= 0 (Sec. 6, constraint of Eq. elasticity_fit), else BAD_MATERIAL and
+ * nothing changes.  Invalidates the prefactorisation.
+ */
+pd_status pd_set_materials(pd_mesh* mesh, const float* gamma_s, const float* gamma_v);
+
+/*
+ * pd_prefactor -- assemble K = M/dt^2 + sum_e V_e (gs+gv) B^T (D^T:D) B
+ * (Sec. 7.1) and precompute the subspace solve on the device in FP64
+ * (Sec. 7.2): per domain the Cholesky factor of K_ii, K_ii^-1 and the
+ * boundary modes Psi = -K_ii^-1 K_ib (Eq. cms_boundary); the reduced
+ * interface matrix S = K_BB + sum_d K_bi Psi and its inverse; then the
+ * per-iteration copies in the requested precision.
+ *   dt    time step (> 0).
+ *   opts  [host] or NULL for defaults.
+ * Synchronous.  Errors: NOT_SPD, NO_MEMORY, INVALID_ARG, UNSUPPORTED, CUDA.
+ */
+pd_status pd_prefactor(pd_mesh* mesh, double dt, const pd_solver_opts* opts);
+
+/* Set / read positions and velocities (n_v x 3 float each, [device]; either may be NULL to skip). */
+pd_status pd_set_state(pd_mesh* mesh, const float* x, const float* v);
+pd_status pd_get_state(pd_mesh* mesh, float* x, float* v);
+
+/*
+ * pd_step -- one implicit-Euler frame (Sec. 7): y = x* + dt v* + dt^2 g,
+ * x^0 = y, then n_iter PD iterations (local step, RHS assembly, subspace
+ * global solve), then v = (x - x*)/dt.
+ *   pin_targets [device] n_pinned x 3 float positions of the pinned
+ *               vertices at the end of the frame, or NULL to hold them.
+ *   gravity     [host]   3 floats (m/s^2), or NULL for (0, 0, -9.81).
+ *   n_iter      PD iterations (1..1000).
+ *   x_out       [device] n_v x 3 float, receives the new positions, or NULL.
+ * Asynchronous on the mesh stream.  Errors: NOT_PREFACTORED, INVALID_ARG, CUDA.
+ */
+pd_status pd_step(pd_mesh* mesh, const float* pin_targets, const float* gravity, int32_t n_iter,
+                  float* x_out);
+
+/* Wait for the mesh stream; report and clear device-side error flags (NONFINITE, NOT_SPD). */
+pd_status pd_sync(pd_mesh* mesh);
+
+/* Sizes and memory of the mesh ([host] out). */
+pd_status pd_get_info(pd_mesh* mesh, pd_mesh_info* out);
+
+/* Text for a status code (static storage). */
+const char* pd_status_string(pd_status status);
+
+/* Description of the last error on the calling thread (static thread-local storage). */
+const char* pd_last_error(void);
+
+/* ---- Diagnostics: single phases of the step, for parity checks ---- */
+
+/*
+ * pd_project -- the local-step projections alone (Sec. 7.1, Eq. pd_local,
+ * Eq. vol_pre) on n deformation gradients.
+ *   F      [device] n x 9 float, row-major 3x3.
+ *   R, V   [device] n x 9 float outputs (either may be NULL): nearest
+ *          rotation and nearest unit-determinant matrix with every target
+ *          singular value >= 0.01.
+ *   sigma  [device] n x 3 float signed singular values (descending
+ *          magnitude, last one carries sign(det F)), or NULL.
+ *   stream cudaStream_t.
+ */
+pd_status pd_project(const float* F, int32_t n, float* R, float* V, float* sigma, void* stream);
+
+/*
+ * pd_local_rhs -- local step plus RHS assembly at positions x with inertial
+ * target y (both [device] n_v x 3): b = (M/dt^2) y + sum_e V_e B^T D^T :
+ * (gs R + gv V) - K_fp x_p for free vertices (Sec. 7.1, b); rows of pinned
+ * vertices are set to 0.  b [device] n_v x 3.  Requires pd_prefactor.
+ */
+pd_status pd_local_rhs(pd_mesh* mesh, const float* x, const float* y, float* b);
+
+/*
+ * pd_solve -- the subspace global solve alone (Sec. 7.2): x_f = K_ff^-1 r_f
+ * for the free vertices; rows of pinned vertices of x are set to 0.
+ * r, x [device] n_v x 3 (may not alias).  Requires pd_prefactor.
+ */
+pd_status pd_solve(pd_mesh* mesh, const float* r, float* x);
+
+/*
+ * pd_phase_times -- mean device time per launch (ms) of each kernel class
+ * during the last frame replayed with timing enabled (see
+ * pd_enable_timing); out[k] for k < n_out, in the order named by
+ * pd_phase_name(k).  Returns the number of phases in *n_phases.
+ */
+pd_status pd_enable_timing(pd_mesh* mesh, int32_t enable);
+pd_status pd_phase_times(pd_mesh* mesh, float* out, int32_t n_out, int32_t* n_phases);
+const char* pd_phase_name(int32_t k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PD_GB300_H */

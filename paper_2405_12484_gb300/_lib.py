@@ -1,0 +1,83 @@
+"""ctypes binding of libpdgb300.so (argument marshalling only).
+
+Every function of include/pd.h is exposed under the same name.  The
+library must be built (``paper_2405_12484_gb300.build.build()``); importing
+this module without it raises ImportError -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpdgb300.so")
+
+PD_OK = 0
+PD_ERR_INVALID_ARG = -1
+PD_ERR_BAD_MESH = -2
+PD_ERR_BAD_MATERIAL = -3
+PD_ERR_NOT_PREFACTORED = -4
+PD_ERR_NOT_SPD = -5
+PD_ERR_NO_MEMORY = -6
+PD_ERR_NONFINITE = -7
+PD_ERR_TIMEOUT = -8
+PD_ERR_CUDA = -9
+PD_ERR_UNSUPPORTED = -10
+
+PD_PREC_FP32 = 0
+PD_PREC_BF16 = 1
+PD_PREC_TF32 = 2
+
+
+class pd_solver_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("refine_steps", C.c_int32), ("use_graphs", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class pd_mesh_info(C.Structure):
+    _fields_ = [("n_vertices", C.c_int32), ("n_tets", C.c_int32), ("n_domains", C.c_int32),
+                ("n_pinned", C.c_int32), ("n_interface", C.c_int32), ("n_internal", C.c_int32),
+                ("max_domain_internal", C.c_int32), ("max_domain_boundary", C.c_int32),
+                ("device_bytes", C.c_int64), ("prefactor_seconds", C.c_double),
+                ("launches_per_iter", C.c_int32), ("launches_per_frame", C.c_int32),
+                ("phase_bytes", C.c_int64 * 16)]
+
+
+# (name, restype, argtypes) exactly as declared in include/pd.h
+SIGNATURES = [
+    ("pd_create_mesh", C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_double,
+                                   C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("pd_destroy_mesh", None, [C.c_void_p]),
+    ("pd_set_materials", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_prefactor", C.c_int32, [C.c_void_p, C.c_double, C.POINTER(pd_solver_opts)]),
+    ("pd_set_state", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_get_state", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_step", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    ("pd_sync", C.c_int32, [C.c_void_p]),
+    ("pd_get_info", C.c_int32, [C.c_void_p, C.POINTER(pd_mesh_info)]),
+    ("pd_status_string", C.c_char_p, [C.c_int32]),
+    ("pd_last_error", C.c_char_p, []),
+    ("pd_project", C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_local_rhs", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_solve", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_enable_timing", C.c_int32, [C.c_void_p, C.c_int32]),
+    ("pd_phase_times", C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    ("pd_phase_name", C.c_char_p, [C.c_int32]),
+]
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libpdgb300.so not built at {path}: run paper_2405_12484_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+class PDError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status

@@ -1,0 +1,259 @@
+// Per-iteration domain-decomposed subspace solve (Sec. 7.2) on sm_103a.
+//
+// With the internal/boundary split of every domain d (Eq. dd) and the
+// boundary modes Psi_d = -K_ii^-1 K_ib (Eq. cms_boundary), the Galerkin
+// projection onto the subspace of Eq. global_subspace with the full set of
+// internal modes gives the exact solution of K x = b in four phases:
+//   condense : [t_d; c_d] = [K_ii^-1; Psi_d^T] b_i            (per domain)
+//   gather   : c = b_B + sum_d E_d c_d                          (per interface vertex, fixed order)
+//   coarse   : x_B = S^-1 c,  S = K_BB + sum_d K_bi Psi_d       (reduced interface system)
+//   backsub  : x_i = t_d + Psi_d x_B(d)                         (per domain)
+// Every product is a dense matrix times three right-hand sides (x, y, z
+// share the scalar matrix, K = K_s (x) I_3): HBM-bound streaming of the
+// matrices with 16-byte loads, FP32 accumulation, vectors staged in shared
+// memory, fixed-order warp reductions (deterministic), no atomics.
+#include "pd_internal.h"
+
+namespace pdg {
+
+namespace {
+
+template <class T>
+struct VecN;
+template <>
+struct VecN<float> {
+    static constexpr int N = 4;
+};
+template <>
+struct VecN<__nv_bfloat16> {
+    static constexpr int N = 8;
+};
+
+__device__ __forceinline__ void load_vec(const float* p, float (&v)[4]) {
+    float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+
+__device__ __forceinline__ void load_vec(const __nv_bfloat16* p, float (&v)[8]) {
+    uint4 a = __ldcs(reinterpret_cast<const uint4*>(p));
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&a);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float2 f = __bfloat1622float2(h[k]);
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
+    }
+}
+
+// y[r] = add[r] + A[r, 0:cols] . xs  for r < rows; groups of LPR lanes own
+// two rows at a time; 256 threads.
+template <class T, int LPR>
+__device__ __forceinline__ void block_rows(const T* __restrict__ A, int rows, int ld, int cols,
+                                           const float4* __restrict__ xs, float4* __restrict__ y,
+                                           const float4* __restrict__ add) {
+    constexpr int VN = VecN<T>::N;
+    constexpr int G = 256 / LPR;
+    const int lane = threadIdx.x % LPR;
+    const int grp = threadIdx.x / LPR;
+    // the trip count is uniform across the block so every lane reaches the shuffles
+    for (int base = 0; base < rows; base += 2 * G) {
+        const int r0 = base + 2 * grp;
+        const bool one = r0 < rows;
+        const bool two = (r0 + 1) < rows;
+        const T* a0 = A + (int64_t)(one ? r0 : 0) * ld;
+        const T* a1 = A + (int64_t)(two ? r0 + 1 : (one ? r0 : 0)) * ld;
+        const int ncol = one ? cols : 0;
+        float s00 = 0.f, s01 = 0.f, s02 = 0.f, s10 = 0.f, s11 = 0.f, s12 = 0.f;
+#pragma unroll 4
+        for (int c = lane * VN; c < ncol; c += LPR * VN) {
+            float v0[VN], v1[VN];
+            load_vec(a0 + c, v0);
+            load_vec(a1 + c, v1);
+#pragma unroll
+            for (int j = 0; j < VN; ++j) {
+                float4 xv = xs[c + j];
+                s00 = fmaf(v0[j], xv.x, s00);
+                s01 = fmaf(v0[j], xv.y, s01);
+                s02 = fmaf(v0[j], xv.z, s02);
+                s10 = fmaf(v1[j], xv.x, s10);
+                s11 = fmaf(v1[j], xv.y, s11);
+                s12 = fmaf(v1[j], xv.z, s12);
+            }
+        }
+#pragma unroll
+        for (int off = LPR / 2; off > 0; off >>= 1) {
+            s00 += __shfl_xor_sync(0xffffffffu, s00, off, LPR);
+            s01 += __shfl_xor_sync(0xffffffffu, s01, off, LPR);
+            s02 += __shfl_xor_sync(0xffffffffu, s02, off, LPR);
+            s10 += __shfl_xor_sync(0xffffffffu, s10, off, LPR);
+            s11 += __shfl_xor_sync(0xffffffffu, s11, off, LPR);
+            s12 += __shfl_xor_sync(0xffffffffu, s12, off, LPR);
+        }
+        if (lane == 0 && one) {
+            float4 a = add ? add[r0] : make_float4(0.f, 0.f, 0.f, 0.f);
+            y[r0] = make_float4(a.x + s00, a.y + s01, a.z + s02, 0.f);
+            if (two) {
+                float4 b = add ? add[r0 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                y[r0 + 1] = make_float4(b.x + s10, b.y + s11, b.z + s12, 0.f);
+            }
+        }
+    }
+}
+
+constexpr int kMaxSubCols = 2048;   // largest per-domain internal / boundary count handled in shared memory
+
+// condense: one task = a row block of G_d = [K_ii^-1; Psi_d^T]; x = b_i (contiguous)
+template <class T>
+__global__ void __launch_bounds__(256) k_condense(const GemvTask* __restrict__ tasks, const T* __restrict__ pool,
+                                                  const float4* __restrict__ b, float4* __restrict__ tc) {
+    __shared__ float4 xs[kMaxSubCols];
+    const GemvTask tk = tasks[blockIdx.x];
+    for (int k = threadIdx.x; k < tk.cols; k += blockDim.x)
+        xs[k] = (k < tk.x_n) ? b[tk.x_off + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    block_rows<T, 8>(pool + tk.a_off, tk.rows, tk.ld, tk.cols, xs, tc + tk.y_off, nullptr);
+}
+
+// backsub: one task = a row block of Psi_d; x = x_B gathered through the domain's boundary list
+template <class T>
+__global__ void __launch_bounds__(256) k_backsub(const GemvTask* __restrict__ tasks, const T* __restrict__ pool,
+                                                 const int* __restrict__ bidx, const float4* __restrict__ xB,
+                                                 const float4* __restrict__ tc, float4* __restrict__ xout) {
+    __shared__ float4 xs[kMaxSubCols];
+    const GemvTask tk = tasks[blockIdx.x];
+    for (int k = threadIdx.x; k < tk.cols; k += blockDim.x)
+        xs[k] = (k < tk.x_n) ? xB[bidx[tk.x_off + k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    block_rows<T, 8>(pool + tk.a_off, tk.rows, tk.ld, tk.cols, xs, xout + tk.y_off, tc + tk.add_off);
+}
+
+// gather: c_B[j] = b_B[j] + sum over the domains touching j of their c_d entry (fixed order)
+__global__ void k_gather(int n_B, const int* __restrict__ ptr, const int* __restrict__ rows,
+                         const float4* __restrict__ bB, const float4* __restrict__ tc, float4* __restrict__ cB) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_B) return;
+    float4 acc = bB[j];
+    for (int k = ptr[j]; k < ptr[j + 1]; ++k) {
+        float4 c = tc[rows[k]];
+        acc.x += c.x; acc.y += c.y; acc.z += c.z;
+    }
+    cB[j] = acc;
+}
+
+constexpr int kCoarseChunk = 2048;
+
+// coarse: block (rb, ch) forms rows [rb*RPC, +RPC) of S^-1 times the column chunk ch of c_B
+template <class T>
+__global__ void __launch_bounds__(256) k_coarse(const T* __restrict__ S, int n_B, int ld, int rpc,
+                                                const float4* __restrict__ cB, float4* __restrict__ part) {
+    __shared__ float4 xs[kCoarseChunk];
+    const int c0 = blockIdx.y * kCoarseChunk;
+    const int ncol = min(kCoarseChunk, ld - c0);   // ld is a multiple of the vector width
+    for (int k = threadIdx.x; k < ncol; k += blockDim.x) {
+        int c = c0 + k;
+        xs[k] = (c < n_B) ? cB[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const int r0 = blockIdx.x * rpc;
+    const int rows = min(rpc, n_B - r0);
+    if (rows <= 0) return;
+    block_rows<T, 32>(S + (int64_t)r0 * ld + c0, rows, ld, ncol, xs, part + (int64_t)blockIdx.y * n_B + r0,
+                      nullptr);
+}
+
+// reduce: x_B[j] = sum over chunks (fixed order) of part[ch][j]
+__global__ void k_reduce(int n_B, int n_chunks, const float4* __restrict__ part, float4* __restrict__ xB) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_B) return;
+    float4 acc = part[j];
+    for (int c = 1; c < n_chunks; ++c) {
+        float4 p = part[(int64_t)c * n_B + j];
+        acc.x += p.x; acc.y += p.y; acc.z += p.z;
+    }
+    xB[j] = make_float4(acc.x, acc.y, acc.z, 0.f);
+}
+
+// r = b - K x over free vertices with FP64 accumulation (refinement residual)
+__global__ void k_residual(int n_free, const int* __restrict__ ptr, const int* __restrict__ col,
+                           const double* __restrict__ val, const float4* __restrict__ b, const float4* __restrict__ x,
+                           float4* __restrict__ r) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_free) return;
+    float4 bb = b[i];
+    double ax = bb.x, ay = bb.y, az = bb.z;
+    for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+        double kv = val[k];
+        float4 xv = x[col[k]];
+        ax -= kv * (double)xv.x;
+        ay -= kv * (double)xv.y;
+        az -= kv * (double)xv.z;
+    }
+    r[i] = make_float4((float)ax, (float)ay, (float)az, 0.f);
+}
+
+__global__ void k_axpy(int n, const float4* __restrict__ dx, float4* __restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 a = x[i], d = dx[i];
+    x[i] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w);
+}
+
+inline int nblk(int n, int b) { return (n + b - 1) / b; }
+
+template <class T>
+void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaStream_t s) {
+    phase_begin(m, PH_CONDENSE, s);
+    k_condense<T><<<m->n_tasks_cond, 256, 0, s>>>(m->d_tasks_cond.p, pool, b, m->d_tc.p);
+    PDG_CHECK_LAUNCH();
+    phase_end(m, s);
+    if (m->n_B > 0) {
+        phase_begin(m, PH_GATHER, s);
+        k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, m->d_tc.p,
+                                                  m->d_cB.p);
+        PDG_CHECK_LAUNCH();
+        phase_end(m, s);
+        phase_begin(m, PH_COARSE, s);
+        dim3 grid(nblk(m->n_B, m->coarse_rows_per_cta), m->coarse_nchunks);
+        k_coarse<T><<<grid, 256, 0, s>>>(pool + m->off_S, m->n_B, m->ld_S, m->coarse_rows_per_cta, m->d_cB.p,
+                                         m->d_part.p);
+        PDG_CHECK_LAUNCH();
+        phase_end(m, s);
+        phase_begin(m, PH_REDUCE, s);
+        k_reduce<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->coarse_nchunks, m->d_part.p, xout + m->n_int);
+        PDG_CHECK_LAUNCH();
+        phase_end(m, s);
+    }
+    if (m->n_tasks_back > 0) {
+        phase_begin(m, PH_BACKSUB, s);
+        k_backsub<T><<<m->n_tasks_back, 256, 0, s>>>(m->d_tasks_back.p, pool, m->d_bidx.p, xout + m->n_int,
+                                                    m->d_tc.p, xout);
+        PDG_CHECK_LAUNCH();
+        phase_end(m, s);
+    }
+}
+
+}  // namespace
+
+int dd_max_sub_cols() { return kMaxSubCols; }
+int dd_coarse_chunk() { return kCoarseChunk; }
+
+void launch_dd_solve(pd_mesh* m, const float4* b, float4* xout, cudaStream_t s, bool /*timed*/) {
+    if (m->prec == PD_PREC_BF16)
+        dd_solve_t<__nv_bfloat16>(m, m->d_mat16.p, b, xout, s);
+    else
+        dd_solve_t<float>(m, m->d_mat32.p, b, xout, s);
+}
+
+void launch_residual(const pd_mesh* m, const float4* b, const float4* x, float4* r, cudaStream_t s) {
+    if (m->n_free <= 0) return;
+    k_residual<<<nblk(m->n_free, 256), 256, 0, s>>>(m->n_free, m->d_K_ptr.p, m->d_K_col.p, m->d_K_val.p, b, x, r);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_axpy_free(const pd_mesh* m, const float4* dx, float4* x, cudaStream_t s) {
+    if (m->n_free <= 0) return;
+    k_axpy<<<nblk(m->n_free, 256), 256, 0, s>>>(m->n_free, dx, x);
+    PDG_CHECK_LAUNCH();
+}
+
+}  // namespace pdg

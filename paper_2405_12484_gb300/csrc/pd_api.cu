@@ -1,0 +1,1028 @@
+// C ABI of libpdgb300: mesh set-up, prefactorisation orchestration, frame
+// stepping with CUDA graphs, diagnostics.  Declarations and argument
+// contracts are in include/pd.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <utility>
+
+#include "pd_internal.h"
+
+namespace pdg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+// defined in the kernel translation units
+void launch_weights_raw(int n_t, const float* vol, const float* gs, const float* gv, float4* geo, cudaStream_t s);
+void dense_spd_inverse(double* A, int n, int lda, int64_t sA, double* X, int ldx, int64_t sX, int batch, int* d_err,
+                       cudaStream_t s);
+int dense_block();
+int dd_max_sub_cols();
+int dd_coarse_chunk();
+void launch_prefactor_helpers_scatter_coo(double* S, int ld, const int* r, const int* c, const double* v, int n,
+                                          cudaStream_t s);
+void launch_prefactor_add_block(double* S, int ldS, const double* Sd, int ldSd, const int* bidx, int nb,
+                                cudaStream_t s);
+void launch_cast_block(const double* src, int lds, int rows, int cols, int transpose, int prec, float* dst32,
+                       __nv_bfloat16* dst16, int64_t dst_off, int ldd, cudaStream_t s);
+
+static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+void phase_begin(pd_mesh* m, int phase, cudaStream_t s) {
+    if (!m->timing_armed || !(m->timing_mask & (1 << phase))) return;
+    size_t k = (size_t)m->ev_used;
+    if (2 * k + 1 >= m->ev_pool.size()) {
+        cudaEvent_t a, b;
+        PDG_CUDA(cudaEventCreate(&a));
+        PDG_CUDA(cudaEventCreate(&b));
+        m->ev_pool.push_back(a);
+        m->ev_pool.push_back(b);
+    }
+    if (m->ev_phase.size() <= k) m->ev_phase.resize(k + 1);
+    m->ev_phase[k] = phase;
+    cudaStreamCaptureStatus st;
+    PDG_CUDA(cudaStreamIsCapturing(s, &st));
+    unsigned flags = (st == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : cudaEventRecordDefault;
+    PDG_CUDA(cudaEventRecordWithFlags(m->ev_pool[2 * k], s, flags));
+    m->ev_open = true;
+}
+
+void phase_end(pd_mesh* m, cudaStream_t s) {
+    if (!m->timing_armed || !m->ev_open) return;   // only close a pair opened by phase_begin
+    m->ev_open = false;
+    size_t k = (size_t)m->ev_used;
+    cudaStreamCaptureStatus st;
+    PDG_CUDA(cudaStreamIsCapturing(s, &st));
+    unsigned flags = (st == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : cudaEventRecordDefault;
+    PDG_CUDA(cudaEventRecordWithFlags(m->ev_pool[2 * k + 1], s, flags));
+    m->ev_used++;
+}
+
+}  // namespace pdg
+
+using namespace pdg;
+
+pd_mesh::~pd_mesh() {
+    for (auto& kv : graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (auto e : ev_pool) cudaEventDestroy(e);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+}
+
+#define PD_API_BEGIN try {
+#define PD_API_END                                   \
+    }                                                \
+    catch (const pdg::Fail& f) {                     \
+        return f.code;                               \
+    }                                                \
+    catch (const std::bad_alloc&) {                  \
+        pdg::set_error("host allocation failed");    \
+        return PD_ERR_NO_MEMORY;                     \
+    }                                                \
+    catch (...) {                                    \
+        pdg::set_error("unexpected host exception"); \
+        return PD_ERR_CUDA;                          \
+    }
+
+static pd_status fail(pd_status code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+template <class T>
+static void upload(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
+    d.alloc(h.size());
+    if (!h.empty()) PDG_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+extern "C" {
+
+const char* pd_status_string(pd_status s) {
+    switch (s) {
+        case PD_OK: return "ok";
+        case PD_ERR_INVALID_ARG: return "invalid argument";
+        case PD_ERR_BAD_MESH: return "bad mesh";
+        case PD_ERR_BAD_MATERIAL: return "bad material (gamma must be finite and >= 0)";
+        case PD_ERR_NOT_PREFACTORED: return "not prefactored";
+        case PD_ERR_NOT_SPD: return "matrix not positive definite";
+        case PD_ERR_NO_MEMORY: return "out of memory";
+        case PD_ERR_NONFINITE: return "non-finite state";
+        case PD_ERR_TIMEOUT: return "timeout";
+        case PD_ERR_CUDA: return "CUDA error";
+        case PD_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char* pd_last_error(void) { return g_last_error.c_str(); }
+
+static const char* kPhaseNames[PH_COUNT] = {"inertia", "local", "assemble", "dd_condense", "dd_gather",
+                                            "dd_coarse", "dd_reduce", "dd_backsub", "residual", "velocity"};
+
+const char* pd_phase_name(int32_t k) { return (k >= 0 && k < PH_COUNT) ? kPhaseNames[k] : "?"; }
+
+void pd_destroy_mesh(pd_mesh* m) {
+    if (!m) return;
+    cudaStreamSynchronize(m->stream);
+    delete m;
+}
+
+pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tets, int32_t n_t,
+                         const double* vertex_mass, double density, const int32_t* tet_domain, int32_t n_domains,
+                         const uint8_t* pinned, void* cuda_stream, pd_mesh** out) {
+    if (!out) return fail(PD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!rest_xyz || !tets || n_v <= 0 || n_t <= 0 || n_domains <= 0 || n_domains > n_t)
+        return fail(PD_ERR_INVALID_ARG, "null input or size out of range");
+    if (!vertex_mass && !(density > 0.0 && std::isfinite(density)))
+        return fail(PD_ERR_INVALID_ARG, "density must be > 0 when vertex_mass is NULL");
+    pd_mesh* m = new (std::nothrow) pd_mesh();
+    if (!m) return fail(PD_ERR_NO_MEMORY, "host allocation failed");
+    PD_API_BEGIN
+    struct Guard {
+        pd_mesh* m;
+        bool keep = false;
+        ~Guard() {
+            if (!keep) delete m;
+        }
+    } guard{m};
+    m->n_v = n_v;
+    m->n_t = n_t;
+    m->n_dom = n_domains;
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+
+    // ---- validate tets, rest operators (Dm^-1, V_e); fix orientation
+    std::vector<int32_t> T(tets, tets + 4 * (size_t)n_t);
+    std::vector<double> dminv_old(9 * (size_t)n_t), vol_old(n_t);
+    for (int32_t t = 0; t < n_t; ++t) {
+        int32_t* q = &T[4 * (size_t)t];
+        for (int k = 0; k < 4; ++k)
+            if (q[k] < 0 || q[k] >= n_v) return fail(PD_ERR_BAD_MESH, "tet vertex index out of range");
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (q[a] == q[b]) return fail(PD_ERR_BAD_MESH, "tet with a repeated vertex");
+        auto X = [&](int k, int c) { return rest_xyz[3 * (size_t)q[k] + c]; };
+        double D[3][3];
+        for (int c = 0; c < 3; ++c)
+            for (int k = 0; k < 3; ++k) D[c][k] = X(k + 1, c) - X(0, c);   // columns = edges
+        double det = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
+                     D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                     D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+        if (det < 0) {
+            std::swap(q[2], q[3]);
+            for (int c = 0; c < 3; ++c) std::swap(D[c][1], D[c][2]);
+            det = -det;
+        }
+        double e2 = 0;
+        for (int c = 0; c < 3; ++c)
+            for (int k = 0; k < 3; ++k) e2 = std::max(e2, D[c][k] * D[c][k]);
+        if (!(det > 1e-12 * e2 * std::sqrt(e2)) || !std::isfinite(det))
+            return fail(PD_ERR_BAD_MESH, "degenerate tet (rest volume <= 0)");
+        double inv[3][3];
+        inv[0][0] = (D[1][1] * D[2][2] - D[1][2] * D[2][1]) / det;
+        inv[0][1] = (D[0][2] * D[2][1] - D[0][1] * D[2][2]) / det;
+        inv[0][2] = (D[0][1] * D[1][2] - D[0][2] * D[1][1]) / det;
+        inv[1][0] = (D[1][2] * D[2][0] - D[1][0] * D[2][2]) / det;
+        inv[1][1] = (D[0][0] * D[2][2] - D[0][2] * D[2][0]) / det;
+        inv[1][2] = (D[0][2] * D[1][0] - D[0][0] * D[1][2]) / det;
+        inv[2][0] = (D[1][0] * D[2][1] - D[1][1] * D[2][0]) / det;
+        inv[2][1] = (D[0][1] * D[2][0] - D[0][0] * D[2][1]) / det;
+        inv[2][2] = (D[0][0] * D[1][1] - D[0][1] * D[1][0]) / det;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) dminv_old[9 * (size_t)t + 3 * i + j] = inv[i][j];
+        vol_old[t] = det / 6.0;
+    }
+
+    // ---- domains
+    std::vector<int32_t> tdom(n_t);
+    if (tet_domain) {
+        for (int32_t t = 0; t < n_t; ++t) {
+            if (tet_domain[t] < 0 || tet_domain[t] >= n_domains)
+                return fail(PD_ERR_INVALID_ARG, "tet_domain out of range");
+            tdom[t] = tet_domain[t];
+        }
+    } else {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int32_t v = 0; v < n_v; ++v)
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = std::min(lo[c], rest_xyz[3 * (size_t)v + c]);
+                hi[c] = std::max(hi[c], rest_xyz[3 * (size_t)v + c]);
+            }
+        int ax = 0;
+        for (int c = 1; c < 3; ++c)
+            if (hi[c] - lo[c] > hi[ax] - lo[ax]) ax = c;
+        std::vector<std::pair<double, int32_t>> key(n_t);
+        for (int32_t t = 0; t < n_t; ++t) {
+            double s = 0;
+            for (int k = 0; k < 4; ++k) s += rest_xyz[3 * (size_t)T[4 * (size_t)t + k] + ax];
+            key[t] = {s, t};
+        }
+        std::stable_sort(key.begin(), key.end());
+        for (int32_t r = 0; r < n_t; ++r) tdom[key[r].second] = (int32_t)((int64_t)r * n_domains / n_t);
+    }
+
+    // ---- vertex classes
+    std::vector<int32_t> vdom(n_v, -1);
+    std::vector<uint8_t> multi(n_v, 0);
+    for (int32_t t = 0; t < n_t; ++t)
+        for (int k = 0; k < 4; ++k) {
+            int32_t v = T[4 * (size_t)t + k];
+            if (vdom[v] < 0) vdom[v] = tdom[t];
+            else if (vdom[v] != tdom[t]) multi[v] = 1;
+        }
+    std::vector<uint8_t> pin(n_v, 0);
+    if (pinned)
+        for (int32_t v = 0; v < n_v; ++v) pin[v] = pinned[v] ? 1 : 0;
+    for (int32_t v = 0; v < n_v; ++v)
+        if (vdom[v] < 0 && !pin[v]) return fail(PD_ERR_BAD_MESH, "vertex not used by any tet (and not pinned)");
+
+    // ---- new numbering: [domain internals][interface][pinned], each in increasing old id
+    m->dom_n_int.assign(n_domains, 0);
+    int32_t n_pin = 0, n_B = 0;
+    for (int32_t v = 0; v < n_v; ++v) {
+        if (pin[v]) n_pin++;
+        else if (multi[v]) n_B++;
+        else m->dom_n_int[vdom[v]]++;
+    }
+    m->dom_int_off.assign(n_domains, 0);
+    int32_t acc = 0;
+    for (int32_t d = 0; d < n_domains; ++d) {
+        m->dom_int_off[d] = acc;
+        acc += m->dom_n_int[d];
+    }
+    m->n_int = acc;
+    m->n_B = n_B;
+    m->n_pin = n_pin;
+    m->n_free = acc + n_B;
+    m->new_of_old.assign(n_v, -1);
+    m->old_of_new.assign(n_v, -1);
+    {
+        std::vector<int32_t> fill(m->dom_int_off);
+        int32_t nb = m->n_int, np = m->n_free;
+        for (int32_t v = 0; v < n_v; ++v) {
+            int32_t nv;
+            if (pin[v]) nv = np++;
+            else if (multi[v]) nv = nb++;
+            else nv = fill[vdom[v]]++;
+            m->new_of_old[v] = nv;
+            m->old_of_new[nv] = v;
+        }
+    }
+
+    // ---- tets sorted by domain (stable), in new vertex ids
+    m->tet_old_of_new.resize(n_t);
+    std::iota(m->tet_old_of_new.begin(), m->tet_old_of_new.end(), 0);
+    std::stable_sort(m->tet_old_of_new.begin(), m->tet_old_of_new.end(),
+                     [&](int32_t a, int32_t b) { return tdom[a] < tdom[b]; });
+    m->tets_new.resize(4 * (size_t)n_t);
+    m->tet_dom.resize(n_t);
+    m->vol.resize(n_t);
+    m->Dminv.resize(9 * (size_t)n_t);
+    for (int32_t t = 0; t < n_t; ++t) {
+        int32_t o = m->tet_old_of_new[t];
+        for (int k = 0; k < 4; ++k) m->tets_new[4 * (size_t)t + k] = m->new_of_old[T[4 * (size_t)o + k]];
+        m->tet_dom[t] = tdom[o];
+        m->vol[t] = vol_old[o];
+        for (int k = 0; k < 9; ++k) m->Dminv[9 * (size_t)t + k] = dminv_old[9 * (size_t)o + k];
+    }
+
+    // ---- masses (new order)
+    m->mass.assign(n_v, 0.0);
+    if (vertex_mass) {
+        for (int32_t v = 0; v < n_v; ++v) {
+            if (!(vertex_mass[v] > 0.0) || !std::isfinite(vertex_mass[v]))
+                return fail(PD_ERR_INVALID_ARG, "vertex_mass must be finite and > 0");
+            m->mass[m->new_of_old[v]] = vertex_mass[v];
+        }
+    } else {
+        for (int32_t t = 0; t < n_t; ++t)
+            for (int k = 0; k < 4; ++k) m->mass[m->tets_new[4 * (size_t)t + k]] += density * m->vol[t] / 4.0;
+    }
+
+    // ---- per-domain boundary lists: interface vertices sharing a tet with an internal vertex of d
+    m->dom_bnd.assign(n_domains, {});
+    {
+        std::vector<int32_t> mark(n_B, -1);
+        for (int32_t t = 0; t < n_t; ++t) {
+            const int32_t d = m->tet_dom[t];
+            const int32_t* q = &m->tets_new[4 * (size_t)t];
+            bool has_int = false;
+            for (int k = 0; k < 4; ++k) has_int |= (q[k] < m->n_int);
+            if (!has_int) continue;
+            for (int k = 0; k < 4; ++k) {
+                int32_t v = q[k];
+                if (v >= m->n_int && v < m->n_free) {
+                    int32_t j = v - m->n_int;
+                    if (mark[j] != d) {
+                        mark[j] = d;
+                        m->dom_bnd[d].push_back(j);
+                    }
+                }
+            }
+        }
+        for (auto& b : m->dom_bnd) {
+            std::sort(b.begin(), b.end());
+            b.erase(std::unique(b.begin(), b.end()), b.end());
+        }
+    }
+    int32_t max_ni = 0, max_nb = 0;
+    for (int32_t d = 0; d < n_domains; ++d) {
+        max_ni = std::max(max_ni, m->dom_n_int[d]);
+        max_nb = std::max(max_nb, (int32_t)m->dom_bnd[d].size());
+    }
+    if (max_ni > dd_max_sub_cols() || max_nb > dd_max_sub_cols())
+        return fail(PD_ERR_UNSUPPORTED, "a domain has more than 2048 internal or boundary vertices; use more domains");
+
+    // ---- CSR patterns of K_ff and K_fp; vertex -> (tet, corner) incidences
+    {
+        std::vector<std::vector<int32_t>> rows(m->n_free), prow(m->n_free);
+        for (int32_t t = 0; t < n_t; ++t) {
+            const int32_t* q = &m->tets_new[4 * (size_t)t];
+            for (int a = 0; a < 4; ++a) {
+                if (q[a] >= m->n_free) continue;
+                for (int b = 0; b < 4; ++b) {
+                    if (q[b] < m->n_free) rows[q[a]].push_back(q[b]);
+                    else prow[q[a]].push_back(q[b] - m->n_free);
+                }
+            }
+        }
+        m->K_rowptr.assign(m->n_free + 1, 0);
+        m->Kfp_rowptr.assign(m->n_free + 1, 0);
+        for (int32_t i = 0; i < m->n_free; ++i) {
+            auto& r = rows[i];
+            std::sort(r.begin(), r.end());
+            r.erase(std::unique(r.begin(), r.end()), r.end());
+            auto& p = prow[i];
+            std::sort(p.begin(), p.end());
+            p.erase(std::unique(p.begin(), p.end()), p.end());
+            m->K_rowptr[i + 1] = m->K_rowptr[i] + (int32_t)r.size();
+            m->Kfp_rowptr[i + 1] = m->Kfp_rowptr[i] + (int32_t)p.size();
+        }
+        m->K_col.resize(m->K_rowptr.back());
+        m->Kfp_col.resize(m->Kfp_rowptr.back());
+        for (int32_t i = 0; i < m->n_free; ++i) {
+            std::copy(rows[i].begin(), rows[i].end(), m->K_col.begin() + m->K_rowptr[i]);
+            std::copy(prow[i].begin(), prow[i].end(), m->Kfp_col.begin() + m->Kfp_rowptr[i]);
+        }
+    }
+    std::vector<int32_t> inc_ptr(m->n_free + 1, 0), inc;
+    {
+        for (int32_t t = 0; t < n_t; ++t)
+            for (int k = 0; k < 4; ++k) {
+                int32_t v = m->tets_new[4 * (size_t)t + k];
+                if (v < m->n_free) inc_ptr[v + 1]++;
+            }
+        for (int32_t i = 0; i < m->n_free; ++i) inc_ptr[i + 1] += inc_ptr[i];
+        inc.resize(inc_ptr.back());
+        std::vector<int32_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+        for (int32_t t = 0; t < n_t; ++t)
+            for (int k = 0; k < 4; ++k) {
+                int32_t v = m->tets_new[4 * (size_t)t + k];
+                if (v < m->n_free) inc[fill[v]++] = 4 * t + k;   // increasing (t, corner) order
+            }
+    }
+
+    // ---- device uploads: topology, geometry, state (first CUDA call of the set-up)
+    PDG_CUDA(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t s = m->stream;
+    std::vector<int4> ht(n_t);
+    std::vector<float4> hg(3 * (size_t)n_t);
+    for (int32_t t = 0; t < n_t; ++t) {
+        const int32_t* q = &m->tets_new[4 * (size_t)t];
+        ht[t] = make_int4(q[0], q[1], q[2], q[3]);
+        const double* D = &m->Dminv[9 * (size_t)t];
+        for (int r = 0; r < 3; ++r)
+            hg[(size_t)r * n_t + t] = make_float4((float)D[3 * r], (float)D[3 * r + 1], (float)D[3 * r + 2], 0.f);
+    }
+    upload(m->d_tets, ht, s);
+    upload(m->d_geo, hg, s);
+    upload(m->d_inc_ptr, inc_ptr, s);
+    upload(m->d_inc, inc, s);
+    upload(m->d_old_of_new, m->old_of_new, s);
+    std::vector<float4> hx(n_v);
+    for (int32_t i = 0; i < n_v; ++i) {
+        int32_t o = m->old_of_new[i];
+        hx[i] = make_float4((float)rest_xyz[3 * (size_t)o], (float)rest_xyz[3 * (size_t)o + 1],
+                            (float)rest_xyz[3 * (size_t)o + 2], 0.f);
+    }
+    upload(m->d_x, hx, s);
+    m->d_xprev.alloc(n_v);
+    m->d_v.alloc(n_v);
+    PDG_CUDA(cudaMemsetAsync(m->d_v.p, 0, sizeof(float4) * n_v, s));
+    PDG_CUDA(cudaMemcpyAsync(m->d_xprev.p, m->d_x.p, sizeof(float4) * n_v, cudaMemcpyDeviceToDevice, s));
+    m->d_force.alloc(4 * (size_t)n_t);
+    m->d_by0.alloc(std::max(m->n_free, 1));
+    m->d_b.alloc(std::max(m->n_free, 1));
+    m->d_pin_tgt.alloc(std::max(n_pin, 1));
+    m->d_r.alloc(std::max(m->n_free, 1));
+    m->d_dx.alloc(n_v);
+    PDG_CUDA(cudaMemsetAsync(m->d_dx.p, 0, sizeof(float4) * n_v, s));
+    m->d_err.alloc(1);
+    PDG_CUDA(cudaMemsetAsync(m->d_err.p, 0, sizeof(int32_t), s));
+    PDG_CUDA(cudaStreamSynchronize(s));
+    guard.keep = true;
+    *out = m;
+    return PD_OK;
+    PD_API_END
+}
+
+pd_status pd_set_materials(pd_mesh* m, const float* gamma_s, const float* gamma_v) {
+    if (!m || !gamma_s || !gamma_v) return fail(PD_ERR_INVALID_ARG, "null argument");
+    PD_API_BEGIN
+    const int32_t n_t = m->n_t;
+    std::vector<float> gs(n_t), gv(n_t);
+    auto fetch = [&](const float* src, std::vector<float>& dst) {
+        if (is_device_ptr(src)) {
+            PDG_CUDA(cudaMemcpyAsync(dst.data(), src, sizeof(float) * n_t, cudaMemcpyDeviceToHost, m->stream));
+            PDG_CUDA(cudaStreamSynchronize(m->stream));
+        } else {
+            std::memcpy(dst.data(), src, sizeof(float) * n_t);
+        }
+    };
+    fetch(gamma_s, gs);
+    fetch(gamma_v, gv);
+    for (int32_t t = 0; t < n_t; ++t)
+        if (!(gs[t] >= 0.f) || !(gv[t] >= 0.f) || !std::isfinite(gs[t]) || !std::isfinite(gv[t]))
+            return fail(PD_ERR_BAD_MATERIAL, "gamma must be finite and >= 0");
+    m->gamma_s.resize(n_t);
+    m->gamma_v.resize(n_t);
+    std::vector<float> vol(n_t);
+    for (int32_t t = 0; t < n_t; ++t) {
+        m->gamma_s[t] = gs[m->tet_old_of_new[t]];
+        m->gamma_v[t] = gv[m->tet_old_of_new[t]];
+        vol[t] = (float)m->vol[t];
+    }
+    DBuf<float> dvol, dgs, dgv;
+    upload(dvol, vol, m->stream);
+    upload(dgs, m->gamma_s, m->stream);
+    upload(dgv, m->gamma_v, m->stream);
+    launch_weights_raw(n_t, dvol.p, dgs.p, dgv.p, m->d_geo.p, m->stream);
+    PDG_CUDA(cudaStreamSynchronize(m->stream));
+    m->materials_set = true;
+    m->prefactored = false;
+    return PD_OK;
+    PD_API_END
+}
+
+pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
+    if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(PD_ERR_INVALID_ARG, "dt must be > 0");
+    if (!m->materials_set) return fail(PD_ERR_BAD_MATERIAL, "materials not set");
+    pd_solver_opts o{PD_PREC_FP32, 0, 1, 0};
+    if (opts) o = *opts;
+    if (o.precision < PD_PREC_FP32 || o.precision > PD_PREC_TF32 || o.refine_steps < 0 || o.refine_steps > 2 ||
+        o.reserved != 0)
+        return fail(PD_ERR_INVALID_ARG, "bad solver options");
+    PD_API_BEGIN
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = m->stream;
+    m->prefactored = false;
+    for (auto& kv : m->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    m->graphs.clear();
+    const int32_t n_free = m->n_free, n_int = m->n_int, n_B = m->n_B, n_dom = m->n_dom;
+    const double inv_h2 = 1.0 / (dt * dt);
+
+    // ---- scalar K over free vertices and the free-pinned block (FP64, host, fixed order)
+    m->K_val.assign(m->K_col.size(), 0.0);
+    m->Kfp_val.assign(m->Kfp_col.size(), 0.0);
+    auto addK = [&](int32_t a, int32_t b, double v) {
+        if (b < n_free) {
+            auto beg = m->K_col.begin() + m->K_rowptr[a], end = m->K_col.begin() + m->K_rowptr[a + 1];
+            m->K_val[std::lower_bound(beg, end, b) - m->K_col.begin()] += v;
+        } else {
+            int32_t p = b - n_free;
+            auto beg = m->Kfp_col.begin() + m->Kfp_rowptr[a], end = m->Kfp_col.begin() + m->Kfp_rowptr[a + 1];
+            m->Kfp_val[std::lower_bound(beg, end, p) - m->Kfp_col.begin()] += v;
+        }
+    };
+    for (int32_t t = 0; t < m->n_t; ++t) {
+        const double* D = &m->Dminv[9 * (size_t)t];
+        double g[4][3];
+        for (int c = 0; c < 3; ++c) {
+            g[1][c] = D[c];
+            g[2][c] = D[3 + c];
+            g[3][c] = D[6 + c];
+            g[0][c] = -(D[c] + D[3 + c] + D[6 + c]);
+        }
+        const double w = m->vol[t] * ((double)m->gamma_s[t] + (double)m->gamma_v[t]);
+        const int32_t* q = &m->tets_new[4 * (size_t)t];
+        for (int a = 0; a < 4; ++a) {
+            if (q[a] >= n_free) continue;
+            for (int b = 0; b < 4; ++b)
+                addK(q[a], q[b], w * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]));
+        }
+    }
+    for (int32_t i = 0; i < n_free; ++i) addK(i, i, m->mass[i] * inv_h2);
+
+    // per-iteration small arrays
+    {
+        std::vector<float> mh2(std::max(n_free, 1));
+        for (int32_t i = 0; i < n_free; ++i) mh2[i] = (float)(m->mass[i] * inv_h2);
+        upload(m->d_mh2, mh2, s);
+        upload(m->d_kfp_ptr, m->Kfp_rowptr, s);
+        std::vector<int32_t> kc(m->Kfp_col);
+        std::vector<float> kv(m->Kfp_val.size());
+        for (size_t k = 0; k < kv.size(); ++k) kv[k] = (float)m->Kfp_val[k];
+        upload(m->d_kfp_col, kc, s);
+        upload(m->d_kfp_val, kv, s);
+        upload(m->d_K_ptr, m->K_rowptr, s);
+        upload(m->d_K_col, m->K_col, s);
+        upload(m->d_K_val, m->K_val, s);
+    }
+
+    // ---- per-domain dense blocks K_ii (padded with identity) and K_ib
+    const int nb64 = dense_block();
+    int32_t max_ni = 1, max_nb = 1;
+    for (int32_t d = 0; d < n_dom; ++d) {
+        max_ni = std::max(max_ni, m->dom_n_int[d]);
+        max_nb = std::max(max_nb, (int32_t)m->dom_bnd[d].size());
+    }
+    const int NI = (int)round_up(max_ni, nb64);
+    const int NBp = (int)round_up(max_nb, 8);
+    const int64_t sKii = (int64_t)NI * NI, sKib = (int64_t)NI * NBp, sSd = (int64_t)NBp * NBp;
+    std::vector<double> hKii((size_t)n_dom * sKii, 0.0), hKib((size_t)n_dom * sKib, 0.0);
+    {
+        std::vector<int32_t> pos(std::max(n_B, 1), -1);
+        for (int32_t d = 0; d < n_dom; ++d) {
+            double* Kii = &hKii[(size_t)d * sKii];
+            double* Kib = &hKib[(size_t)d * sKib];
+            const auto& bl = m->dom_bnd[d];
+            for (int32_t k = 0; k < (int32_t)bl.size(); ++k) pos[bl[k]] = k;
+            const int32_t off = m->dom_int_off[d], ni = m->dom_n_int[d];
+            for (int32_t r = ni; r < NI; ++r) Kii[(size_t)r * NI + r] = 1.0;
+            for (int32_t r = 0; r < ni; ++r) {
+                const int32_t i = off + r;
+                for (int32_t k = m->K_rowptr[i]; k < m->K_rowptr[i + 1]; ++k) {
+                    const int32_t c = m->K_col[k];
+                    if (c >= off && c < off + ni) Kii[(size_t)r * NI + (c - off)] = m->K_val[k];
+                    else if (c >= n_int) Kib[(size_t)r * NBp + pos[c - n_int]] = m->K_val[k];
+                    else return fail(PD_ERR_BAD_MESH, "internal vertex coupled to another domain's internal vertex");
+                }
+            }
+            for (int32_t k = 0; k < (int32_t)bl.size(); ++k) pos[bl[k]] = -1;
+        }
+    }
+    DBuf<double> dKii, dXii, dKib, dPsi, dSd;
+    upload(dKii, hKii, s);
+    upload(dKib, hKib, s);
+    hKii.clear(); hKii.shrink_to_fit();
+    hKib.clear(); hKib.shrink_to_fit();
+    dXii.alloc((size_t)n_dom * sKii);
+    dPsi.alloc((size_t)n_dom * sKib);
+    dSd.alloc((size_t)n_dom * sSd);
+    PDG_CUDA(cudaMemsetAsync(m->d_err.p, 0, sizeof(int32_t), s));
+    dense_spd_inverse(dKii.p, NI, NI, sKii, dXii.p, NI, sKii, n_dom, m->d_err.p, s);
+    // Psi = -K_ii^-1 K_ib ;  S_d = K_ib^T Psi = -K_bi K_ii^-1 K_ib
+    dense_gemm(false, false, NI, NBp, NI, -1.0, dXii.p, NI, sKii, dKib.p, NBp, sKib, 0.0, dPsi.p, NBp, sKib, n_dom,
+               false, s);
+    dense_gemm(true, false, NBp, NBp, NI, 1.0, dKib.p, NBp, sKib, dPsi.p, NBp, sKib, 0.0, dSd.p, NBp, sSd, n_dom,
+               false, s);
+    dKii.free();
+    dKib.free();
+
+    // ---- boundary index lists and the reduced interface matrix S = K_BB + sum_d S_d
+    std::vector<int32_t> bidx_off(n_dom + 1, 0), bidx;
+    for (int32_t d = 0; d < n_dom; ++d) bidx_off[d + 1] = bidx_off[d] + (int32_t)m->dom_bnd[d].size();
+    bidx.reserve(bidx_off.back());
+    for (int32_t d = 0; d < n_dom; ++d) bidx.insert(bidx.end(), m->dom_bnd[d].begin(), m->dom_bnd[d].end());
+    upload(m->d_bidx, bidx, s);
+    const int nBp = (int)round_up(std::max(n_B, 1), nb64);
+    DBuf<double> dS, dXS;
+    if (n_B > 0) {
+        dS.alloc((size_t)nBp * nBp);
+        dXS.alloc((size_t)nBp * nBp);
+        dense_set_identity(dS.p, nBp, nBp, 0, 1, s);
+        std::vector<int32_t> cr, cc;
+        std::vector<double> cv;
+        for (int32_t j = 0; j < n_B; ++j) {
+            const int32_t i = n_int + j;
+            for (int32_t k = m->K_rowptr[i]; k < m->K_rowptr[i + 1]; ++k)
+                if (m->K_col[k] >= n_int) {
+                    cr.push_back(j);
+                    cc.push_back(m->K_col[k] - n_int);
+                    cv.push_back(m->K_val[k]);
+                }
+        }
+        // diagonal entries of the padding stay 1; real diagonal entries are overwritten
+        DBuf<int32_t> dcr, dcc;
+        DBuf<double> dcv;
+        upload(dcr, cr, s);
+        upload(dcc, cc, s);
+        upload(dcv, cv, s);
+        launch_prefactor_helpers_scatter_coo(dS.p, nBp, dcr.p, dcc.p, dcv.p, (int)cv.size(), s);
+        for (int32_t d = 0; d < n_dom; ++d) {
+            const int nbd = (int)m->dom_bnd[d].size();
+            if (nbd == 0 || m->dom_n_int[d] == 0) continue;
+            launch_prefactor_add_block(dS.p, nBp, dSd.p + (size_t)d * sSd, NBp, m->d_bidx.p + bidx_off[d], nbd, s);
+        }
+        PDG_CUDA(cudaStreamSynchronize(s));
+        dense_spd_inverse(dS.p, nBp, nBp, 0, dXS.p, nBp, 0, 1, m->d_err.p, s);
+    }
+    dSd.free();
+
+    // ---- per-iteration matrix pool: per domain G_d = [K_ii^-1; Psi^T], Psi_d; then S^-1
+    m->prec = o.precision;
+    m->refine = o.refine_steps;
+    m->use_graphs = o.use_graphs != 0;
+    std::vector<int64_t> g_off(n_dom), p_off(n_dom);
+    std::vector<int32_t> ldG(n_dom), ldP(n_dom), tc_off(n_dom);
+    int64_t pool = 0;
+    int32_t tcr = 0;
+    for (int32_t d = 0; d < n_dom; ++d) {
+        const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
+        ldG[d] = (int32_t)round_up(std::max(ni, 1), 8);
+        ldP[d] = (int32_t)round_up(std::max(nbd, 1), 8);
+        g_off[d] = pool;
+        pool += (int64_t)(ni + nbd) * ldG[d];
+        p_off[d] = pool;
+        pool += (int64_t)ni * ldP[d];
+        pool = round_up(pool, 8);
+        tc_off[d] = tcr;
+        tcr += ni + nbd;
+    }
+    m->off_S = pool;
+    m->ld_S = (int32_t)round_up(std::max(n_B, 1), 8);
+    pool += (int64_t)n_B * m->ld_S;
+    pool = std::max<int64_t>(pool, 8);
+    m->d_mat32.free();
+    m->d_mat16.free();
+    if (m->prec == PD_PREC_BF16) {
+        m->d_mat16.alloc(pool);
+        PDG_CUDA(cudaMemsetAsync(m->d_mat16.p, 0, sizeof(__nv_bfloat16) * pool, s));
+    } else {
+        m->d_mat32.alloc(pool);
+        PDG_CUDA(cudaMemsetAsync(m->d_mat32.p, 0, sizeof(float) * pool, s));
+    }
+    for (int32_t d = 0; d < n_dom; ++d) {
+        const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
+        if (ni == 0) continue;
+        const double* Xd = dXii.p + (size_t)d * sKii;
+        const double* Pd = dPsi.p + (size_t)d * sKib;
+        launch_cast_block(Xd, NI, ni, ni, 0, m->prec, m->d_mat32.p, m->d_mat16.p, g_off[d], ldG[d], s);
+        if (nbd > 0) {
+            launch_cast_block(Pd, NBp, nbd, ni, 1, m->prec, m->d_mat32.p, m->d_mat16.p,
+                              g_off[d] + (int64_t)ni * ldG[d], ldG[d], s);
+            launch_cast_block(Pd, NBp, ni, nbd, 0, m->prec, m->d_mat32.p, m->d_mat16.p, p_off[d], ldP[d], s);
+        }
+    }
+    if (n_B > 0)
+        launch_cast_block(dXS.p, nBp, n_B, n_B, 0, m->prec, m->d_mat32.p, m->d_mat16.p, m->off_S, m->ld_S, s);
+
+    // ---- tasks
+    const int VN = (m->prec == PD_PREC_BF16) ? 8 : 4;
+    const int RB = 64;
+    std::vector<GemvTask> tc_tasks, bk_tasks;
+    for (int32_t d = 0; d < n_dom; ++d) {
+        const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
+        if (ni == 0) continue;
+        for (int32_t r0 = 0; r0 < ni + nbd; r0 += RB) {
+            GemvTask t{};
+            t.a_off = g_off[d] + (int64_t)r0 * ldG[d];
+            t.rows = std::min(RB, ni + nbd - r0);
+            t.ld = ldG[d];
+            t.cols = (int32_t)round_up(ni, VN);
+            t.x_off = m->dom_int_off[d];
+            t.x_n = ni;
+            t.y_off = tc_off[d] + r0;
+            tc_tasks.push_back(t);
+        }
+        for (int32_t r0 = 0; r0 < ni; r0 += RB) {
+            GemvTask t{};
+            t.a_off = p_off[d] + (int64_t)r0 * ldP[d];
+            t.rows = std::min(RB, ni - r0);
+            t.ld = ldP[d];
+            t.cols = nbd > 0 ? (int32_t)round_up(nbd, VN) : 0;
+            t.x_off = bidx_off[d];
+            t.x_n = nbd;
+            t.y_off = m->dom_int_off[d] + r0;
+            t.add_off = tc_off[d] + r0;
+            bk_tasks.push_back(t);
+        }
+    }
+    upload(m->d_tasks_cond, tc_tasks, s);
+    upload(m->d_tasks_back, bk_tasks, s);
+    m->n_tasks_cond = (int32_t)tc_tasks.size();
+    m->n_tasks_back = (int32_t)bk_tasks.size();
+    m->n_tc = tcr;
+    m->d_tc.alloc(std::max(tcr, 1));
+    // interface gather lists (domains in increasing order)
+    {
+        std::vector<int32_t> gp(n_B + 1, 0), gl;
+        std::vector<std::vector<int32_t>> lists(n_B);
+        for (int32_t d = 0; d < n_dom; ++d) {
+            const int32_t ni = m->dom_n_int[d];
+            if (ni == 0) continue;
+            const auto& bl = m->dom_bnd[d];
+            for (int32_t k = 0; k < (int32_t)bl.size(); ++k) lists[bl[k]].push_back(tc_off[d] + ni + k);
+        }
+        for (int32_t j = 0; j < n_B; ++j) {
+            gp[j + 1] = gp[j] + (int32_t)lists[j].size();
+            gl.insert(gl.end(), lists[j].begin(), lists[j].end());
+        }
+        upload(m->d_gat_ptr, gp, s);
+        upload(m->d_gat, gl, s);
+    }
+    m->d_cB.alloc(std::max(n_B, 1));
+    m->coarse_rows_per_cta = 64;
+    m->coarse_chunk = dd_coarse_chunk();
+    m->coarse_nchunks = (int32_t)((m->ld_S + m->coarse_chunk - 1) / m->coarse_chunk);
+    m->d_part.alloc((size_t)std::max(n_B, 1) * m->coarse_nchunks);
+
+    // ---- algorithmic bytes per launch of each phase (each array counted once)
+    {
+        const int64_t es = (m->prec == PD_PREC_BF16) ? 2 : 4;
+        int64_t mat_c = 0, mat_b = 0, nbd_tot = 0;
+        for (const auto& t : tc_tasks) mat_c += (int64_t)t.rows * t.cols * es;
+        for (const auto& t : bk_tasks) mat_b += (int64_t)t.rows * t.cols * es;
+        for (int32_t d = 0; d < n_dom; ++d)
+            if (m->dom_n_int[d] > 0) nbd_tot += (int64_t)m->dom_bnd[d].size();
+        const int64_t nv = m->n_v, nf = n_free, nt = m->n_t, ninc = (int64_t)4 * nt;
+        const int64_t nkfp = (int64_t)m->Kfp_col.size(), nk = (int64_t)m->K_col.size();
+        const int64_t ngat = nbd_tot;
+        const int64_t colsS = (int64_t)round_up(std::max(n_B, 1), VN);
+        for (int k = 0; k < 16; ++k) m->phase_bytes[k] = 0;
+        m->phase_bytes[PH_INERTIA] = nv * 48 + nf * (16 + 4 + 16 + 4) + nkfp * 8 + (int64_t)m->n_pin * 16;
+        m->phase_bytes[PH_LOCAL] = nt * (16 + 48 + 64) + nv * 16;
+        m->phase_bytes[PH_ASSEMBLE] = nf * (4 + 16 + 16) + ninc * (4 + 16);
+        m->phase_bytes[PH_CONDENSE] = mat_c + (int64_t)n_int * 16 + (int64_t)tcr * 16;
+        m->phase_bytes[PH_GATHER] = (int64_t)n_B * (4 + 16 + 16) + ngat * (4 + 16);
+        m->phase_bytes[PH_COARSE] = (int64_t)n_B * colsS * es + (int64_t)n_B * 16 +
+                                    (int64_t)m->coarse_nchunks * n_B * 16;
+        m->phase_bytes[PH_REDUCE] = (int64_t)m->coarse_nchunks * n_B * 16 + (int64_t)n_B * 16;
+        m->phase_bytes[PH_BACKSUB] = mat_b + nbd_tot * (4 + 16) + (int64_t)n_int * 32;
+        m->phase_bytes[PH_RESIDUAL] = nk * (4 + 8 + 16) + nf * (4 + 16 + 16);
+        m->phase_bytes[PH_VELOCITY] = nv * 48;
+        int dd = 1 + (n_B > 0 ? 3 : 0) + (m->n_tasks_back > 0 ? 1 : 0);
+        m->launches_per_iter = 2 + dd + m->refine * (2 + dd);
+    }
+
+    PDG_CUDA(cudaStreamSynchronize(s));
+    int32_t herr = 0;
+    PDG_CUDA(cudaMemcpy(&herr, m->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (herr & ERR_NOT_SPD) {
+        PDG_CUDA(cudaMemset(m->d_err.p, 0, sizeof(int32_t)));
+        return fail(PD_ERR_NOT_SPD, "a Cholesky pivot was not positive");
+    }
+    m->dt = dt;
+    m->prefactored = true;
+    m->prefactor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return PD_OK;
+    PD_API_END
+}
+
+pd_status pd_set_state(pd_mesh* m, const float* x, const float* v) {
+    if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
+    PD_API_BEGIN
+    if (x) launch_gather_in(m, x, m->d_x.p, m->stream);
+    if (v) launch_gather_in(m, v, m->d_v.p, m->stream);
+    return PD_OK;
+    PD_API_END
+}
+
+pd_status pd_get_state(pd_mesh* m, float* x, float* v) {
+    if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
+    PD_API_BEGIN
+    if (x) launch_scatter_out(m, m->d_x.p, x, 0, m->stream);
+    if (v) launch_scatter_out(m, m->d_v.p, v, 0, m->stream);
+    return PD_OK;
+    PD_API_END
+}
+
+}  // extern "C"
+
+static void run_frame(pd_mesh* m, int n_iter, const float g[3], cudaStream_t s) {
+    const float h = (float)m->dt;
+    phase_begin(m, PH_INERTIA, s);
+    launch_inertia(m, h, g[0], g[1], g[2], s);
+    phase_end(m, s);
+    for (int it = 0; it < n_iter; ++it) {
+        phase_begin(m, PH_LOCAL, s);
+        launch_local(m, m->d_x.p, m->d_force.p, s);
+        phase_end(m, s);
+        phase_begin(m, PH_ASSEMBLE, s);
+        launch_assemble(m, m->d_by0.p, m->d_force.p, m->d_b.p, s);
+        phase_end(m, s);
+        launch_dd_solve(m, m->d_b.p, m->d_x.p, s, false);
+        for (int r = 0; r < m->refine; ++r) {
+            phase_begin(m, PH_RESIDUAL, s);
+            launch_residual(m, m->d_b.p, m->d_x.p, m->d_r.p, s);
+            phase_end(m, s);
+            launch_dd_solve(m, m->d_r.p, m->d_dx.p, s, false);
+            launch_axpy_free(m, m->d_dx.p, m->d_x.p, s);
+        }
+    }
+    phase_begin(m, PH_VELOCITY, s);
+    launch_velocity(m, 1.0f / h, s);
+    phase_end(m, s);
+}
+
+extern "C" {
+
+pd_status pd_step(pd_mesh* m, const float* pin_targets, const float* gravity, int32_t n_iter, float* x_out) {
+    if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
+    if (!m->prefactored) return fail(PD_ERR_NOT_PREFACTORED, "pd_prefactor has not run since the last change");
+    if (n_iter < 1 || n_iter > 1000) return fail(PD_ERR_INVALID_ARG, "n_iter out of range");
+    PD_API_BEGIN
+    float g[3] = {0.f, 0.f, -9.81f};
+    if (gravity) {
+        g[0] = gravity[0];
+        g[1] = gravity[1];
+        g[2] = gravity[2];
+    }
+    cudaStream_t s = m->stream;
+    if (pin_targets) launch_pin_copy(m, pin_targets, s);
+    else launch_pin_hold(m, s);
+    if (m->use_graphs) {
+        std::vector<uint32_t> key(6);
+        key[0] = (uint32_t)n_iter;
+        std::memcpy(&key[1], g, sizeof(g));
+        key[4] = (uint32_t)m->refine;
+        key[5] = (uint32_t)m->timing_mask;
+        auto it = m->graphs.find(key);
+        if (it == m->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            m->timing_armed = m->timing_mask != 0;
+            m->ev_used = 0;
+            PDG_CUDA(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                run_frame(m, n_iter, g, m->cap_stream);
+            } catch (...) {
+                cudaStreamEndCapture(m->cap_stream, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                m->timing_armed = false;
+                throw;
+            }
+            m->timing_armed = false;
+            PDG_CUDA(cudaStreamEndCapture(m->cap_stream, &graph));
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            PDG_CUDA(e);
+            it = m->graphs.emplace(key, pd_mesh::GraphEntry{exec}).first;
+        }
+        PDG_CUDA(cudaGraphLaunch(it->second.exec, s));
+    } else {
+        m->timing_armed = m->timing_mask != 0;
+        m->ev_used = 0;
+        try {
+            run_frame(m, n_iter, g, s);
+        } catch (...) {
+            m->timing_armed = false;
+            throw;
+        }
+        m->timing_armed = false;
+    }
+    if (x_out) launch_scatter_out(m, m->d_x.p, x_out, 0, s);
+    return PD_OK;
+    PD_API_END
+}
+
+pd_status pd_sync(pd_mesh* m) {
+    if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
+    PD_API_BEGIN
+    PDG_CUDA(cudaStreamSynchronize(m->stream));
+    int32_t herr = 0;
+    PDG_CUDA(cudaMemcpy(&herr, m->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (herr) {
+        PDG_CUDA(cudaMemset(m->d_err.p, 0, sizeof(int32_t)));
+        if (herr & ERR_NONFINITE) return fail(PD_ERR_NONFINITE, "non-finite positions or velocities");
+        return fail(PD_ERR_NOT_SPD, "a Cholesky pivot was not positive");
+    }
+    return PD_OK;
+    PD_API_END
+}
+
+pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
+    if (!m || !out) return fail(PD_ERR_INVALID_ARG, "null argument");
+    out->n_vertices = m->n_v;
+    out->n_tets = m->n_t;
+    out->n_domains = m->n_dom;
+    out->n_pinned = m->n_pin;
+    out->n_interface = m->n_B;
+    out->n_internal = m->n_int;
+    int32_t mi = 0, mb = 0;
+    for (int32_t d = 0; d < m->n_dom; ++d) {
+        mi = std::max(mi, m->dom_n_int[d]);
+        mb = std::max(mb, (int32_t)m->dom_bnd[d].size());
+    }
+    out->max_domain_internal = mi;
+    out->max_domain_boundary = mb;
+    int64_t bytes = 0;
+    bytes += m->d_tets.bytes() + m->d_geo.bytes() + m->d_x.bytes() + m->d_xprev.bytes() + m->d_v.bytes();
+    bytes += m->d_force.bytes() + m->d_by0.bytes() + m->d_b.bytes() + m->d_pin_tgt.bytes() + m->d_mh2.bytes();
+    bytes += m->d_inc_ptr.bytes() + m->d_inc.bytes() + m->d_kfp_ptr.bytes() + m->d_kfp_col.bytes();
+    bytes += m->d_kfp_val.bytes() + m->d_old_of_new.bytes() + m->d_mat32.bytes() + m->d_mat16.bytes();
+    bytes += m->d_tasks_cond.bytes() + m->d_tasks_back.bytes() + m->d_tc.bytes() + m->d_bidx.bytes();
+    bytes += m->d_gat_ptr.bytes() + m->d_gat.bytes() + m->d_cB.bytes() + m->d_part.bytes();
+    bytes += m->d_K_ptr.bytes() + m->d_K_col.bytes() + m->d_K_val.bytes() + m->d_r.bytes() + m->d_dx.bytes();
+    out->device_bytes = bytes;
+    out->prefactor_seconds = m->prefactor_seconds;
+    out->launches_per_iter = m->launches_per_iter;
+    out->launches_per_frame = 3;   // pin copy (or hold), inertia, velocity
+    for (int k = 0; k < 16; ++k) out->phase_bytes[k] = m->phase_bytes[k];
+    return PD_OK;
+}
+
+pd_status pd_project(const float* F, int32_t n, float* R, float* V, float* sigma, void* stream) {
+    if (n < 0 || (n > 0 && !F)) return fail(PD_ERR_INVALID_ARG, "bad arguments");
+    PD_API_BEGIN
+    launch_project(F, n, R, V, sigma, static_cast<cudaStream_t>(stream));
+    return PD_OK;
+    PD_API_END
+}
+
+pd_status pd_local_rhs(pd_mesh* m, const float* x, const float* y, float* b) {
+    if (!m || !x || !y || !b) return fail(PD_ERR_INVALID_ARG, "null argument");
+    if (!m->prefactored) return fail(PD_ERR_NOT_PREFACTORED, "pd_prefactor has not run");
+    PD_API_BEGIN
+    cudaStream_t s = m->stream;
+    DBuf<float4> xi, yi, by0, bb, frc;
+    xi.alloc(m->n_v);
+    yi.alloc(m->n_v);
+    by0.alloc(std::max(m->n_free, 1));
+    bb.alloc(m->n_v);
+    frc.alloc(4 * (size_t)m->n_t);
+    launch_gather_in(m, x, xi.p, s);
+    launch_gather_in(m, y, yi.p, s);
+    // pinned positions for the K_fp term come from x
+    if (m->n_pin > 0)
+        PDG_CUDA(cudaMemcpyAsync(m->d_pin_tgt.p, xi.p + m->n_free, sizeof(float4) * m->n_pin,
+                                 cudaMemcpyDeviceToDevice, s));
+    launch_by0_from_y(m, yi.p, by0.p, s);
+    launch_local(m, xi.p, frc.p, s);
+    launch_assemble(m, by0.p, frc.p, bb.p, s);
+    launch_scatter_out(m, bb.p, b, 1, s);
+    PDG_CUDA(cudaStreamSynchronize(s));
+    return PD_OK;
+    PD_API_END
+}
+
+pd_status pd_solve(pd_mesh* m, const float* r, float* x) {
+    if (!m || !r || !x) return fail(PD_ERR_INVALID_ARG, "null argument");
+    if (!m->prefactored) return fail(PD_ERR_NOT_PREFACTORED, "pd_prefactor has not run");
+    PD_API_BEGIN
+    cudaStream_t s = m->stream;
+    DBuf<float4> ri, xi;
+    ri.alloc(m->n_v);
+    xi.alloc(m->n_v);
+    PDG_CUDA(cudaMemsetAsync(xi.p, 0, sizeof(float4) * m->n_v, s));
+    launch_gather_in(m, r, ri.p, s);
+    launch_dd_solve(m, ri.p, xi.p, s, false);
+    for (int k = 0; k < m->refine; ++k) {
+        DBuf<float4> rr, dx;
+        rr.alloc(std::max(m->n_free, 1));
+        dx.alloc(m->n_v);
+        launch_residual(m, ri.p, xi.p, rr.p, s);
+        launch_dd_solve(m, rr.p, dx.p, s, false);
+        launch_axpy_free(m, dx.p, xi.p, s);
+        PDG_CUDA(cudaStreamSynchronize(s));
+    }
+    launch_scatter_out(m, xi.p, x, 1, s);
+    PDG_CUDA(cudaStreamSynchronize(s));
+    return PD_OK;
+    PD_API_END
+}
+
+pd_status pd_enable_timing(pd_mesh* m, int32_t mask) {
+    if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
+    m->timing_mask = mask < 0 ? ((1 << PH_COUNT) - 1) : (mask & ((1 << PH_COUNT) - 1));
+    return PD_OK;
+}
+
+pd_status pd_phase_times(pd_mesh* m, float* out, int32_t n_out, int32_t* n_phases) {
+    if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
+    PD_API_BEGIN
+    if (n_phases) *n_phases = PH_COUNT;
+    std::vector<double> sum(PH_COUNT, 0.0);
+    std::vector<int> cnt(PH_COUNT, 0);
+    PDG_CUDA(cudaStreamSynchronize(m->stream));
+    for (int32_t k = 0; k < m->ev_used; ++k) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, m->ev_pool[2 * k], m->ev_pool[2 * k + 1]);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        sum[m->ev_phase[k]] += ms;
+        cnt[m->ev_phase[k]]++;
+    }
+    for (int32_t p = 0; p < n_out && p < PH_COUNT; ++p) out[p] = cnt[p] ? (float)(sum[p] / cnt[p]) : 0.f;
+    return PD_OK;
+    PD_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,199 @@
+// Internal declarations of libpdgb300: mesh object, device buffers, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+#include <map>
+
+#include "../../include/pd.h"
+
+namespace pdg {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+
+struct Fail {
+    pd_status code;
+};
+
+#define PDG_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            ::pdg::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));              \
+            throw ::pdg::Fail{e_ == cudaErrorMemoryAllocation ? PD_ERR_NO_MEMORY : PD_ERR_CUDA}; \
+        }                                                                                     \
+    } while (0)
+
+#define PDG_CHECK_LAUNCH() PDG_CUDA(cudaGetLastError())
+
+// Device error flag bits (d_err).
+enum : int { ERR_NONFINITE = 1, ERR_NOT_SPD = 2 };
+
+// ---------------------------------------------------------------- device buffer
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    void alloc(size_t count) {
+        free();
+        if (count == 0) count = 1;
+        void* q = nullptr;
+        PDG_CUDA(cudaMalloc(&q, count * sizeof(T)));
+        p = static_cast<T*>(q);
+        n = count;
+    }
+    void free() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+    ~DBuf() { free(); }
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+};
+
+// Per-iteration dense product over a row block of one matrix ("task").
+struct GemvTask {
+    int64_t a_off;     // element offset of the block's first row in the matrix pool
+    int32_t rows;      // rows in this block
+    int32_t ld;        // row stride (elements, multiple of 8)
+    int32_t cols;      // columns to stream (multiple of 4, <= ld)
+    int32_t x_off;     // condense: first vertex of b; backsub: offset into the boundary index list
+    int32_t x_n;       // number of x entries (condense: n_i; backsub: n_bd)
+    int32_t y_off;     // first output row
+    int32_t add_off;   // backsub: first row of t to add
+    int32_t pad;
+};
+
+enum Phase : int {
+    PH_INERTIA = 0, PH_LOCAL, PH_ASSEMBLE, PH_CONDENSE, PH_GATHER, PH_COARSE, PH_REDUCE,
+    PH_BACKSUB, PH_RESIDUAL, PH_VELOCITY, PH_COUNT
+};
+
+// ---------------------------------------------------------------- mesh
+struct pd_mesh_impl;
+
+}  // namespace pdg
+
+struct pd_mesh {
+    // sizes
+    int32_t n_v = 0, n_t = 0, n_dom = 0, n_pin = 0, n_free = 0, n_int = 0, n_B = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+
+    // host-side topology (new vertex numbering: [domain internals][interface][pinned])
+    std::vector<int32_t> new_of_old, old_of_new;  // vertex maps
+    std::vector<int32_t> tet_old_of_new;          // tet order: sorted by domain
+    std::vector<int32_t> tets_new;                // n_t x 4, new vertex ids
+    std::vector<int32_t> tet_dom;                 // domain of each (sorted) tet
+    std::vector<double> vol;                      // rest volume of each (sorted) tet
+    std::vector<double> Dminv;                    // n_t x 9 (sorted tets)
+    std::vector<double> mass;                     // n_v (new numbering)
+    std::vector<int32_t> dom_int_off, dom_n_int;  // per domain: first internal vertex, count
+    std::vector<std::vector<int32_t>> dom_bnd;    // per domain: interface ids (0..n_B) coupled to its internals
+    // CSR of the scalar matrix over free vertices (new numbering) and of the free-pinned block
+    std::vector<int32_t> K_rowptr, K_col;         // n_free rows, columns < n_free
+    std::vector<int32_t> Kfp_rowptr, Kfp_col;     // n_free rows, columns = pinned slot (0..n_pin)
+    std::vector<double> K_val, Kfp_val;
+    std::vector<float> gamma_s, gamma_v;          // sorted tet order
+
+    // device: geometry and state
+    pdg::DBuf<int4> d_tets;         // n_t
+    pdg::DBuf<float4> d_geo;        // 3 * n_t: rows g1|g2|g3 (xyz) + (ws, wv, 0) in .w
+    pdg::DBuf<float4> d_x, d_xprev, d_v;   // n_v each
+    pdg::DBuf<float4> d_force;      // 4 * n_t
+    pdg::DBuf<float4> d_by0;        // n_free
+    pdg::DBuf<float4> d_b;          // n_free
+    pdg::DBuf<float4> d_pin_tgt;    // n_pin
+    pdg::DBuf<float> d_mh2;         // n_free: m / dt^2
+    pdg::DBuf<int32_t> d_inc_ptr, d_inc;   // free-vertex -> (tet*4+corner) CSR
+    pdg::DBuf<int32_t> d_kfp_ptr, d_kfp_col;
+    pdg::DBuf<float> d_kfp_val;
+    pdg::DBuf<int32_t> d_old_of_new;       // n_v
+    pdg::DBuf<int32_t> d_err;              // device error flags
+
+    // device: subspace solve (per-iteration data)
+    int32_t prec = PD_PREC_FP32;
+    int32_t refine = 0;
+    pdg::DBuf<float> d_mat32;               // matrix pool (FP32 or TF32-rounded)
+    pdg::DBuf<__nv_bfloat16> d_mat16;       // matrix pool (BF16)
+    int64_t off_S = 0;                      // pool offset of S^-1
+    int32_t ld_S = 0;
+    pdg::DBuf<pdg::GemvTask> d_tasks_cond, d_tasks_back;
+    int32_t n_tasks_cond = 0, n_tasks_back = 0;
+    pdg::DBuf<float4> d_tc;                 // stacked [t_d; c_d] rows of every domain
+    int32_t n_tc = 0;
+    pdg::DBuf<int32_t> d_bidx;              // concatenated per-domain boundary index lists
+    pdg::DBuf<int32_t> d_gat_ptr, d_gat;    // interface vertex -> rows of tc holding its c_d pieces
+    pdg::DBuf<float4> d_cB;                 // n_B condensed interface RHS
+    pdg::DBuf<float4> d_part;               // coarse partial sums: n_chunks x n_B
+    int32_t coarse_chunk = 0, coarse_nchunks = 0, coarse_rows_per_cta = 0;
+    // FP64 residual for refinement
+    pdg::DBuf<int32_t> d_K_ptr, d_K_col;
+    pdg::DBuf<double> d_K_val;
+    pdg::DBuf<float4> d_r, d_dx;             // refinement residual / correction (n_free)
+
+    // state flags
+    bool materials_set = false;
+    bool prefactored = false;
+    double dt = 0.0;
+    bool use_graphs = true;
+    double prefactor_seconds = 0.0;
+    int64_t phase_bytes[16] = {0};
+    int32_t launches_per_iter = 0;
+
+    // graphs: key = (n_iter, gravity bits)
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::map<std::vector<uint32_t>, GraphEntry> graphs;
+
+    // timing
+    int32_t timing_mask = 0;
+    std::vector<cudaEvent_t> ev_pool;       // pairs (start, stop)
+    std::vector<int32_t> ev_phase;          // phase of each pair
+    int32_t ev_used = 0;
+    bool timing_armed = false;
+    bool ev_open = false;
+
+    ~pd_mesh();
+};
+
+namespace pdg {
+
+// ---------------------------------------------------------------- kernels (launchers)
+void launch_project(const float* F, int n, float* R, float* V, float* sig, cudaStream_t s);
+void launch_local(const pd_mesh* m, const float4* x, float4* force, cudaStream_t s);
+void launch_assemble(const pd_mesh* m, const float4* by0, const float4* force, float4* b, cudaStream_t s);
+void launch_inertia(const pd_mesh* m, float h, float gx, float gy, float gz, cudaStream_t s);
+void launch_velocity(const pd_mesh* m, float inv_h, cudaStream_t s);
+void launch_pin_copy(const pd_mesh* m, const float* user_targets, cudaStream_t s);
+void launch_pin_hold(const pd_mesh* m, cudaStream_t s);
+void launch_scatter_out(const pd_mesh* m, const float4* src, float* dst, int free_only, cudaStream_t s);
+void launch_gather_in(const pd_mesh* m, const float* src, float4* dst, cudaStream_t s);
+void launch_by0_from_y(const pd_mesh* m, const float4* y, float4* by0, cudaStream_t s);
+
+// subspace solve: b (free, new order) -> x positions of free vertices written into `xout`
+// (float4 array indexed by new vertex id).
+void launch_dd_solve(pd_mesh* m, const float4* b, float4* xout, cudaStream_t s, bool timed);
+void launch_residual(const pd_mesh* m, const float4* b, const float4* x, float4* r, cudaStream_t s);
+void launch_axpy_free(const pd_mesh* m, const float4* dx, float4* x, cudaStream_t s);
+
+// FP64 dense factorisations (device), used by the prefactorisation.
+void dense_gemm(bool ta, bool tb, int M, int N, int K, double alpha, const double* A, int lda,
+                int64_t sA, const double* B, int ldb, int64_t sB, double beta, double* C, int ldc,
+                int64_t sC, int batch, bool lower_only, cudaStream_t s);
+void dense_set_identity(double* A, int n, int lda, int64_t strideA, int batch, cudaStream_t s);
+
+// timing helpers (no-ops unless the phase is in the mesh's timing mask)
+void phase_begin(pd_mesh* m, int phase, cudaStream_t s);
+void phase_end(pd_mesh* m, cudaStream_t s);
+
+}  // namespace pdg

@@ -1,0 +1,170 @@
+"""Thin Python wrapper over the C ABI: torch tensors in, device pointers out.
+
+PyTorch only provides device memory and streams here; every step of the
+simulation runs in libpdgb300's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = _lib.load()
+    return _LIB
+
+
+def _check(status: int, where: str):
+    if status != _lib.PD_OK:
+        L = lib()
+        raise _lib.PDError(status, where, f"{L.pd_status_string(status).decode()}: {L.pd_last_error().decode()}")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dev_f32(a, shape=None, device="cuda"):
+    if a is None:
+        return None
+    t = a if isinstance(a, torch.Tensor) else torch.as_tensor(np.asarray(a))
+    t = t.to(device=device, dtype=torch.float32).contiguous()
+    if shape is not None:
+        t = t.reshape(shape)
+    return t
+
+
+PRECISIONS = {"fp32": _lib.PD_PREC_FP32, "bf16": _lib.PD_PREC_BF16, "tf32": _lib.PD_PREC_TF32}
+
+
+class Mesh:
+    """A tet mesh resident on the GPU, stepped by domain-decomposed PD."""
+
+    def __init__(self, rest, tets, pinned=None, tet_domain=None, n_domains=1, density=300.0, vertex_mass=None,
+                 stream: torch.cuda.Stream | None = None):
+        L = lib()
+        self.rest = np.ascontiguousarray(rest, dtype=np.float64)
+        self.tets = np.ascontiguousarray(tets, dtype=np.int32)
+        self.n_v = int(self.rest.shape[0])
+        self.n_t = int(self.tets.shape[0])
+        pin = None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8)
+        dom = None if tet_domain is None else np.ascontiguousarray(tet_domain, dtype=np.int32)
+        mass = None if vertex_mass is None else np.ascontiguousarray(vertex_mass, dtype=np.float64)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.n_pinned = 0 if pin is None else int((pin != 0).sum())
+        h = C.c_void_p()
+        st = L.pd_create_mesh(self.rest.ctypes.data, self.n_v, self.tets.ctypes.data, self.n_t,
+                              None if mass is None else mass.ctypes.data, float(density),
+                              None if dom is None else dom.ctypes.data, int(n_domains),
+                              None if pin is None else pin.ctypes.data, C.c_void_p(self.stream.cuda_stream),
+                              C.byref(h))
+        _check(st, "pd_create_mesh")
+        self._h = h
+        self._keep = {}
+
+    # -- lifecycle -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pd_destroy_mesh(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up ----------------------------------------------------------------
+    def set_materials(self, gamma_s, gamma_v):
+        gs = np.ascontiguousarray(np.asarray(gamma_s, dtype=np.float32)) if not isinstance(gamma_s, torch.Tensor) \
+            else gamma_s.to(torch.float32).contiguous()
+        gv = np.ascontiguousarray(np.asarray(gamma_v, dtype=np.float32)) if not isinstance(gamma_v, torch.Tensor) \
+            else gamma_v.to(torch.float32).contiguous()
+        p_s = gs.ctypes.data if isinstance(gs, np.ndarray) else gs.data_ptr()
+        p_v = gv.ctypes.data if isinstance(gv, np.ndarray) else gv.data_ptr()
+        _check(lib().pd_set_materials(self._h, C.c_void_p(p_s), C.c_void_p(p_v)), "pd_set_materials")
+
+    def prefactor(self, dt, precision="fp32", refine_steps=0, use_graphs=True):
+        o = _lib.pd_solver_opts(PRECISIONS[precision], int(refine_steps), 1 if use_graphs else 0, 0)
+        _check(lib().pd_prefactor(self._h, float(dt), C.byref(o)), "pd_prefactor")
+
+    # -- state -----------------------------------------------------------------
+    def set_state(self, x=None, v=None):
+        xt = _dev_f32(x, (self.n_v, 3))
+        vt = _dev_f32(v, (self.n_v, 3))
+        _check(lib().pd_set_state(self._h, _ptr(xt), _ptr(vt)), "pd_set_state")
+        self._keep["state"] = (xt, vt)   # keep alive until the stream has consumed them
+
+    def get_state(self):
+        x = torch.empty((self.n_v, 3), device="cuda", dtype=torch.float32)
+        v = torch.empty((self.n_v, 3), device="cuda", dtype=torch.float32)
+        _check(lib().pd_get_state(self._h, _ptr(x), _ptr(v)), "pd_get_state")
+        return x, v
+
+    def step(self, pin_targets=None, gravity=(0.0, 0.0, -9.81), n_iter=10, x_out=None):
+        pt = _dev_f32(pin_targets, (self.n_pinned, 3)) if pin_targets is not None else None
+        g = (C.c_float * 3)(*[float(a) for a in gravity])
+        _check(lib().pd_step(self._h, _ptr(pt), g, int(n_iter), _ptr(x_out)), "pd_step")
+        self._keep["pins"] = pt
+        return x_out
+
+    def sync(self):
+        _check(lib().pd_sync(self._h), "pd_sync")
+
+    def info(self) -> dict:
+        i = _lib.pd_mesh_info()
+        _check(lib().pd_get_info(self._h, C.byref(i)), "pd_get_info")
+        d = {k: getattr(i, k) for k, _ in _lib.pd_mesh_info._fields_ if k != "phase_bytes"}
+        d["phase_bytes"] = {PHASES[k]: int(i.phase_bytes[k]) for k in range(len(PHASES))}
+        return d
+
+    # -- diagnostics -------------------------------------------------------------
+    def local_rhs(self, x, y):
+        xt = _dev_f32(x, (self.n_v, 3))
+        yt = _dev_f32(y, (self.n_v, 3))
+        b = torch.empty((self.n_v, 3), device="cuda", dtype=torch.float32)
+        _check(lib().pd_local_rhs(self._h, _ptr(xt), _ptr(yt), _ptr(b)), "pd_local_rhs")
+        return b
+
+    def solve(self, r):
+        rt = _dev_f32(r, (self.n_v, 3))
+        x = torch.empty((self.n_v, 3), device="cuda", dtype=torch.float32)
+        _check(lib().pd_solve(self._h, _ptr(rt), _ptr(x)), "pd_solve")
+        return x
+
+    def enable_timing(self, mask=-1):
+        _check(lib().pd_enable_timing(self._h, int(mask)), "pd_enable_timing")
+
+    def phase_times(self) -> dict:
+        out = (C.c_float * 16)()
+        n = C.c_int32()
+        _check(lib().pd_phase_times(self._h, out, 16, C.byref(n)), "pd_phase_times")
+        return {lib().pd_phase_name(k).decode(): float(out[k]) for k in range(n.value)}
+
+
+def project(F: torch.Tensor, with_sigma=True):
+    """Rotation and volume targets of a batch of deformation gradients (n, 3, 3)."""
+    F = F.to(device="cuda", dtype=torch.float32).contiguous()
+    n = F.shape[0]
+    R = torch.empty_like(F)
+    V = torch.empty_like(F)
+    s = torch.empty((n, 3), device="cuda", dtype=torch.float32) if with_sigma else None
+    _check(lib().pd_project(_ptr(F), n, _ptr(R), _ptr(V), _ptr(s), C.c_void_p(torch.cuda.current_stream().cuda_stream)),
+           "pd_project")
+    return R, V, s
+
+
+PHASES = ["inertia", "local", "assemble", "dd_condense", "dd_gather", "dd_coarse", "dd_reduce", "dd_backsub",
+          "residual", "velocity"]
+
+
+def phase_bit(name: str) -> int:
+    return 1 << PHASES.index(name)
