@@ -202,10 +202,12 @@ inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
 template <class T>
 void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaStream_t s) {
-    phase_begin(m, PH_CONDENSE, s);
-    k_condense<T><<<m->n_tasks_cond, 256, 0, s>>>(m->d_tasks_cond.p, pool, b, m->d_tc.p);
-    PDG_CHECK_LAUNCH();
-    phase_end(m, s);
+    if (m->n_tasks_cond > 0) {
+        phase_begin(m, PH_CONDENSE, s);
+        k_condense<T><<<m->n_tasks_cond, 256, 0, s>>>(m->d_tasks_cond.p, pool, b, m->d_tc.p);
+        PDG_CHECK_LAUNCH();
+        phase_end(m, s);
+    }
     if (m->n_B > 0) {
         phase_begin(m, PH_GATHER, s);
         k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, m->d_tc.p,

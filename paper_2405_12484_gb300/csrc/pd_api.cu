@@ -766,7 +766,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->phase_bytes[PH_BACKSUB] = mat_b + nbd_tot * (4 + 16) + (int64_t)n_int * 32;
         m->phase_bytes[PH_RESIDUAL] = nk * (4 + 8 + 16) + nf * (4 + 16 + 16);
         m->phase_bytes[PH_VELOCITY] = nv * 48;
-        int dd = 1 + (n_B > 0 ? 3 : 0) + (m->n_tasks_back > 0 ? 1 : 0);
+        int dd = (m->n_tasks_cond > 0 ? 1 : 0) + (n_B > 0 ? 3 : 0) + (m->n_tasks_back > 0 ? 1 : 0);
         m->launches_per_iter = 2 + dd + m->refine * (2 + dd);
     }
 
