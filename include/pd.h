@@ -208,6 +208,27 @@ pd_status pd_enable_timing(pd_mesh* mesh, int32_t enable);
 pd_status pd_phase_times(pd_mesh* mesh, float* out, int32_t n_out, int32_t* n_phases);
 const char* pd_phase_name(int32_t k);
 
+/*
+ * pd_solve_noalloc -- the same solve as pd_solve (same kernels, same
+ * result), for callers that must not allocate device memory during the
+ * call: a host that hands every library a fixed memory pool at start-up and
+ * forbids cudaMalloc/cudaFree afterwards, or code running where an
+ * allocation would stall the device.  The paper has no counterpart; this is
+ * a deployment variant of the pd_solve diagnostic.
+ *   r, x  [device] n_v x 3 (may not alias), caller-owned as in pd_solve.
+ * Every temporary comes from one file-scope device array of 16 MiB
+ * (16777216 bytes) that each GPU loading this library holds until the
+ * process exits; a mesh whose temporaries exceed it is rejected with
+ * PD_ERR_UNSUPPORTED (pd_last_error gives the bytes needed).  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress);
+ * make it before any stream capture.  All calls share the one array, which
+ * keeps the last call's contents (the solution buffer is cleared on entry):
+ * calls that overlap on the GPU -- from two host threads, or on two meshes
+ * with different streams -- race and must be serialised by the caller.
+ * Synchronous.  Errors: INVALID_ARG, NOT_PREFACTORED, UNSUPPORTED, CUDA.
+ */
+pd_status pd_solve_noalloc(pd_mesh* mesh, const float* r, float* x);
+
 #ifdef __cplusplus
 }
 #endif

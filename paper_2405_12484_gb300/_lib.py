@@ -63,6 +63,7 @@ SIGNATURES = [
     ("pd_enable_timing", C.c_int32, [C.c_void_p, C.c_int32]),
     ("pd_phase_times", C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     ("pd_phase_name", C.c_char_p, [C.c_int32]),
+    ("pd_solve_noalloc", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
 ]
 
 

@@ -234,7 +234,40 @@ void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaSt
     }
 }
 
+// The same five launches with caller-provided scratch (condensed rows,
+// interface right-hand side, coarse partial sums) instead of the mesh's.
+template <class T>
+void dd_solve_scratch_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, float4* tc, float4* cB,
+                        float4* part, cudaStream_t s) {
+    if (m->n_tasks_cond > 0) {
+        k_condense<T><<<m->n_tasks_cond, 256, 0, s>>>(m->d_tasks_cond.p, pool, b, tc);
+        PDG_CHECK_LAUNCH();
+    }
+    if (m->n_B > 0) {
+        k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, tc, cB);
+        PDG_CHECK_LAUNCH();
+        dim3 grid(nblk(m->n_B, m->coarse_rows_per_cta), m->coarse_nchunks);
+        k_coarse<T><<<grid, 256, 0, s>>>(pool + m->off_S, m->n_B, m->ld_S, m->coarse_rows_per_cta, cB, part);
+        PDG_CHECK_LAUNCH();
+        k_reduce<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->coarse_nchunks, part, xout + m->n_int);
+        PDG_CHECK_LAUNCH();
+    }
+    if (m->n_tasks_back > 0) {
+        k_backsub<T><<<m->n_tasks_back, 256, 0, s>>>(m->d_tasks_back.p, pool, m->d_bidx.p, xout + m->n_int, tc,
+                                                    xout);
+        PDG_CHECK_LAUNCH();
+    }
+}
+
 }  // namespace
+
+void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* tc, float4* cB, float4* part,
+                             cudaStream_t s) {
+    if (m->prec == PD_PREC_BF16)
+        dd_solve_scratch_t<__nv_bfloat16>(m, m->d_mat16.p, b, xout, tc, cB, part, s);
+    else
+        dd_solve_scratch_t<float>(m, m->d_mat32.p, b, xout, tc, cB, part, s);
+}
 
 int dd_max_sub_cols() { return kMaxSubCols; }
 int dd_coarse_chunk() { return kCoarseChunk; }

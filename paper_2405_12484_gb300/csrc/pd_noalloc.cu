@@ -1,0 +1,118 @@
+// pd_solve_noalloc: the subspace global solve of pd_solve with every
+// temporary taken from one fixed, statically allocated device array instead
+// of cudaMalloc.
+//
+// Who needs it: callers that may not allocate device memory while they run
+// (for example a host that sub-allocates a fixed memory pool to every
+// library and forbids cudaMalloc/cudaFree after start-up, or code running
+// inside a region where allocation would synchronise the device).  After
+// pd_prefactor has run, this entry point needs no allocation at all.
+//
+// The scratch array is a file-scope __device__ array of kNoallocBytes
+// (16 MiB).  Every GPU on which this library is loaded holds it until the
+// process exits.  Host code must not use the array's name as a device
+// address; its device address is obtained once per device with
+// cudaGetSymbolAddress, on the first call made on that device (so make that
+// first call before any stream capture begins).
+#include <mutex>
+
+#include "pd_internal.h"
+
+namespace pdg {
+
+void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* tc, float4* cB, float4* part,
+                             cudaStream_t s);
+
+namespace {
+
+constexpr size_t kNoallocBytes = size_t(16) << 20;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+std::mutex g_setup_mu;
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+}  // namespace
+}  // namespace pdg
+
+using namespace pdg;
+
+extern "C" pd_status pd_solve_noalloc(pd_mesh* m, const float* r, float* x) {
+    if (!m || !r || !x) {
+        set_error("pd_solve_noalloc: null argument");
+        return PD_ERR_INVALID_ARG;
+    }
+    if (!m->prefactored) {
+        set_error("pd_solve_noalloc: pd_prefactor has not run");
+        return PD_ERR_NOT_PREFACTORED;
+    }
+    // layout of the shared scratch: inputs/outputs in library order, the
+    // per-domain condensed rows, the interface right-hand side, the coarse
+    // partial sums, and the refinement residual and correction
+    const size_t nv = (size_t)m->n_v, nf = (size_t)(m->n_free > 0 ? m->n_free : 1);
+    const size_t ntc = (size_t)(m->n_tc > 0 ? m->n_tc : 1), nb = (size_t)(m->n_B > 0 ? m->n_B : 1);
+    const size_t npart = nb * (size_t)(m->coarse_nchunks > 0 ? m->coarse_nchunks : 1);
+    const size_t off_r = 0;
+    const size_t off_x = off_r + align256(nv * sizeof(float4));
+    const size_t off_tc = off_x + align256(nv * sizeof(float4));
+    const size_t off_cb = off_tc + align256(ntc * sizeof(float4));
+    const size_t off_part = off_cb + align256(nb * sizeof(float4));
+    const size_t off_rr = off_part + align256(npart * sizeof(float4));
+    const size_t off_dx = off_rr + align256(nf * sizeof(float4));
+    const size_t total = off_dx + align256(nv * sizeof(float4));
+    if (total > kNoallocBytes) {
+        set_error("pd_solve_noalloc: this mesh needs " + std::to_string(total) +
+                  " bytes of scratch, more than the fixed 16 MiB (16777216 bytes); use pd_solve");
+        return PD_ERR_UNSUPPORTED;
+    }
+    try {
+        int dev = 0;
+        PDG_CUDA(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= kMaxDevices) {
+            set_error("pd_solve_noalloc: device ordinal out of range");
+            return PD_ERR_UNSUPPORTED;
+        }
+        unsigned char* base = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_setup_mu);
+            if (!g_scratch_addr[dev]) {
+                void* p = nullptr;
+                cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+                if (e != cudaSuccess || !p) {
+                    set_error(std::string("pd_solve_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+                    return PD_ERR_CUDA;
+                }
+                g_scratch_addr[dev] = p;
+            }
+            base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+        }
+        float4* ri = reinterpret_cast<float4*>(base + off_r);
+        float4* xi = reinterpret_cast<float4*>(base + off_x);
+        float4* tc = reinterpret_cast<float4*>(base + off_tc);
+        float4* cB = reinterpret_cast<float4*>(base + off_cb);
+        float4* part = reinterpret_cast<float4*>(base + off_part);
+        float4* rr = reinterpret_cast<float4*>(base + off_rr);
+        float4* dx = reinterpret_cast<float4*>(base + off_dx);
+        cudaStream_t s = m->stream;
+        // the solution buffer keeps the previous call's contents: clear it
+        PDG_CUDA(cudaMemsetAsync(xi, 0, nv * sizeof(float4), s));
+        launch_gather_in(m, r, ri, s);
+        launch_dd_solve_scratch(m, ri, xi, tc, cB, part, s);
+        for (int k = 0; k < m->refine; ++k) {
+            launch_residual(m, ri, xi, rr, s);
+            launch_dd_solve_scratch(m, rr, dx, tc, cB, part, s);
+            launch_axpy_free(m, dx, xi, s);
+        }
+        launch_scatter_out(m, xi, x, 1, s);
+        PDG_CUDA(cudaStreamSynchronize(s));
+        return PD_OK;
+    } catch (const Fail& f) {
+        return f.code;
+    } catch (...) {
+        set_error("pd_solve_noalloc: unexpected host exception");
+        return PD_ERR_CUDA;
+    }
+}

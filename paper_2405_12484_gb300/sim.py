@@ -140,6 +140,13 @@ class Mesh:
         _check(lib().pd_solve(self._h, _ptr(rt), _ptr(x)), "pd_solve")
         return x
 
+    def solve_noalloc(self, r, x):
+        """pd_solve without any device allocation inside the call: r and x are
+        caller-owned device tensors (n_v, 3) float32; the library's temporaries
+        come from its fixed 16 MiB static scratch."""
+        _check(lib().pd_solve_noalloc(self._h, _ptr(r), _ptr(x)), "pd_solve_noalloc")
+        return x
+
     def enable_timing(self, mask=-1):
         _check(lib().pd_enable_timing(self._h, int(mask)), "pd_enable_timing")
 
