@@ -161,6 +161,82 @@ __global__ void __launch_bounds__(256) k_coarse(const T* __restrict__ S, int n_B
                       nullptr);
 }
 
+// coarse, balanced form: one 512-thread block per SM holds all of c_B in
+// shared memory (three float planes); the (row pair, 2048-column chunk) units
+// of S^-1 are split into equal contiguous ranges, one per warp, so every warp
+// streams the same number of bytes.  Each unit's partial sums go to
+// part[chunk][row].
+constexpr int kCoarseWarps = 16;
+
+template <class T>
+__global__ void __launch_bounds__(512, 1) k_coarse_bal(const T* __restrict__ S, int n_B, int ld, int cols, int nch,
+                                                         const float4* __restrict__ cB, float4* __restrict__ part) {
+    extern __shared__ float xsm[];
+    float* x0 = xsm;
+    float* x1 = xsm + cols;
+    float* x2 = xsm + 2 * cols;
+    for (int k = threadIdx.x; k < cols; k += blockDim.x) {
+        float4 v = (k < n_B) ? cB[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        x0[k] = v.x;
+        x1[k] = v.y;
+        x2[k] = v.z;
+    }
+    __syncthreads();
+    constexpr int VN = VecN<T>::N;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kCoarseWarps + (threadIdx.x >> 5);
+    const int64_t W = (int64_t)gridDim.x * kCoarseWarps;
+    const int n_rp = (n_B + 1) / 2;
+    const int64_t U = (int64_t)n_rp * nch;
+    const int64_t u0 = U * gw / W, u1 = U * (gw + 1) / W;
+    for (int64_t u = u0; u < u1; ++u) {
+        const int rp = (int)(u / nch), ch = (int)(u % nch);
+        const int r0 = 2 * rp;
+        const bool two = (r0 + 1) < n_B;
+        const T* a0 = S + (int64_t)r0 * ld;
+        const T* a1 = S + (int64_t)(two ? r0 + 1 : r0) * ld;
+        const int cb = ch * kCoarseChunk, ce = min(cols, cb + kCoarseChunk);
+        float s00 = 0.f, s01 = 0.f, s02 = 0.f, s10 = 0.f, s11 = 0.f, s12 = 0.f;
+#pragma unroll 8
+        for (int c = cb + lane * VN; c < ce; c += 32 * VN) {
+            float v0[VN], v1[VN];
+            load_vec(a0 + c, v0);
+            load_vec(a1 + c, v1);
+#pragma unroll
+            for (int j = 0; j < VN; j += 4) {
+                const float4 p0 = *reinterpret_cast<const float4*>(x0 + c + j);
+                const float4 p1 = *reinterpret_cast<const float4*>(x1 + c + j);
+                const float4 p2 = *reinterpret_cast<const float4*>(x2 + c + j);
+                const float q0[4] = {p0.x, p0.y, p0.z, p0.w};
+                const float q1[4] = {p1.x, p1.y, p1.z, p1.w};
+                const float q2[4] = {p2.x, p2.y, p2.z, p2.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    s00 = fmaf(v0[j + k], q0[k], s00);
+                    s01 = fmaf(v0[j + k], q1[k], s01);
+                    s02 = fmaf(v0[j + k], q2[k], s02);
+                    s10 = fmaf(v1[j + k], q0[k], s10);
+                    s11 = fmaf(v1[j + k], q1[k], s11);
+                    s12 = fmaf(v1[j + k], q2[k], s12);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            s00 += __shfl_xor_sync(0xffffffffu, s00, off);
+            s01 += __shfl_xor_sync(0xffffffffu, s01, off);
+            s02 += __shfl_xor_sync(0xffffffffu, s02, off);
+            s10 += __shfl_xor_sync(0xffffffffu, s10, off);
+            s11 += __shfl_xor_sync(0xffffffffu, s11, off);
+            s12 += __shfl_xor_sync(0xffffffffu, s12, off);
+        }
+        if (lane == 0) {
+            part[(int64_t)ch * n_B + r0] = make_float4(s00, s01, s02, 0.f);
+            if (two) part[(int64_t)ch * n_B + r0 + 1] = make_float4(s10, s11, s12, 0.f);
+        }
+    }
+}
+
 // reduce: x_B[j] = sum over chunks (fixed order) of part[ch][j]
 __global__ void k_reduce(int n_B, int n_chunks, const float4* __restrict__ part, float4* __restrict__ xB) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -201,6 +277,19 @@ __global__ void k_axpy(int n, const float4* __restrict__ dx, float4* __restrict_
 inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
 template <class T>
+void launch_coarse(pd_mesh* m, const T* pool, const float4* cB, float4* part, cudaStream_t s) {
+    if (m->coarse_blocks > 0) {
+        const size_t smem = sizeof(float) * 3 * (size_t)m->ld_S;
+        k_coarse_bal<T><<<m->coarse_blocks, 32 * kCoarseWarps, smem, s>>>(pool + m->off_S, m->n_B, m->ld_S, m->ld_S,
+                                                                          m->coarse_nchunks, cB, part);
+    } else {
+        dim3 grid(nblk(m->n_B, m->coarse_rows_per_cta), m->coarse_nchunks);
+        k_coarse<T><<<grid, 256, 0, s>>>(pool + m->off_S, m->n_B, m->ld_S, m->coarse_rows_per_cta, cB, part);
+    }
+    PDG_CHECK_LAUNCH();
+}
+
+template <class T>
 void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaStream_t s) {
     if (m->n_tasks_cond > 0) {
         phase_begin(m, PH_CONDENSE, s);
@@ -215,10 +304,7 @@ void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaSt
         PDG_CHECK_LAUNCH();
         phase_end(m, s);
         phase_begin(m, PH_COARSE, s);
-        dim3 grid(nblk(m->n_B, m->coarse_rows_per_cta), m->coarse_nchunks);
-        k_coarse<T><<<grid, 256, 0, s>>>(pool + m->off_S, m->n_B, m->ld_S, m->coarse_rows_per_cta, m->d_cB.p,
-                                         m->d_part.p);
-        PDG_CHECK_LAUNCH();
+        launch_coarse<T>(m, pool, m->d_cB.p, m->d_part.p, s);
         phase_end(m, s);
         phase_begin(m, PH_REDUCE, s);
         k_reduce<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->coarse_nchunks, m->d_part.p, xout + m->n_int);
@@ -246,9 +332,7 @@ void dd_solve_scratch_t(pd_mesh* m, const T* pool, const float4* b, float4* xout
     if (m->n_B > 0) {
         k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, tc, cB);
         PDG_CHECK_LAUNCH();
-        dim3 grid(nblk(m->n_B, m->coarse_rows_per_cta), m->coarse_nchunks);
-        k_coarse<T><<<grid, 256, 0, s>>>(pool + m->off_S, m->n_B, m->ld_S, m->coarse_rows_per_cta, cB, part);
-        PDG_CHECK_LAUNCH();
+        launch_coarse<T>(m, pool, cB, part, s);
         k_reduce<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->coarse_nchunks, part, xout + m->n_int);
         PDG_CHECK_LAUNCH();
     }
@@ -270,6 +354,21 @@ void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* 
 }
 
 int dd_max_sub_cols() { return kMaxSubCols; }
+
+// Number of blocks of the balanced coarse kernel (one per SM), or 0 when the
+// interface vector does not fit in shared memory and the chunked kernel is used.
+int dd_configure_coarse(int ld_S) {
+    const size_t smem = sizeof(float) * 3 * (size_t)ld_S;
+    int dev = 0, sms = 0, optin = 0;
+    PDG_CUDA(cudaGetDevice(&dev));
+    PDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PDG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (smem > (size_t)optin || sms <= 0) return 0;
+    PDG_CUDA(cudaFuncSetAttribute(k_coarse_bal<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PDG_CUDA(cudaFuncSetAttribute(k_coarse_bal<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    return sms;
+}
 int dd_coarse_chunk() { return kCoarseChunk; }
 
 void launch_dd_solve(pd_mesh* m, const float4* b, float4* xout, cudaStream_t s, bool /*timed*/) {

@@ -103,10 +103,10 @@ __device__ void svd3(const float (&F)[3][3], float (&U)[3][3], float (&s)[3], fl
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) W[i][j] = (i == j) ? 1.f : 0.f;
-    const float scale = a00 + a11 + a22;
-    for (int sweep = 0; sweep < 6; ++sweep) {
-        float off = a01 * a01 + a02 * a02 + a12 * a12;
-        if (off <= 1e-14f * scale * scale + 1e-38f) break;
+    // four cyclic sweeps reach FP32 rounding (quadratic convergence); a fixed
+    // count keeps the warp convergent
+#pragma unroll 1
+    for (int sweep = 0; sweep < 4; ++sweep) {
         jacobi_pair(a00, a11, a01, a02, a12, W, 0, 1);   // pair (0,1), r = 2
         jacobi_pair(a00, a22, a02, a01, a12, W, 0, 2);   // pair (0,2), r = 1
         jacobi_pair(a11, a22, a12, a01, a02, W, 1, 2);   // pair (1,2), r = 0
@@ -159,31 +159,40 @@ template <int K>
 __device__ bool solve_face(const float (&sh)[2], float st, float logp, float t_hi, float (&d)[2], float& t_out) {
     float v, dv;
     const float tm = fmaxf(0.5f * st, kClamp);
-    if (!face_eval<K>(sh, st, logp, kClamp, v, dv, d)) return false;
-    const float f_lo = v;
     if (!face_eval<K>(sh, st, logp, tm, v, dv, d)) return false;
     float t;
     if (v <= 0.0f) {
-        // + branch: psi increasing on [tm, inf); bracket [a, b], Newton safeguarded by bisection
+        // + branch: psi increasing on [tm, inf); bracket [a, b], Newton safeguarded by bisection.
+        // Four steps from the uniform-scaling guess converge in the common case; the
+        // bracketed loop continues only for the rare element that has not.
         float a = tm, b = fmaxf(t_hi, tm);
         float prod = st;
 #pragma unroll
         for (int k = 0; k < K; ++k) prod *= sh[k];
         t = (st > 0.f && prod > 0.f) ? st * expf((logp - logf(prod)) / (K + 1)) : 0.5f * (a + b);
         t = fminf(fmaxf(t, a), b);
-        for (int it = 0; it < 40; ++it) {
+#pragma unroll 1
+        for (int it = 0; it < 4; ++it) {
             face_eval<K>(sh, st, logp, t, v, dv, d);
             if (v <= 0.0f) a = t; else b = t;
             float tn = t - v / dv;
             if (!(tn > a && tn < b)) tn = 0.5f * (a + b);
-            float step = fabsf(tn - t);
             t = tn;
-            if (step <= 2e-7f * t || b - a <= 2e-7f * t) break;
+        }
+        face_eval<K>(sh, st, logp, t, v, dv, d);
+#pragma unroll 1
+        for (int it = 0; it < 40 && fabsf(v) > 2e-6f && (b - a) > 1e-7f * t; ++it) {
+            if (v <= 0.0f) a = t; else b = t;
+            float tn = t - v / dv;
+            if (!(tn > a && tn < b)) tn = 0.5f * (a + b);
+            t = tn;
+            face_eval<K>(sh, st, logp, t, v, dv, d);
         }
     } else {
         // - branch for d_t: a sign change on [0.01, tm) is needed
-        if (f_lo >= 0.0f) return false;
+        if (!face_eval<K>(sh, st, logp, kClamp, v, dv, d) || v >= 0.0f) return false;
         float a = kClamp, b = tm;
+#pragma unroll 1
         for (int it = 0; it < 40; ++it) {
             float mid = 0.5f * (a + b);
             face_eval<K>(sh, st, logp, mid, v, dv, d);
@@ -191,8 +200,8 @@ __device__ bool solve_face(const float (&sh)[2], float st, float logp, float t_h
             if (b - a <= 1e-7f * mid) break;
         }
         t = 0.5f * (a + b);
+        face_eval<K>(sh, st, logp, t, v, dv, d);
     }
-    face_eval<K>(sh, st, logp, t, v, dv, d);
     t_out = t;
     return true;
 }

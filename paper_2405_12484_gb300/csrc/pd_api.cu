@@ -23,6 +23,7 @@ void dense_spd_inverse(double* A, int n, int lda, int64_t sA, double* X, int ldx
 int dense_block();
 int dd_max_sub_cols();
 int dd_coarse_chunk();
+int dd_configure_coarse(int ld_S);
 void launch_prefactor_helpers_scatter_coo(double* S, int ld, const int* r, const int* c, const double* v, int n,
                                           cudaStream_t s);
 void launch_prefactor_add_block(double* S, int ldS, const double* Sd, int ldSd, const int* bidx, int nb,
@@ -741,6 +742,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     m->coarse_chunk = dd_coarse_chunk();
     m->coarse_nchunks = (int32_t)((m->ld_S + m->coarse_chunk - 1) / m->coarse_chunk);
     m->d_part.alloc((size_t)std::max(n_B, 1) * m->coarse_nchunks);
+    m->coarse_blocks = (n_B > 0) ? dd_configure_coarse(m->ld_S) : 0;
 
     // ---- algorithmic bytes per launch of each phase (each array counted once)
     {

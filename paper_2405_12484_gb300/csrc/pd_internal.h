@@ -135,6 +135,7 @@ struct pd_mesh {
     pdg::DBuf<float4> d_cB;                 // n_B condensed interface RHS
     pdg::DBuf<float4> d_part;               // coarse partial sums: n_chunks x n_B
     int32_t coarse_chunk = 0, coarse_nchunks = 0, coarse_rows_per_cta = 0;
+    int32_t coarse_blocks = 0;              // > 0: balanced coarse kernel with this many blocks
     // FP64 residual for refinement
     pdg::DBuf<int32_t> d_K_ptr, d_K_col;
     pdg::DBuf<double> d_K_val;
