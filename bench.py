@@ -36,6 +36,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["fp32", "bf16", "tf32"], default="fp32")
     p.add_argument("--refine", type=int, default=0)
+    p.add_argument("--correction", action="store_true",
+                   help="solve each PD iteration for the correction b - K x (FP64 residual)")
     p.add_argument("--iters", type=int, default=20, help="PD iterations per frame")
     p.add_argument("--small", action="store_true", help="small shell (profiling captures)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -242,7 +244,8 @@ def main():
     m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density, stream=stream)
     m.set_materials(w.gamma_s, w.gamma_v)
     t0 = time.perf_counter()
-    m.prefactor(w.dt, precision=args.precision, refine_steps=args.refine, use_graphs=True)
+    m.prefactor(w.dt, precision=args.precision, refine_steps=args.refine, use_graphs=True,
+                correction=args.correction)
     prefactor_s = time.perf_counter() - t0
     info = m.info()
     K, W = args.steps, max(3, args.warmup)
@@ -342,7 +345,8 @@ def main():
             "config": {"workload": f"{w.name}: 390,000-tet thick cylindrical shell, 98,475 vertices, 200 domains"
                        if not args.small else f"{w.name} (small profiling case)",
                        "pd_iters_per_frame": n_iter, "dt": w.dt, "precision": args.precision,
-                       "refine_steps": args.refine, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "refine_steps": args.refine, "correction_form": args.correction,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "per-iteration working set > 129 MB L2 (S^-1 alone ~0.77 GB): no flush needed",
                        "n_interface": info["n_interface"], "prefactor_s": prefactor_s},
             "frame_ms": {"p50": frame_sorted[len(frame_sorted) // 2],

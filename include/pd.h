@@ -68,11 +68,21 @@ enum {
     PD_PREC_TF32 = 2    /* TF32-rounded storage, FP32 accumulation */
 };
 
+/* pd_solver_opts.flags */
+enum {
+    /* Solve each PD iteration's global step for the correction: r = b - K x_k
+     * with FP64 accumulation, x_{k+1} = x_k + S(r) where S is the subspace
+     * solve in the chosen precision.  Equal to x_{k+1} = S(b) in exact
+     * arithmetic; with low-precision matrices the error only scales the small
+     * correction, so PD's own iterations act as iterative refinement. */
+    PD_SOLVE_CORRECTION = 1
+};
+
 typedef struct pd_solver_opts {
     int32_t precision;     /* PD_PREC_*; default PD_PREC_FP32 */
-    int32_t refine_steps;  /* 0..2 refinement steps per PD iteration with an FP64 residual r = b - K x */
+    int32_t refine_steps;  /* 0..2 extra refinement steps per PD iteration with an FP64 residual r = b - K x */
     int32_t use_graphs;    /* 1: replay each frame as a captured CUDA graph (default), 0: plain launches */
-    int32_t reserved;      /* must be 0 */
+    int32_t flags;         /* PD_SOLVE_* bits; 0 = direct solve x = S(b) */
 } pd_solver_opts;
 
 typedef struct pd_mesh pd_mesh;   /* opaque, library-owned */

@@ -28,10 +28,12 @@ PD_PREC_FP32 = 0
 PD_PREC_BF16 = 1
 PD_PREC_TF32 = 2
 
+PD_SOLVE_CORRECTION = 1
+
 
 class pd_solver_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("refine_steps", C.c_int32), ("use_graphs", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("flags", C.c_int32)]
 
 
 class pd_mesh_info(C.Structure):

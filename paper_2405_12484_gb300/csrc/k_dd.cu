@@ -47,12 +47,12 @@ __device__ __forceinline__ void load_vec(const __nv_bfloat16* p, float (&v)[8]) 
 
 // y[r] = add[r] + A[r, 0:cols] . xs  for r < rows; groups of LPR lanes own
 // two rows at a time; 256 threads.
-template <class T, int LPR>
-__device__ __forceinline__ void block_rows(const T* __restrict__ A, int rows, int ld, int cols,
-                                           const float4* __restrict__ xs, float4* __restrict__ y,
-                                           const float4* __restrict__ add) {
+template <class T, int LPR, int NT>
+__device__ __forceinline__ void block_rows_n(const T* __restrict__ A, int rows, int ld, int cols,
+                                             const float4* __restrict__ xs, float4* __restrict__ y,
+                                             const float4* __restrict__ add) {
     constexpr int VN = VecN<T>::N;
-    constexpr int G = 256 / LPR;
+    constexpr int G = NT / LPR;
     const int lane = threadIdx.x % LPR;
     const int grp = threadIdx.x / LPR;
     // the trip count is uniform across the block so every lane reaches the shuffles
@@ -100,6 +100,13 @@ __device__ __forceinline__ void block_rows(const T* __restrict__ A, int rows, in
     }
 }
 
+template <class T, int LPR>
+__device__ __forceinline__ void block_rows(const T* __restrict__ A, int rows, int ld, int cols,
+                                           const float4* __restrict__ xs, float4* __restrict__ y,
+                                           const float4* __restrict__ add) {
+    block_rows_n<T, LPR, 256>(A, rows, ld, cols, xs, y, add);
+}
+
 constexpr int kMaxSubCols = 2048;   // largest per-domain internal / boundary count handled in shared memory
 
 // condense: one task = a row block of G_d = [K_ii^-1; Psi_d^T]; x = b_i (contiguous)
@@ -125,6 +132,43 @@ __global__ void __launch_bounds__(256) k_backsub(const GemvTask* __restrict__ ta
         xs[k] = (k < tk.x_n) ? xB[bidx[tk.x_off + k]] : make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     block_rows<T, 8>(pool + tk.a_off, tk.rows, tk.ld, tk.cols, xs, xout + tk.y_off, tc + tk.add_off);
+}
+
+// Balanced per-domain products.  The rows of every domain's matrix are
+// concatenated into one list; block c takes rows [R c / C, R (c+1) / C) and
+// walks the (at most a few) domains its slice overlaps: it stages that
+// domain's vector in shared memory (contiguous b_i, or x_B gathered through
+// the boundary list) and streams its share of the rows.
+template <class T, bool GATHER>
+__global__ void __launch_bounds__(512) k_segments(const SegDesc* __restrict__ segs, const int* __restrict__ cta_seg,
+                                                  int64_t total_rows, const T* __restrict__ pool,
+                                                  const float4* __restrict__ xsrc, const int* __restrict__ bidx,
+                                                  const float4* __restrict__ add, float4* __restrict__ out) {
+    __shared__ float4 xs[kMaxSubCols];
+    const int64_t r_begin = total_rows * blockIdx.x / gridDim.x;
+    const int64_t r_end = total_rows * (blockIdx.x + 1) / gridDim.x;
+    int si = cta_seg[blockIdx.x];
+    while (true) {
+        const SegDesc sd = segs[si];
+        const int64_t s0 = sd.grow, s1 = sd.grow + sd.rows;
+        if (s0 >= r_end) break;
+        const int64_t lo = r_begin > s0 ? r_begin : s0;
+        const int64_t hi = r_end < s1 ? r_end : s1;
+        if (hi > lo) {
+            __syncthreads();   // previous segment's readers are done with xs
+            for (int k = threadIdx.x; k < sd.cols; k += blockDim.x) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k < sd.x_n) v = GATHER ? xsrc[bidx[sd.x_off + k]] : xsrc[sd.x_off + k];
+                xs[k] = v;
+            }
+            __syncthreads();
+            const int r_local = (int)(lo - s0);
+            block_rows_n<T, 8, 512>(pool + sd.a_off + (int64_t)r_local * sd.ld, (int)(hi - lo), sd.ld, sd.cols, xs,
+                                    out + sd.y_off + r_local, add ? add + sd.add_off + r_local : nullptr);
+        }
+        ++si;
+        if (s1 >= r_end) break;
+    }
 }
 
 // gather: c_B[j] = b_B[j] + sum over the domains touching j of their c_d entry (fixed order)
@@ -290,11 +334,32 @@ void launch_coarse(pd_mesh* m, const T* pool, const float4* cB, float4* part, cu
 }
 
 template <class T>
+void launch_condense(pd_mesh* m, const T* pool, const float4* b, float4* tc, cudaStream_t s) {
+    if (m->seg_blocks_cond > 0) {
+        k_segments<T, false><<<m->seg_blocks_cond, 512, 0, s>>>(m->d_segs_cond.p, m->d_cta_cond.p, m->seg_rows_cond,
+                                                                pool, b, nullptr, nullptr, tc);
+    } else {
+        k_condense<T><<<m->n_tasks_cond, 256, 0, s>>>(m->d_tasks_cond.p, pool, b, tc);
+    }
+    PDG_CHECK_LAUNCH();
+}
+
+template <class T>
+void launch_backsub(pd_mesh* m, const T* pool, const float4* xB, const float4* tc, float4* xout, cudaStream_t s) {
+    if (m->seg_blocks_back > 0) {
+        k_segments<T, true><<<m->seg_blocks_back, 512, 0, s>>>(m->d_segs_back.p, m->d_cta_back.p, m->seg_rows_back,
+                                                               pool, xB, m->d_bidx.p, tc, xout);
+    } else {
+        k_backsub<T><<<m->n_tasks_back, 256, 0, s>>>(m->d_tasks_back.p, pool, m->d_bidx.p, xB, tc, xout);
+    }
+    PDG_CHECK_LAUNCH();
+}
+
+template <class T>
 void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaStream_t s) {
     if (m->n_tasks_cond > 0) {
         phase_begin(m, PH_CONDENSE, s);
-        k_condense<T><<<m->n_tasks_cond, 256, 0, s>>>(m->d_tasks_cond.p, pool, b, m->d_tc.p);
-        PDG_CHECK_LAUNCH();
+        launch_condense<T>(m, pool, b, m->d_tc.p, s);
         phase_end(m, s);
     }
     if (m->n_B > 0) {
@@ -313,9 +378,7 @@ void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaSt
     }
     if (m->n_tasks_back > 0) {
         phase_begin(m, PH_BACKSUB, s);
-        k_backsub<T><<<m->n_tasks_back, 256, 0, s>>>(m->d_tasks_back.p, pool, m->d_bidx.p, xout + m->n_int,
-                                                    m->d_tc.p, xout);
-        PDG_CHECK_LAUNCH();
+        launch_backsub<T>(m, pool, xout + m->n_int, m->d_tc.p, xout, s);
         phase_end(m, s);
     }
 }
@@ -325,10 +388,7 @@ void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaSt
 template <class T>
 void dd_solve_scratch_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, float4* tc, float4* cB,
                         float4* part, cudaStream_t s) {
-    if (m->n_tasks_cond > 0) {
-        k_condense<T><<<m->n_tasks_cond, 256, 0, s>>>(m->d_tasks_cond.p, pool, b, tc);
-        PDG_CHECK_LAUNCH();
-    }
+    if (m->n_tasks_cond > 0) launch_condense<T>(m, pool, b, tc, s);
     if (m->n_B > 0) {
         k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, tc, cB);
         PDG_CHECK_LAUNCH();
@@ -336,11 +396,7 @@ void dd_solve_scratch_t(pd_mesh* m, const T* pool, const float4* b, float4* xout
         k_reduce<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->coarse_nchunks, part, xout + m->n_int);
         PDG_CHECK_LAUNCH();
     }
-    if (m->n_tasks_back > 0) {
-        k_backsub<T><<<m->n_tasks_back, 256, 0, s>>>(m->d_tasks_back.p, pool, m->d_bidx.p, xout + m->n_int, tc,
-                                                    xout);
-        PDG_CHECK_LAUNCH();
-    }
+    if (m->n_tasks_back > 0) launch_backsub<T>(m, pool, xout + m->n_int, tc, xout, s);
 }
 
 }  // namespace

@@ -485,7 +485,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     pd_solver_opts o{PD_PREC_FP32, 0, 1, 0};
     if (opts) o = *opts;
     if (o.precision < PD_PREC_FP32 || o.precision > PD_PREC_TF32 || o.refine_steps < 0 || o.refine_steps > 2 ||
-        o.reserved != 0)
+        (o.flags & ~PD_SOLVE_CORRECTION) != 0)
         return fail(PD_ERR_INVALID_ARG, "bad solver options");
     PD_API_BEGIN
     auto t0 = std::chrono::steady_clock::now();
@@ -638,6 +638,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     // ---- per-iteration matrix pool: per domain G_d = [K_ii^-1; Psi^T], Psi_d; then S^-1
     m->prec = o.precision;
     m->refine = o.refine_steps;
+    m->correction = (o.flags & PD_SOLVE_CORRECTION) != 0;
     m->use_graphs = o.use_graphs != 0;
     std::vector<int64_t> g_off(n_dom), p_off(n_dom);
     std::vector<int32_t> ldG(n_dom), ldP(n_dom), tc_off(n_dom);
@@ -716,6 +717,66 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     }
     upload(m->d_tasks_cond, tc_tasks, s);
     upload(m->d_tasks_back, bk_tasks, s);
+    // balanced form: one segment per domain, blocks over the concatenated rows
+    {
+        int sms = 0, dev = 0;
+        PDG_CUDA(cudaGetDevice(&dev));
+        PDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        std::vector<SegDesc> sc, sb;
+        int64_t rc = 0, rb = 0;
+        for (int32_t d = 0; d < n_dom; ++d) {
+            const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
+            if (ni == 0) continue;
+            SegDesc a{};
+            a.a_off = g_off[d];
+            a.grow = rc;
+            a.rows = ni + nbd;
+            a.ld = ldG[d];
+            a.cols = (int32_t)round_up(ni, VN);
+            a.x_off = m->dom_int_off[d];
+            a.x_n = ni;
+            a.y_off = tc_off[d];
+            sc.push_back(a);
+            rc += a.rows;
+            SegDesc b{};
+            b.a_off = p_off[d];
+            b.grow = rb;
+            b.rows = ni;
+            b.ld = ldP[d];
+            b.cols = nbd > 0 ? (int32_t)round_up(nbd, VN) : 0;
+            b.x_off = bidx_off[d];
+            b.x_n = nbd;
+            b.y_off = m->dom_int_off[d];
+            b.add_off = tc_off[d];
+            sb.push_back(b);
+            rb += b.rows;
+        }
+        auto plan = [&](const std::vector<SegDesc>& segs, int64_t total, DBuf<SegDesc>& dsegs, DBuf<int32_t>& dcta,
+                        int32_t& blocks) {
+            blocks = 0;
+            if (segs.empty() || total <= 0) return;
+            int64_t want = (int64_t)2 * std::max(sms, 1);
+            blocks = (int32_t)std::min<int64_t>(want, total);
+            std::vector<int32_t> first(blocks);
+            size_t si = 0;
+            for (int32_t c = 0; c < blocks; ++c) {
+                const int64_t r0 = total * c / blocks;
+                while (si + 1 < segs.size() && segs[si].grow + segs[si].rows <= r0) ++si;
+                first[c] = (int32_t)si;
+            }
+            // sentinel segment past the end stops every block's walk
+            std::vector<SegDesc> all(segs);
+            SegDesc end{};
+            end.grow = total;
+            all.push_back(end);
+            upload(dsegs, all, s);
+            upload(dcta, first, s);
+        };
+        plan(sc, rc, m->d_segs_cond, m->d_cta_cond, m->seg_blocks_cond);
+        plan(sb, rb, m->d_segs_back, m->d_cta_back, m->seg_blocks_back);
+        m->seg_rows_cond = rc;
+        m->seg_rows_back = rb;
+    }
     m->n_tasks_cond = (int32_t)tc_tasks.size();
     m->n_tasks_back = (int32_t)bk_tasks.size();
     m->n_tc = tcr;
@@ -769,7 +830,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->phase_bytes[PH_RESIDUAL] = nk * (4 + 8 + 16) + nf * (4 + 16 + 16);
         m->phase_bytes[PH_VELOCITY] = nv * 48;
         int dd = (m->n_tasks_cond > 0 ? 1 : 0) + (n_B > 0 ? 3 : 0) + (m->n_tasks_back > 0 ? 1 : 0);
-        m->launches_per_iter = 2 + dd + m->refine * (2 + dd);
+        m->launches_per_iter = 2 + dd + (m->correction ? 2 : 0) + m->refine * (2 + dd);
     }
 
     PDG_CUDA(cudaStreamSynchronize(s));
@@ -818,7 +879,15 @@ static void run_frame(pd_mesh* m, int n_iter, const float g[3], cudaStream_t s) 
         phase_begin(m, PH_ASSEMBLE, s);
         launch_assemble(m, m->d_by0.p, m->d_force.p, m->d_b.p, s);
         phase_end(m, s);
-        launch_dd_solve(m, m->d_b.p, m->d_x.p, s, false);
+        if (m->correction) {
+            phase_begin(m, PH_RESIDUAL, s);
+            launch_residual(m, m->d_b.p, m->d_x.p, m->d_r.p, s);
+            phase_end(m, s);
+            launch_dd_solve(m, m->d_r.p, m->d_dx.p, s, false);
+            launch_axpy_free(m, m->d_dx.p, m->d_x.p, s);
+        } else {
+            launch_dd_solve(m, m->d_b.p, m->d_x.p, s, false);
+        }
         for (int r = 0; r < m->refine; ++r) {
             phase_begin(m, PH_RESIDUAL, s);
             launch_residual(m, m->d_b.p, m->d_x.p, m->d_r.p, s);

@@ -72,6 +72,16 @@ struct GemvTask {
     int32_t pad;
 };
 
+// One domain's matrix in the balanced per-domain kernels.
+struct SegDesc {
+    int64_t a_off;     // pool offset of the matrix
+    int64_t grow;      // first row in the concatenated row list
+    int32_t rows, ld, cols;
+    int32_t x_off, x_n;  // vector source: b offset (condense) or boundary-list offset (backsub)
+    int32_t y_off, add_off;
+    int32_t pad;
+};
+
 enum Phase : int {
     PH_INERTIA = 0, PH_LOCAL, PH_ASSEMBLE, PH_CONDENSE, PH_GATHER, PH_COARSE, PH_REDUCE,
     PH_BACKSUB, PH_RESIDUAL, PH_VELOCITY, PH_COUNT
@@ -122,12 +132,17 @@ struct pd_mesh {
     // device: subspace solve (per-iteration data)
     int32_t prec = PD_PREC_FP32;
     int32_t refine = 0;
+    bool correction = false;                // PD_SOLVE_CORRECTION
     pdg::DBuf<float> d_mat32;               // matrix pool (FP32 or TF32-rounded)
     pdg::DBuf<__nv_bfloat16> d_mat16;       // matrix pool (BF16)
     int64_t off_S = 0;                      // pool offset of S^-1
     int32_t ld_S = 0;
     pdg::DBuf<pdg::GemvTask> d_tasks_cond, d_tasks_back;
     int32_t n_tasks_cond = 0, n_tasks_back = 0;
+    pdg::DBuf<pdg::SegDesc> d_segs_cond, d_segs_back;   // balanced per-domain kernels
+    pdg::DBuf<int32_t> d_cta_cond, d_cta_back;          // first segment of each block
+    int64_t seg_rows_cond = 0, seg_rows_back = 0;
+    int32_t seg_blocks_cond = 0, seg_blocks_back = 0;
     pdg::DBuf<float4> d_tc;                 // stacked [t_d; c_d] rows of every domain
     int32_t n_tc = 0;
     pdg::DBuf<int32_t> d_bidx;              // concatenated per-domain boundary index lists

@@ -92,8 +92,9 @@ class Mesh:
         p_v = gv.ctypes.data if isinstance(gv, np.ndarray) else gv.data_ptr()
         _check(lib().pd_set_materials(self._h, C.c_void_p(p_s), C.c_void_p(p_v)), "pd_set_materials")
 
-    def prefactor(self, dt, precision="fp32", refine_steps=0, use_graphs=True):
-        o = _lib.pd_solver_opts(PRECISIONS[precision], int(refine_steps), 1 if use_graphs else 0, 0)
+    def prefactor(self, dt, precision="fp32", refine_steps=0, use_graphs=True, correction=False):
+        flags = _lib.PD_SOLVE_CORRECTION if correction else 0
+        o = _lib.pd_solver_opts(PRECISIONS[precision], int(refine_steps), 1 if use_graphs else 0, flags)
         _check(lib().pd_prefactor(self._h, float(dt), C.byref(o)), "pd_prefactor")
 
     # -- state -----------------------------------------------------------------

@@ -293,3 +293,41 @@ def test_shell_full_size_one_frame():
     disp = float(np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo - w.rest))
     _record("shell_full_size", {"e_n": e, "e_disp": disp, "info": info})
     assert e < 1e-5
+
+
+@pytest.mark.parametrize("prec,refine,correction,tol", [("bf16", 0, True, 1e-5), ("tf32", 0, True, 1e-5),
+                                                         ("bf16", 1, False, 1e-5), ("fp32", 0, True, 1e-5)])
+def test_one_step_error_mixed_precision(slab_traj, prec, refine, correction, tol):
+    """Mixed precision: BF16/TF32 matrices with FP64-residual refinement or the
+    correction form, one-step error against the FP64 oracle."""
+    w, xs, vs = slab_traj
+    from paper_2405_12484_gb300.sim import Mesh
+    m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density)
+    m.set_materials(w.gamma_s, w.gamma_v)
+    m.prefactor(w.dt, precision=prec, refine_steps=refine, correction=correction)
+    out = torch.empty((w.n_v, 3), device="cuda")
+    errs = {}
+    for n in (1, 25, 60, 100):
+        m.set_state(torch.as_tensor(xs[n - 1], dtype=torch.float32), torch.as_tensor(vs[n - 1], dtype=torch.float32))
+        m.step(torch.as_tensor(w.pin_targets(n - 1), dtype=torch.float32), w.gravity, w.n_iter, x_out=out)
+        m.sync()
+        errs[n] = rel(out.cpu().numpy(), xs[n])
+    _record(f"one_step_slab_{prec}_r{refine}_c{int(correction)}", {str(k): v for k, v in errs.items()})
+    assert max(errs.values()) < tol, errs
+
+
+def test_shell_full_size_mixed_precision():
+    """The 390K-tet shell, BF16 matrices in the correction form, 2 PD iterations
+    against the oracle (the FP32 run of the same frame is in the test above)."""
+    w = sweater_shell()
+    m, o = make_pair(w, precision="bf16")
+    m.prefactor(w.dt, precision="bf16", correction=True)
+    x = torch.empty((w.n_v, 3), device="cuda")
+    m.step(torch.as_tensor(w.pin_targets(0), dtype=torch.float32), w.gravity, 2, x_out=x)
+    m.sync()
+    xo, _ = o.step(w.rest, np.zeros_like(w.rest), w.pin_targets(0), w.gravity, 2)
+    e = rel(x.cpu().numpy(), xo)
+    _record("shell_full_size_bf16_correction", {"e_n": e,
+                                                "e_disp": float(np.linalg.norm(x.cpu().numpy() - xo)
+                                                                / np.linalg.norm(xo - w.rest))})
+    assert e < 1e-5
