@@ -218,6 +218,57 @@ pd_status pd_enable_timing(pd_mesh* mesh, int32_t enable);
 pd_status pd_phase_times(pd_mesh* mesh, float* out, int32_t n_out, int32_t* n_phases);
 const char* pd_phase_name(int32_t k);
 
+/* ---- Differentiation: equilibrium steps and the adjoint step (Sec. 6.1) ---- */
+
+typedef struct pd_adjoint pd_adjoint;   /* opaque workspace: CG vectors and the adjoint states */
+
+/*
+ * pd_adjoint_create -- workspace for pd_equilibrium_step / pd_adjoint_step on
+ * one mesh.  cg_iters (1..500): preconditioned-CG iterations per linear
+ * solve with the true Hessian H = M/dt^2 + sum_e d^2E_e/dx^2 (Sec. 6.1,
+ * Eq. adjoint_state_solve); the preconditioner is the mesh's subspace solve
+ * of the PD matrix K.  The workspace holds lambda_{n+1}, lambda_{n+2}
+ * (zero after creation and after pd_adjoint_reset).
+ */
+pd_status pd_adjoint_create(pd_mesh* mesh, int32_t cg_iters, pd_adjoint** out);
+void pd_adjoint_destroy(pd_adjoint* adj);
+pd_status pd_adjoint_reset(pd_adjoint* adj);
+
+/*
+ * pd_equilibrium_step -- one time step solved to equilibrium (Eq. g):
+ * n_pd_iter PD iterations as pd_step, then n_newton (0..50) Newton steps
+ * H dx = -g(x), g = (M/dt^2)(x - y) + grad E(x).  Same arguments as pd_step;
+ * the mesh state (x, v) advances.  Asynchronous.
+ */
+pd_status pd_equilibrium_step(pd_mesh* mesh, pd_adjoint* adj, const float* pin_targets, const float* gravity,
+                              int32_t n_pd_iter, int32_t n_newton, float* x_out);
+
+/*
+ * pd_adjoint_step -- one backward step of the adjoint recurrence for a loss
+ * L(x_1..x_N) over equilibrium steps (Sec. 6.1, Eq. adjoint_state and
+ * Eq. adjoint_state_solve, chained in time because x_n enters the inertial
+ * targets of steps n+1 and n+2):
+ *   H(x_n) lambda_n = dL/dx_n + (M/dt^2)(2 lambda_{n+1} - lambda_{n+2}),
+ *   dL/dgamma^s_e -= V_e <F_e - R(F_e), sum_c lambda_c (outer) g_c>,
+ *   dL/dgamma^v_e -= V_e <F_e - V(F_e), sum_c lambda_c (outer) g_c>.
+ * Call for n = N, N-1, ..., 1 after pd_adjoint_reset.
+ *   x_n          [device] n_v x 3 equilibrium positions of step n.
+ *   dL_dx        [device] n_v x 3 partial derivative of L with respect to x_n
+ *                (rows of pinned vertices are ignored).
+ *   dL_dgamma_s, dL_dgamma_v [device] n_t floats, caller's tet order,
+ *                accumulated (the caller zeroes them before step N).
+ * Asynchronous.  Errors: INVALID_ARG, NOT_PREFACTORED, CUDA.
+ */
+pd_status pd_adjoint_step(pd_mesh* mesh, pd_adjoint* adj, const float* x_n, const float* dL_dx,
+                          float* dL_dgamma_s, float* dL_dgamma_v);
+
+/* Diagnostics: H(x) v with v = 0 on pinned vertices (rows of pinned vertices
+ * of Hv are 0), and the equilibrium residual g(x) of Eq. g for the step that
+ * started at (x_prev, v_prev).  All [device] n_v x 3.  Synchronous. */
+pd_status pd_hessian_vec(pd_mesh* mesh, const float* x, const float* v, float* Hv);
+pd_status pd_residual(pd_mesh* mesh, const float* x, const float* x_prev, const float* v_prev,
+                      const float* gravity, float* g);
+
 /*
  * pd_solve_noalloc -- the same solve as pd_solve (same kernels, same
  * result), for callers that must not allocate device memory during the

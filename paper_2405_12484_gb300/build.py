@@ -14,7 +14,7 @@ LIB = os.path.join(HERE, "libpdgb300.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 # the local step is FP32 ALU work: approximate division/sqrt and fast log/exp
 # intrinsics (accuracy checked against the FP64 oracle by the parity tests)
-FILE_FLAGS = {"k_local.cu": ["--use_fast_math"]}
+FILE_FLAGS = {"k_local.cu": ["--use_fast_math"], "k_adjoint.cu": ["--use_fast_math"]}
 
 
 def _nvcc() -> str:
@@ -33,7 +33,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
     srcs = sources()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "pd.h"))
     newest_dep = max(os.path.getmtime(p) for p in srcs + headers)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest_dep:

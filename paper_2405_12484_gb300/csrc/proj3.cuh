@@ -1,0 +1,238 @@
+// Device functions of the per-tet projections (Sec. 7.1, Eq. pd_local,
+// Eq. vol_pre), shared by the local step and the adjoint kernels.
+//
+// SVD: cyclic Jacobi eigen-decomposition of F^T F (Golub & Van Loan,
+// "Matrix Computations", the two-sided symmetric Schur rotation), sorted
+// eigenvectors W in SO(3), then a Givens QR of F W (the structure used by
+// McAdams et al. 2011, "Computing the SVD of 3x3 matrices with minimal
+// branching") so that U in SO(3) and the last singular value carries the
+// sign of det F.
+//
+// Volume target: minimise sum (d_i - s_i)^2 s.t. prod d = 1, d_i >= 0.01.
+// KKT: (d_i - s_i) d_i = mu for the free targets.  The smallest target
+// t = d_3 parameterises every candidate root: mu = t (t - s_3) and
+// d_{1,2} = (s_i + sqrt(s_i^2 + 4 mu)) / 2.  On t >= s_3/2 the product is
+// increasing (all roots on the + branch: safeguarded Newton); on
+// [0.01, s_3/2) d_3 is the - root of its quadratic (bisection on the sign
+// change).  If neither holds, d_3 is clamped to 0.01 and the same
+// construction solves d_1 d_2 = 100; failing that d = (1e4, 0.01, 0.01).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace pdg {
+namespace proj {
+
+constexpr float kClamp = 0.01f;
+
+static __device__ __forceinline__ void jacobi_pair(float& app, float& aqq, float& apq, float& arp, float& arq,
+                                            float (&v)[3][3], int p, int q) {
+    if (fabsf(apq) < 1e-30f) return;
+    float tau = (aqq - app) / (2.0f * apq);
+    float t;
+    if (fabsf(tau) > 1e18f) {
+        t = 0.5f / tau;
+    } else {
+        t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+    }
+    float c = rsqrtf(1.0f + t * t);
+    float s = t * c;
+    app -= t * apq;
+    aqq += t * apq;
+    apq = 0.0f;
+    float rp = c * arp - s * arq;
+    float rq = s * arp + c * arq;
+    arp = rp;
+    arq = rq;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float vp = v[k][p], vq = v[k][q];
+        v[k][p] = c * vp - s * vq;
+        v[k][q] = s * vp + c * vq;
+    }
+}
+
+static __device__ __forceinline__ void swap_cols(float (&v)[3][3], int i, int j) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float a = v[k][i];
+        v[k][i] = -v[k][j];   // negate one column: det stays +1
+        v[k][j] = a;
+    }
+}
+
+static __device__ __forceinline__ void givens_rows(float (&b)[3][3], float (&u)[3][3], int i, int j, int col) {
+    float a = b[i][col], c_ = b[j][col];
+    float r2 = a * a + c_ * c_;
+    if (r2 <= 1e-38f) return;
+    float ir = rsqrtf(r2);
+    float c = a * ir, s = c_ * ir;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float bi = b[i][k], bj = b[j][k];
+        b[i][k] = c * bi + s * bj;
+        b[j][k] = -s * bi + c * bj;
+    }
+    // U <- U G^T
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float ui = u[k][i], uj = u[k][j];
+        u[k][i] = c * ui + s * uj;
+        u[k][j] = -s * ui + c * uj;
+    }
+}
+
+// F = U diag(s) W^T, U, W in SO(3), |s0| >= |s1| >= |s2|, s0, s1 >= 0.
+static __device__ __forceinline__ void svd3(const float (&F)[3][3], float (&U)[3][3], float (&s)[3], float (&W)[3][3]) {
+    // A = F^T F (symmetric)
+    float a00 = 0.f, a01 = 0.f, a02 = 0.f, a11 = 0.f, a12 = 0.f, a22 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a00 += F[k][0] * F[k][0];
+        a01 += F[k][0] * F[k][1];
+        a02 += F[k][0] * F[k][2];
+        a11 += F[k][1] * F[k][1];
+        a12 += F[k][1] * F[k][2];
+        a22 += F[k][2] * F[k][2];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) W[i][j] = (i == j) ? 1.f : 0.f;
+    // four cyclic sweeps reach FP32 rounding (quadratic convergence); a fixed
+    // count keeps the warp convergent
+#pragma unroll 1
+    for (int sweep = 0; sweep < 4; ++sweep) {
+        jacobi_pair(a00, a11, a01, a02, a12, W, 0, 1);   // pair (0,1), r = 2
+        jacobi_pair(a00, a22, a02, a01, a12, W, 0, 2);   // pair (0,2), r = 1
+        jacobi_pair(a11, a22, a12, a01, a02, W, 1, 2);   // pair (1,2), r = 0
+    }
+    float l0 = a00, l1 = a11, l2 = a22;
+    if (l0 < l1) { float t = l0; l0 = l1; l1 = t; swap_cols(W, 0, 1); }
+    if (l0 < l2) { float t = l0; l0 = l2; l2 = t; swap_cols(W, 0, 2); }
+    if (l1 < l2) { float t = l1; l1 = l2; l2 = t; swap_cols(W, 1, 2); }
+    // B = F W, then QR by Givens rotations: B = U R
+    float B[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) B[i][j] = F[i][0] * W[0][j] + F[i][1] * W[1][j] + F[i][2] * W[2][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) U[i][j] = (i == j) ? 1.f : 0.f;
+    givens_rows(B, U, 0, 1, 0);
+    givens_rows(B, U, 0, 2, 0);
+    givens_rows(B, U, 1, 2, 1);
+    s[0] = B[0][0];
+    s[1] = B[1][1];
+    s[2] = B[2][2];
+}
+
+// psi(t) = ln t + sum_k ln r+(sh_k, t (t - st)) - logp, and its derivative.
+template <int K>
+static __device__ __forceinline__ bool face_eval(const float (&sh)[2], float st, float logp, float t, float& val,
+                                          float& dval, float (&d)[2]) {
+    float mu = t * (t - st);
+    val = logf(t) - logp;
+    dval = 1.0f / t;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float disc = fmaxf(sh[k] * sh[k] + 4.0f * mu, 0.0f);
+        float sq = sqrtf(disc);
+        float dk = 0.5f * (sh[k] + sq);
+        ok = ok && (dk >= kClamp);
+        d[k] = dk;
+        val += logf(fmaxf(dk, 1e-30f));
+        if (sq > 0.f) dval += (2.0f * t - st) / (sq * dk);
+    }
+    return ok;
+}
+
+// Solve one face: free targets sh[0..K) on the + branch, d_t = t, product exp(logp).
+template <int K>
+static __device__ __forceinline__ bool solve_face(const float (&sh)[2], float st, float logp, float t_hi, float (&d)[2], float& t_out) {
+    float v, dv;
+    const float tm = fmaxf(0.5f * st, kClamp);
+    if (!face_eval<K>(sh, st, logp, tm, v, dv, d)) return false;
+    float t;
+    if (v <= 0.0f) {
+        // + branch: psi increasing on [tm, inf); bracket [a, b], Newton safeguarded by bisection.
+        // Four steps from the uniform-scaling guess converge in the common case; the
+        // bracketed loop continues only for the rare element that has not.
+        float a = tm, b = fmaxf(t_hi, tm);
+        float prod = st;
+#pragma unroll
+        for (int k = 0; k < K; ++k) prod *= sh[k];
+        t = (st > 0.f && prod > 0.f) ? st * expf((logp - logf(prod)) / (K + 1)) : 0.5f * (a + b);
+        t = fminf(fmaxf(t, a), b);
+#pragma unroll 1
+        for (int it = 0; it < 4; ++it) {
+            face_eval<K>(sh, st, logp, t, v, dv, d);
+            if (v <= 0.0f) a = t; else b = t;
+            float tn = t - v / dv;
+            if (!(tn > a && tn < b)) tn = 0.5f * (a + b);
+            t = tn;
+        }
+        face_eval<K>(sh, st, logp, t, v, dv, d);
+#pragma unroll 1
+        for (int it = 0; it < 40 && fabsf(v) > 2e-6f && (b - a) > 1e-7f * t; ++it) {
+            if (v <= 0.0f) a = t; else b = t;
+            float tn = t - v / dv;
+            if (!(tn > a && tn < b)) tn = 0.5f * (a + b);
+            t = tn;
+            face_eval<K>(sh, st, logp, t, v, dv, d);
+        }
+    } else {
+        // - branch for d_t: a sign change on [0.01, tm) is needed
+        if (!face_eval<K>(sh, st, logp, kClamp, v, dv, d) || v >= 0.0f) return false;
+        float a = kClamp, b = tm;
+#pragma unroll 1
+        for (int it = 0; it < 40; ++it) {
+            float mid = 0.5f * (a + b);
+            face_eval<K>(sh, st, logp, mid, v, dv, d);
+            if (v <= 0.0f) a = mid; else b = mid;
+            if (b - a <= 1e-7f * mid) break;
+        }
+        t = 0.5f * (a + b);
+        face_eval<K>(sh, st, logp, t, v, dv, d);
+    }
+    t_out = t;
+    return true;
+}
+
+static __device__ __forceinline__ void volume_targets(const float (&s)[3], float (&dd)[3]) {
+    float d[2], t;
+    {
+        const float sh[2] = {s[0], s[1]};
+        if (solve_face<2>(sh, s[2], 0.0f, fmaxf(1.0f, s[2] + 1.0f), d, t)) {
+            dd[0] = d[0]; dd[1] = d[1]; dd[2] = t;
+            return;
+        }
+    }
+    {
+        const float sh[2] = {s[0], 0.f};
+        const float logp = -logf(kClamp);
+        if (solve_face<1>(sh, s[1], logp, fmaxf(10.0f, s[1] + 10.0f), d, t)) {
+            dd[0] = d[0]; dd[1] = t; dd[2] = kClamp;
+            return;
+        }
+    }
+    dd[0] = 1.0f / (kClamp * kClamp);
+    dd[1] = kClamp;
+    dd[2] = kClamp;
+}
+
+// P = U diag(c) W^T
+static __device__ __forceinline__ void udwt(const float (&U)[3][3], const float (&c)[3], const float (&W)[3][3],
+                                     float (&P)[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            P[i][j] = U[i][0] * c[0] * W[j][0] + U[i][1] * c[1] * W[j][1] + U[i][2] * c[2] * W[j][2];
+}
+
+}  // namespace proj
+}  // namespace pdg

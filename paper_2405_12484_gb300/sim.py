@@ -158,6 +158,63 @@ class Mesh:
         return {lib().pd_phase_name(k).decode(): float(out[k]) for k in range(n.value)}
 
 
+class Adjoint:
+    """Workspace for equilibrium steps and backward adjoint steps on one mesh."""
+
+    def __init__(self, mesh: Mesh, cg_iters=30):
+        self.mesh = mesh
+        h = C.c_void_p()
+        _check(lib().pd_adjoint_create(mesh._h, int(cg_iters), C.byref(h)), "pd_adjoint_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pd_adjoint_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        _check(lib().pd_adjoint_reset(self._h), "pd_adjoint_reset")
+
+    def equilibrium_step(self, pin_targets=None, gravity=(0.0, 0.0, -9.81), n_pd_iter=10, n_newton=3, x_out=None):
+        m = self.mesh
+        pt = _dev_f32(pin_targets, (m.n_pinned, 3)) if pin_targets is not None else None
+        g = (C.c_float * 3)(*[float(a) for a in gravity])
+        _check(lib().pd_equilibrium_step(m._h, self._h, _ptr(pt), g, int(n_pd_iter), int(n_newton), _ptr(x_out)),
+               "pd_equilibrium_step")
+        m._keep["pins"] = pt
+        return x_out
+
+    def step(self, x_n, dL_dx, dL_dgs, dL_dgv):
+        """One backward step; dL_dgs / dL_dgv (n_t float32 device) are accumulated."""
+        m = self.mesh
+        xt = _dev_f32(x_n, (m.n_v, 3))
+        gt = _dev_f32(dL_dx, (m.n_v, 3))
+        _check(lib().pd_adjoint_step(m._h, self._h, _ptr(xt), _ptr(gt), _ptr(dL_dgs), _ptr(dL_dgv)),
+               "pd_adjoint_step")
+        m._keep["adj"] = (xt, gt)
+
+    def hessian_vec(self, x, v):
+        m = self.mesh
+        out = torch.empty((m.n_v, 3), device="cuda", dtype=torch.float32)
+        _check(lib().pd_hessian_vec(m._h, _ptr(_dev_f32(x, (m.n_v, 3))), _ptr(_dev_f32(v, (m.n_v, 3))), _ptr(out)),
+               "pd_hessian_vec")
+        return out
+
+    def residual(self, x, x_prev, v_prev, gravity=(0.0, 0.0, -9.81)):
+        m = self.mesh
+        out = torch.empty((m.n_v, 3), device="cuda", dtype=torch.float32)
+        g = (C.c_float * 3)(*[float(a) for a in gravity])
+        _check(lib().pd_residual(m._h, _ptr(_dev_f32(x, (m.n_v, 3))), _ptr(_dev_f32(x_prev, (m.n_v, 3))),
+                                 _ptr(_dev_f32(v_prev, (m.n_v, 3))), g, _ptr(out)), "pd_residual")
+        return out
+
+
 def project(F: torch.Tensor, with_sigma=True):
     """Rotation and volume targets of a batch of deformation gradients (n, 3, 3)."""
     F = F.to(device="cuda", dtype=torch.float32).contiguous()

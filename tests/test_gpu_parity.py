@@ -296,7 +296,8 @@ def test_shell_full_size_one_frame():
 
 
 @pytest.mark.parametrize("prec,refine,correction,tol", [("bf16", 0, True, 1e-5), ("tf32", 0, True, 1e-5),
-                                                         ("bf16", 1, False, 1e-5), ("fp32", 0, True, 1e-5)])
+                                                         ("bf16", 1, False, 1e-3), ("bf16", 2, False, 1e-4),
+                                                         ("fp32", 0, True, 1e-5)])
 def test_one_step_error_mixed_precision(slab_traj, prec, refine, correction, tol):
     """Mixed precision: BF16/TF32 matrices with FP64-residual refinement or the
     correction form, one-step error against the FP64 oracle."""
