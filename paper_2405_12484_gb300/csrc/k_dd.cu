@@ -100,6 +100,61 @@ __device__ __forceinline__ void block_rows_n(const T* __restrict__ A, int rows, 
     }
 }
 
+// Same product with RPG rows per lane group sharing every x value read from
+// shared memory (shared-memory bytes per matrix byte = VN / RPG).
+template <class T, int LPR, int NT, int RPG>
+__device__ __forceinline__ void block_rows_g(const T* __restrict__ A, int rows, int ld, int cols,
+                                             const float4* __restrict__ xs, float4* __restrict__ y,
+                                             const float4* __restrict__ add) {
+    constexpr int VN = VecN<T>::N;
+    constexpr int G = NT / LPR;
+    const int lane = threadIdx.x % LPR;
+    const int grp = threadIdx.x / LPR;
+    for (int base = 0; base < rows; base += RPG * G) {   // block-uniform trip count
+        const int r0 = base + RPG * grp;
+        const bool any = r0 < rows;
+        const T* a[RPG];
+#pragma unroll
+        for (int k = 0; k < RPG; ++k) a[k] = A + (int64_t)((r0 + k < rows) ? r0 + k : (any ? r0 : 0)) * ld;
+        const int ncol = any ? cols : 0;
+        float acc[RPG][3];
+#pragma unroll
+        for (int k = 0; k < RPG; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
+#pragma unroll 2
+        for (int c = lane * VN; c < ncol; c += LPR * VN) {
+            float v[RPG][VN];
+#pragma unroll
+            for (int k = 0; k < RPG; ++k) load_vec(a[k] + c, v[k]);
+#pragma unroll
+            for (int j = 0; j < VN; ++j) {
+                const float4 xv = xs[c + j];
+#pragma unroll
+                for (int k = 0; k < RPG; ++k) {
+                    acc[k][0] = fmaf(v[k][j], xv.x, acc[k][0]);
+                    acc[k][1] = fmaf(v[k][j], xv.y, acc[k][1]);
+                    acc[k][2] = fmaf(v[k][j], xv.z, acc[k][2]);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = LPR / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < RPG; ++k) {
+                acc[k][0] += __shfl_xor_sync(0xffffffffu, acc[k][0], off, LPR);
+                acc[k][1] += __shfl_xor_sync(0xffffffffu, acc[k][1], off, LPR);
+                acc[k][2] += __shfl_xor_sync(0xffffffffu, acc[k][2], off, LPR);
+            }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < RPG; ++k) {
+                if (r0 + k >= rows) break;
+                const float4 b = add ? add[r0 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                y[r0 + k] = make_float4(b.x + acc[k][0], b.y + acc[k][1], b.z + acc[k][2], 0.f);
+            }
+        }
+    }
+}
+
 template <class T, int LPR>
 __device__ __forceinline__ void block_rows(const T* __restrict__ A, int rows, int ld, int cols,
                                            const float4* __restrict__ xs, float4* __restrict__ y,
@@ -163,8 +218,8 @@ __global__ void __launch_bounds__(512) k_segments(const SegDesc* __restrict__ se
             }
             __syncthreads();
             const int r_local = (int)(lo - s0);
-            block_rows_n<T, 8, 512>(pool + sd.a_off + (int64_t)r_local * sd.ld, (int)(hi - lo), sd.ld, sd.cols, xs,
-                                    out + sd.y_off + r_local, add ? add + sd.add_off + r_local : nullptr);
+            block_rows_g<T, 8, 512, 4>(pool + sd.a_off + (int64_t)r_local * sd.ld, (int)(hi - lo), sd.ld, sd.cols,
+                                       xs, out + sd.y_off + r_local, add ? add + sd.add_off + r_local : nullptr);
         }
         ++si;
         if (s1 >= r_end) break;
@@ -213,8 +268,19 @@ __global__ void __launch_bounds__(256) k_coarse(const T* __restrict__ S, int n_B
 constexpr int kCoarseWarps = 16;
 
 template <class T>
+struct CoarseRows;
+template <>
+struct CoarseRows<float> {
+    static constexpr int R = 2;
+};
+template <>
+struct CoarseRows<__nv_bfloat16> {
+    static constexpr int R = 4;
+};
+
+template <class T>
 __global__ void __launch_bounds__(512, 1) k_coarse_bal(const T* __restrict__ S, int n_B, int ld, int cols, int nch,
-                                                         const float4* __restrict__ cB, float4* __restrict__ part) {
+                                                        const float4* __restrict__ cB, float4* __restrict__ part) {
     extern __shared__ float xsm[];
     float* x0 = xsm;
     float* x1 = xsm + cols;
@@ -227,25 +293,28 @@ __global__ void __launch_bounds__(512, 1) k_coarse_bal(const T* __restrict__ S, 
     }
     __syncthreads();
     constexpr int VN = VecN<T>::N;
+    constexpr int RU = CoarseRows<T>::R;   // rows per unit: x values reused RU times
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kCoarseWarps + (threadIdx.x >> 5);
     const int64_t W = (int64_t)gridDim.x * kCoarseWarps;
-    const int n_rp = (n_B + 1) / 2;
-    const int64_t U = (int64_t)n_rp * nch;
+    const int n_rg = (n_B + RU - 1) / RU;
+    const int64_t U = (int64_t)n_rg * nch;
     const int64_t u0 = U * gw / W, u1 = U * (gw + 1) / W;
     for (int64_t u = u0; u < u1; ++u) {
-        const int rp = (int)(u / nch), ch = (int)(u % nch);
-        const int r0 = 2 * rp;
-        const bool two = (r0 + 1) < n_B;
-        const T* a0 = S + (int64_t)r0 * ld;
-        const T* a1 = S + (int64_t)(two ? r0 + 1 : r0) * ld;
+        const int rg = (int)(u / nch), ch = (int)(u % nch);
+        const int r0 = RU * rg;
+        const T* a[RU];
+#pragma unroll
+        for (int k = 0; k < RU; ++k) a[k] = S + (int64_t)((r0 + k < n_B) ? r0 + k : r0) * ld;
         const int cb = ch * kCoarseChunk, ce = min(cols, cb + kCoarseChunk);
-        float s00 = 0.f, s01 = 0.f, s02 = 0.f, s10 = 0.f, s11 = 0.f, s12 = 0.f;
-#pragma unroll 8
+        float acc[RU][3];
+#pragma unroll
+        for (int k = 0; k < RU; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
+#pragma unroll 4
         for (int c = cb + lane * VN; c < ce; c += 32 * VN) {
-            float v0[VN], v1[VN];
-            load_vec(a0 + c, v0);
-            load_vec(a1 + c, v1);
+            float v[RU][VN];
+#pragma unroll
+            for (int k = 0; k < RU; ++k) load_vec(a[k] + c, v[k]);
 #pragma unroll
             for (int j = 0; j < VN; j += 4) {
                 const float4 p0 = *reinterpret_cast<const float4*>(x0 + c + j);
@@ -255,28 +324,27 @@ __global__ void __launch_bounds__(512, 1) k_coarse_bal(const T* __restrict__ S, 
                 const float q1[4] = {p1.x, p1.y, p1.z, p1.w};
                 const float q2[4] = {p2.x, p2.y, p2.z, p2.w};
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    s00 = fmaf(v0[j + k], q0[k], s00);
-                    s01 = fmaf(v0[j + k], q1[k], s01);
-                    s02 = fmaf(v0[j + k], q2[k], s02);
-                    s10 = fmaf(v1[j + k], q0[k], s10);
-                    s11 = fmaf(v1[j + k], q1[k], s11);
-                    s12 = fmaf(v1[j + k], q2[k], s12);
-                }
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int k = 0; k < RU; ++k) {
+                        acc[k][0] = fmaf(v[k][j + i], q0[i], acc[k][0]);
+                        acc[k][1] = fmaf(v[k][j + i], q1[i], acc[k][1]);
+                        acc[k][2] = fmaf(v[k][j + i], q2[i], acc[k][2]);
+                    }
             }
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            s00 += __shfl_xor_sync(0xffffffffu, s00, off);
-            s01 += __shfl_xor_sync(0xffffffffu, s01, off);
-            s02 += __shfl_xor_sync(0xffffffffu, s02, off);
-            s10 += __shfl_xor_sync(0xffffffffu, s10, off);
-            s11 += __shfl_xor_sync(0xffffffffu, s11, off);
-            s12 += __shfl_xor_sync(0xffffffffu, s12, off);
-        }
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < RU; ++k) {
+                acc[k][0] += __shfl_xor_sync(0xffffffffu, acc[k][0], off);
+                acc[k][1] += __shfl_xor_sync(0xffffffffu, acc[k][1], off);
+                acc[k][2] += __shfl_xor_sync(0xffffffffu, acc[k][2], off);
+            }
         if (lane == 0) {
-            part[(int64_t)ch * n_B + r0] = make_float4(s00, s01, s02, 0.f);
-            if (two) part[(int64_t)ch * n_B + r0 + 1] = make_float4(s10, s11, s12, 0.f);
+#pragma unroll
+            for (int k = 0; k < RU; ++k)
+                if (r0 + k < n_B) part[(int64_t)ch * n_B + r0 + k] = make_float4(acc[k][0], acc[k][1], acc[k][2], 0.f);
         }
     }
 }

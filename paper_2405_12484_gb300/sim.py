@@ -202,16 +202,16 @@ class Adjoint:
     def hessian_vec(self, x, v):
         m = self.mesh
         out = torch.empty((m.n_v, 3), device="cuda", dtype=torch.float32)
-        _check(lib().pd_hessian_vec(m._h, _ptr(_dev_f32(x, (m.n_v, 3))), _ptr(_dev_f32(v, (m.n_v, 3))), _ptr(out)),
-               "pd_hessian_vec")
+        xt, vt = _dev_f32(x, (m.n_v, 3)), _dev_f32(v, (m.n_v, 3))   # held until the call returns
+        _check(lib().pd_hessian_vec(m._h, _ptr(xt), _ptr(vt), _ptr(out)), "pd_hessian_vec")
         return out
 
     def residual(self, x, x_prev, v_prev, gravity=(0.0, 0.0, -9.81)):
         m = self.mesh
         out = torch.empty((m.n_v, 3), device="cuda", dtype=torch.float32)
         g = (C.c_float * 3)(*[float(a) for a in gravity])
-        _check(lib().pd_residual(m._h, _ptr(_dev_f32(x, (m.n_v, 3))), _ptr(_dev_f32(x_prev, (m.n_v, 3))),
-                                 _ptr(_dev_f32(v_prev, (m.n_v, 3))), g, _ptr(out)), "pd_residual")
+        xt, xpt, vpt = (_dev_f32(t, (m.n_v, 3)) for t in (x, x_prev, v_prev))   # held until the call returns
+        _check(lib().pd_residual(m._h, _ptr(xt), _ptr(xpt), _ptr(vpt), g, _ptr(out)), "pd_residual")
         return out
 
 
