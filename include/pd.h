@@ -269,6 +269,58 @@ pd_status pd_hessian_vec(pd_mesh* mesh, const float* x, const float* v, float* H
 pd_status pd_residual(pd_mesh* mesh, const float* x, const float* x_prev, const float* v_prev,
                       const float* gravity, float* g);
 
+/* ---- Serving: many garment simulations resident on one GPU ---- */
+
+typedef struct pd_server pd_server;   /* opaque */
+typedef int64_t pd_request_id;
+
+enum { PD_REQ_QUEUED = 0, PD_REQ_ACTIVE = 1, PD_REQ_DONE = 2, PD_REQ_FAILED = 3 };
+
+/* One simulation request.  Arrays are [host] and copied by pd_submit. */
+typedef struct pd_request {
+    const double* rest_xyz;  int32_t n_v;        /* as pd_create_mesh */
+    const int32_t* tets;     int32_t n_t;
+    const int32_t* tet_domain; int32_t n_domains;
+    const uint8_t* pinned;                      /* or NULL */
+    const float* gamma_s;    const float* gamma_v;   /* per tet, >= 0 (Sec. 6) */
+    double density, dt;
+    int32_t n_frames;                           /* frames to advance, >= 1 */
+    float gravity[3];
+    /* pinned targets at time t: rest + drive_amp * sin(2 pi drive_freq t) along drive_axis (0, 1, 2) */
+    float drive_amp, drive_freq;
+    int32_t drive_axis;
+} pd_request;
+
+/*
+ * pd_server_create -- a serving loop on one stream.  hbm_budget_bytes caps
+ * the device memory of resident requests (their steady footprint plus the
+ * transient FP64 prefactorisation of the one being admitted); max_slots caps
+ * how many are resident; n_iter is the PD iteration count of every frame.
+ */
+pd_status pd_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t n_iter, void* cuda_stream,
+                           pd_server** out);
+void pd_server_destroy(pd_server* server);
+
+/* Queue a request (host copy of its arrays); returns its id.  Admission happens in pd_server_tick. */
+pd_status pd_submit(pd_server* server, const pd_request* request, pd_request_id* id);
+
+/*
+ * pd_server_tick -- retire requests that finished, admit queued requests
+ * in arrival order while slots and the budget allow (mesh set-up and FP64
+ * prefactorisation on the device), then advance every resident request by
+ * one frame in shared batched launches (one captured CUDA graph per set of
+ * resident requests; the local steps, assemblies and subspace solves of all
+ * requests run in the same kernels).  Synchronous; *frame_ms receives the
+ * GPU time of that batched frame (every resident request's frame latency).
+ */
+pd_status pd_server_tick(pd_server* server, int32_t* n_active, float* frame_ms);
+
+pd_status pd_poll(pd_server* server, pd_request_id id, int32_t* state, int32_t* frames_done);
+/* Final positions (n_v x 3, [host]) and per-frame GPU latencies (n_frames floats, [host]) of a finished request. */
+pd_status pd_fetch(pd_server* server, pd_request_id id, float* x_out, float* frame_ms);
+pd_status pd_release(pd_server* server, pd_request_id id);
+pd_status pd_server_stats(pd_server* server, int32_t* n_queued, int32_t* n_active, int64_t* used_bytes);
+
 /*
  * pd_solve_noalloc -- the same solve as pd_solve (same kernels, same
  * result), for callers that must not allocate device memory during the

@@ -45,6 +45,17 @@ class pd_mesh_info(C.Structure):
                 ("phase_bytes", C.c_int64 * 16)]
 
 
+PD_REQ_QUEUED, PD_REQ_ACTIVE, PD_REQ_DONE, PD_REQ_FAILED = 0, 1, 2, 3
+
+
+class pd_request(C.Structure):
+    _fields_ = [("rest_xyz", C.c_void_p), ("n_v", C.c_int32), ("tets", C.c_void_p), ("n_t", C.c_int32),
+                ("tet_domain", C.c_void_p), ("n_domains", C.c_int32), ("pinned", C.c_void_p),
+                ("gamma_s", C.c_void_p), ("gamma_v", C.c_void_p), ("density", C.c_double), ("dt", C.c_double),
+                ("n_frames", C.c_int32), ("gravity", C.c_float * 3), ("drive_amp", C.c_float),
+                ("drive_freq", C.c_float), ("drive_axis", C.c_int32)]
+
+
 # (name, restype, argtypes) exactly as declared in include/pd.h
 SIGNATURES = [
     ("pd_create_mesh", C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_double,
@@ -74,6 +85,15 @@ SIGNATURES = [
     ("pd_adjoint_step", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pd_hessian_vec", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pd_residual", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_server_create", C.c_int32, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("pd_server_destroy", None, [C.c_void_p]),
+    ("pd_submit", C.c_int32, [C.c_void_p, C.POINTER(pd_request), C.POINTER(C.c_int64)]),
+    ("pd_server_tick", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    ("pd_poll", C.c_int32, [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    ("pd_fetch", C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    ("pd_release", C.c_int32, [C.c_void_p, C.c_int64]),
+    ("pd_server_stats", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int64)]),
 ]
 
 

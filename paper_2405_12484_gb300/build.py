@@ -14,7 +14,8 @@ LIB = os.path.join(HERE, "libpdgb300.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 # the local step is FP32 ALU work: approximate division/sqrt and fast log/exp
 # intrinsics (accuracy checked against the FP64 oracle by the parity tests)
-FILE_FLAGS = {"k_local.cu": ["--use_fast_math"], "k_adjoint.cu": ["--use_fast_math"]}
+FILE_FLAGS = {"k_local.cu": ["--use_fast_math"], "k_adjoint.cu": ["--use_fast_math"],
+              "k_batch.cu": ["--use_fast_math"]}
 
 
 def _nvcc() -> str:

@@ -226,6 +226,38 @@ __global__ void __launch_bounds__(512) k_segments(const SegDesc* __restrict__ se
     }
 }
 
+// Batched per-domain products of the serving loop: the segments of every
+// slot are concatenated; pointers come from the descriptors (FP32 storage).
+template <bool GATHER>
+__global__ void __launch_bounds__(512) k_segments_b(const SegDescB* __restrict__ segs, const int* __restrict__ cta_seg,
+                                                    int64_t total_rows) {
+    __shared__ float4 xs[kMaxSubCols];
+    const int64_t r_begin = total_rows * blockIdx.x / gridDim.x;
+    const int64_t r_end = total_rows * (blockIdx.x + 1) / gridDim.x;
+    int si = cta_seg[blockIdx.x];
+    while (true) {
+        const SegDescB sd = segs[si];
+        const int64_t s0 = sd.grow, s1 = sd.grow + sd.rows;
+        if (s0 >= r_end) break;
+        const int64_t lo = r_begin > s0 ? r_begin : s0;
+        const int64_t hi = r_end < s1 ? r_end : s1;
+        if (hi > lo) {
+            __syncthreads();
+            for (int k = threadIdx.x; k < sd.cols; k += blockDim.x) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k < sd.x_n) v = GATHER ? sd.xsrc[sd.bidx[k]] : sd.xsrc[k];
+                xs[k] = v;
+            }
+            __syncthreads();
+            const int r_local = (int)(lo - s0);
+            block_rows_g<float, 8, 512, 4>(sd.A + (int64_t)r_local * sd.ld, (int)(hi - lo), sd.ld, sd.cols, xs,
+                                           sd.out + r_local, sd.add ? sd.add + r_local : nullptr);
+        }
+        ++si;
+        if (s1 >= r_end) break;
+    }
+}
+
 // gather: c_B[j] = b_B[j] + sum over the domains touching j of their c_d entry (fixed order)
 __global__ void k_gather(int n_B, const int* __restrict__ ptr, const int* __restrict__ rows,
                          const float4* __restrict__ bB, const float4* __restrict__ tc, float4* __restrict__ cB) {
@@ -345,6 +377,81 @@ __global__ void __launch_bounds__(512, 1) k_coarse_bal(const T* __restrict__ S, 
 #pragma unroll
             for (int k = 0; k < RU; ++k)
                 if (r0 + k < n_B) part[(int64_t)ch * n_B + r0 + k] = make_float4(acc[k][0], acc[k][1], acc[k][2], 0.f);
+        }
+    }
+}
+
+// Batched coarse products: the (row pair, chunk) units of every slot's S^-1
+// are concatenated; block c takes units [U c / C, U (c+1) / C), stages each
+// overlapped slot's c_B in shared memory and splits that piece evenly over
+// its warps.  Each unit is computed exactly as in k_coarse_bal.
+__global__ void __launch_bounds__(512, 1) k_coarse_b(const CoarseDescB* __restrict__ cd, int n_desc, int64_t U,
+                                                      int max_cols) {
+    extern __shared__ float xsm[];
+    float* x0 = xsm;
+    float* x1 = xsm + max_cols;
+    float* x2 = xsm + 2 * max_cols;
+    constexpr int VN = 4;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t b0 = U * blockIdx.x / gridDim.x, b1 = U * (blockIdx.x + 1) / gridDim.x;
+    for (int di = 0; di < n_desc; ++di) {
+        const CoarseDescB D = cd[di];
+        const int64_t nu = (int64_t)((D.n_B + 1) / 2) * D.nch;
+        const int64_t lo = b0 > D.u0 ? b0 : D.u0;
+        const int64_t hi = b1 < D.u0 + nu ? b1 : D.u0 + nu;
+        if (hi <= lo) continue;
+        __syncthreads();
+        for (int k = threadIdx.x; k < D.ld; k += blockDim.x) {
+            float4 v = (k < D.n_B) ? D.cB[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            x0[k] = v.x;
+            x1[k] = v.y;
+            x2[k] = v.z;
+        }
+        __syncthreads();
+        const int64_t n = hi - lo;
+        const int64_t w0 = lo + n * warp / kCoarseWarps, w1 = lo + n * (warp + 1) / kCoarseWarps;
+        for (int64_t u = w0; u < w1; ++u) {
+            const int64_t ul = u - D.u0;
+            const int rp = (int)(ul / D.nch), ch = (int)(ul % D.nch);
+            const int r0 = 2 * rp;
+            const bool two = (r0 + 1) < D.n_B;
+            const float* a0 = D.S + (int64_t)r0 * D.ld;
+            const float* a1 = D.S + (int64_t)(two ? r0 + 1 : r0) * D.ld;
+            const int cb = ch * kCoarseChunk, ce = min(D.ld, cb + kCoarseChunk);
+            float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll 4
+            for (int c = cb + lane * VN; c < ce; c += 32 * VN) {
+                float v[2][VN];
+                load_vec(a0 + c, v[0]);
+                load_vec(a1 + c, v[1]);
+                const float4 p0 = *reinterpret_cast<const float4*>(x0 + c);
+                const float4 p1 = *reinterpret_cast<const float4*>(x1 + c);
+                const float4 p2 = *reinterpret_cast<const float4*>(x2 + c);
+                const float q0[4] = {p0.x, p0.y, p0.z, p0.w};
+                const float q1[4] = {p1.x, p1.y, p1.z, p1.w};
+                const float q2[4] = {p2.x, p2.y, p2.z, p2.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        acc[k][0] = fmaf(v[k][i], q0[i], acc[k][0]);
+                        acc[k][1] = fmaf(v[k][i], q1[i], acc[k][1]);
+                        acc[k][2] = fmaf(v[k][i], q2[i], acc[k][2]);
+                    }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    acc[k][0] += __shfl_xor_sync(0xffffffffu, acc[k][0], off);
+                    acc[k][1] += __shfl_xor_sync(0xffffffffu, acc[k][1], off);
+                    acc[k][2] += __shfl_xor_sync(0xffffffffu, acc[k][2], off);
+                }
+            if (lane == 0) {
+                D.part[(int64_t)ch * D.n_B + r0] = make_float4(acc[0][0], acc[0][1], acc[0][2], 0.f);
+                if (two) D.part[(int64_t)ch * D.n_B + r0 + 1] = make_float4(acc[1][0], acc[1][1], acc[1][2], 0.f);
+            }
         }
     }
 }
@@ -475,6 +582,31 @@ void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* 
         dd_solve_scratch_t<__nv_bfloat16>(m, m->d_mat16.p, b, xout, tc, cB, part, s);
     else
         dd_solve_scratch_t<float>(m, m->d_mat32.p, b, xout, tc, cB, part, s);
+}
+
+void launch_segments_b(bool gather, const SegDescB* segs, const int* cta_seg, int64_t total_rows, int blocks,
+                       cudaStream_t s) {
+    if (blocks <= 0) return;
+    if (gather) k_segments_b<true><<<blocks, 512, 0, s>>>(segs, cta_seg, total_rows);
+    else k_segments_b<false><<<blocks, 512, 0, s>>>(segs, cta_seg, total_rows);
+    PDG_CHECK_LAUNCH();
+}
+
+// Returns false when the largest interface vector does not fit in shared memory.
+bool configure_coarse_b(int max_cols) {
+    int dev = 0, optin = 0;
+    PDG_CUDA(cudaGetDevice(&dev));
+    PDG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t smem = sizeof(float) * 3 * (size_t)max_cols;
+    if (smem > (size_t)optin) return false;
+    PDG_CUDA(cudaFuncSetAttribute(k_coarse_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return true;
+}
+
+void launch_coarse_b(const CoarseDescB* cd, int n_desc, int64_t U, int max_cols, int blocks, cudaStream_t s) {
+    if (blocks <= 0 || U <= 0) return;
+    k_coarse_b<<<blocks, 32 * kCoarseWarps, sizeof(float) * 3 * (size_t)max_cols, s>>>(cd, n_desc, U, max_cols);
+    PDG_CHECK_LAUNCH();
 }
 
 int dd_max_sub_cols() { return kMaxSubCols; }

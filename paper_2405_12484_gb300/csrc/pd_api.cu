@@ -774,6 +774,8 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         };
         plan(sc, rc, m->d_segs_cond, m->d_cta_cond, m->seg_blocks_cond);
         plan(sb, rb, m->d_segs_back, m->d_cta_back, m->seg_blocks_back);
+        m->h_segs_cond = sc;
+        m->h_segs_back = sb;
         m->seg_rows_cond = rc;
         m->seg_rows_back = rb;
     }

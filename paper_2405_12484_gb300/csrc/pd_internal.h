@@ -82,6 +82,45 @@ struct SegDesc {
     int32_t pad;
 };
 
+// One resident request of the serving loop, as the batched kernels see it.
+struct BatchSlot {
+    const int4* tets;
+    const float4* geo;
+    float4 *x, *xprev, *v, *force, *by0, *b, *pin_tgt;
+    const float4* pin_rest;
+    const float* mh2;
+    const int *inc_ptr, *inc, *kfp_ptr, *kfp_col;
+    const float* kfp_val;
+    float4 *tc, *cB, *part;
+    const int *gat_ptr, *gat;
+    int* err;
+    int* frame;          // frames completed (device counter)
+    int n_t, n_v, n_free, n_pin, n_int, n_B, nch;
+    float h, gx, gy, gz;
+    float drive_amp, drive_w;
+    int drive_axis;
+};
+
+// A per-domain matrix of one slot in the batched per-domain kernels.
+struct SegDescB {
+    const float* A;        // first row
+    const float4* xsrc;    // vector source (contiguous, or gathered through bidx)
+    const int* bidx;
+    const float4* add;
+    float4* out;
+    int64_t grow;          // first row in the concatenated row list
+    int32_t rows, ld, cols, x_n;
+};
+
+// The interface matrix S^-1 of one slot in the batched coarse kernel.
+struct CoarseDescB {
+    const float* S;
+    const float4* cB;
+    float4* part;
+    int64_t u0;            // first unit of this slot in the concatenated unit list
+    int32_t n_B, ld, nch, pad;
+};
+
 enum Phase : int {
     PH_INERTIA = 0, PH_LOCAL, PH_ASSEMBLE, PH_CONDENSE, PH_GATHER, PH_COARSE, PH_REDUCE,
     PH_BACKSUB, PH_RESIDUAL, PH_VELOCITY, PH_COUNT
@@ -143,6 +182,7 @@ struct pd_mesh {
     pdg::DBuf<int32_t> d_cta_cond, d_cta_back;          // first segment of each block
     int64_t seg_rows_cond = 0, seg_rows_back = 0;
     int32_t seg_blocks_cond = 0, seg_blocks_back = 0;
+    std::vector<pdg::SegDesc> h_segs_cond, h_segs_back;   // host copies (serving batches)
     pdg::DBuf<float4> d_tc;                 // stacked [t_d; c_d] rows of every domain
     int32_t n_tc = 0;
     pdg::DBuf<int32_t> d_bidx;              // concatenated per-domain boundary index lists

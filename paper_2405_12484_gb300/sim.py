@@ -215,6 +215,72 @@ class Adjoint:
         return out
 
 
+class Server:
+    """Serving loop: resident garment simulations advanced in shared batched launches."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=64, n_iter=20, stream: torch.cuda.Stream | None = None):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib().pd_server_create(int(hbm_budget_bytes), int(max_slots), int(n_iter),
+                                      C.c_void_p(self.stream.cuda_stream), C.byref(h)), "pd_server_create")
+        self._h = h
+        self._nv = {}
+        self._nf = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pd_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, w, n_frames, drive=None):
+        """Queue a Workload-like object (rest, tets, tet_domain, n_domains, pinned, gamma_s, gamma_v,
+        density, dt, gravity); drive = (amp, freq, axis) of the pinned vertices or None."""
+        rest = np.ascontiguousarray(w.rest, np.float64)
+        tets = np.ascontiguousarray(w.tets, np.int32)
+        dom = np.ascontiguousarray(w.tet_domain, np.int32)
+        pin = np.ascontiguousarray(w.pinned, np.uint8)
+        gs = np.ascontiguousarray(w.gamma_s, np.float32)
+        gv = np.ascontiguousarray(w.gamma_v, np.float32)
+        amp, freq, axis = drive if drive is not None else (0.0, 0.0, 0)
+        q = _lib.pd_request(rest.ctypes.data, rest.shape[0], tets.ctypes.data, tets.shape[0], dom.ctypes.data,
+                            int(w.n_domains), pin.ctypes.data, gs.ctypes.data, gv.ctypes.data, float(w.density),
+                            float(w.dt), int(n_frames), (C.c_float * 3)(*w.gravity), float(amp), float(freq),
+                            int(axis))
+        rid = C.c_int64()
+        _check(lib().pd_submit(self._h, C.byref(q), C.byref(rid)), "pd_submit")
+        self._nv[rid.value] = rest.shape[0]
+        self._nf[rid.value] = int(n_frames)
+        return rid.value
+
+    def tick(self):
+        n = C.c_int32()
+        ms = C.c_float()
+        _check(lib().pd_server_tick(self._h, C.byref(n), C.byref(ms)), "pd_server_tick")
+        return n.value, ms.value
+
+    def poll(self, rid):
+        st, fd = C.c_int32(), C.c_int32()
+        _check(lib().pd_poll(self._h, int(rid), C.byref(st), C.byref(fd)), "pd_poll")
+        return st.value, fd.value
+
+    def fetch(self, rid):
+        x = np.empty((self._nv[rid], 3), np.float32)
+        ms = np.empty(self._nf[rid], np.float32)
+        _check(lib().pd_fetch(self._h, int(rid), x.ctypes.data, ms.ctypes.data), "pd_fetch")
+        return x, ms
+
+    def stats(self):
+        q, a, u = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(lib().pd_server_stats(self._h, C.byref(q), C.byref(a), C.byref(u)), "pd_server_stats")
+        return {"queued": q.value, "active": a.value, "used_bytes": u.value}
+
+
 def project(F: torch.Tensor, with_sigma=True):
     """Rotation and volume targets of a batch of deformation gradients (n, 3, 3)."""
     F = F.to(device="cuda", dtype=torch.float32).contiguous()

@@ -1,0 +1,94 @@
+"""Serving loop: resident requests advanced in shared batched launches.
+
+Each request's result must be the same alone and in a mix (bitwise: its
+values are computed with the same arithmetic in every batch), match the
+single-mesh stepper, and requests beyond the HBM budget must wait in the
+queue and still complete.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from workloads.meshes import slab_workload, sweater_shell  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _requests():
+    a = slab_workload(8, 8, 2, 0.01, 6, (2, 2), seed=21, n_iter=20, name="r-slab8")
+    b = sweater_shell(seed=22, n_theta=40, n_z=12, n_r=2, dom_theta=4, dom_z=2)
+    c = slab_workload(12, 6, 2, 0.01, 5, (3, 1), seed=23, n_iter=20, name="r-slab12")
+    d = sweater_shell(seed=24, n_theta=26, n_z=8, n_r=2, dom_theta=2, dom_z=2)
+    return [(a, None), (b, (0.2, 1.0, 0)), (c, None), (d, (0.2, 1.0, 0))]
+
+
+def _run(reqs, frames, budget=1 << 34, stagger=True):
+    from paper_2405_12484_gb300.sim import Server
+    S = Server(budget, max_slots=16, n_iter=20)
+    ids = []
+    pending = list(reqs)
+    ticks = 0
+    max_active = 0
+    saw_queue = False
+    while pending or any(S.poll(i)[0] in (0, 1) for i in ids):
+        if pending and (not stagger or ticks % 3 == 0):
+            w, drive = pending.pop(0)
+            ids.append(S.submit(w, frames, drive))
+        n, _ = S.tick()
+        st = S.stats()
+        saw_queue |= st["queued"] > 0 and st["active"] > 0
+        max_active = max(max_active, n)
+        ticks += 1
+        assert ticks < 10000
+    out = [S.fetch(i)[0] for i in ids]
+    S.close()
+    return out, max_active, saw_queue
+
+
+def test_results_are_identical_alone_and_in_the_mix():
+    reqs = _requests()
+    frames = 6
+    mix, max_active, _ = _run(reqs, frames)
+    assert max_active >= 3
+    for k, r in enumerate(reqs):
+        alone, _, _ = _run([r], frames)
+        assert np.array_equal(alone[0], mix[k]), k
+
+
+def test_serving_matches_the_single_mesh_stepper():
+    from paper_2405_12484_gb300.sim import Mesh
+    reqs = _requests()
+    frames = 5
+    mix, _, _ = _run(reqs, frames)
+    for k, (w, drive) in enumerate(reqs):
+        m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density)
+        m.set_materials(w.gamma_s, w.gamma_v)
+        m.prefactor(w.dt)
+        x = torch.empty((w.n_v, 3), device="cuda")
+        for n in range(frames):
+            pins = w.pin_targets(n) if drive is not None else None
+            m.step(None if pins is None else torch.as_tensor(pins, dtype=torch.float32), w.gravity, 20, x_out=x)
+        m.sync()
+        ref = x.cpu().numpy().astype(np.float64)
+        e = np.linalg.norm(mix[k] - ref) / np.linalg.norm(ref)
+        assert e < 1e-5, (k, e)
+        m.close()
+
+
+def test_admission_waits_for_the_hbm_budget():
+    reqs = _requests()
+    # a budget that holds roughly one request at a time
+    mix_ok, max_active, saw_queue = _run(reqs, 4, budget=60 << 20, stagger=False)
+    assert saw_queue
+    assert max_active < len(reqs)
+    alone = [_run([r], 4)[0][0] for r in reqs]
+    for k in range(len(reqs)):
+        assert np.array_equal(alone[k], mix_ok[k])
