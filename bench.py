@@ -75,6 +75,12 @@ def barrier(world):
         dist.barrier()
 
 
+def whole_job_rate(units_per_rank: int, local_ms: float, world: int) -> tuple:
+    """(value, max_ms): units of all ranks / slowest rank's time (replicas: weak scaling)."""
+    t = max_over_ranks(local_ms, world)
+    return world * units_per_rank / (t / 1e3), t
+
+
 def max_over_ranks(x: float, world: int) -> float:
     if world <= 1:
         return x
@@ -278,9 +284,8 @@ def main():
     frame_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
     total_ms = ev[0].elapsed_time(ev[K])
     phase = m.phase_times()   # the dominant kernel, timed on its own stream inside the captured frames
-    total_ms = max_over_ranks(total_ms, world)
+    value, total_ms = whole_job_rate(K * n_iter, total_ms, world)
     ms_frame = total_ms / K
-    value = world * K * n_iter / (total_ms / 1e3)
 
     peak, peak_kind = measured_peaks()
     dom_ms = phase.get(dominant, 0.0)
@@ -321,8 +326,7 @@ def main():
         out_h[k].copy_(x_out, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-    e2e_value = world * K * n_iter / (e2e_ms / 1e3)
+    e2e_value, e2e_ms = whole_job_rate(K * n_iter, e0.elapsed_time(e1), world)
     m.sync()
 
     cpu = None
