@@ -42,6 +42,10 @@ def parse():
     p.add_argument("--small", action="store_true", help="small shell (profiling captures)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--phase-report", action="store_true", help="also time every phase after the timed region")
+    p.add_argument("--serving", action="store_true",
+                   help="also run the serving stream (64 Poisson requests, 5K-200K tets, 60 frames each)")
+    p.add_argument("--serving-requests", type=int, default=64)
+    p.add_argument("--serving-budget-gib", type=float, default=16.0)
     return p.parse_args()
 
 
@@ -183,6 +187,77 @@ print(json.dumps({{"seconds": dt, "iters": {n_iter_sample}}}))
         return None, r.stderr[-500:]
     d = json.loads(r.stdout.strip().splitlines()[-1])
     return d, None
+
+
+def run_serving(args):
+    """Serving stream: Poisson arrivals of garment requests of mixed sizes, continuous batching.
+
+    Returns a dict with p50/p99 frame latency, aggregate tets*iters/s and the
+    same requests run one at a time on the plain FP32 stepper."""
+    import numpy as np
+    import torch
+
+    from paper_2405_12484_gb300.sim import Mesh, Server
+    from workloads.meshes import request_workload, serving_requests
+    reqs = serving_requests(n_req=args.serving_requests)
+    frames = 60
+    works = []
+    for arrival, gen, size, seed in reqs:
+        w = request_workload(gen, size, seed, n_iter=20)
+        drive = (0.2, 1.0, 0) if gen == "shell" else None
+        works.append((arrival, w, drive))
+    budget = int(args.serving_budget_gib * (1 << 30))
+    S = Server(budget, max_slots=64, n_iter=20)
+    t0 = time.perf_counter()
+    subs, pending = [], list(works)        # subs: (request id, n_tets, arrival)
+    frame_ms, active_hist = [], []
+
+    def unfinished():
+        return any(S.poll(i)[0] in (0, 1) for i, _, _ in subs)
+
+    while pending or unfinished():
+        now = time.perf_counter() - t0
+        while pending and pending[0][0] <= now:
+            a, w, d = pending.pop(0)
+            subs.append((S.submit(w, frames, d), w.n_t, a))
+        n, ms = S.tick()
+        if n > 0:
+            frame_ms.append(ms)
+            active_hist.append(n)
+        elif pending:
+            time.sleep(min(0.002, max(0.0, pending[0][0] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    tet_iters = sum(nt for _, nt, _ in subs) * frames * 20
+    lat = sorted(frame_ms)
+    S.close()
+    # one at a time, plain single-mesh stepper
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    gpu_ms = 0.0
+    for _, w, d in works:
+        m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density)
+        m.set_materials(w.gamma_s, w.gamma_v)
+        m.prefactor(w.dt)
+        pins = [torch.as_tensor(w.pin_targets(n), dtype=torch.float32, device="cuda") for n in range(frames)] \
+            if d is not None else [None] * frames
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for n in range(frames):
+            m.step(pins[n], w.gravity, 20)
+        e1.record()
+        e1.synchronize()
+        gpu_ms += e0.elapsed_time(e1)
+        m.close()
+    wall_seq = time.perf_counter() - t1
+    return {"requests": len(works), "frames_per_request": frames, "pd_iters_per_frame": 20,
+            "hbm_budget_gib": args.serving_budget_gib,
+            "frame_ms_p50": lat[len(lat) // 2], "frame_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "mean_resident": float(np.mean(active_hist)), "max_resident": int(max(active_hist)),
+            "wall_s": wall, "tet_iters_per_s_wall": tet_iters / wall,
+            "tet_iters_per_s_gpu": tet_iters / (sum(frame_ms) / 1e3),
+            "one_at_a_time": {"wall_s": wall_seq, "gpu_frame_s": gpu_ms / 1e3,
+                              "tet_iters_per_s_gpu": tet_iters / (gpu_ms / 1e3),
+                              "tet_iters_per_s_wall": tet_iters / wall_seq}}
 
 
 def run_reference(args, rank, world):
@@ -365,6 +440,8 @@ def main():
         }
         if phases:
             line["phases"] = phases
+        if args.serving:
+            line["serving"] = run_serving(args)
         print(json.dumps(line))
     m.close()
     if world > 1:

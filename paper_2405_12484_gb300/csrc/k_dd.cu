@@ -120,7 +120,7 @@ __device__ __forceinline__ void block_rows_g(const T* __restrict__ A, int rows, 
         float acc[RPG][3];
 #pragma unroll
         for (int k = 0; k < RPG; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
-#pragma unroll 2
+#pragma unroll 4
         for (int c = lane * VN; c < ncol; c += LPR * VN) {
             float v[RPG][VN];
 #pragma unroll
@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(512) k_segments(const SegDesc* __restrict__ se
             }
             __syncthreads();
             const int r_local = (int)(lo - s0);
-            block_rows_g<T, 8, 512, 4>(pool + sd.a_off + (int64_t)r_local * sd.ld, (int)(hi - lo), sd.ld, sd.cols,
-                                       xs, out + sd.y_off + r_local, add ? add + sd.add_off + r_local : nullptr);
+            block_rows_g<T, 32, 512, 4>(pool + sd.a_off + (int64_t)r_local * sd.ld, (int)(hi - lo), sd.ld, sd.cols,
+                                        xs, out + sd.y_off + r_local, add ? add + sd.add_off + r_local : nullptr);
         }
         ++si;
         if (s1 >= r_end) break;
@@ -250,8 +250,8 @@ __global__ void __launch_bounds__(512) k_segments_b(const SegDescB* __restrict__
             }
             __syncthreads();
             const int r_local = (int)(lo - s0);
-            block_rows_g<float, 8, 512, 4>(sd.A + (int64_t)r_local * sd.ld, (int)(hi - lo), sd.ld, sd.cols, xs,
-                                           sd.out + r_local, sd.add ? sd.add + r_local : nullptr);
+            block_rows_g<float, 32, 512, 4>(sd.A + (int64_t)r_local * sd.ld, (int)(hi - lo), sd.ld, sd.cols, xs,
+                                            sd.out + r_local, sd.add ? sd.add + r_local : nullptr);
         }
         ++si;
         if (s1 >= r_end) break;
