@@ -319,7 +319,10 @@ pd_status pd_poll(pd_server* server, pd_request_id id, int32_t* state, int32_t* 
 /* Final positions (n_v x 3, [host]) and per-frame GPU latencies (n_frames floats, [host]) of a finished request. */
 pd_status pd_fetch(pd_server* server, pd_request_id id, float* x_out, float* frame_ms);
 pd_status pd_release(pd_server* server, pd_request_id id);
-pd_status pd_server_stats(pd_server* server, int32_t* n_queued, int32_t* n_active, int64_t* used_bytes);
+/* Queue length, resident requests, their estimated device bytes, and the largest admission-time
+ * estimate (resident + new request + its prefactorisation workspace) seen so far. */
+pd_status pd_server_stats(pd_server* server, int32_t* n_queued, int32_t* n_active, int64_t* used_bytes,
+                          int64_t* peak_bytes);
 
 /*
  * pd_solve_noalloc -- the same solve as pd_solve (same kernels, same

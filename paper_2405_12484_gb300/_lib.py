@@ -93,7 +93,7 @@ SIGNATURES = [
     ("pd_fetch", C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("pd_release", C.c_int32, [C.c_void_p, C.c_int64]),
     ("pd_server_stats", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
-                                    C.POINTER(C.c_int64)]),
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
 ]
 
 

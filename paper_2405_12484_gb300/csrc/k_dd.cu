@@ -12,6 +12,8 @@
 // share the scalar matrix, K = K_s (x) I_3): HBM-bound streaming of the
 // matrices with 16-byte loads, FP32 accumulation, vectors staged in shared
 // memory, fixed-order warp reductions (deterministic), no atomics.
+#include <algorithm>
+
 #include "pd_internal.h"
 
 namespace pdg {
@@ -102,59 +104,6 @@ __device__ __forceinline__ void block_rows_n(const T* __restrict__ A, int rows, 
 
 // Same product with RPG rows per lane group sharing every x value read from
 // shared memory (shared-memory bytes per matrix byte = VN / RPG).
-template <class T, int LPR, int NT, int RPG>
-__device__ __forceinline__ void block_rows_g(const T* __restrict__ A, int rows, int ld, int cols,
-                                             const float4* __restrict__ xs, float4* __restrict__ y,
-                                             const float4* __restrict__ add) {
-    constexpr int VN = VecN<T>::N;
-    constexpr int G = NT / LPR;
-    const int lane = threadIdx.x % LPR;
-    const int grp = threadIdx.x / LPR;
-    for (int base = 0; base < rows; base += RPG * G) {   // block-uniform trip count
-        const int r0 = base + RPG * grp;
-        const bool any = r0 < rows;
-        const T* a[RPG];
-#pragma unroll
-        for (int k = 0; k < RPG; ++k) a[k] = A + (int64_t)((r0 + k < rows) ? r0 + k : (any ? r0 : 0)) * ld;
-        const int ncol = any ? cols : 0;
-        float acc[RPG][3];
-#pragma unroll
-        for (int k = 0; k < RPG; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
-#pragma unroll 4
-        for (int c = lane * VN; c < ncol; c += LPR * VN) {
-            float v[RPG][VN];
-#pragma unroll
-            for (int k = 0; k < RPG; ++k) load_vec(a[k] + c, v[k]);
-#pragma unroll
-            for (int j = 0; j < VN; ++j) {
-                const float4 xv = xs[c + j];
-#pragma unroll
-                for (int k = 0; k < RPG; ++k) {
-                    acc[k][0] = fmaf(v[k][j], xv.x, acc[k][0]);
-                    acc[k][1] = fmaf(v[k][j], xv.y, acc[k][1]);
-                    acc[k][2] = fmaf(v[k][j], xv.z, acc[k][2]);
-                }
-            }
-        }
-#pragma unroll
-        for (int off = LPR / 2; off > 0; off >>= 1)
-#pragma unroll
-            for (int k = 0; k < RPG; ++k) {
-                acc[k][0] += __shfl_xor_sync(0xffffffffu, acc[k][0], off, LPR);
-                acc[k][1] += __shfl_xor_sync(0xffffffffu, acc[k][1], off, LPR);
-                acc[k][2] += __shfl_xor_sync(0xffffffffu, acc[k][2], off, LPR);
-            }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < RPG; ++k) {
-                if (r0 + k >= rows) break;
-                const float4 b = add ? add[r0 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                y[r0 + k] = make_float4(b.x + acc[k][0], b.y + acc[k][1], b.z + acc[k][2], 0.f);
-            }
-        }
-    }
-}
-
 template <class T, int LPR>
 __device__ __forceinline__ void block_rows(const T* __restrict__ A, int rows, int ld, int cols,
                                            const float4* __restrict__ xs, float4* __restrict__ y,
@@ -164,97 +113,77 @@ __device__ __forceinline__ void block_rows(const T* __restrict__ A, int rows, in
 
 constexpr int kMaxSubCols = 2048;   // largest per-domain internal / boundary count handled in shared memory
 
-// condense: one task = a row block of G_d = [K_ii^-1; Psi_d^T]; x = b_i (contiguous)
-template <class T>
-__global__ void __launch_bounds__(256) k_condense(const GemvTask* __restrict__ tasks, const T* __restrict__ pool,
-                                                  const float4* __restrict__ b, float4* __restrict__ tc) {
-    __shared__ float4 xs[kMaxSubCols];
-    const GemvTask tk = tasks[blockIdx.x];
-    for (int k = threadIdx.x; k < tk.cols; k += blockDim.x)
-        xs[k] = (k < tk.x_n) ? b[tk.x_off + k] : make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-    block_rows<T, 8>(pool + tk.a_off, tk.rows, tk.ld, tk.cols, xs, tc + tk.y_off, nullptr);
-}
+// Column-oriented per-domain products ("axpy form"): y = add + sum_k A[k, :] x_k
+// with A stored so that each output is a column (rows k of A are contiguous).
+// One block = one output chunk of one domain matrix: each lane owns VN
+// consecutive outputs, the 4 warps split k into equal ranges, x_k is a
+// shared-memory broadcast, and the warps' partial sums are combined in a
+// fixed order (deterministic).  No cross-lane reductions, fully coalesced
+// 16-byte row loads.
+constexpr int kAxWarps = 4;
 
-// backsub: one task = a row block of Psi_d; x = x_B gathered through the domain's boundary list
-template <class T>
-__global__ void __launch_bounds__(256) k_backsub(const GemvTask* __restrict__ tasks, const T* __restrict__ pool,
-                                                 const int* __restrict__ bidx, const float4* __restrict__ xB,
-                                                 const float4* __restrict__ tc, float4* __restrict__ xout) {
-    __shared__ float4 xs[kMaxSubCols];
-    const GemvTask tk = tasks[blockIdx.x];
-    for (int k = threadIdx.x; k < tk.cols; k += blockDim.x)
-        xs[k] = (k < tk.x_n) ? xB[bidx[tk.x_off + k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+template <class T, bool BATCHED>
+__global__ void __launch_bounds__(32 * kAxWarps) k_axpy_form(const AxDesc* __restrict__ descs,
+                                                              const AxBlock* __restrict__ blocks, AxBases single,
+                                                              const AxBases* __restrict__ multi) {
+    constexpr int VN = VecN<T>::N;
+    constexpr int OW = 32 * VN;
+    extern __shared__ float4 xs[];   // K_max entries (dynamic)
+    __shared__ float red[kAxWarps - 1][OW][3];
+    const AxBlock bk = blocks[blockIdx.x];
+    const AxDesc D = descs[bk.desc];
+    const AxBases B = BATCHED ? multi[D.slot] : single;
+    const T* A = reinterpret_cast<const T*>(B.pool) + D.a_off;
+    const float4* x = B.x + D.x_off;
+    for (int k = threadIdx.x; k < D.K; k += blockDim.x) xs[k] = (D.bidx_off >= 0) ? x[B.bidx[D.bidx_off + k]] : x[k];
     __syncthreads();
-    block_rows<T, 8>(pool + tk.a_off, tk.rows, tk.ld, tk.cols, xs, xout + tk.y_off, tc + tk.add_off);
-}
-
-// Balanced per-domain products.  The rows of every domain's matrix are
-// concatenated into one list; block c takes rows [R c / C, R (c+1) / C) and
-// walks the (at most a few) domains its slice overlaps: it stages that
-// domain's vector in shared memory (contiguous b_i, or x_B gathered through
-// the boundary list) and streams its share of the rows.
-template <class T, bool GATHER>
-__global__ void __launch_bounds__(512) k_segments(const SegDesc* __restrict__ segs, const int* __restrict__ cta_seg,
-                                                  int64_t total_rows, const T* __restrict__ pool,
-                                                  const float4* __restrict__ xsrc, const int* __restrict__ bidx,
-                                                  const float4* __restrict__ add, float4* __restrict__ out) {
-    __shared__ float4 xs[kMaxSubCols];
-    const int64_t r_begin = total_rows * blockIdx.x / gridDim.x;
-    const int64_t r_end = total_rows * (blockIdx.x + 1) / gridDim.x;
-    int si = cta_seg[blockIdx.x];
-    while (true) {
-        const SegDesc sd = segs[si];
-        const int64_t s0 = sd.grow, s1 = sd.grow + sd.rows;
-        if (s0 >= r_end) break;
-        const int64_t lo = r_begin > s0 ? r_begin : s0;
-        const int64_t hi = r_end < s1 ? r_end : s1;
-        if (hi > lo) {
-            __syncthreads();   // previous segment's readers are done with xs
-            for (int k = threadIdx.x; k < sd.cols; k += blockDim.x) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (k < sd.x_n) v = GATHER ? xsrc[bidx[sd.x_off + k]] : xsrc[sd.x_off + k];
-                xs[k] = v;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int o = bk.o0 + lane * VN;              // first output of this lane
+    const int k0 = D.K * warp / kAxWarps, k1 = D.K * (warp + 1) / kAxWarps;
+    float acc[VN][3];
+#pragma unroll
+    for (int i = 0; i < VN; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+    if (o < D.n_out) {
+        const T* a = A + o;
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+            float v[VN];
+            load_vec(a + (int64_t)k * D.ld, v);
+            const float4 xk = xs[k];
+#pragma unroll
+            for (int i = 0; i < VN; ++i) {
+                acc[i][0] = fmaf(v[i], xk.x, acc[i][0]);
+                acc[i][1] = fmaf(v[i], xk.y, acc[i][1]);
+                acc[i][2] = fmaf(v[i], xk.z, acc[i][2]);
             }
-            __syncthreads();
-            const int r_local = (int)(lo - s0);
-            block_rows_g<T, 32, 512, 4>(pool + sd.a_off + (int64_t)r_local * sd.ld, (int)(hi - lo), sd.ld, sd.cols,
-                                        xs, out + sd.y_off + r_local, add ? add + sd.add_off + r_local : nullptr);
         }
-        ++si;
-        if (s1 >= r_end) break;
     }
-}
-
-// Batched per-domain products of the serving loop: the segments of every
-// slot are concatenated; pointers come from the descriptors (FP32 storage).
-template <bool GATHER>
-__global__ void __launch_bounds__(512) k_segments_b(const SegDescB* __restrict__ segs, const int* __restrict__ cta_seg,
-                                                    int64_t total_rows) {
-    __shared__ float4 xs[kMaxSubCols];
-    const int64_t r_begin = total_rows * blockIdx.x / gridDim.x;
-    const int64_t r_end = total_rows * (blockIdx.x + 1) / gridDim.x;
-    int si = cta_seg[blockIdx.x];
-    while (true) {
-        const SegDescB sd = segs[si];
-        const int64_t s0 = sd.grow, s1 = sd.grow + sd.rows;
-        if (s0 >= r_end) break;
-        const int64_t lo = r_begin > s0 ? r_begin : s0;
-        const int64_t hi = r_end < s1 ? r_end : s1;
-        if (hi > lo) {
-            __syncthreads();
-            for (int k = threadIdx.x; k < sd.cols; k += blockDim.x) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (k < sd.x_n) v = GATHER ? sd.xsrc[sd.bidx[k]] : sd.xsrc[k];
-                xs[k] = v;
-            }
-            __syncthreads();
-            const int r_local = (int)(lo - s0);
-            block_rows_g<float, 32, 512, 4>(sd.A + (int64_t)r_local * sd.ld, (int)(hi - lo), sd.ld, sd.cols, xs,
-                                            sd.out + r_local, sd.add ? sd.add + r_local : nullptr);
+    if (warp > 0) {
+#pragma unroll
+        for (int i = 0; i < VN; ++i) {
+            red[warp - 1][lane * VN + i][0] = acc[i][0];
+            red[warp - 1][lane * VN + i][1] = acc[i][1];
+            red[warp - 1][lane * VN + i][2] = acc[i][2];
         }
-        ++si;
-        if (s1 >= r_end) break;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float4* out = B.out + D.out_off;
+        const float4* add = (D.add_off >= 0) ? B.add + D.add_off : nullptr;
+#pragma unroll
+        for (int i = 0; i < VN; ++i) {
+            const int oi = o + i;
+            if (oi >= D.n_out) break;
+            float r0 = acc[i][0], r1 = acc[i][1], r2 = acc[i][2];
+#pragma unroll
+            for (int w = 0; w < kAxWarps - 1; ++w) {
+                r0 += red[w][lane * VN + i][0];
+                r1 += red[w][lane * VN + i][1];
+                r2 += red[w][lane * VN + i][2];
+            }
+            const float4 b = add ? add[oi] : make_float4(0.f, 0.f, 0.f, 0.f);
+            out[oi] = make_float4(b.x + r0, b.y + r1, b.z + r2, 0.f);
+        }
     }
 }
 
@@ -510,29 +439,23 @@ void launch_coarse(pd_mesh* m, const T* pool, const float4* cB, float4* part, cu
 
 template <class T>
 void launch_condense(pd_mesh* m, const T* pool, const float4* b, float4* tc, cudaStream_t s) {
-    if (m->seg_blocks_cond > 0) {
-        k_segments<T, false><<<m->seg_blocks_cond, 512, 0, s>>>(m->d_segs_cond.p, m->d_cta_cond.p, m->seg_rows_cond,
-                                                                pool, b, nullptr, nullptr, tc);
-    } else {
-        k_condense<T><<<m->n_tasks_cond, 256, 0, s>>>(m->d_tasks_cond.p, pool, b, tc);
-    }
+    AxBases B{pool, b, nullptr, nullptr, tc};
+    k_axpy_form<T, false><<<m->ax_blocks_cond, 32 * kAxWarps, sizeof(float4) * m->ax_kmax_cond, s>>>(
+        m->d_ax_desc_cond.p, m->d_ax_blk_cond.p, B, nullptr);
     PDG_CHECK_LAUNCH();
 }
 
 template <class T>
 void launch_backsub(pd_mesh* m, const T* pool, const float4* xB, const float4* tc, float4* xout, cudaStream_t s) {
-    if (m->seg_blocks_back > 0) {
-        k_segments<T, true><<<m->seg_blocks_back, 512, 0, s>>>(m->d_segs_back.p, m->d_cta_back.p, m->seg_rows_back,
-                                                               pool, xB, m->d_bidx.p, tc, xout);
-    } else {
-        k_backsub<T><<<m->n_tasks_back, 256, 0, s>>>(m->d_tasks_back.p, pool, m->d_bidx.p, xB, tc, xout);
-    }
+    AxBases B{pool, xB, m->d_bidx.p, tc, xout};
+    k_axpy_form<T, false><<<m->ax_blocks_back, 32 * kAxWarps, sizeof(float4) * m->ax_kmax_back, s>>>(
+        m->d_ax_desc_back.p, m->d_ax_blk_back.p, B, nullptr);
     PDG_CHECK_LAUNCH();
 }
 
 template <class T>
 void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaStream_t s) {
-    if (m->n_tasks_cond > 0) {
+    if (m->ax_blocks_cond > 0) {
         phase_begin(m, PH_CONDENSE, s);
         launch_condense<T>(m, pool, b, m->d_tc.p, s);
         phase_end(m, s);
@@ -551,7 +474,7 @@ void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaSt
         PDG_CHECK_LAUNCH();
         phase_end(m, s);
     }
-    if (m->n_tasks_back > 0) {
+    if (m->ax_blocks_back > 0) {
         phase_begin(m, PH_BACKSUB, s);
         launch_backsub<T>(m, pool, xout + m->n_int, m->d_tc.p, xout, s);
         phase_end(m, s);
@@ -563,7 +486,7 @@ void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaSt
 template <class T>
 void dd_solve_scratch_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, float4* tc, float4* cB,
                         float4* part, cudaStream_t s) {
-    if (m->n_tasks_cond > 0) launch_condense<T>(m, pool, b, tc, s);
+    if (m->ax_blocks_cond > 0) launch_condense<T>(m, pool, b, tc, s);
     if (m->n_B > 0) {
         k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, tc, cB);
         PDG_CHECK_LAUNCH();
@@ -571,7 +494,7 @@ void dd_solve_scratch_t(pd_mesh* m, const T* pool, const float4* b, float4* xout
         k_reduce<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->coarse_nchunks, part, xout + m->n_int);
         PDG_CHECK_LAUNCH();
     }
-    if (m->n_tasks_back > 0) launch_backsub<T>(m, pool, xout + m->n_int, tc, xout, s);
+    if (m->ax_blocks_back > 0) launch_backsub<T>(m, pool, xout + m->n_int, tc, xout, s);
 }
 
 }  // namespace
@@ -584,13 +507,15 @@ void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* 
         dd_solve_scratch_t<float>(m, m->d_mat32.p, b, xout, tc, cB, part, s);
 }
 
-void launch_segments_b(bool gather, const SegDescB* segs, const int* cta_seg, int64_t total_rows, int blocks,
-                       cudaStream_t s) {
-    if (blocks <= 0) return;
-    if (gather) k_segments_b<true><<<blocks, 512, 0, s>>>(segs, cta_seg, total_rows);
-    else k_segments_b<false><<<blocks, 512, 0, s>>>(segs, cta_seg, total_rows);
+void launch_axpy_b(const AxDesc* descs, const AxBlock* blocks, const AxBases* bases, int n_blocks, int k_max,
+                   cudaStream_t s) {
+    if (n_blocks <= 0) return;
+    k_axpy_form<float, true><<<n_blocks, 32 * kAxWarps, sizeof(float4) * std::max(k_max, 1), s>>>(descs, blocks,
+                                                                                                AxBases{}, bases);
     PDG_CHECK_LAUNCH();
 }
+
+int ax_outputs_per_block(int prec) { return 32 * (prec == PD_PREC_BF16 ? 8 : 4); }
 
 // Returns false when the largest interface vector does not fit in shared memory.
 bool configure_coarse_b(int max_cols) {

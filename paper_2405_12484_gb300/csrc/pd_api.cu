@@ -24,6 +24,7 @@ int dense_block();
 int dd_max_sub_cols();
 int dd_coarse_chunk();
 int dd_configure_coarse(int ld_S);
+int ax_outputs_per_block(int prec);
 void launch_prefactor_helpers_scatter_coo(double* S, int ld, const int* r, const int* c, const double* v, int n,
                                           cudaStream_t s);
 void launch_prefactor_add_block(double* S, int ldS, const double* Sd, int ldSd, const int* bidx, int nb,
@@ -596,11 +597,12 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     dKib.free();
 
     // ---- boundary index lists and the reduced interface matrix S = K_BB + sum_d S_d
-    std::vector<int32_t> bidx_off(n_dom + 1, 0), bidx;
-    for (int32_t d = 0; d < n_dom; ++d) bidx_off[d + 1] = bidx_off[d] + (int32_t)m->dom_bnd[d].size();
-    bidx.reserve(bidx_off.back());
-    for (int32_t d = 0; d < n_dom; ++d) bidx.insert(bidx.end(), m->dom_bnd[d].begin(), m->dom_bnd[d].end());
-    upload(m->d_bidx, bidx, s);
+    std::vector<int32_t> sbidx_off(n_dom + 1, 0), sbidx;
+    for (int32_t d = 0; d < n_dom; ++d) sbidx_off[d + 1] = sbidx_off[d] + (int32_t)m->dom_bnd[d].size();
+    sbidx.reserve(sbidx_off.back());
+    for (int32_t d = 0; d < n_dom; ++d) sbidx.insert(sbidx.end(), m->dom_bnd[d].begin(), m->dom_bnd[d].end());
+    DBuf<int32_t> d_sbidx;
+    upload(d_sbidx, sbidx, s);
     const int nBp = (int)round_up(std::max(n_B, 1), nb64);
     DBuf<double> dS, dXS;
     if (n_B > 0) {
@@ -628,30 +630,34 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         for (int32_t d = 0; d < n_dom; ++d) {
             const int nbd = (int)m->dom_bnd[d].size();
             if (nbd == 0 || m->dom_n_int[d] == 0) continue;
-            launch_prefactor_add_block(dS.p, nBp, dSd.p + (size_t)d * sSd, NBp, m->d_bidx.p + bidx_off[d], nbd, s);
+            launch_prefactor_add_block(dS.p, nBp, dSd.p + (size_t)d * sSd, NBp, d_sbidx.p + sbidx_off[d], nbd, s);
         }
         PDG_CUDA(cudaStreamSynchronize(s));
         dense_spd_inverse(dS.p, nBp, nBp, 0, dXS.p, nBp, 0, 1, m->d_err.p, s);
     }
     dSd.free();
 
-    // ---- per-iteration matrix pool: per domain G_d = [K_ii^-1; Psi^T], Psi_d; then S^-1
+    // ---- per-iteration matrix pool.  Per domain: H_d = [K_ii^-1 | Psi_d]
+    // (n_i x (n_i + n_bd), row k holds the coefficients of b_k for every
+    // output of the condensation, K_ii^-1 being symmetric) and Psi_d^T
+    // (n_bd x n_i, row j holds the coefficients of x_B[j] for every internal
+    // output of the back-substitution); then S^-1 (n_B x n_B).
     m->prec = o.precision;
     m->refine = o.refine_steps;
     m->correction = (o.flags & PD_SOLVE_CORRECTION) != 0;
     m->use_graphs = o.use_graphs != 0;
-    std::vector<int64_t> g_off(n_dom), p_off(n_dom);
-    std::vector<int32_t> ldG(n_dom), ldP(n_dom), tc_off(n_dom);
+    std::vector<int64_t> h_off(n_dom), t_off(n_dom);
+    std::vector<int32_t> ldH(n_dom), ldT(n_dom), tc_off(n_dom);
     int64_t pool = 0;
     int32_t tcr = 0;
     for (int32_t d = 0; d < n_dom; ++d) {
         const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
-        ldG[d] = (int32_t)round_up(std::max(ni, 1), 8);
-        ldP[d] = (int32_t)round_up(std::max(nbd, 1), 8);
-        g_off[d] = pool;
-        pool += (int64_t)(ni + nbd) * ldG[d];
-        p_off[d] = pool;
-        pool += (int64_t)ni * ldP[d];
+        ldH[d] = (int32_t)round_up(std::max(ni + nbd, 1), 8);
+        ldT[d] = (int32_t)round_up(std::max(ni, 1), 8);
+        h_off[d] = pool;
+        pool += (int64_t)ni * ldH[d];
+        t_off[d] = pool;
+        pool += (int64_t)nbd * ldT[d];
         pool = round_up(pool, 8);
         tc_off[d] = tcr;
         tcr += ni + nbd;
@@ -674,113 +680,66 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         if (ni == 0) continue;
         const double* Xd = dXii.p + (size_t)d * sKii;
         const double* Pd = dPsi.p + (size_t)d * sKib;
-        launch_cast_block(Xd, NI, ni, ni, 0, m->prec, m->d_mat32.p, m->d_mat16.p, g_off[d], ldG[d], s);
+        launch_cast_block(Xd, NI, ni, ni, 0, m->prec, m->d_mat32.p, m->d_mat16.p, h_off[d], ldH[d], s);
         if (nbd > 0) {
-            launch_cast_block(Pd, NBp, nbd, ni, 1, m->prec, m->d_mat32.p, m->d_mat16.p,
-                              g_off[d] + (int64_t)ni * ldG[d], ldG[d], s);
-            launch_cast_block(Pd, NBp, ni, nbd, 0, m->prec, m->d_mat32.p, m->d_mat16.p, p_off[d], ldP[d], s);
+            launch_cast_block(Pd, NBp, ni, nbd, 0, m->prec, m->d_mat32.p, m->d_mat16.p, h_off[d] + ni, ldH[d], s);
+            launch_cast_block(Pd, NBp, nbd, ni, 1, m->prec, m->d_mat32.p, m->d_mat16.p, t_off[d], ldT[d], s);
         }
     }
     if (n_B > 0)
         launch_cast_block(dXS.p, nBp, n_B, n_B, 0, m->prec, m->d_mat32.p, m->d_mat16.p, m->off_S, m->ld_S, s);
 
-    // ---- tasks
+    // ---- descriptors of the per-domain products: one block per output chunk
     const int VN = (m->prec == PD_PREC_BF16) ? 8 : 4;
-    const int RB = 64;
-    std::vector<GemvTask> tc_tasks, bk_tasks;
-    for (int32_t d = 0; d < n_dom; ++d) {
-        const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
-        if (ni == 0) continue;
-        for (int32_t r0 = 0; r0 < ni + nbd; r0 += RB) {
-            GemvTask t{};
-            t.a_off = g_off[d] + (int64_t)r0 * ldG[d];
-            t.rows = std::min(RB, ni + nbd - r0);
-            t.ld = ldG[d];
-            t.cols = (int32_t)round_up(ni, VN);
-            t.x_off = m->dom_int_off[d];
-            t.x_n = ni;
-            t.y_off = tc_off[d] + r0;
-            tc_tasks.push_back(t);
-        }
-        for (int32_t r0 = 0; r0 < ni; r0 += RB) {
-            GemvTask t{};
-            t.a_off = p_off[d] + (int64_t)r0 * ldP[d];
-            t.rows = std::min(RB, ni - r0);
-            t.ld = ldP[d];
-            t.cols = nbd > 0 ? (int32_t)round_up(nbd, VN) : 0;
-            t.x_off = bidx_off[d];
-            t.x_n = nbd;
-            t.y_off = m->dom_int_off[d] + r0;
-            t.add_off = tc_off[d] + r0;
-            bk_tasks.push_back(t);
-        }
-    }
-    upload(m->d_tasks_cond, tc_tasks, s);
-    upload(m->d_tasks_back, bk_tasks, s);
-    // balanced form: one segment per domain, blocks over the concatenated rows
+    std::vector<int32_t> bidx_off(n_dom + 1, 0), bidx;
+    for (int32_t d = 0; d < n_dom; ++d) bidx_off[d + 1] = bidx_off[d] + (int32_t)m->dom_bnd[d].size();
+    bidx.reserve(bidx_off.back());
+    for (int32_t d = 0; d < n_dom; ++d) bidx.insert(bidx.end(), m->dom_bnd[d].begin(), m->dom_bnd[d].end());
+    upload(m->d_bidx, bidx, s);
     {
-        int sms = 0, dev = 0;
-        PDG_CUDA(cudaGetDevice(&dev));
-        PDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        std::vector<SegDesc> sc, sb;
-        int64_t rc = 0, rb = 0;
+        const int OW = ax_outputs_per_block(m->prec);
+        std::vector<AxDesc> dc, db;
+        std::vector<AxBlock> bc, bb;
         for (int32_t d = 0; d < n_dom; ++d) {
             const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
             if (ni == 0) continue;
-            SegDesc a{};
-            a.a_off = g_off[d];
-            a.grow = rc;
-            a.rows = ni + nbd;
-            a.ld = ldG[d];
-            a.cols = (int32_t)round_up(ni, VN);
-            a.x_off = m->dom_int_off[d];
-            a.x_n = ni;
-            a.y_off = tc_off[d];
-            sc.push_back(a);
-            rc += a.rows;
-            SegDesc b{};
-            b.a_off = p_off[d];
-            b.grow = rb;
-            b.rows = ni;
-            b.ld = ldP[d];
-            b.cols = nbd > 0 ? (int32_t)round_up(nbd, VN) : 0;
-            b.x_off = bidx_off[d];
-            b.x_n = nbd;
-            b.y_off = m->dom_int_off[d];
+            AxDesc c{};
+            c.a_off = h_off[d];
+            c.x_off = m->dom_int_off[d];
+            c.bidx_off = -1;
+            c.add_off = -1;
+            c.out_off = tc_off[d];
+            c.K = ni;
+            c.ld = ldH[d];
+            c.n_out = ni + nbd;
+            for (int32_t o0 = 0; o0 < c.n_out; o0 += OW) bc.push_back(AxBlock{(int32_t)dc.size(), o0});
+            dc.push_back(c);
+            AxDesc b{};
+            b.a_off = t_off[d];
+            b.x_off = 0;
+            b.bidx_off = bidx_off[d];
             b.add_off = tc_off[d];
-            sb.push_back(b);
-            rb += b.rows;
+            b.out_off = m->dom_int_off[d];
+            b.K = nbd;
+            b.ld = ldT[d];
+            b.n_out = ni;
+            for (int32_t o0 = 0; o0 < b.n_out; o0 += OW) bb.push_back(AxBlock{(int32_t)db.size(), o0});
+            db.push_back(b);
         }
-        auto plan = [&](const std::vector<SegDesc>& segs, int64_t total, DBuf<SegDesc>& dsegs, DBuf<int32_t>& dcta,
-                        int32_t& blocks) {
-            blocks = 0;
-            if (segs.empty() || total <= 0) return;
-            int64_t want = (int64_t)2 * std::max(sms, 1);
-            blocks = (int32_t)std::min<int64_t>(want, total);
-            std::vector<int32_t> first(blocks);
-            size_t si = 0;
-            for (int32_t c = 0; c < blocks; ++c) {
-                const int64_t r0 = total * c / blocks;
-                while (si + 1 < segs.size() && segs[si].grow + segs[si].rows <= r0) ++si;
-                first[c] = (int32_t)si;
-            }
-            // sentinel segment past the end stops every block's walk
-            std::vector<SegDesc> all(segs);
-            SegDesc end{};
-            end.grow = total;
-            all.push_back(end);
-            upload(dsegs, all, s);
-            upload(dcta, first, s);
-        };
-        plan(sc, rc, m->d_segs_cond, m->d_cta_cond, m->seg_blocks_cond);
-        plan(sb, rb, m->d_segs_back, m->d_cta_back, m->seg_blocks_back);
-        m->h_segs_cond = sc;
-        m->h_segs_back = sb;
-        m->seg_rows_cond = rc;
-        m->seg_rows_back = rb;
+        upload(m->d_ax_desc_cond, dc, s);
+        upload(m->d_ax_desc_back, db, s);
+        upload(m->d_ax_blk_cond, bc, s);
+        upload(m->d_ax_blk_back, bb, s);
+        m->ax_blocks_cond = (int32_t)bc.size();
+        m->ax_blocks_back = (int32_t)bb.size();
+        m->h_ax_desc_cond = dc;
+        m->h_ax_desc_back = db;
+        m->ax_kmax_cond = 1;
+        m->ax_kmax_back = 1;
+        for (const auto& a : dc) m->ax_kmax_cond = std::max(m->ax_kmax_cond, a.K);
+        for (const auto& a : db) m->ax_kmax_back = std::max(m->ax_kmax_back, a.K);
+        (void)VN;
     }
-    m->n_tasks_cond = (int32_t)tc_tasks.size();
-    m->n_tasks_back = (int32_t)bk_tasks.size();
     m->n_tc = tcr;
     m->d_tc.alloc(std::max(tcr, 1));
     // interface gather lists (domains in increasing order)
@@ -811,8 +770,8 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     {
         const int64_t es = (m->prec == PD_PREC_BF16) ? 2 : 4;
         int64_t mat_c = 0, mat_b = 0, nbd_tot = 0;
-        for (const auto& t : tc_tasks) mat_c += (int64_t)t.rows * t.cols * es;
-        for (const auto& t : bk_tasks) mat_b += (int64_t)t.rows * t.cols * es;
+        for (const auto& a : m->h_ax_desc_cond) mat_c += (int64_t)a.K * round_up(a.n_out, VN) * es;
+        for (const auto& a : m->h_ax_desc_back) mat_b += (int64_t)a.K * round_up(a.n_out, VN) * es;
         for (int32_t d = 0; d < n_dom; ++d)
             if (m->dom_n_int[d] > 0) nbd_tot += (int64_t)m->dom_bnd[d].size();
         const int64_t nv = m->n_v, nf = n_free, nt = m->n_t, ninc = (int64_t)4 * nt;
@@ -831,7 +790,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->phase_bytes[PH_BACKSUB] = mat_b + nbd_tot * (4 + 16) + (int64_t)n_int * 32;
         m->phase_bytes[PH_RESIDUAL] = nk * (4 + 8 + 16) + nf * (4 + 16 + 16);
         m->phase_bytes[PH_VELOCITY] = nv * 48;
-        int dd = (m->n_tasks_cond > 0 ? 1 : 0) + (n_B > 0 ? 3 : 0) + (m->n_tasks_back > 0 ? 1 : 0);
+        int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (n_B > 0 ? 3 : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
         m->launches_per_iter = 2 + dd + (m->correction ? 2 : 0) + m->refine * (2 + dd);
     }
 
@@ -999,7 +958,8 @@ pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
     bytes += m->d_force.bytes() + m->d_by0.bytes() + m->d_b.bytes() + m->d_pin_tgt.bytes() + m->d_mh2.bytes();
     bytes += m->d_inc_ptr.bytes() + m->d_inc.bytes() + m->d_kfp_ptr.bytes() + m->d_kfp_col.bytes();
     bytes += m->d_kfp_val.bytes() + m->d_old_of_new.bytes() + m->d_mat32.bytes() + m->d_mat16.bytes();
-    bytes += m->d_tasks_cond.bytes() + m->d_tasks_back.bytes() + m->d_tc.bytes() + m->d_bidx.bytes();
+    bytes += m->d_ax_desc_cond.bytes() + m->d_ax_desc_back.bytes() + m->d_ax_blk_cond.bytes();
+    bytes += m->d_ax_blk_back.bytes() + m->d_tc.bytes() + m->d_bidx.bytes();
     bytes += m->d_gat_ptr.bytes() + m->d_gat.bytes() + m->d_cB.bytes() + m->d_part.bytes();
     bytes += m->d_K_ptr.bytes() + m->d_K_col.bytes() + m->d_K_val.bytes() + m->d_r.bytes() + m->d_dx.bytes();
     out->device_bytes = bytes;

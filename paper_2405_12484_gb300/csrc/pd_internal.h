@@ -59,27 +59,27 @@ struct DBuf {
     DBuf& operator=(const DBuf&) = delete;
 };
 
-// Per-iteration dense product over a row block of one matrix ("task").
-struct GemvTask {
-    int64_t a_off;     // element offset of the block's first row in the matrix pool
-    int32_t rows;      // rows in this block
-    int32_t ld;        // row stride (elements, multiple of 8)
-    int32_t cols;      // columns to stream (multiple of 4, <= ld)
-    int32_t x_off;     // condense: first vertex of b; backsub: offset into the boundary index list
-    int32_t x_n;       // number of x entries (condense: n_i; backsub: n_bd)
-    int32_t y_off;     // first output row
-    int32_t add_off;   // backsub: first row of t to add
-    int32_t pad;
+// Column-oriented per-domain product y[o] = add[o] + sum_k A[k][o] x_k: base
+// pointers of one launch (or of one serving slot) and the offsets of one
+// domain matrix into them.
+struct AxBases {
+    const void* pool;      // matrix pool (float or bf16)
+    const float4* x;       // vector source
+    const int* bidx;       // gather list (boundary products) or null
+    const float4* add;     // added to the result, or null
+    float4* out;
 };
-
-// One domain's matrix in the balanced per-domain kernels.
-struct SegDesc {
-    int64_t a_off;     // pool offset of the matrix
-    int64_t grow;      // first row in the concatenated row list
-    int32_t rows, ld, cols;
-    int32_t x_off, x_n;  // vector source: b offset (condense) or boundary-list offset (backsub)
-    int32_t y_off, add_off;
-    int32_t pad;
+struct AxDesc {
+    int64_t a_off;         // pool offset of row 0
+    int32_t x_off;         // x offset (contiguous source)
+    int32_t bidx_off;      // >= 0: x_k = x[bidx[bidx_off + k]]
+    int32_t add_off;       // >= 0: add offset
+    int32_t out_off;
+    int32_t K, ld, n_out;  // rows, row stride, outputs
+    int32_t slot;          // serving slot (batched launches)
+};
+struct AxBlock {
+    int32_t desc, o0;      // descriptor and first output of one block
 };
 
 // One resident request of the serving loop, as the batched kernels see it.
@@ -99,17 +99,6 @@ struct BatchSlot {
     float h, gx, gy, gz;
     float drive_amp, drive_w;
     int drive_axis;
-};
-
-// A per-domain matrix of one slot in the batched per-domain kernels.
-struct SegDescB {
-    const float* A;        // first row
-    const float4* xsrc;    // vector source (contiguous, or gathered through bidx)
-    const int* bidx;
-    const float4* add;
-    float4* out;
-    int64_t grow;          // first row in the concatenated row list
-    int32_t rows, ld, cols, x_n;
 };
 
 // The interface matrix S^-1 of one slot in the batched coarse kernel.
@@ -176,13 +165,11 @@ struct pd_mesh {
     pdg::DBuf<__nv_bfloat16> d_mat16;       // matrix pool (BF16)
     int64_t off_S = 0;                      // pool offset of S^-1
     int32_t ld_S = 0;
-    pdg::DBuf<pdg::GemvTask> d_tasks_cond, d_tasks_back;
-    int32_t n_tasks_cond = 0, n_tasks_back = 0;
-    pdg::DBuf<pdg::SegDesc> d_segs_cond, d_segs_back;   // balanced per-domain kernels
-    pdg::DBuf<int32_t> d_cta_cond, d_cta_back;          // first segment of each block
-    int64_t seg_rows_cond = 0, seg_rows_back = 0;
-    int32_t seg_blocks_cond = 0, seg_blocks_back = 0;
-    std::vector<pdg::SegDesc> h_segs_cond, h_segs_back;   // host copies (serving batches)
+    pdg::DBuf<pdg::AxDesc> d_ax_desc_cond, d_ax_desc_back;   // per-domain products (axpy form)
+    pdg::DBuf<pdg::AxBlock> d_ax_blk_cond, d_ax_blk_back;
+    int32_t ax_blocks_cond = 0, ax_blocks_back = 0;
+    int32_t ax_kmax_cond = 1, ax_kmax_back = 1;             // largest K (shared-memory vector size)
+    std::vector<pdg::AxDesc> h_ax_desc_cond, h_ax_desc_back;   // host copies (serving batches)
     pdg::DBuf<float4> d_tc;                 // stacked [t_d; c_d] rows of every domain
     int32_t n_tc = 0;
     pdg::DBuf<int32_t> d_bidx;              // concatenated per-domain boundary index lists

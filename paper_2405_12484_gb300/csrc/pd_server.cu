@@ -22,8 +22,9 @@ void launch_b_assemble(const BatchSlot* slots, const int* off, int n_slots, int 
 void launch_b_gather(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_b_reduce(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_b_velocity(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
-void launch_segments_b(bool gather, const SegDescB* segs, const int* cta_seg, int64_t total_rows, int blocks,
-                       cudaStream_t s);
+void launch_axpy_b(const AxDesc* descs, const AxBlock* blocks, const AxBases* bases, int n_blocks, int k_max,
+                   cudaStream_t s);
+int ax_outputs_per_block(int prec);
 bool configure_coarse_b(int max_cols);
 void launch_coarse_b(const CoarseDescB* cd, int n_desc, int64_t U, int max_cols, int blocks, cudaStream_t s);
 
@@ -68,7 +69,7 @@ struct pd_server {
     std::map<pd_request_id, std::unique_ptr<Request>> reqs;
     std::deque<pd_request_id> queue;
     std::vector<pd_request_id> active;
-    int64_t used = 0;
+    int64_t used = 0, peak = 0;
     bool dirty = true;
     cudaGraphExec_t graph = nullptr;
     int sms = 0;
@@ -76,10 +77,10 @@ struct pd_server {
     DBuf<BatchSlot> d_slots;
     DBuf<int32_t> d_off[PH_NB];
     int blocks[PH_NB] = {0};
-    DBuf<SegDescB> d_segc, d_segb;
-    DBuf<int32_t> d_ctac, d_ctab;
-    int64_t rows_c = 0, rows_b = 0;
-    int blocks_c = 0, blocks_b = 0;
+    DBuf<AxDesc> d_axc, d_axb;
+    DBuf<AxBlock> d_blkc, d_blkb;
+    DBuf<AxBases> d_basc, d_basb;
+    int blocks_c = 0, blocks_b = 0, kmax_c = 1, kmax_b = 1;
     DBuf<CoarseDescB> d_cd;
     int n_cd = 0, max_cols = 0, coarse_blocks = 0;
     int64_t units = 0;
@@ -122,9 +123,12 @@ static void rebuild(pd_server* S) {
     std::vector<BatchSlot> slots(n);
     std::vector<int32_t> off[PH_NB];
     for (auto& o : off) o.assign(n + 1, 0);
-    std::vector<SegDescB> segc, segb;
+    std::vector<AxDesc> axc, axb;
+    std::vector<AxBlock> blkc, blkb;
+    std::vector<AxBases> basc(n), basb(n);
     std::vector<CoarseDescB> cd;
-    int64_t rc = 0, rb = 0, units = 0;
+    int64_t units = 0;
+    const int OW = ax_outputs_per_block(PD_PREC_FP32);
     int max_cols = 0;
     for (int k = 0; k < n; ++k) {
         Request& R = *S->reqs[S->active[k]];
@@ -172,35 +176,17 @@ static void rebuild(pd_server* S) {
                                 (m->n_v + 255) / 256};
         for (int p = 0; p < PH_NB; ++p) off[p][k + 1] = off[p][k] + cnt[p];
         const float* pool = m->d_mat32.p;
-        for (const SegDesc& sd : m->h_segs_cond) {
-            SegDescB d{};
-            d.A = pool + sd.a_off;
-            d.xsrc = m->d_b.p + sd.x_off;
-            d.bidx = nullptr;
-            d.add = nullptr;
-            d.out = m->d_tc.p + sd.y_off;
-            d.grow = rc;
-            d.rows = sd.rows;
-            d.ld = sd.ld;
-            d.cols = sd.cols;
-            d.x_n = sd.x_n;
-            segc.push_back(d);
-            rc += sd.rows;
+        basc[k] = AxBases{pool, m->d_b.p, nullptr, nullptr, m->d_tc.p};
+        basb[k] = AxBases{pool, m->d_x.p + m->n_int, m->d_bidx.p, m->d_tc.p, m->d_x.p};
+        for (AxDesc a : m->h_ax_desc_cond) {
+            a.slot = k;
+            for (int32_t o0 = 0; o0 < a.n_out; o0 += OW) blkc.push_back(AxBlock{(int32_t)axc.size(), o0});
+            axc.push_back(a);
         }
-        for (const SegDesc& sd : m->h_segs_back) {
-            SegDescB d{};
-            d.A = pool + sd.a_off;
-            d.xsrc = m->d_x.p + m->n_int;
-            d.bidx = m->d_bidx.p + sd.x_off;
-            d.add = m->d_tc.p + sd.add_off;
-            d.out = m->d_x.p + sd.y_off;
-            d.grow = rb;
-            d.rows = sd.rows;
-            d.ld = sd.ld;
-            d.cols = sd.cols;
-            d.x_n = sd.x_n;
-            segb.push_back(d);
-            rb += sd.rows;
+        for (AxDesc a : m->h_ax_desc_back) {
+            a.slot = k;
+            for (int32_t o0 = 0; o0 < a.n_out; o0 += OW) blkb.push_back(AxBlock{(int32_t)axb.size(), o0});
+            axb.push_back(a);
         }
         if (m->n_B > 0) {
             CoarseDescB c{};
@@ -226,28 +212,17 @@ static void rebuild(pd_server* S) {
         up(S->d_off[p], off[p]);
         S->blocks[p] = off[p][n];
     }
-    auto plan = [&](std::vector<SegDescB>& segs, int64_t total, DBuf<SegDescB>& dsegs, DBuf<int32_t>& dcta,
-                    int& blocks) {
-        blocks = 0;
-        if (segs.empty() || total <= 0) return;
-        blocks = (int)std::min<int64_t>((int64_t)2 * S->sms, total);
-        std::vector<int32_t> first(blocks);
-        size_t si = 0;
-        for (int c = 0; c < blocks; ++c) {
-            const int64_t r0 = total * c / blocks;
-            while (si + 1 < segs.size() && segs[si].grow + segs[si].rows <= r0) ++si;
-            first[c] = (int32_t)si;
-        }
-        SegDescB end{};
-        end.grow = total;
-        segs.push_back(end);
-        up(dsegs, segs);
-        up(dcta, first);
-    };
-    plan(segc, rc, S->d_segc, S->d_ctac, S->blocks_c);
-    plan(segb, rb, S->d_segb, S->d_ctab, S->blocks_b);
-    S->rows_c = rc;
-    S->rows_b = rb;
+    up(S->d_axc, axc);
+    up(S->d_axb, axb);
+    up(S->d_blkc, blkc);
+    up(S->d_blkb, blkb);
+    up(S->d_basc, basc);
+    up(S->d_basb, basb);
+    S->blocks_c = (int)blkc.size();
+    S->blocks_b = (int)blkb.size();
+    S->kmax_c = S->kmax_b = 1;
+    for (const auto& a : axc) S->kmax_c = std::max(S->kmax_c, a.K);
+    for (const auto& a : axb) S->kmax_b = std::max(S->kmax_b, a.K);
     up(S->d_cd, cd);
     S->n_cd = (int)cd.size();
     S->units = units;
@@ -269,11 +244,11 @@ static void rebuild(pd_server* S) {
         for (int it = 0; it < S->n_iter; ++it) {
             launch_b_local(sl, S->d_off[PH_LOC].p, n, S->blocks[PH_LOC], c);
             launch_b_assemble(sl, S->d_off[PH_ASM].p, n, S->blocks[PH_ASM], c);
-            launch_segments_b(false, S->d_segc.p, S->d_ctac.p, S->rows_c, S->blocks_c, c);
+            launch_axpy_b(S->d_axc.p, S->d_blkc.p, S->d_basc.p, S->blocks_c, S->kmax_c, c);
             launch_b_gather(sl, S->d_off[PH_GAT].p, n, S->blocks[PH_GAT], c);
             launch_coarse_b(S->d_cd.p, S->n_cd, S->units, S->max_cols, S->coarse_blocks, c);
             launch_b_reduce(sl, S->d_off[PH_RED].p, n, S->blocks[PH_RED], c);
-            launch_segments_b(true, S->d_segb.p, S->d_ctab.p, S->rows_b, S->blocks_b, c);
+            launch_axpy_b(S->d_axb.p, S->d_blkb.p, S->d_basb.p, S->blocks_b, S->kmax_b, c);
         }
         launch_b_velocity(sl, S->d_off[PH_VEL].p, n, S->blocks[PH_VEL], c);
     } catch (...) {
@@ -313,6 +288,7 @@ static bool admit(pd_server* S, Request& R) {
     }
     R.mesh = m;
     R.steady_bytes = steady;
+    S->peak = std::max(S->peak, S->used + steady + transient);
     S->used += steady;
     // pinned rest positions (increasing vertex id) and the frame counter
     std::vector<float4> pr;
@@ -484,11 +460,13 @@ pd_status pd_release(pd_server* S, pd_request_id id) {
     return PD_OK;
 }
 
-pd_status pd_server_stats(pd_server* S, int32_t* n_queued, int32_t* n_active, int64_t* used_bytes) {
+pd_status pd_server_stats(pd_server* S, int32_t* n_queued, int32_t* n_active, int64_t* used_bytes,
+                          int64_t* peak_bytes) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
     if (n_queued) *n_queued = (int32_t)S->queue.size();
     if (n_active) *n_active = (int32_t)S->active.size();
     if (used_bytes) *used_bytes = S->used;
+    if (peak_bytes) *peak_bytes = S->peak;
     return PD_OK;
 }
 

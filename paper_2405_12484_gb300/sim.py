@@ -276,9 +276,9 @@ class Server:
         return x, ms
 
     def stats(self):
-        q, a, u = C.c_int32(), C.c_int32(), C.c_int64()
-        _check(lib().pd_server_stats(self._h, C.byref(q), C.byref(a), C.byref(u)), "pd_server_stats")
-        return {"queued": q.value, "active": a.value, "used_bytes": u.value}
+        q, a, u, pk = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib().pd_server_stats(self._h, C.byref(q), C.byref(a), C.byref(u), C.byref(pk)), "pd_server_stats")
+        return {"queued": q.value, "active": a.value, "used_bytes": u.value, "peak_bytes": pk.value}
 
 
 def project(F: torch.Tensor, with_sigma=True):

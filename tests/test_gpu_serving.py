@@ -30,7 +30,7 @@ def _requests():
     return [(a, None), (b, (0.2, 1.0, 0)), (c, None), (d, (0.2, 1.0, 0))]
 
 
-def _run(reqs, frames, budget=1 << 34, stagger=True):
+def _run(reqs, frames, budget=1 << 34, stagger=True, stats=None):
     from paper_2405_12484_gb300.sim import Server
     S = Server(budget, max_slots=16, n_iter=20)
     ids = []
@@ -38,24 +38,28 @@ def _run(reqs, frames, budget=1 << 34, stagger=True):
     ticks = 0
     max_active = 0
     saw_queue = False
+    peak = 0
     while pending or any(S.poll(i)[0] in (0, 1) for i in ids):
         if pending and (not stagger or ticks % 3 == 0):
             w, drive = pending.pop(0)
             ids.append(S.submit(w, frames, drive))
         n, _ = S.tick()
         st = S.stats()
+        peak = max(peak, st["peak_bytes"])
         saw_queue |= st["queued"] > 0 and st["active"] > 0
         max_active = max(max_active, n)
         ticks += 1
         assert ticks < 10000
     out = [S.fetch(i)[0] for i in ids]
     S.close()
+    if stats is not None:
+        stats["peak"] = peak
     return out, max_active, saw_queue
 
 
 def test_results_are_identical_alone_and_in_the_mix():
     reqs = _requests()
-    frames = 6
+    frames = 12
     mix, max_active, _ = _run(reqs, frames)
     assert max_active >= 3
     for k, r in enumerate(reqs):
@@ -85,10 +89,17 @@ def test_serving_matches_the_single_mesh_stepper():
 
 def test_admission_waits_for_the_hbm_budget():
     reqs = _requests()
-    # a budget that holds roughly one request at a time
-    mix_ok, max_active, saw_queue = _run(reqs, 4, budget=60 << 20, stagger=False)
+    big = reqs[1]
+    reqs = [big, (sweater_shell(seed=25, n_theta=40, n_z=12, n_r=2, dom_theta=4, dom_z=2), big[1])] + reqs[:1] + reqs[2:]
+    alone, peaks = [], []
+    for r in reqs:
+        st = {}
+        alone.append(_run([r], 4, stats=st)[0][0])
+        peaks.append(st["peak"])
+    # room for the largest request and its prefactorisation, not for two of them
+    budget = int(1.05 * max(peaks))
+    mix, max_active, saw_queue = _run(reqs, 4, budget=budget, stagger=False)
     assert saw_queue
     assert max_active < len(reqs)
-    alone = [_run([r], 4)[0][0] for r in reqs]
     for k in range(len(reqs)):
-        assert np.array_equal(alone[k], mix_ok[k])
+        assert np.array_equal(alone[k], mix[k])
