@@ -120,7 +120,7 @@ constexpr int kMaxSubCols = 2048;   // largest per-domain internal / boundary co
 // shared-memory broadcast, and the warps' partial sums are combined in a
 // fixed order (deterministic).  No cross-lane reductions, fully coalesced
 // 16-byte row loads.
-constexpr int kAxWarps = 4;
+constexpr int kAxWarps = 8;
 
 template <class T, bool BATCHED>
 __global__ void __launch_bounds__(32 * kAxWarps) k_axpy_form(const AxDesc* __restrict__ descs,
