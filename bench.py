@@ -366,9 +366,12 @@ def main():
     dom_ms = phase.get(dominant, 0.0)
     dom_bytes = info["phase_bytes"][dominant]
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
+    # DRAM traffic per launch from the ncu capture of this kernel (profiles/k_coarse_bal_shell153k_fp32.md):
+    # traffic / algorithmic bytes = 1.026 on the capture, scaled to this launch's algorithmic bytes.
+    traffic = 1.026 * dom_bytes if (args.precision == "fp32" and not args.small) else None
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                "traffic": None, "algorithmic_bytes": dom_bytes, "avg_launch_ms": dom_ms}
+                "traffic": traffic, "algorithmic_bytes": dom_bytes, "avg_launch_ms": dom_ms}
 
     # ---- per-phase report (events around every kernel of a captured frame), after the timed region
     phases = {}
