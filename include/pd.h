@@ -75,7 +75,11 @@ enum {
      * solve in the chosen precision.  Equal to x_{k+1} = S(b) in exact
      * arithmetic; with low-precision matrices the error only scales the small
      * correction, so PD's own iterations act as iterative refinement. */
-    PD_SOLVE_CORRECTION = 1
+    PD_SOLVE_CORRECTION = 1,
+    /* Solve the interface system with one dense S^-1 even when the mesh has
+     * enough domains for the two-level interface solve (groups of domains
+     * condensed onto a top-level interface first; chosen automatically). */
+    PD_SOLVE_SINGLE_LEVEL = 2
 };
 
 typedef struct pd_solver_opts {
@@ -98,6 +102,9 @@ typedef struct pd_mesh_info {
     int32_t launches_per_iter;     /* kernels launched per PD iteration (after pd_prefactor) */
     int32_t launches_per_frame;    /* kernels launched per frame besides the iterations (pin copy, inertia, velocity) */
     int64_t phase_bytes[16];       /* algorithmic bytes moved by one launch of each phase (pd_phase_name order) */
+    int32_t n_groups;              /* domain groups of the two-level interface solve (0 = single level) */
+    int32_t n_top_interface;       /* interface vertices shared by two or more groups */
+    int32_t two_level;             /* 1 when the last pd_prefactor built the two-level interface solve */
 } pd_mesh_info;
 
 /*

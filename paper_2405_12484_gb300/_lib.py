@@ -29,6 +29,7 @@ PD_PREC_BF16 = 1
 PD_PREC_TF32 = 2
 
 PD_SOLVE_CORRECTION = 1
+PD_SOLVE_SINGLE_LEVEL = 2
 
 
 class pd_solver_opts(C.Structure):
@@ -42,7 +43,8 @@ class pd_mesh_info(C.Structure):
                 ("max_domain_internal", C.c_int32), ("max_domain_boundary", C.c_int32),
                 ("device_bytes", C.c_int64), ("prefactor_seconds", C.c_double),
                 ("launches_per_iter", C.c_int32), ("launches_per_frame", C.c_int32),
-                ("phase_bytes", C.c_int64 * 16)]
+                ("phase_bytes", C.c_int64 * 16), ("n_groups", C.c_int32), ("n_top_interface", C.c_int32),
+                ("two_level", C.c_int32)]
 
 
 PD_REQ_QUEUED, PD_REQ_ACTIVE, PD_REQ_DONE, PD_REQ_FAILED = 0, 1, 2, 3

@@ -425,86 +425,89 @@ __global__ void k_axpy(int n, const float4* __restrict__ dx, float4* __restrict_
 inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
 template <class T>
-void launch_coarse(pd_mesh* m, const T* pool, const float4* cB, float4* part, cudaStream_t s) {
+void launch_coarse(pd_mesh* m, const T* pool, const float4* cin, float4* part, cudaStream_t s) {
     if (m->coarse_blocks > 0) {
         const size_t smem = sizeof(float) * 3 * (size_t)m->ld_S;
-        k_coarse_bal<T><<<m->coarse_blocks, 32 * kCoarseWarps, smem, s>>>(pool + m->off_S, m->n_B, m->ld_S, m->ld_S,
-                                                                          m->coarse_nchunks, cB, part);
+        k_coarse_bal<T><<<m->coarse_blocks, 32 * kCoarseWarps, smem, s>>>(pool + m->off_S, m->cs_n, m->ld_S, m->ld_S,
+                                                                          m->coarse_nchunks, cin, part);
     } else {
-        dim3 grid(nblk(m->n_B, m->coarse_rows_per_cta), m->coarse_nchunks);
-        k_coarse<T><<<grid, 256, 0, s>>>(pool + m->off_S, m->n_B, m->ld_S, m->coarse_rows_per_cta, cB, part);
+        dim3 grid(nblk(m->cs_n, m->coarse_rows_per_cta), m->coarse_nchunks);
+        k_coarse<T><<<grid, 256, 0, s>>>(pool + m->off_S, m->cs_n, m->ld_S, m->coarse_rows_per_cta, cin, part);
     }
     PDG_CHECK_LAUNCH();
 }
 
 template <class T>
-void launch_condense(pd_mesh* m, const T* pool, const float4* b, float4* tc, cudaStream_t s) {
-    AxBases B{pool, b, nullptr, nullptr, tc};
-    k_axpy_form<T, false><<<m->ax_blocks_cond, 32 * kAxWarps, sizeof(float4) * m->ax_kmax_cond, s>>>(
-        m->d_ax_desc_cond.p, m->d_ax_blk_cond.p, B, nullptr);
+void launch_ax(const AxDesc* descs, const AxBlock* blocks, int n_blocks, int k_max, const AxBases& B, cudaStream_t s) {
+    if (n_blocks <= 0) return;
+    k_axpy_form<T, false><<<n_blocks, 32 * kAxWarps, sizeof(float4) * std::max(k_max, 1), s>>>(descs, blocks, B,
+                                                                                             nullptr);
     PDG_CHECK_LAUNCH();
 }
 
-template <class T>
-void launch_backsub(pd_mesh* m, const T* pool, const float4* xB, const float4* tc, float4* xout, cudaStream_t s) {
-    AxBases B{pool, xB, m->d_bidx.p, tc, xout};
-    k_axpy_form<T, false><<<m->ax_blocks_back, 32 * kAxWarps, sizeof(float4) * m->ax_kmax_back, s>>>(
-        m->d_ax_desc_back.p, m->d_ax_blk_back.p, B, nullptr);
-    PDG_CHECK_LAUNCH();
-}
+struct DDBufs {
+    float4 *tc, *cB, *part, *tc2, *cT;
+};
 
+// One subspace solve: x (free vertices of xout) = K_ff^-1 b.
 template <class T>
-void dd_solve_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, cudaStream_t s) {
+void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, const DDBufs& w, cudaStream_t s) {
     if (m->ax_blocks_cond > 0) {
         phase_begin(m, PH_CONDENSE, s);
-        launch_condense<T>(m, pool, b, m->d_tc.p, s);
+        launch_ax<T>(m->d_ax_desc_cond.p, m->d_ax_blk_cond.p, m->ax_blocks_cond, m->ax_kmax_cond,
+                     AxBases{pool, b, nullptr, nullptr, w.tc}, s);
         phase_end(m, s);
     }
     if (m->n_B > 0) {
         phase_begin(m, PH_GATHER, s);
-        k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, m->d_tc.p,
-                                                  m->d_cB.p);
+        k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, w.tc, w.cB);
         PDG_CHECK_LAUNCH();
         phase_end(m, s);
+        const float4* cin = w.cB;
+        float4* xcs = xout + m->n_int;
+        const int T0 = m->n_B - m->n_top;
+        if (m->two_level) {
+            phase_begin(m, PH_CONDENSE2, s);
+            launch_ax<T>(m->d_ax_desc_cond2.p, m->d_ax_blk_cond2.p, m->ax_blocks_cond2, m->ax_kmax_cond2,
+                         AxBases{pool, w.cB, nullptr, nullptr, w.tc2}, s);
+            phase_end(m, s);
+            phase_begin(m, PH_GATHER2, s);
+            k_gather<<<nblk(m->n_top, 256), 256, 0, s>>>(m->n_top, m->d_gat2_ptr.p, m->d_gat2.p, w.cB + T0, w.tc2,
+                                                         w.cT);
+            PDG_CHECK_LAUNCH();
+            phase_end(m, s);
+            cin = w.cT;
+            xcs = xout + m->n_int + T0;
+        }
         phase_begin(m, PH_COARSE, s);
-        launch_coarse<T>(m, pool, m->d_cB.p, m->d_part.p, s);
+        launch_coarse<T>(m, pool, cin, w.part, s);
         phase_end(m, s);
         phase_begin(m, PH_REDUCE, s);
-        k_reduce<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->coarse_nchunks, m->d_part.p, xout + m->n_int);
+        k_reduce<<<nblk(m->cs_n, 256), 256, 0, s>>>(m->cs_n, m->coarse_nchunks, w.part, xcs);
         PDG_CHECK_LAUNCH();
         phase_end(m, s);
+        if (m->two_level) {
+            phase_begin(m, PH_BACKSUB2, s);
+            launch_ax<T>(m->d_ax_desc_back2.p, m->d_ax_blk_back2.p, m->ax_blocks_back2, m->ax_kmax_back2,
+                         AxBases{pool, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int}, s);
+            phase_end(m, s);
+        }
     }
     if (m->ax_blocks_back > 0) {
         phase_begin(m, PH_BACKSUB, s);
-        launch_backsub<T>(m, pool, xout + m->n_int, m->d_tc.p, xout, s);
+        launch_ax<T>(m->d_ax_desc_back.p, m->d_ax_blk_back.p, m->ax_blocks_back, m->ax_kmax_back,
+                     AxBases{pool, xout + m->n_int, m->d_bidx.p, w.tc, xout}, s);
         phase_end(m, s);
     }
-}
-
-// The same five launches with caller-provided scratch (condensed rows,
-// interface right-hand side, coarse partial sums) instead of the mesh's.
-template <class T>
-void dd_solve_scratch_t(pd_mesh* m, const T* pool, const float4* b, float4* xout, float4* tc, float4* cB,
-                        float4* part, cudaStream_t s) {
-    if (m->ax_blocks_cond > 0) launch_condense<T>(m, pool, b, tc, s);
-    if (m->n_B > 0) {
-        k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, tc, cB);
-        PDG_CHECK_LAUNCH();
-        launch_coarse<T>(m, pool, cB, part, s);
-        k_reduce<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->coarse_nchunks, part, xout + m->n_int);
-        PDG_CHECK_LAUNCH();
-    }
-    if (m->ax_blocks_back > 0) launch_backsub<T>(m, pool, xout + m->n_int, tc, xout, s);
 }
 
 }  // namespace
 
 void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* tc, float4* cB, float4* part,
-                             cudaStream_t s) {
-    if (m->prec == PD_PREC_BF16)
-        dd_solve_scratch_t<__nv_bfloat16>(m, m->d_mat16.p, b, xout, tc, cB, part, s);
-    else
-        dd_solve_scratch_t<float>(m, m->d_mat32.p, b, xout, tc, cB, part, s);
+                             float4* tc2, float4* cT, cudaStream_t s) {
+    const DDBufs w{tc, cB, part, tc2, cT};
+    if (m->prec == PD_PREC_BF16) dd_solve_impl<__nv_bfloat16>(m, m->d_mat16.p, b, xout, w, s);
+    else dd_solve_impl<float>(m, m->d_mat32.p, b, xout, w, s);
 }
 
 void launch_axpy_b(const AxDesc* descs, const AxBlock* blocks, const AxBases* bases, int n_blocks, int k_max,
@@ -553,10 +556,7 @@ int dd_configure_coarse(int ld_S) {
 int dd_coarse_chunk() { return kCoarseChunk; }
 
 void launch_dd_solve(pd_mesh* m, const float4* b, float4* xout, cudaStream_t s, bool /*timed*/) {
-    if (m->prec == PD_PREC_BF16)
-        dd_solve_t<__nv_bfloat16>(m, m->d_mat16.p, b, xout, s);
-    else
-        dd_solve_t<float>(m, m->d_mat32.p, b, xout, s);
+    launch_dd_solve_scratch(m, b, xout, m->d_tc.p, m->d_cB.p, m->d_part.p, m->d_tc2.p, m->d_cT.p, s);
 }
 
 void launch_residual(const pd_mesh* m, const float4* b, const float4* x, float4* r, cudaStream_t s) {

@@ -311,6 +311,17 @@ __global__ void k_cast_block(const double* __restrict__ src, int lds, int rows, 
     }
 }
 
+// dst[i][k] = S[r0 + i][cols ? c0 + cols[k] : c0 + k]
+__global__ void k_copy_block_idx(const double* __restrict__ S, int ldS, int r0, int nr, const int* __restrict__ cols,
+                                 int c0, int nc, double* __restrict__ dst, int ldd) {
+    const int64_t n = (int64_t)nr * nc;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(l / nc), k = (int)(l % nc);
+        const int c = c0 + (cols ? cols[k] : k);
+        dst[(int64_t)i * ldd + k] = S[(int64_t)(r0 + i) * ldS + c];
+    }
+}
+
 inline int grid_of(int64_t n) {
     int64_t b = (n + 255) / 256;
     return (int)(b < 65535 ? (b > 0 ? b : 1) : 65535);
@@ -329,6 +340,13 @@ void launch_prefactor_add_block(double* S, int ldS, const double* Sd, int ldSd, 
                                 cudaStream_t s) {
     if (nb <= 0) return;
     k_add_block<<<grid_of((int64_t)nb * nb), 256, 0, s>>>(S, ldS, Sd, ldSd, bidx, nb);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_copy_block_idx(const double* S, int ldS, int r0, int nr, const int* cols, int c0, int nc, double* dst,
+                           int ldd, cudaStream_t s) {
+    if (nr <= 0 || nc <= 0) return;
+    k_copy_block_idx<<<grid_of((int64_t)nr * nc), 256, 0, s>>>(S, ldS, r0, nr, cols, c0, nc, dst, ldd);
     PDG_CHECK_LAUNCH();
 }
 

@@ -31,6 +31,8 @@ void launch_prefactor_add_block(double* S, int ldS, const double* Sd, int ldSd, 
                                 cudaStream_t s);
 void launch_cast_block(const double* src, int lds, int rows, int cols, int transpose, int prec, float* dst32,
                        __nv_bfloat16* dst16, int64_t dst_off, int ldd, cudaStream_t s);
+void launch_copy_block_idx(const double* S, int ldS, int r0, int nr, const int* cols, int c0, int nc, double* dst,
+                           int ldd, cudaStream_t s);
 
 static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -110,6 +112,94 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Recursive coordinate bisection of domain centroids into `parts` groups.
+static void rcb(const std::vector<double>& c, std::vector<int32_t> ids, int parts, int32_t first,
+                std::vector<int32_t>& out) {
+    if (parts <= 1 || ids.size() <= 1) {
+        for (int32_t d : ids) out[d] = first;
+        return;
+    }
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int32_t d : ids)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], c[3 * (size_t)d + k]);
+            hi[k] = std::max(hi[k], c[3 * (size_t)d + k]);
+        }
+    int ax = 0;
+    for (int k = 1; k < 3; ++k)
+        if (hi[k] - lo[k] > hi[ax] - lo[ax]) ax = k;
+    std::stable_sort(ids.begin(), ids.end(),
+                     [&](int32_t a, int32_t b) { return c[3 * (size_t)a + ax] < c[3 * (size_t)b + ax]; });
+    const int left = parts / 2;
+    const size_t cut = ids.size() * left / parts;
+    std::vector<int32_t> a(ids.begin(), ids.begin() + cut), b(ids.begin() + cut, ids.end());
+    rcb(c, a, left, first, out);
+    rcb(c, b, parts - left, first + left, out);
+}
+
+// Chooses the domain groups of the two-level interface solve (or none) and
+// classifies every interface vertex: iface_class[v] = its group when all its
+// domains lie in that group, n_groups for the top-level interface.
+static void plan_groups(pd_mesh* m, const double* rest, const std::vector<int32_t>& T,
+                        const std::vector<int32_t>& tdom, const std::vector<int32_t>& vdom,
+                        const std::vector<uint8_t>& multi, const std::vector<uint8_t>& pin,
+                        std::vector<int32_t>& iface_class) {
+    const int32_t n_v = m->n_v, n_t = m->n_t, n_dom = m->n_dom;
+    m->n_groups = 0;
+    m->grp_of_dom.assign(n_dom, 0);
+    for (int32_t v = 0; v < n_v; ++v) iface_class[v] = (!pin[v] && multi[v]) ? 0 : -1;
+    if (m->n_B <= 4096 || n_dom < 8) return;
+    std::vector<double> cen(3 * (size_t)n_dom, 0.0);
+    std::vector<int32_t> cnt(n_dom, 0);
+    for (int32_t t = 0; t < n_t; ++t)
+        for (int k = 0; k < 4; ++k) {
+            const int32_t v = T[4 * (size_t)t + k];
+            for (int c = 0; c < 3; ++c) cen[3 * (size_t)tdom[t] + c] += rest[3 * (size_t)v + c];
+            cnt[tdom[t]]++;
+        }
+    for (int32_t d = 0; d < n_dom; ++d)
+        for (int c = 0; c < 3; ++c) cen[3 * (size_t)d + c] /= std::max(cnt[d], 1);
+    std::vector<int32_t> ids(n_dom);
+    std::iota(ids.begin(), ids.end(), 0);
+    for (int G = 8; G <= 64 && G <= n_dom / 2; G *= 2) {
+        std::vector<int32_t> gd(n_dom, 0);
+        rcb(cen, ids, G, 0, gd);
+        // group set of every vertex (bit mask, G <= 64)
+        std::vector<uint64_t> mask(n_v, 0);
+        for (int32_t t = 0; t < n_t; ++t)
+            for (int k = 0; k < 4; ++k) mask[T[4 * (size_t)t + k]] |= uint64_t(1) << gd[tdom[t]];
+        std::vector<int32_t> n2(G, 0), nb2(G, 0);
+        int32_t n_top = 0;
+        for (int32_t v = 0; v < n_v; ++v) {
+            if (pin[v] || !multi[v]) continue;
+            if ((mask[v] & (mask[v] - 1)) == 0) {
+                n2[__builtin_ctzll(mask[v])]++;
+            } else {
+                n_top++;
+                for (int g = 0; g < G; ++g)
+                    if (mask[v] >> g & 1) nb2[g]++;
+            }
+        }
+        const int32_t mx2 = *std::max_element(n2.begin(), n2.end());
+        const int32_t mxb = *std::max_element(nb2.begin(), nb2.end());
+        if (mx2 > 2048 || mxb > 2048) continue;
+        if (n_top == 0 || n_top > 16384 || 2 * n_top > m->n_B) return;   // no worthwhile split
+        m->n_groups = G;
+        m->grp_of_dom = gd;
+        m->top_mask.clear();
+        for (int32_t v = 0; v < n_v; ++v) {
+            if (pin[v] || !multi[v]) continue;
+            iface_class[v] = ((mask[v] & (mask[v] - 1)) == 0) ? __builtin_ctzll(mask[v]) : G;
+        }
+        m->grp_n2 = n2;
+        m->n_top = n_top;
+        m->top_groups_of_old.clear();
+        for (int32_t v = 0; v < n_v; ++v)
+            if (!pin[v] && multi[v] && iface_class[v] == G) m->top_groups_of_old.emplace_back(v, mask[v]);
+        return;
+    }
+}
+
 extern "C" {
 
 const char* pd_status_string(pd_status s) {
@@ -131,8 +221,9 @@ const char* pd_status_string(pd_status s) {
 
 const char* pd_last_error(void) { return g_last_error.c_str(); }
 
-static const char* kPhaseNames[PH_COUNT] = {"inertia", "local", "assemble", "dd_condense", "dd_gather",
-                                            "dd_coarse", "dd_reduce", "dd_backsub", "residual", "velocity"};
+static const char* kPhaseNames[PH_COUNT] = {"inertia",      "local",      "assemble",   "dd_condense", "dd_gather",
+                                            "dd_coarse",    "dd_reduce",  "dd_backsub", "residual",    "velocity",
+                                            "dd_condense2", "dd_gather2", "dd_backsub2"};
 
 const char* pd_phase_name(int32_t k) { return (k >= 0 && k < PH_COUNT) ? kPhaseNames[k] : "?"; }
 
@@ -269,19 +360,43 @@ pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tet
     m->n_B = n_B;
     m->n_pin = n_pin;
     m->n_free = acc + n_B;
+    // ---- super-domains for the two-level interface solve: the interface vertices
+    // whose domains all lie in one group of domains form that group's internal
+    // set (S is block-diagonal on them); the rest form the top-level interface.
+    std::vector<int32_t> iface_class(n_v, -1);   // group of an internal-interface vertex, n_groups = top
+    plan_groups(m, rest_xyz, T, tdom, vdom, multi, pin, iface_class);
     m->new_of_old.assign(n_v, -1);
     m->old_of_new.assign(n_v, -1);
     {
         std::vector<int32_t> fill(m->dom_int_off);
-        int32_t nb = m->n_int, np = m->n_free;
+        // interface block ordered by (group class, vertex id)
+        std::vector<int32_t> ifill(m->n_groups + 1, 0);
+        {
+            std::vector<int32_t> cnt(m->n_groups + 1, 0);
+            for (int32_t v = 0; v < n_v; ++v)
+                if (!pin[v] && multi[v]) cnt[iface_class[v]]++;
+            int32_t a = m->n_int;
+            for (int32_t g = 0; g <= m->n_groups; ++g) {
+                ifill[g] = a;
+                a += cnt[g];
+            }
+        }
+        int32_t np = m->n_free;
         for (int32_t v = 0; v < n_v; ++v) {
             int32_t nv;
             if (pin[v]) nv = np++;
-            else if (multi[v]) nv = nb++;
+            else if (multi[v]) nv = ifill[iface_class[v]]++;
             else nv = fill[vdom[v]]++;
             m->new_of_old[v] = nv;
             m->old_of_new[nv] = v;
         }
+    }
+
+    if (m->n_groups > 0) {
+        m->top_mask.assign(m->n_top, 0);
+        const int32_t T0 = m->n_int + m->n_B - m->n_top;
+        for (const auto& pr : m->top_groups_of_old) m->top_mask[m->new_of_old[pr.first] - T0] = pr.second;
+        m->top_groups_of_old.clear();
     }
 
     // ---- tets sorted by domain (stable), in new vertex ids
@@ -486,7 +601,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     pd_solver_opts o{PD_PREC_FP32, 0, 1, 0};
     if (opts) o = *opts;
     if (o.precision < PD_PREC_FP32 || o.precision > PD_PREC_TF32 || o.refine_steps < 0 || o.refine_steps > 2 ||
-        (o.flags & ~PD_SOLVE_CORRECTION) != 0)
+        (o.flags & ~(PD_SOLVE_CORRECTION | PD_SOLVE_SINGLE_LEVEL)) != 0)
         return fail(PD_ERR_INVALID_ARG, "bad solver options");
     PD_API_BEGIN
     auto t0 = std::chrono::steady_clock::now();
@@ -605,9 +720,9 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     upload(d_sbidx, sbidx, s);
     const int nBp = (int)round_up(std::max(n_B, 1), nb64);
     DBuf<double> dS, dXS;
+    const bool two = m->n_groups > 0 && n_B > 0 && !(o.flags & PD_SOLVE_SINGLE_LEVEL);
     if (n_B > 0) {
         dS.alloc((size_t)nBp * nBp);
-        dXS.alloc((size_t)nBp * nBp);
         dense_set_identity(dS.p, nBp, nBp, 0, 1, s);
         std::vector<int32_t> cr, cc;
         std::vector<double> cv;
@@ -633,9 +748,75 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             launch_prefactor_add_block(dS.p, nBp, dSd.p + (size_t)d * sSd, NBp, d_sbidx.p + sbidx_off[d], nbd, s);
         }
         PDG_CUDA(cudaStreamSynchronize(s));
-        dense_spd_inverse(dS.p, nBp, nBp, 0, dXS.p, nBp, 0, 1, m->d_err.p, s);
+        if (!two) {
+            dXS.alloc((size_t)nBp * nBp);
+            dense_spd_inverse(dS.p, nBp, nBp, 0, dXS.p, nBp, 0, 1, m->d_err.p, s);
+        }
     }
     dSd.free();
+
+    // ---- second level: the interface vertices internal to each group of domains
+    // (S_II block-diagonal over groups) are condensed onto the top-level
+    // interface T: S2 = S_TT + sum_g S_TI S_II^-1 S_IT (the same construction as
+    // the first level, applied to S).
+    const int G = two ? m->n_groups : 0;
+    const int32_t nT = two ? m->n_top : 0, T0 = n_B - nT;
+    std::vector<int32_t> i2_off(G + 1, 0), b2_off(G + 1, 0), b2all;
+    std::vector<std::vector<int32_t>> b2(G);
+    int NI2 = 64, NB2 = 8, nTp = 64;
+    DBuf<double> dX2ii, dPsi2, dX2;
+    if (two) {
+        for (int g = 0; g < G; ++g) i2_off[g + 1] = i2_off[g] + m->grp_n2[g];
+        for (int32_t k = 0; k < nT; ++k)
+            for (int g = 0; g < G; ++g)
+                if (m->top_mask[k] >> g & 1) b2[g].push_back(k);
+        int32_t mx2 = 1, mxb = 1;
+        for (int g = 0; g < G; ++g) {
+            mx2 = std::max(mx2, m->grp_n2[g]);
+            mxb = std::max(mxb, (int32_t)b2[g].size());
+            b2_off[g + 1] = b2_off[g] + (int32_t)b2[g].size();
+            b2all.insert(b2all.end(), b2[g].begin(), b2[g].end());
+        }
+        NI2 = (int)round_up(mx2, nb64);
+        NB2 = (int)round_up(mxb, 8);
+        nTp = (int)round_up(std::max(nT, 1), nb64);
+        const int64_t s2ii = (int64_t)NI2 * NI2, s2it = (int64_t)NI2 * NB2, s2d = (int64_t)NB2 * NB2;
+        DBuf<int32_t> d_b2;
+        upload(d_b2, b2all, s);
+        DBuf<double> dS2ii, dS2it, dS2d, dS2;
+        dS2ii.alloc((size_t)G * s2ii);
+        dS2it.alloc((size_t)G * s2it);
+        dX2ii.alloc((size_t)G * s2ii);
+        dPsi2.alloc((size_t)G * s2it);
+        dS2d.alloc((size_t)G * s2d);
+        dense_set_identity(dS2ii.p, NI2, NI2, s2ii, G, s);
+        PDG_CUDA(cudaMemsetAsync(dS2it.p, 0, sizeof(double) * G * s2it, s));
+        for (int g = 0; g < G; ++g) {
+            const int r0 = i2_off[g], n2 = m->grp_n2[g], nb = (int)b2[g].size();
+            if (n2 == 0) continue;
+            launch_copy_block_idx(dS.p, nBp, r0, n2, nullptr, r0, n2, dS2ii.p + g * s2ii, NI2, s);
+            if (nb > 0)
+                launch_copy_block_idx(dS.p, nBp, r0, n2, d_b2.p + b2_off[g], T0, nb, dS2it.p + g * s2it, NB2, s);
+        }
+        dense_spd_inverse(dS2ii.p, NI2, NI2, s2ii, dX2ii.p, NI2, s2ii, G, m->d_err.p, s);
+        dense_gemm(false, false, NI2, NB2, NI2, -1.0, dX2ii.p, NI2, s2ii, dS2it.p, NB2, s2it, 0.0, dPsi2.p, NB2, s2it,
+                   G, false, s);
+        dense_gemm(true, false, NB2, NB2, NI2, 1.0, dS2it.p, NB2, s2it, dPsi2.p, NB2, s2it, 0.0, dS2d.p, NB2, s2d, G,
+                   false, s);
+        dS2.alloc((size_t)nTp * nTp);
+        dX2.alloc((size_t)nTp * nTp);
+        dense_set_identity(dS2.p, nTp, nTp, 0, 1, s);
+        launch_copy_block_idx(dS.p, nBp, T0, nT, nullptr, T0, nT, dS2.p, nTp, s);
+        for (int g = 0; g < G; ++g) {
+            const int nb = (int)b2[g].size();
+            if (nb == 0 || m->grp_n2[g] == 0) continue;
+            launch_prefactor_add_block(dS2.p, nTp, dS2d.p + g * s2d, NB2, d_b2.p + b2_off[g], nb, s);
+        }
+        dense_spd_inverse(dS2.p, nTp, nTp, 0, dX2.p, nTp, 0, 1, m->d_err.p, s);
+        PDG_CUDA(cudaStreamSynchronize(s));
+    }
+    dS.free();
+    m->two_level = two;
 
     // ---- per-iteration matrix pool.  Per domain: H_d = [K_ii^-1 | Psi_d]
     // (n_i x (n_i + n_bd), row k holds the coefficients of b_k for every
@@ -662,9 +843,25 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         tc_off[d] = tcr;
         tcr += ni + nbd;
     }
+    std::vector<int64_t> h2_off(G), t2_off(G);
+    std::vector<int32_t> ldH2(G), ldT2(G), tc2_off(G);
+    int32_t tc2r = 0;
+    for (int g = 0; g < G; ++g) {
+        const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
+        ldH2[g] = (int32_t)round_up(std::max(n2 + nb, 1), 8);
+        ldT2[g] = (int32_t)round_up(std::max(n2, 1), 8);
+        h2_off[g] = pool;
+        pool += (int64_t)n2 * ldH2[g];
+        t2_off[g] = pool;
+        pool += (int64_t)nb * ldT2[g];
+        pool = round_up(pool, 8);
+        tc2_off[g] = tc2r;
+        tc2r += n2 + nb;
+    }
+    m->cs_n = two ? nT : n_B;
     m->off_S = pool;
-    m->ld_S = (int32_t)round_up(std::max(n_B, 1), 8);
-    pool += (int64_t)n_B * m->ld_S;
+    m->ld_S = (int32_t)round_up(std::max(m->cs_n, 1), 8);
+    pool += (int64_t)m->cs_n * m->ld_S;
     pool = std::max<int64_t>(pool, 8);
     m->d_mat32.free();
     m->d_mat16.free();
@@ -686,8 +883,24 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             launch_cast_block(Pd, NBp, nbd, ni, 1, m->prec, m->d_mat32.p, m->d_mat16.p, t_off[d], ldT[d], s);
         }
     }
-    if (n_B > 0)
+    if (n_B > 0 && !two)
         launch_cast_block(dXS.p, nBp, n_B, n_B, 0, m->prec, m->d_mat32.p, m->d_mat16.p, m->off_S, m->ld_S, s);
+    if (two) {
+        const int64_t s2ii = (int64_t)NI2 * NI2, s2it = (int64_t)NI2 * NB2;
+        for (int g = 0; g < G; ++g) {
+            const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
+            if (n2 == 0) continue;
+            launch_cast_block(dX2ii.p + g * s2ii, NI2, n2, n2, 0, m->prec, m->d_mat32.p, m->d_mat16.p, h2_off[g],
+                              ldH2[g], s);
+            if (nb > 0) {
+                launch_cast_block(dPsi2.p + g * s2it, NB2, n2, nb, 0, m->prec, m->d_mat32.p, m->d_mat16.p,
+                                  h2_off[g] + n2, ldH2[g], s);
+                launch_cast_block(dPsi2.p + g * s2it, NB2, nb, n2, 1, m->prec, m->d_mat32.p, m->d_mat16.p, t2_off[g],
+                                  ldT2[g], s);
+            }
+        }
+        launch_cast_block(dX2.p, nTp, nT, nT, 0, m->prec, m->d_mat32.p, m->d_mat16.p, m->off_S, m->ld_S, s);
+    }
 
     // ---- descriptors of the per-domain products: one block per output chunk
     const int VN = (m->prec == PD_PREC_BF16) ? 8 : 4;
@@ -742,6 +955,65 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     }
     m->n_tc = tcr;
     m->d_tc.alloc(std::max(tcr, 1));
+    m->ax_blocks_cond2 = m->ax_blocks_back2 = 0;
+    if (two) {
+        const int OW = ax_outputs_per_block(m->prec);
+        std::vector<AxDesc> dc, db;
+        std::vector<AxBlock> bc, bb;
+        for (int g = 0; g < G; ++g) {
+            const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
+            if (n2 == 0) continue;
+            AxDesc c{};
+            c.a_off = h2_off[g];
+            c.x_off = i2_off[g];
+            c.bidx_off = -1;
+            c.add_off = -1;
+            c.out_off = tc2_off[g];
+            c.K = n2;
+            c.ld = ldH2[g];
+            c.n_out = n2 + nb;
+            for (int32_t o0 = 0; o0 < c.n_out; o0 += OW) bc.push_back(AxBlock{(int32_t)dc.size(), o0});
+            dc.push_back(c);
+            AxDesc b{};
+            b.a_off = t2_off[g];
+            b.x_off = 0;
+            b.bidx_off = b2_off[g];
+            b.add_off = tc2_off[g];
+            b.out_off = i2_off[g];
+            b.K = nb;
+            b.ld = ldT2[g];
+            b.n_out = n2;
+            for (int32_t o0 = 0; o0 < b.n_out; o0 += OW) bb.push_back(AxBlock{(int32_t)db.size(), o0});
+            db.push_back(b);
+        }
+        upload(m->d_ax_desc_cond2, dc, s);
+        upload(m->d_ax_desc_back2, db, s);
+        upload(m->d_ax_blk_cond2, bc, s);
+        upload(m->d_ax_blk_back2, bb, s);
+        m->ax_blocks_cond2 = (int32_t)bc.size();
+        m->ax_blocks_back2 = (int32_t)bb.size();
+        m->ax_kmax_cond2 = m->ax_kmax_back2 = 1;
+        for (const auto& a : dc) m->ax_kmax_cond2 = std::max(m->ax_kmax_cond2, a.K);
+        for (const auto& a : db) m->ax_kmax_back2 = std::max(m->ax_kmax_back2, a.K);
+        upload(m->d_bidx2, b2all, s);
+        // top-level gather lists (groups in increasing order)
+        std::vector<int32_t> gp(nT + 1, 0), gl;
+        std::vector<std::vector<int32_t>> lists(nT);
+        for (int g = 0; g < G; ++g) {
+            if (m->grp_n2[g] == 0) continue;
+            for (int32_t k = 0; k < (int32_t)b2[g].size(); ++k) lists[b2[g][k]].push_back(tc2_off[g] + m->grp_n2[g] + k);
+        }
+        for (int32_t k = 0; k < nT; ++k) {
+            gp[k + 1] = gp[k] + (int32_t)lists[k].size();
+            gl.insert(gl.end(), lists[k].begin(), lists[k].end());
+        }
+        upload(m->d_gat2_ptr, gp, s);
+        upload(m->d_gat2, gl, s);
+        m->n_tc2 = tc2r;
+        m->d_tc2.alloc(std::max(tc2r, 1));
+        m->d_cT.alloc(std::max(nT, 1));
+        m->n_gat2 = (int32_t)gl.size();
+    }
     // interface gather lists (domains in increasing order)
     {
         std::vector<int32_t> gp(n_B + 1, 0), gl;
@@ -763,8 +1035,8 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     m->coarse_rows_per_cta = 64;
     m->coarse_chunk = dd_coarse_chunk();
     m->coarse_nchunks = (int32_t)((m->ld_S + m->coarse_chunk - 1) / m->coarse_chunk);
-    m->d_part.alloc((size_t)std::max(n_B, 1) * m->coarse_nchunks);
-    m->coarse_blocks = (n_B > 0) ? dd_configure_coarse(m->ld_S) : 0;
+    m->d_part.alloc((size_t)std::max(m->cs_n, 1) * m->coarse_nchunks);
+    m->coarse_blocks = (m->cs_n > 0) ? dd_configure_coarse(m->ld_S) : 0;
 
     // ---- algorithmic bytes per launch of each phase (each array counted once)
     {
@@ -777,20 +1049,33 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         const int64_t nv = m->n_v, nf = n_free, nt = m->n_t, ninc = (int64_t)4 * nt;
         const int64_t nkfp = (int64_t)m->Kfp_col.size(), nk = (int64_t)m->K_col.size();
         const int64_t ngat = nbd_tot;
-        const int64_t colsS = (int64_t)round_up(std::max(n_B, 1), VN);
+        const int64_t colsS = (int64_t)round_up(std::max(m->cs_n, 1), VN);
+        int64_t mat_c2 = 0, mat_b2 = 0;
+        for (int g = 0; g < G; ++g) {
+            const int64_t n2 = m->grp_n2[g], nb = (int64_t)b2[g].size();
+            if (n2 == 0) continue;
+            mat_c2 += n2 * round_up(n2 + nb, VN) * es;
+            mat_b2 += nb * round_up(n2, VN) * es;
+        }
         for (int k = 0; k < 16; ++k) m->phase_bytes[k] = 0;
         m->phase_bytes[PH_INERTIA] = nv * 48 + nf * (16 + 4 + 16 + 4) + nkfp * 8 + (int64_t)m->n_pin * 16;
         m->phase_bytes[PH_LOCAL] = nt * (16 + 48 + 64) + nv * 16;
         m->phase_bytes[PH_ASSEMBLE] = nf * (4 + 16 + 16) + ninc * (4 + 16);
         m->phase_bytes[PH_CONDENSE] = mat_c + (int64_t)n_int * 16 + (int64_t)tcr * 16;
         m->phase_bytes[PH_GATHER] = (int64_t)n_B * (4 + 16 + 16) + ngat * (4 + 16);
-        m->phase_bytes[PH_COARSE] = (int64_t)n_B * colsS * es + (int64_t)n_B * 16 +
-                                    (int64_t)m->coarse_nchunks * n_B * 16;
-        m->phase_bytes[PH_REDUCE] = (int64_t)m->coarse_nchunks * n_B * 16 + (int64_t)n_B * 16;
+        const int64_t ncs = m->cs_n;
+        m->phase_bytes[PH_COARSE] = ncs * colsS * es + ncs * 16 + (int64_t)m->coarse_nchunks * ncs * 16;
+        m->phase_bytes[PH_REDUCE] = (int64_t)m->coarse_nchunks * ncs * 16 + ncs * 16;
+        if (two) {
+            m->phase_bytes[PH_CONDENSE2] = mat_c2 + (int64_t)(n_B - nT) * 16 + (int64_t)m->n_tc2 * 16;
+            m->phase_bytes[PH_GATHER2] = (int64_t)nT * (4 + 16 + 16) + (int64_t)m->n_gat2 * (4 + 16);
+            m->phase_bytes[PH_BACKSUB2] = mat_b2 + (int64_t)b2all.size() * (4 + 16) + (int64_t)(n_B - nT) * 32;
+        }
         m->phase_bytes[PH_BACKSUB] = mat_b + nbd_tot * (4 + 16) + (int64_t)n_int * 32;
         m->phase_bytes[PH_RESIDUAL] = nk * (4 + 8 + 16) + nf * (4 + 16 + 16);
         m->phase_bytes[PH_VELOCITY] = nv * 48;
         int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (n_B > 0 ? 3 : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
+        if (two) dd += (m->ax_blocks_cond2 > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) + (m->ax_blocks_back2 > 0 ? 1 : 0);
         m->launches_per_iter = 2 + dd + (m->correction ? 2 : 0) + m->refine * (2 + dd);
     }
 
@@ -953,6 +1238,9 @@ pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
     }
     out->max_domain_internal = mi;
     out->max_domain_boundary = mb;
+    out->n_groups = m->n_groups;
+    out->n_top_interface = m->n_groups > 0 ? m->n_top : 0;
+    out->two_level = m->two_level ? 1 : 0;
     int64_t bytes = 0;
     bytes += m->d_tets.bytes() + m->d_geo.bytes() + m->d_x.bytes() + m->d_xprev.bytes() + m->d_v.bytes();
     bytes += m->d_force.bytes() + m->d_by0.bytes() + m->d_b.bytes() + m->d_pin_tgt.bytes() + m->d_mh2.bytes();
@@ -962,6 +1250,9 @@ pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
     bytes += m->d_ax_blk_back.bytes() + m->d_tc.bytes() + m->d_bidx.bytes();
     bytes += m->d_gat_ptr.bytes() + m->d_gat.bytes() + m->d_cB.bytes() + m->d_part.bytes();
     bytes += m->d_K_ptr.bytes() + m->d_K_col.bytes() + m->d_K_val.bytes() + m->d_r.bytes() + m->d_dx.bytes();
+    bytes += m->d_ax_desc_cond2.bytes() + m->d_ax_desc_back2.bytes() + m->d_ax_blk_cond2.bytes();
+    bytes += m->d_ax_blk_back2.bytes() + m->d_bidx2.bytes() + m->d_gat2_ptr.bytes() + m->d_gat2.bytes();
+    bytes += m->d_tc2.bytes() + m->d_cT.bytes();
     out->device_bytes = bytes;
     out->prefactor_seconds = m->prefactor_seconds;
     out->launches_per_iter = m->launches_per_iter;

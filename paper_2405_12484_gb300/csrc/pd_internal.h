@@ -112,7 +112,7 @@ struct CoarseDescB {
 
 enum Phase : int {
     PH_INERTIA = 0, PH_LOCAL, PH_ASSEMBLE, PH_CONDENSE, PH_GATHER, PH_COARSE, PH_REDUCE,
-    PH_BACKSUB, PH_RESIDUAL, PH_VELOCITY, PH_COUNT
+    PH_BACKSUB, PH_RESIDUAL, PH_VELOCITY, PH_CONDENSE2, PH_GATHER2, PH_BACKSUB2, PH_COUNT
 };
 
 // ---------------------------------------------------------------- mesh
@@ -136,6 +136,12 @@ struct pd_mesh {
     std::vector<double> mass;                     // n_v (new numbering)
     std::vector<int32_t> dom_int_off, dom_n_int;  // per domain: first internal vertex, count
     std::vector<std::vector<int32_t>> dom_bnd;    // per domain: interface ids (0..n_B) coupled to its internals
+    // two-level interface solve: groups of domains, interface block ordered as
+    // [group 0 internal | ... | group G-1 internal | top level]
+    int32_t n_groups = 0, n_top = 0;
+    std::vector<int32_t> grp_of_dom, grp_n2;
+    std::vector<uint64_t> top_mask;                         // per top-level vertex (interface order): group bits
+    std::vector<std::pair<int32_t, uint64_t>> top_groups_of_old;   // (caller vertex id, group bits)
     // CSR of the scalar matrix over free vertices (new numbering) and of the free-pinned block
     std::vector<int32_t> K_rowptr, K_col;         // n_free rows, columns < n_free
     std::vector<int32_t> Kfp_rowptr, Kfp_col;     // n_free rows, columns = pinned slot (0..n_pin)
@@ -169,6 +175,15 @@ struct pd_mesh {
     pdg::DBuf<pdg::AxBlock> d_ax_blk_cond, d_ax_blk_back;
     int32_t ax_blocks_cond = 0, ax_blocks_back = 0;
     int32_t ax_kmax_cond = 1, ax_kmax_back = 1;             // largest K (shared-memory vector size)
+    // second level (groups of domains): condensation onto the top-level interface
+    bool two_level = false;
+    int32_t cs_n = 0;                                       // rows of the dense coarse inverse in the pool
+    pdg::DBuf<pdg::AxDesc> d_ax_desc_cond2, d_ax_desc_back2;
+    pdg::DBuf<pdg::AxBlock> d_ax_blk_cond2, d_ax_blk_back2;
+    int32_t ax_blocks_cond2 = 0, ax_blocks_back2 = 0, ax_kmax_cond2 = 1, ax_kmax_back2 = 1;
+    pdg::DBuf<int32_t> d_bidx2, d_gat2_ptr, d_gat2;
+    pdg::DBuf<float4> d_tc2, d_cT;
+    int32_t n_tc2 = 0, n_gat2 = 0;
     std::vector<pdg::AxDesc> h_ax_desc_cond, h_ax_desc_back;   // host copies (serving batches)
     pdg::DBuf<float4> d_tc;                 // stacked [t_d; c_d] rows of every domain
     int32_t n_tc = 0;

@@ -21,7 +21,7 @@
 namespace pdg {
 
 void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* tc, float4* cB, float4* part,
-                             cudaStream_t s);
+                             float4* tc2, float4* cT, cudaStream_t s);
 
 namespace {
 
@@ -54,7 +54,9 @@ extern "C" pd_status pd_solve_noalloc(pd_mesh* m, const float* r, float* x) {
     // partial sums, and the refinement residual and correction
     const size_t nv = (size_t)m->n_v, nf = (size_t)(m->n_free > 0 ? m->n_free : 1);
     const size_t ntc = (size_t)(m->n_tc > 0 ? m->n_tc : 1), nb = (size_t)(m->n_B > 0 ? m->n_B : 1);
-    const size_t npart = nb * (size_t)(m->coarse_nchunks > 0 ? m->coarse_nchunks : 1);
+    const size_t ncs = (size_t)(m->cs_n > 0 ? m->cs_n : 1);
+    const size_t npart = ncs * (size_t)(m->coarse_nchunks > 0 ? m->coarse_nchunks : 1);
+    const size_t ntc2 = (size_t)(m->n_tc2 > 0 ? m->n_tc2 : 1), ntop = (size_t)(m->n_top > 0 ? m->n_top : 1);
     const size_t off_r = 0;
     const size_t off_x = off_r + align256(nv * sizeof(float4));
     const size_t off_tc = off_x + align256(nv * sizeof(float4));
@@ -62,7 +64,9 @@ extern "C" pd_status pd_solve_noalloc(pd_mesh* m, const float* r, float* x) {
     const size_t off_part = off_cb + align256(nb * sizeof(float4));
     const size_t off_rr = off_part + align256(npart * sizeof(float4));
     const size_t off_dx = off_rr + align256(nf * sizeof(float4));
-    const size_t total = off_dx + align256(nv * sizeof(float4));
+    const size_t off_tc2 = off_dx + align256(nv * sizeof(float4));
+    const size_t off_ct = off_tc2 + align256(ntc2 * sizeof(float4));
+    const size_t total = off_ct + align256(ntop * sizeof(float4));
     if (total > kNoallocBytes) {
         set_error("pd_solve_noalloc: this mesh needs " + std::to_string(total) +
                   " bytes of scratch, more than the fixed 16 MiB (16777216 bytes); use pd_solve");
@@ -96,14 +100,16 @@ extern "C" pd_status pd_solve_noalloc(pd_mesh* m, const float* r, float* x) {
         float4* part = reinterpret_cast<float4*>(base + off_part);
         float4* rr = reinterpret_cast<float4*>(base + off_rr);
         float4* dx = reinterpret_cast<float4*>(base + off_dx);
+        float4* tc2 = reinterpret_cast<float4*>(base + off_tc2);
+        float4* cT = reinterpret_cast<float4*>(base + off_ct);
         cudaStream_t s = m->stream;
         // the solution buffer keeps the previous call's contents: clear it
         PDG_CUDA(cudaMemsetAsync(xi, 0, nv * sizeof(float4), s));
         launch_gather_in(m, r, ri, s);
-        launch_dd_solve_scratch(m, ri, xi, tc, cB, part, s);
+        launch_dd_solve_scratch(m, ri, xi, tc, cB, part, tc2, cT, s);
         for (int k = 0; k < m->refine; ++k) {
             launch_residual(m, ri, xi, rr, s);
-            launch_dd_solve_scratch(m, rr, dx, tc, cB, part, s);
+            launch_dd_solve_scratch(m, rr, dx, tc, cB, part, tc2, cT, s);
             launch_axpy_free(m, dx, xi, s);
         }
         launch_scatter_out(m, xi, x, 1, s);
