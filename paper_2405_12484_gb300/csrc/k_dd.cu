@@ -385,6 +385,98 @@ __global__ void __launch_bounds__(512, 1) k_coarse_b(const CoarseDescB* __restri
     }
 }
 
+// Row-oriented products of many dense blocks in one balanced launch
+// ("row form"): out[r] = add[r] + A[r, 0:cols] . x for every row r of every
+// descriptor, x being the descriptor's contiguous or gathered slice of B.x.
+// The RU-row units of all descriptors are concatenated; block b takes the
+// units [blk_u[b], blk_u[b+1]) (cut on the host so every block streams about
+// the same number of matrix bytes), stages each overlapped descriptor's x in
+// shared memory as three float planes and splits its piece evenly over its
+// warps.  A unit is a full row dot product: lanes stride the row with 16-byte
+// loads, a fixed-order shuffle tree combines them (deterministic).
+template <class T>
+__global__ void __launch_bounds__(32 * kCoarseWarps, 1) k_rowdot(const RowDesc* __restrict__ descs, int n_desc,
+                                                                const int64_t* __restrict__ blk_u, AxBases B,
+                                                                int xcap) {
+    extern __shared__ float xsm[];
+    float* x0 = xsm;
+    float* x1 = xsm + xcap;
+    float* x2 = xsm + 2 * xcap;
+    constexpr int VN = VecN<T>::N;
+    constexpr int RU = CoarseRows<T>::R;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t b0 = blk_u[blockIdx.x], b1 = blk_u[blockIdx.x + 1];
+    const T* pool = reinterpret_cast<const T*>(B.pool);
+    for (int di = 0; di < n_desc; ++di) {
+        const RowDesc D = descs[di];
+        const int64_t nu = (D.rows + RU - 1) / RU;
+        const int64_t lo = b0 > D.u0 ? b0 : D.u0;
+        const int64_t hi = b1 < D.u0 + nu ? b1 : D.u0 + nu;
+        if (hi <= lo) continue;
+        __syncthreads();
+        for (int k = threadIdx.x; k < D.ld; k += blockDim.x) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < D.cols) v = (D.xidx_off >= 0) ? B.x[B.bidx[D.xidx_off + k]] : B.x[D.x_off + k];
+            x0[k] = v.x;
+            x1[k] = v.y;
+            x2[k] = v.z;
+        }
+        __syncthreads();
+        const int64_t n = hi - lo;
+        const int64_t w0 = lo + n * warp / kCoarseWarps, w1 = lo + n * (warp + 1) / kCoarseWarps;
+        for (int64_t u = w0; u < w1; ++u) {
+            const int r0 = RU * (int)(u - D.u0);
+            const T* a[RU];
+#pragma unroll
+            for (int k = 0; k < RU; ++k) a[k] = pool + D.a_off + (int64_t)((r0 + k < D.rows) ? r0 + k : r0) * D.ld;
+            float acc[RU][3];
+#pragma unroll
+            for (int k = 0; k < RU; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
+#pragma unroll 4
+            for (int c = lane * VN; c < D.ld; c += 32 * VN) {
+                float v[RU][VN];
+#pragma unroll
+                for (int k = 0; k < RU; ++k) load_vec(a[k] + c, v[k]);
+#pragma unroll
+                for (int j = 0; j < VN; j += 4) {
+                    const float4 p0 = *reinterpret_cast<const float4*>(x0 + c + j);
+                    const float4 p1 = *reinterpret_cast<const float4*>(x1 + c + j);
+                    const float4 p2 = *reinterpret_cast<const float4*>(x2 + c + j);
+                    const float q0[4] = {p0.x, p0.y, p0.z, p0.w};
+                    const float q1[4] = {p1.x, p1.y, p1.z, p1.w};
+                    const float q2[4] = {p2.x, p2.y, p2.z, p2.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int k = 0; k < RU; ++k) {
+                            acc[k][0] = fmaf(v[k][j + i], q0[i], acc[k][0]);
+                            acc[k][1] = fmaf(v[k][j + i], q1[i], acc[k][1]);
+                            acc[k][2] = fmaf(v[k][j + i], q2[i], acc[k][2]);
+                        }
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int k = 0; k < RU; ++k) {
+                    acc[k][0] += __shfl_xor_sync(0xffffffffu, acc[k][0], off);
+                    acc[k][1] += __shfl_xor_sync(0xffffffffu, acc[k][1], off);
+                    acc[k][2] += __shfl_xor_sync(0xffffffffu, acc[k][2], off);
+                }
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < RU; ++k) {
+                    const int r = r0 + k;
+                    if (r >= D.rows) break;
+                    const float4 ad = (D.add_off >= 0) ? B.add[D.add_off + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    B.out[D.out_off + r] = make_float4(ad.x + acc[k][0], ad.y + acc[k][1], ad.z + acc[k][2], 0.f);
+                }
+            }
+        }
+    }
+}
+
 // reduce: x_B[j] = sum over chunks (fixed order) of part[ch][j]
 __global__ void k_reduce(int n_B, int n_chunks, const float4* __restrict__ part, float4* __restrict__ xB) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -445,6 +537,14 @@ void launch_ax(const AxDesc* descs, const AxBlock* blocks, int n_blocks, int k_m
     PDG_CHECK_LAUNCH();
 }
 
+template <class T>
+void launch_rowdot(const RowPlan& P, const AxBases& B, cudaStream_t s) {
+    if (P.n_blocks <= 0) return;
+    k_rowdot<T><<<P.n_blocks, 32 * kCoarseWarps, sizeof(float) * 3 * (size_t)P.xcap, s>>>(P.descs.p, P.n_desc,
+                                                                                         P.blk_u.p, B, P.xcap);
+    PDG_CHECK_LAUNCH();
+}
+
 struct DDBufs {
     float4 *tc, *cB, *part, *tc2, *cT;
 };
@@ -468,8 +568,7 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
         const int T0 = m->n_B - m->n_top;
         if (m->two_level) {
             phase_begin(m, PH_CONDENSE2, s);
-            launch_ax<T>(m->d_ax_desc_cond2.p, m->d_ax_blk_cond2.p, m->ax_blocks_cond2, m->ax_kmax_cond2,
-                         AxBases{pool, w.cB, nullptr, nullptr, w.tc2}, s);
+            launch_rowdot<T>(m->rows_cond2, AxBases{pool, w.cB, nullptr, nullptr, w.tc2}, s);
             phase_end(m, s);
             phase_begin(m, PH_GATHER2, s);
             k_gather<<<nblk(m->n_top, 256), 256, 0, s>>>(m->n_top, m->d_gat2_ptr.p, m->d_gat2.p, w.cB + T0, w.tc2,
@@ -488,8 +587,8 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
         phase_end(m, s);
         if (m->two_level) {
             phase_begin(m, PH_BACKSUB2, s);
-            launch_ax<T>(m->d_ax_desc_back2.p, m->d_ax_blk_back2.p, m->ax_blocks_back2, m->ax_kmax_back2,
-                         AxBases{pool, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int}, s);
+            launch_rowdot<T>(m->rows_back2, AxBases{pool, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int},
+                             s);
             phase_end(m, s);
         }
     }
@@ -554,6 +653,56 @@ int dd_configure_coarse(int ld_S) {
     return sms;
 }
 int dd_coarse_chunk() { return kCoarseChunk; }
+
+int rowdot_rows_per_unit(int prec) { return prec == PD_PREC_BF16 ? CoarseRows<__nv_bfloat16>::R : CoarseRows<float>::R; }
+
+// Unit numbering and block cuts of a row-form launch: block b gets the units
+// whose cumulative cost (matrix columns streamed plus a fixed per-unit cost)
+// starts in [W b / C, W (b+1) / C), C = one block per SM.
+void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s) {
+    const int RU = rowdot_rows_per_unit(prec);
+    int64_t u = 0;
+    int xcap = 8;
+    double W = 0.0;
+    for (auto& d : descs) {
+        d.u0 = u;
+        const int64_t nu = (d.rows + RU - 1) / RU;
+        u += nu;
+        xcap = std::max(xcap, d.ld);
+        W += (double)nu * (RU * (double)d.ld + 64.0);
+    }
+    P.n_desc = (int)descs.size();
+    P.xcap = xcap;
+    P.n_blocks = 0;
+    if (u == 0) return;
+    int dev = 0, sms = 0;
+    PDG_CUDA(cudaGetDevice(&dev));
+    PDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int C = std::max(1, sms);
+    std::vector<int64_t> cut(C + 1, u);
+    cut[0] = 0;
+    double acc = 0.0;
+    int b = 1;
+    for (const auto& d : descs) {
+        const int64_t nu = (d.rows + RU - 1) / RU;
+        const double cu = RU * (double)d.ld + 64.0;
+        for (int64_t k = 0; k < nu; ++k) {
+            while (b < C && acc >= W * b / C) cut[b++] = d.u0 + k;
+            acc += cu;
+        }
+    }
+    const size_t smem = sizeof(float) * 3 * (size_t)xcap;
+    if (smem > 48 * 1024) {
+        PDG_CUDA(cudaFuncSetAttribute(k_rowdot<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PDG_CUDA(cudaFuncSetAttribute(k_rowdot<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    }
+    upload(P.descs, descs, s);
+    upload(P.blk_u, cut, s);
+    PDG_CUDA(cudaStreamSynchronize(s));
+    P.host = std::move(descs);
+    P.n_blocks = C;
+}
 
 void launch_dd_solve(pd_mesh* m, const float4* b, float4* xout, cudaStream_t s, bool /*timed*/) {
     launch_dd_solve_scratch(m, b, xout, m->d_tc.p, m->d_cB.p, m->d_part.p, m->d_tc2.p, m->d_cT.p, s);

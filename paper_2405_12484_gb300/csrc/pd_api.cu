@@ -25,6 +25,7 @@ int dd_max_sub_cols();
 int dd_coarse_chunk();
 int dd_configure_coarse(int ld_S);
 int ax_outputs_per_block(int prec);
+void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s);
 void launch_prefactor_helpers_scatter_coo(double* S, int ld, const int* r, const int* c, const double* v, int n,
                                           cudaStream_t s);
 void launch_prefactor_add_block(double* S, int ldS, const double* Sd, int ldSd, const int* bidx, int nb,
@@ -37,33 +38,35 @@ void launch_copy_block_idx(const double* S, int ldS, int r0, int nr, const int* 
 static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 void phase_begin(pd_mesh* m, int phase, cudaStream_t s) {
-    if (!m->timing_armed || !(m->timing_mask & (1 << phase))) return;
-    size_t k = (size_t)m->ev_used;
-    if (2 * k + 1 >= m->ev_pool.size()) {
+    if (!m->timing_armed || !m->ev_rec || !(m->timing_mask & (1 << phase))) return;
+    pd_mesh::TimingSet& T = *m->ev_rec;
+    size_t k = (size_t)T.used;
+    if (2 * k + 1 >= T.ev.size()) {
         cudaEvent_t a, b;
         PDG_CUDA(cudaEventCreate(&a));
+        T.ev.push_back(a);
         PDG_CUDA(cudaEventCreate(&b));
-        m->ev_pool.push_back(a);
-        m->ev_pool.push_back(b);
+        T.ev.push_back(b);
     }
-    if (m->ev_phase.size() <= k) m->ev_phase.resize(k + 1);
-    m->ev_phase[k] = phase;
+    if (T.phase.size() <= k) T.phase.resize(k + 1);
+    T.phase[k] = phase;
     cudaStreamCaptureStatus st;
     PDG_CUDA(cudaStreamIsCapturing(s, &st));
     unsigned flags = (st == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : cudaEventRecordDefault;
-    PDG_CUDA(cudaEventRecordWithFlags(m->ev_pool[2 * k], s, flags));
+    PDG_CUDA(cudaEventRecordWithFlags(T.ev[2 * k], s, flags));
     m->ev_open = true;
 }
 
 void phase_end(pd_mesh* m, cudaStream_t s) {
-    if (!m->timing_armed || !m->ev_open) return;   // only close a pair opened by phase_begin
+    if (!m->timing_armed || !m->ev_open || !m->ev_rec) return;   // only close a pair opened by phase_begin
     m->ev_open = false;
-    size_t k = (size_t)m->ev_used;
+    pd_mesh::TimingSet& T = *m->ev_rec;
+    size_t k = (size_t)T.used;
     cudaStreamCaptureStatus st;
     PDG_CUDA(cudaStreamIsCapturing(s, &st));
     unsigned flags = (st == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : cudaEventRecordDefault;
-    PDG_CUDA(cudaEventRecordWithFlags(m->ev_pool[2 * k + 1], s, flags));
-    m->ev_used++;
+    PDG_CUDA(cudaEventRecordWithFlags(T.ev[2 * k + 1], s, flags));
+    T.used++;
 }
 
 }  // namespace pdg
@@ -73,7 +76,7 @@ using namespace pdg;
 pd_mesh::~pd_mesh() {
     for (auto& kv : graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-    for (auto e : ev_pool) cudaEventDestroy(e);
+    graphs.clear();   // the graphs' event sets after their executables
     if (cap_stream) cudaStreamDestroy(cap_stream);
 }
 
@@ -97,11 +100,6 @@ static pd_status fail(pd_status code, const std::string& msg) {
     return code;
 }
 
-template <class T>
-static void upload(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
-    d.alloc(h.size());
-    if (!h.empty()) PDG_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
-}
 
 static bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
@@ -843,17 +841,19 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         tc_off[d] = tcr;
         tcr += ni + nbd;
     }
+    // second level, row form: per group [S_II^-1; Psi2^T] ((n2 + nb) x n2, row o
+    // holds the coefficients of every c_I entry for output o) and Psi2 (n2 x nb)
     std::vector<int64_t> h2_off(G), t2_off(G);
     std::vector<int32_t> ldH2(G), ldT2(G), tc2_off(G);
     int32_t tc2r = 0;
     for (int g = 0; g < G; ++g) {
         const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
-        ldH2[g] = (int32_t)round_up(std::max(n2 + nb, 1), 8);
-        ldT2[g] = (int32_t)round_up(std::max(n2, 1), 8);
+        ldH2[g] = (int32_t)round_up(std::max(n2, 1), 8);
+        ldT2[g] = (int32_t)round_up(std::max(nb, 1), 8);
         h2_off[g] = pool;
-        pool += (int64_t)n2 * ldH2[g];
+        pool += (int64_t)(n2 + nb) * ldH2[g];
         t2_off[g] = pool;
-        pool += (int64_t)nb * ldT2[g];
+        pool += (int64_t)n2 * ldT2[g];
         pool = round_up(pool, 8);
         tc2_off[g] = tc2r;
         tc2r += n2 + nb;
@@ -893,9 +893,9 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             launch_cast_block(dX2ii.p + g * s2ii, NI2, n2, n2, 0, m->prec, m->d_mat32.p, m->d_mat16.p, h2_off[g],
                               ldH2[g], s);
             if (nb > 0) {
-                launch_cast_block(dPsi2.p + g * s2it, NB2, n2, nb, 0, m->prec, m->d_mat32.p, m->d_mat16.p,
-                                  h2_off[g] + n2, ldH2[g], s);
-                launch_cast_block(dPsi2.p + g * s2it, NB2, nb, n2, 1, m->prec, m->d_mat32.p, m->d_mat16.p, t2_off[g],
+                launch_cast_block(dPsi2.p + g * s2it, NB2, nb, n2, 1, m->prec, m->d_mat32.p, m->d_mat16.p,
+                                  h2_off[g] + (int64_t)n2 * ldH2[g], ldH2[g], s);
+                launch_cast_block(dPsi2.p + g * s2it, NB2, n2, nb, 0, m->prec, m->d_mat32.p, m->d_mat16.p, t2_off[g],
                                   ldT2[g], s);
             }
         }
@@ -955,46 +955,38 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     }
     m->n_tc = tcr;
     m->d_tc.alloc(std::max(tcr, 1));
-    m->ax_blocks_cond2 = m->ax_blocks_back2 = 0;
+    m->rows_cond2.n_blocks = m->rows_back2.n_blocks = 0;
+    m->rows_cond2.host.clear();
+    m->rows_back2.host.clear();
     if (two) {
-        const int OW = ax_outputs_per_block(m->prec);
-        std::vector<AxDesc> dc, db;
-        std::vector<AxBlock> bc, bb;
+        std::vector<RowDesc> dc, db;
         for (int g = 0; g < G; ++g) {
             const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
             if (n2 == 0) continue;
-            AxDesc c{};
+            RowDesc c{};
             c.a_off = h2_off[g];
+            c.rows = n2 + nb;
+            c.cols = n2;
+            c.ld = ldH2[g];
             c.x_off = i2_off[g];
-            c.bidx_off = -1;
+            c.xidx_off = -1;
             c.add_off = -1;
             c.out_off = tc2_off[g];
-            c.K = n2;
-            c.ld = ldH2[g];
-            c.n_out = n2 + nb;
-            for (int32_t o0 = 0; o0 < c.n_out; o0 += OW) bc.push_back(AxBlock{(int32_t)dc.size(), o0});
             dc.push_back(c);
-            AxDesc b{};
+            if (nb == 0) continue;
+            RowDesc b{};
             b.a_off = t2_off[g];
+            b.rows = n2;
+            b.cols = nb;
+            b.ld = ldT2[g];
             b.x_off = 0;
-            b.bidx_off = b2_off[g];
+            b.xidx_off = b2_off[g];
             b.add_off = tc2_off[g];
             b.out_off = i2_off[g];
-            b.K = nb;
-            b.ld = ldT2[g];
-            b.n_out = n2;
-            for (int32_t o0 = 0; o0 < b.n_out; o0 += OW) bb.push_back(AxBlock{(int32_t)db.size(), o0});
             db.push_back(b);
         }
-        upload(m->d_ax_desc_cond2, dc, s);
-        upload(m->d_ax_desc_back2, db, s);
-        upload(m->d_ax_blk_cond2, bc, s);
-        upload(m->d_ax_blk_back2, bb, s);
-        m->ax_blocks_cond2 = (int32_t)bc.size();
-        m->ax_blocks_back2 = (int32_t)bb.size();
-        m->ax_kmax_cond2 = m->ax_kmax_back2 = 1;
-        for (const auto& a : dc) m->ax_kmax_cond2 = std::max(m->ax_kmax_cond2, a.K);
-        for (const auto& a : db) m->ax_kmax_back2 = std::max(m->ax_kmax_back2, a.K);
+        build_row_plan(m->rows_cond2, dc, m->prec, s);
+        build_row_plan(m->rows_back2, db, m->prec, s);
         upload(m->d_bidx2, b2all, s);
         // top-level gather lists (groups in increasing order)
         std::vector<int32_t> gp(nT + 1, 0), gl;
@@ -1051,12 +1043,8 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         const int64_t ngat = nbd_tot;
         const int64_t colsS = (int64_t)round_up(std::max(m->cs_n, 1), VN);
         int64_t mat_c2 = 0, mat_b2 = 0;
-        for (int g = 0; g < G; ++g) {
-            const int64_t n2 = m->grp_n2[g], nb = (int64_t)b2[g].size();
-            if (n2 == 0) continue;
-            mat_c2 += n2 * round_up(n2 + nb, VN) * es;
-            mat_b2 += nb * round_up(n2, VN) * es;
-        }
+        for (const auto& d : m->rows_cond2.host) mat_c2 += (int64_t)d.rows * d.ld * es;
+        for (const auto& d : m->rows_back2.host) mat_b2 += (int64_t)d.rows * d.ld * es;
         for (int k = 0; k < 16; ++k) m->phase_bytes[k] = 0;
         m->phase_bytes[PH_INERTIA] = nv * 48 + nf * (16 + 4 + 16 + 4) + nkfp * 8 + (int64_t)m->n_pin * 16;
         m->phase_bytes[PH_LOCAL] = nt * (16 + 48 + 64) + nv * 16;
@@ -1075,7 +1063,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->phase_bytes[PH_RESIDUAL] = nk * (4 + 8 + 16) + nf * (4 + 16 + 16);
         m->phase_bytes[PH_VELOCITY] = nv * 48;
         int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (n_B > 0 ? 3 : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
-        if (two) dd += (m->ax_blocks_cond2 > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) + (m->ax_blocks_back2 > 0 ? 1 : 0);
+        if (two) dd += (m->rows_cond2.n_blocks > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) + (m->rows_back2.n_blocks > 0 ? 1 : 0);
         m->launches_per_iter = 2 + dd + (m->correction ? 2 : 0) + m->refine * (2 + dd);
     }
 
@@ -1172,8 +1160,10 @@ pd_status pd_step(pd_mesh* m, const float* pin_targets, const float* gravity, in
         auto it = m->graphs.find(key);
         if (it == m->graphs.end()) {
             cudaGraph_t graph = nullptr;
+            auto ts = std::make_shared<pd_mesh::TimingSet>();
             m->timing_armed = m->timing_mask != 0;
-            m->ev_used = 0;
+            m->ev_rec = ts.get();
+            m->ev_open = false;
             PDG_CUDA(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
             try {
                 run_frame(m, n_iter, g, m->cap_stream);
@@ -1181,27 +1171,36 @@ pd_status pd_step(pd_mesh* m, const float* pin_targets, const float* gravity, in
                 cudaStreamEndCapture(m->cap_stream, &graph);
                 if (graph) cudaGraphDestroy(graph);
                 m->timing_armed = false;
+                m->ev_rec = nullptr;
                 throw;
             }
             m->timing_armed = false;
+            m->ev_rec = nullptr;
             PDG_CUDA(cudaStreamEndCapture(m->cap_stream, &graph));
             cudaGraphExec_t exec = nullptr;
             cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             PDG_CUDA(e);
-            it = m->graphs.emplace(key, pd_mesh::GraphEntry{exec}).first;
+            it = m->graphs.emplace(key, pd_mesh::GraphEntry{exec, ts}).first;
         }
         PDG_CUDA(cudaGraphLaunch(it->second.exec, s));
+        m->ev_last = it->second.timing;
     } else {
+        if (!m->ev_plain) m->ev_plain = std::make_shared<pd_mesh::TimingSet>();
+        m->ev_plain->used = 0;
         m->timing_armed = m->timing_mask != 0;
-        m->ev_used = 0;
+        m->ev_rec = m->ev_plain.get();
+        m->ev_open = false;
         try {
             run_frame(m, n_iter, g, s);
         } catch (...) {
             m->timing_armed = false;
+            m->ev_rec = nullptr;
             throw;
         }
         m->timing_armed = false;
+        m->ev_rec = nullptr;
+        m->ev_last = m->ev_plain;
     }
     if (x_out) launch_scatter_out(m, m->d_x.p, x_out, 0, s);
     return PD_OK;
@@ -1250,8 +1249,8 @@ pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
     bytes += m->d_ax_blk_back.bytes() + m->d_tc.bytes() + m->d_bidx.bytes();
     bytes += m->d_gat_ptr.bytes() + m->d_gat.bytes() + m->d_cB.bytes() + m->d_part.bytes();
     bytes += m->d_K_ptr.bytes() + m->d_K_col.bytes() + m->d_K_val.bytes() + m->d_r.bytes() + m->d_dx.bytes();
-    bytes += m->d_ax_desc_cond2.bytes() + m->d_ax_desc_back2.bytes() + m->d_ax_blk_cond2.bytes();
-    bytes += m->d_ax_blk_back2.bytes() + m->d_bidx2.bytes() + m->d_gat2_ptr.bytes() + m->d_gat2.bytes();
+    bytes += m->rows_cond2.descs.bytes() + m->rows_cond2.blk_u.bytes() + m->rows_back2.descs.bytes();
+    bytes += m->rows_back2.blk_u.bytes() + m->d_bidx2.bytes() + m->d_gat2_ptr.bytes() + m->d_gat2.bytes();
     bytes += m->d_tc2.bytes() + m->d_cT.bytes();
     out->device_bytes = bytes;
     out->prefactor_seconds = m->prefactor_seconds;
@@ -1334,15 +1333,16 @@ pd_status pd_phase_times(pd_mesh* m, float* out, int32_t n_out, int32_t* n_phase
     std::vector<double> sum(PH_COUNT, 0.0);
     std::vector<int> cnt(PH_COUNT, 0);
     PDG_CUDA(cudaStreamSynchronize(m->stream));
-    for (int32_t k = 0; k < m->ev_used; ++k) {
+    const pd_mesh::TimingSet* T = m->ev_last.get();
+    for (int32_t k = 0; T && k < T->used; ++k) {
         float ms = 0.f;
-        cudaError_t e = cudaEventElapsedTime(&ms, m->ev_pool[2 * k], m->ev_pool[2 * k + 1]);
+        cudaError_t e = cudaEventElapsedTime(&ms, T->ev[2 * k], T->ev[2 * k + 1]);
         if (e != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
-        sum[m->ev_phase[k]] += ms;
-        cnt[m->ev_phase[k]]++;
+        sum[T->phase[k]] += ms;
+        cnt[T->phase[k]]++;
     }
     for (int32_t p = 0; p < n_out && p < PH_COUNT; ++p) out[p] = cnt[p] ? (float)(sum[p] / cnt[p]) : 0.f;
     return PD_OK;

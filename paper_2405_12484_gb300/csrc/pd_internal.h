@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 #include <map>
+#include <memory>
 
 #include "../../include/pd.h"
 
@@ -59,6 +60,14 @@ struct DBuf {
     DBuf& operator=(const DBuf&) = delete;
 };
 
+// Host vector -> new device buffer (asynchronous on s; pageable sources are
+// staged before the call returns).
+template <class T>
+inline void upload(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
+    d.alloc(h.size());
+    if (!h.empty()) PDG_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
 // Column-oriented per-domain product y[o] = add[o] + sum_k A[k][o] x_k: base
 // pointers of one launch (or of one serving slot) and the offsets of one
 // domain matrix into them.
@@ -80,6 +89,27 @@ struct AxDesc {
 };
 struct AxBlock {
     int32_t desc, o0;      // descriptor and first output of one block
+};
+
+// Row-oriented product out[r] = add[r] + A[r, 0:cols] . x of one dense block
+// (offsets into AxBases, as for AxDesc); u0 = first unit of the block in the
+// concatenated unit list of its launch.
+struct RowDesc {
+    int64_t a_off;         // pool offset of row 0
+    int64_t u0;
+    int32_t rows, cols, ld;
+    int32_t x_off;         // x offset (contiguous source)
+    int32_t xidx_off;      // >= 0: x_k = x[bidx[xidx_off + k]]
+    int32_t add_off;       // >= 0: add offset
+    int32_t out_off;
+    int32_t pad;
+};
+// One row-form launch: its descriptors and the unit range of every block.
+struct RowPlan {
+    DBuf<RowDesc> descs;
+    DBuf<int64_t> blk_u;
+    int n_desc = 0, n_blocks = 0, xcap = 8;
+    std::vector<RowDesc> host;     // host copy (byte accounting)
 };
 
 // One resident request of the serving loop, as the batched kernels see it.
@@ -178,9 +208,7 @@ struct pd_mesh {
     // second level (groups of domains): condensation onto the top-level interface
     bool two_level = false;
     int32_t cs_n = 0;                                       // rows of the dense coarse inverse in the pool
-    pdg::DBuf<pdg::AxDesc> d_ax_desc_cond2, d_ax_desc_back2;
-    pdg::DBuf<pdg::AxBlock> d_ax_blk_cond2, d_ax_blk_back2;
-    int32_t ax_blocks_cond2 = 0, ax_blocks_back2 = 0, ax_kmax_cond2 = 1, ax_kmax_back2 = 1;
+    pdg::RowPlan rows_cond2, rows_back2;   // row-form launches of the second level
     pdg::DBuf<int32_t> d_bidx2, d_gat2_ptr, d_gat2;
     pdg::DBuf<float4> d_tc2, d_cT;
     int32_t n_tc2 = 0, n_gat2 = 0;
@@ -207,17 +235,29 @@ struct pd_mesh {
     int64_t phase_bytes[16] = {0};
     int32_t launches_per_iter = 0;
 
-    // graphs: key = (n_iter, gravity bits)
+    // per-phase timing: the event pairs recorded by one captured graph (or by
+    // the plain launches); each graph owns its set, so replaying one graph never
+    // reads events that another graph's capture assigned to other phases
+    struct TimingSet {
+        std::vector<cudaEvent_t> ev;      // pairs (start, stop)
+        std::vector<int32_t> phase;       // phase of each pair
+        int32_t used = 0;
+        ~TimingSet() {
+            for (auto e : ev) cudaEventDestroy(e);
+        }
+    };
+
+    // graphs: key = (n_iter, gravity bits, refinement steps, timing mask)
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
+        std::shared_ptr<TimingSet> timing;
     };
     std::map<std::vector<uint32_t>, GraphEntry> graphs;
 
-    // timing
     int32_t timing_mask = 0;
-    std::vector<cudaEvent_t> ev_pool;       // pairs (start, stop)
-    std::vector<int32_t> ev_phase;          // phase of each pair
-    int32_t ev_used = 0;
+    TimingSet* ev_rec = nullptr;                  // set being recorded into (during capture / plain launches)
+    std::shared_ptr<TimingSet> ev_plain;          // set of the plain launches
+    std::shared_ptr<TimingSet> ev_last;           // set of the last frame launched (read by pd_phase_times)
     bool timing_armed = false;
     bool ev_open = false;
 
