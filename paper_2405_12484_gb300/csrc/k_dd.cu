@@ -120,14 +120,46 @@ constexpr int kMaxSubCols = 2048;   // largest per-domain internal / boundary co
 // shared-memory broadcast, and the warps' partial sums are combined in a
 // fixed order (deterministic).  No cross-lane reductions, fully coalesced
 // 16-byte row loads.
-constexpr int kAxWarps = 8;
+#ifndef PDG_AX_WARPS
+#define PDG_AX_WARPS 8
+#endif
+#ifndef PDG_AX_UNROLL
+#define PDG_AX_UNROLL 4
+#endif
+#ifndef PDG_ROW_UNROLL
+#define PDG_ROW_UNROLL 4
+#endif
+#ifndef PDG_ROW_WARPS
+#define PDG_ROW_WARPS 16
+#endif
+#ifndef PDG_ROW_BPS
+#define PDG_ROW_BPS 2
+#endif
+#ifndef PDG_ROW_RU32
+#define PDG_ROW_RU32 1
+#endif
+#ifndef PDG_COARSE_BPS
+#define PDG_COARSE_BPS 2
+#endif
+#ifndef PDG_AX_M
+#define PDG_AX_M 1
+#endif
+constexpr int kRowWarps = PDG_ROW_WARPS;
+constexpr int kRowBps = PDG_ROW_BPS;
+constexpr int kRowRu32 = PDG_ROW_RU32;
+constexpr int kCoarseBps = PDG_COARSE_BPS;
+constexpr int kAxM = PDG_AX_M;
+constexpr int kAxWarps = PDG_AX_WARPS;
+constexpr int kAxUnroll = PDG_AX_UNROLL;
+constexpr int kRowUnroll = PDG_ROW_UNROLL;
 
 template <class T, bool BATCHED>
 __global__ void __launch_bounds__(32 * kAxWarps) k_axpy_form(const AxDesc* __restrict__ descs,
                                                               const AxBlock* __restrict__ blocks, AxBases single,
                                                               const AxBases* __restrict__ multi) {
     constexpr int VN = VecN<T>::N;
-    constexpr int OW = 32 * VN;
+    constexpr int SW = 32 * VN;          // outputs of one warp-wide sub-chunk
+    constexpr int OW = SW * kAxM;        // outputs of the block
     extern __shared__ float4 xs[];   // K_max entries (dynamic)
     __shared__ float red[kAxWarps - 1][OW][3];
     const AxBlock bk = blocks[blockIdx.x];
@@ -138,52 +170,64 @@ __global__ void __launch_bounds__(32 * kAxWarps) k_axpy_form(const AxDesc* __res
     for (int k = threadIdx.x; k < D.K; k += blockDim.x) xs[k] = (D.bidx_off >= 0) ? x[B.bidx[D.bidx_off + k]] : x[k];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int o = bk.o0 + lane * VN;              // first output of this lane
     const int k0 = D.K * warp / kAxWarps, k1 = D.K * (warp + 1) / kAxWarps;
-    float acc[VN][3];
+    float acc[kAxM][VN][3];
 #pragma unroll
-    for (int i = 0; i < VN; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
-    if (o < D.n_out) {
-        const T* a = A + o;
-#pragma unroll 4
+    for (int j = 0; j < kAxM; ++j)
+#pragma unroll
+        for (int i = 0; i < VN; ++i) acc[j][i][0] = acc[j][i][1] = acc[j][i][2] = 0.f;
+    bool valid[kAxM];
+#pragma unroll
+    for (int j = 0; j < kAxM; ++j) valid[j] = bk.o0 + j * SW + lane * VN < D.n_out;
+    if (valid[0]) {
+        const T* a = A + bk.o0 + lane * VN;
+#pragma unroll kAxUnroll
         for (int k = k0; k < k1; ++k) {
-            float v[VN];
-            load_vec(a + (int64_t)k * D.ld, v);
             const float4 xk = xs[k];
 #pragma unroll
-            for (int i = 0; i < VN; ++i) {
-                acc[i][0] = fmaf(v[i], xk.x, acc[i][0]);
-                acc[i][1] = fmaf(v[i], xk.y, acc[i][1]);
-                acc[i][2] = fmaf(v[i], xk.z, acc[i][2]);
+            for (int j = 0; j < kAxM; ++j) {
+                if (!valid[j]) continue;
+                float v[VN];
+                load_vec(a + (int64_t)k * D.ld + j * SW, v);
+#pragma unroll
+                for (int i = 0; i < VN; ++i) {
+                    acc[j][i][0] = fmaf(v[i], xk.x, acc[j][i][0]);
+                    acc[j][i][1] = fmaf(v[i], xk.y, acc[j][i][1]);
+                    acc[j][i][2] = fmaf(v[i], xk.z, acc[j][i][2]);
+                }
             }
         }
     }
     if (warp > 0) {
 #pragma unroll
-        for (int i = 0; i < VN; ++i) {
-            red[warp - 1][lane * VN + i][0] = acc[i][0];
-            red[warp - 1][lane * VN + i][1] = acc[i][1];
-            red[warp - 1][lane * VN + i][2] = acc[i][2];
-        }
+        for (int j = 0; j < kAxM; ++j)
+#pragma unroll
+            for (int i = 0; i < VN; ++i) {
+                red[warp - 1][j * SW + lane * VN + i][0] = acc[j][i][0];
+                red[warp - 1][j * SW + lane * VN + i][1] = acc[j][i][1];
+                red[warp - 1][j * SW + lane * VN + i][2] = acc[j][i][2];
+            }
     }
     __syncthreads();
     if (warp == 0) {
         float4* out = B.out + D.out_off;
         const float4* add = (D.add_off >= 0) ? B.add + D.add_off : nullptr;
 #pragma unroll
-        for (int i = 0; i < VN; ++i) {
-            const int oi = o + i;
-            if (oi >= D.n_out) break;
-            float r0 = acc[i][0], r1 = acc[i][1], r2 = acc[i][2];
+        for (int j = 0; j < kAxM; ++j)
 #pragma unroll
-            for (int w = 0; w < kAxWarps - 1; ++w) {
-                r0 += red[w][lane * VN + i][0];
-                r1 += red[w][lane * VN + i][1];
-                r2 += red[w][lane * VN + i][2];
+            for (int i = 0; i < VN; ++i) {
+                const int oi = bk.o0 + j * SW + lane * VN + i;
+                if (oi >= D.n_out) break;
+                float r0 = acc[j][i][0], r1 = acc[j][i][1], r2 = acc[j][i][2];
+#pragma unroll
+                for (int w = 0; w < kAxWarps - 1; ++w) {
+                    r0 += red[w][j * SW + lane * VN + i][0];
+                    r1 += red[w][j * SW + lane * VN + i][1];
+                    r2 += red[w][j * SW + lane * VN + i][2];
+                }
+                const float4 b = add ? add[oi] : make_float4(0.f, 0.f, 0.f, 0.f);
+                out[oi] = make_float4(b.x + r0, b.y + r1, b.z + r2, 0.f);
             }
-            const float4 b = add ? add[oi] : make_float4(0.f, 0.f, 0.f, 0.f);
-            out[oi] = make_float4(b.x + r0, b.y + r1, b.z + r2, 0.f);
-        }
     }
 }
 
@@ -240,7 +284,7 @@ struct CoarseRows<__nv_bfloat16> {
 };
 
 template <class T>
-__global__ void __launch_bounds__(512, 1) k_coarse_bal(const T* __restrict__ S, int n_B, int ld, int cols, int nch,
+__global__ void __launch_bounds__(512, kCoarseBps) k_coarse_bal(const T* __restrict__ S, int n_B, int ld, int cols, int nch,
                                                         const float4* __restrict__ cB, float4* __restrict__ part) {
     extern __shared__ float xsm[];
     float* x0 = xsm;
@@ -395,7 +439,16 @@ __global__ void __launch_bounds__(512, 1) k_coarse_b(const CoarseDescB* __restri
 // warps.  A unit is a full row dot product: lanes stride the row with 16-byte
 // loads, a fixed-order shuffle tree combines them (deterministic).
 template <class T>
-__global__ void __launch_bounds__(32 * kCoarseWarps, 1) k_rowdot(const RowDesc* __restrict__ descs, int n_desc,
+struct RowRows {
+    static constexpr int R = 4;
+};
+template <>
+struct RowRows<float> {
+    static constexpr int R = kRowRu32;
+};
+
+template <class T>
+__global__ void __launch_bounds__(32 * kRowWarps, kRowBps) k_rowdot(const RowDesc* __restrict__ descs, int n_desc,
                                                                 const int64_t* __restrict__ blk_u, AxBases B,
                                                                 int xcap) {
     extern __shared__ float xsm[];
@@ -403,7 +456,7 @@ __global__ void __launch_bounds__(32 * kCoarseWarps, 1) k_rowdot(const RowDesc* 
     float* x1 = xsm + xcap;
     float* x2 = xsm + 2 * xcap;
     constexpr int VN = VecN<T>::N;
-    constexpr int RU = CoarseRows<T>::R;
+    constexpr int RU = RowRows<T>::R;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int64_t b0 = blk_u[blockIdx.x], b1 = blk_u[blockIdx.x + 1];
@@ -424,7 +477,7 @@ __global__ void __launch_bounds__(32 * kCoarseWarps, 1) k_rowdot(const RowDesc* 
         }
         __syncthreads();
         const int64_t n = hi - lo;
-        const int64_t w0 = lo + n * warp / kCoarseWarps, w1 = lo + n * (warp + 1) / kCoarseWarps;
+        const int64_t w0 = lo + n * warp / kRowWarps, w1 = lo + n * (warp + 1) / kRowWarps;
         for (int64_t u = w0; u < w1; ++u) {
             const int r0 = RU * (int)(u - D.u0);
             const T* a[RU];
@@ -433,7 +486,7 @@ __global__ void __launch_bounds__(32 * kCoarseWarps, 1) k_rowdot(const RowDesc* 
             float acc[RU][3];
 #pragma unroll
             for (int k = 0; k < RU; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
-#pragma unroll 4
+#pragma unroll kRowUnroll
             for (int c = lane * VN; c < D.ld; c += 32 * VN) {
                 float v[RU][VN];
 #pragma unroll
@@ -540,7 +593,7 @@ void launch_ax(const AxDesc* descs, const AxBlock* blocks, int n_blocks, int k_m
 template <class T>
 void launch_rowdot(const RowPlan& P, const AxBases& B, cudaStream_t s) {
     if (P.n_blocks <= 0) return;
-    k_rowdot<T><<<P.n_blocks, 32 * kCoarseWarps, sizeof(float) * 3 * (size_t)P.xcap, s>>>(P.descs.p, P.n_desc,
+    k_rowdot<T><<<P.n_blocks, 32 * kRowWarps, sizeof(float) * 3 * (size_t)P.xcap, s>>>(P.descs.p, P.n_desc,
                                                                                          P.blk_u.p, B, P.xcap);
     PDG_CHECK_LAUNCH();
 }
@@ -552,6 +605,18 @@ struct DDBufs {
 // One subspace solve: x (free vertices of xout) = K_ff^-1 b.
 template <class T>
 void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, const DDBufs& w, cudaStream_t s) {
+    // the interior part t = K_ii^-1 b_i runs on a side stream beside the
+    // interface solve and is joined before the back-substitution
+    const bool fork1 = m->ax_blocks_int > 0;
+    if (fork1) {
+        PDG_CUDA(cudaEventRecord(m->ev_fork[0], s));
+        PDG_CUDA(cudaStreamWaitEvent(m->side[0], m->ev_fork[0], 0));
+        phase_begin(m, PH_INTERIOR, m->side[0]);
+        launch_ax<T>(m->d_ax_desc_int.p, m->d_ax_blk_int.p, m->ax_blocks_int, m->ax_kmax_int,
+                     AxBases{pool, b, nullptr, nullptr, w.tc}, m->side[0]);
+        phase_end(m, m->side[0]);
+        PDG_CUDA(cudaEventRecord(m->ev_join[0], m->side[0]));
+    }
     if (m->ax_blocks_cond > 0) {
         phase_begin(m, PH_CONDENSE, s);
         launch_ax<T>(m->d_ax_desc_cond.p, m->d_ax_blk_cond.p, m->ax_blocks_cond, m->ax_kmax_cond,
@@ -566,7 +631,17 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
         const float4* cin = w.cB;
         float4* xcs = xout + m->n_int;
         const int T0 = m->n_B - m->n_top;
+        bool fork2 = false;
         if (m->two_level) {
+            fork2 = m->rows_int2.n_blocks > 0;
+            if (fork2) {
+                PDG_CUDA(cudaEventRecord(m->ev_fork[1], s));
+                PDG_CUDA(cudaStreamWaitEvent(m->side[1], m->ev_fork[1], 0));
+                phase_begin(m, PH_INTERIOR2, m->side[1]);
+                launch_rowdot<T>(m->rows_int2, AxBases{pool, w.cB, nullptr, nullptr, w.tc2}, m->side[1]);
+                phase_end(m, m->side[1]);
+                PDG_CUDA(cudaEventRecord(m->ev_join[1], m->side[1]));
+            }
             phase_begin(m, PH_CONDENSE2, s);
             launch_rowdot<T>(m->rows_cond2, AxBases{pool, w.cB, nullptr, nullptr, w.tc2}, s);
             phase_end(m, s);
@@ -586,12 +661,14 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
         PDG_CHECK_LAUNCH();
         phase_end(m, s);
         if (m->two_level) {
+            if (fork2) PDG_CUDA(cudaStreamWaitEvent(s, m->ev_join[1], 0));
             phase_begin(m, PH_BACKSUB2, s);
             launch_rowdot<T>(m->rows_back2, AxBases{pool, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int},
                              s);
             phase_end(m, s);
         }
     }
+    if (fork1) PDG_CUDA(cudaStreamWaitEvent(s, m->ev_join[0], 0));
     if (m->ax_blocks_back > 0) {
         phase_begin(m, PH_BACKSUB, s);
         launch_ax<T>(m->d_ax_desc_back.p, m->d_ax_blk_back.p, m->ax_blocks_back, m->ax_kmax_back,
@@ -617,7 +694,7 @@ void launch_axpy_b(const AxDesc* descs, const AxBlock* blocks, const AxBases* ba
     PDG_CHECK_LAUNCH();
 }
 
-int ax_outputs_per_block(int prec) { return 32 * (prec == PD_PREC_BF16 ? 8 : 4); }
+int ax_outputs_per_block(int prec) { return 32 * kAxM * (prec == PD_PREC_BF16 ? 8 : 4); }
 
 // Returns false when the largest interface vector does not fit in shared memory.
 bool configure_coarse_b(int max_cols) {
@@ -650,11 +727,12 @@ int dd_configure_coarse(int ld_S) {
     PDG_CUDA(cudaFuncSetAttribute(k_coarse_bal<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PDG_CUDA(cudaFuncSetAttribute(k_coarse_bal<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-    return sms;
+    const int bps = (smem * kCoarseBps <= (size_t)optin) ? kCoarseBps : 1;
+    return sms * bps;
 }
 int dd_coarse_chunk() { return kCoarseChunk; }
 
-int rowdot_rows_per_unit(int prec) { return prec == PD_PREC_BF16 ? CoarseRows<__nv_bfloat16>::R : CoarseRows<float>::R; }
+int rowdot_rows_per_unit(int prec) { return prec == PD_PREC_BF16 ? RowRows<__nv_bfloat16>::R : RowRows<float>::R; }
 
 // Unit numbering and block cuts of a row-form launch: block b gets the units
 // whose cumulative cost (matrix columns streamed plus a fixed per-unit cost)
@@ -678,7 +756,7 @@ void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream
     int dev = 0, sms = 0;
     PDG_CUDA(cudaGetDevice(&dev));
     PDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int C = std::max(1, sms);
+    const int C = std::max(1, sms) * kRowBps;
     std::vector<int64_t> cut(C + 1, u);
     cut[0] = 0;
     double acc = 0.0;

@@ -78,6 +78,11 @@ pd_mesh::~pd_mesh() {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     graphs.clear();   // the graphs' event sets after their executables
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (int k = 0; k < 2; ++k) {
+        if (side[k]) cudaStreamDestroy(side[k]);
+        if (ev_fork[k]) cudaEventDestroy(ev_fork[k]);
+        if (ev_join[k]) cudaEventDestroy(ev_join[k]);
+    }
 }
 
 #define PD_API_BEGIN try {
@@ -221,7 +226,8 @@ const char* pd_last_error(void) { return g_last_error.c_str(); }
 
 static const char* kPhaseNames[PH_COUNT] = {"inertia",      "local",      "assemble",   "dd_condense", "dd_gather",
                                             "dd_coarse",    "dd_reduce",  "dd_backsub", "residual",    "velocity",
-                                            "dd_condense2", "dd_gather2", "dd_backsub2"};
+                                            "dd_condense2", "dd_gather2", "dd_backsub2", "dd_interior",
+                                            "dd_interior2"};
 
 const char* pd_phase_name(int32_t k) { return (k >= 0 && k < PH_COUNT) ? kPhaseNames[k] : "?"; }
 
@@ -512,6 +518,11 @@ pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tet
 
     // ---- device uploads: topology, geometry, state (first CUDA call of the set-up)
     PDG_CUDA(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        PDG_CUDA(cudaStreamCreateWithFlags(&m->side[k], cudaStreamNonBlocking));
+        PDG_CUDA(cudaEventCreateWithFlags(&m->ev_fork[k], cudaEventDisableTiming));
+        PDG_CUDA(cudaEventCreateWithFlags(&m->ev_join[k], cudaEventDisableTiming));
+    }
     cudaStream_t s = m->stream;
     std::vector<int4> ht(n_t);
     std::vector<float4> hg(3 * (size_t)n_t);
@@ -825,19 +836,24 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     m->refine = o.refine_steps;
     m->correction = (o.flags & PD_SOLVE_CORRECTION) != 0;
     m->use_graphs = o.use_graphs != 0;
-    std::vector<int64_t> h_off(n_dom), t_off(n_dom);
-    std::vector<int32_t> ldH(n_dom), ldT(n_dom), tc_off(n_dom);
+    // per domain: K_ii^-1 (n_i x n_i), Psi_d (n_i x n_bd, row k = coefficients of
+    // b_k for every boundary mode) and Psi_d^T (n_bd x n_i); row strides rounded
+    // to 8 entries so every row starts on a 16-byte boundary
+    std::vector<int64_t> h_off(n_dom), p_off(n_dom), t_off(n_dom);
+    std::vector<int32_t> ldH(n_dom), ldP(n_dom), ldT(n_dom), tc_off(n_dom);
     int64_t pool = 0;
     int32_t tcr = 0;
     for (int32_t d = 0; d < n_dom; ++d) {
         const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
-        ldH[d] = (int32_t)round_up(std::max(ni + nbd, 1), 8);
-        ldT[d] = (int32_t)round_up(std::max(ni, 1), 8);
+        ldH[d] = (int32_t)round_up(std::max(ni, 1), 8);
+        ldP[d] = (int32_t)round_up(std::max(nbd, 1), 8);
+        ldT[d] = ldH[d];
         h_off[d] = pool;
         pool += (int64_t)ni * ldH[d];
+        p_off[d] = pool;
+        pool += (int64_t)ni * ldP[d];
         t_off[d] = pool;
         pool += (int64_t)nbd * ldT[d];
-        pool = round_up(pool, 8);
         tc_off[d] = tcr;
         tcr += ni + nbd;
     }
@@ -879,7 +895,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         const double* Pd = dPsi.p + (size_t)d * sKib;
         launch_cast_block(Xd, NI, ni, ni, 0, m->prec, m->d_mat32.p, m->d_mat16.p, h_off[d], ldH[d], s);
         if (nbd > 0) {
-            launch_cast_block(Pd, NBp, ni, nbd, 0, m->prec, m->d_mat32.p, m->d_mat16.p, h_off[d] + ni, ldH[d], s);
+            launch_cast_block(Pd, NBp, ni, nbd, 0, m->prec, m->d_mat32.p, m->d_mat16.p, p_off[d], ldP[d], s);
             launch_cast_block(Pd, NBp, nbd, ni, 1, m->prec, m->d_mat32.p, m->d_mat16.p, t_off[d], ldT[d], s);
         }
     }
@@ -910,23 +926,35 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     for (int32_t d = 0; d < n_dom; ++d) bidx.insert(bidx.end(), m->dom_bnd[d].begin(), m->dom_bnd[d].end());
     upload(m->d_bidx, bidx, s);
     {
+        // condensation split in two launches: the boundary modes c_d = Psi_d^T b_i
+        // (on the path to the interface solve) and the interior part
+        // t_d = K_ii^-1 b_i (needed only by the back-substitution)
         const int OW = ax_outputs_per_block(m->prec);
-        std::vector<AxDesc> dc, db;
-        std::vector<AxBlock> bc, bb;
+        std::vector<AxDesc> dc, di, db;
+        std::vector<AxBlock> bc, bi, bb;
         for (int32_t d = 0; d < n_dom; ++d) {
             const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
             if (ni == 0) continue;
             AxDesc c{};
-            c.a_off = h_off[d];
+            c.a_off = p_off[d];
             c.x_off = m->dom_int_off[d];
             c.bidx_off = -1;
             c.add_off = -1;
-            c.out_off = tc_off[d];
+            c.out_off = tc_off[d] + ni;
             c.K = ni;
-            c.ld = ldH[d];
-            c.n_out = ni + nbd;
-            for (int32_t o0 = 0; o0 < c.n_out; o0 += OW) bc.push_back(AxBlock{(int32_t)dc.size(), o0});
-            dc.push_back(c);
+            c.ld = ldP[d];
+            c.n_out = nbd;
+            if (nbd > 0) {
+                for (int32_t o0 = 0; o0 < c.n_out; o0 += OW) bc.push_back(AxBlock{(int32_t)dc.size(), o0});
+                dc.push_back(c);
+            }
+            AxDesc t = c;
+            t.a_off = h_off[d];
+            t.out_off = tc_off[d];
+            t.ld = ldH[d];
+            t.n_out = ni;
+            for (int32_t o0 = 0; o0 < t.n_out; o0 += OW) bi.push_back(AxBlock{(int32_t)di.size(), o0});
+            di.push_back(t);
             AxDesc b{};
             b.a_off = t_off[d];
             b.x_off = 0;
@@ -940,40 +968,54 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             db.push_back(b);
         }
         upload(m->d_ax_desc_cond, dc, s);
+        upload(m->d_ax_desc_int, di, s);
         upload(m->d_ax_desc_back, db, s);
         upload(m->d_ax_blk_cond, bc, s);
+        upload(m->d_ax_blk_int, bi, s);
         upload(m->d_ax_blk_back, bb, s);
         m->ax_blocks_cond = (int32_t)bc.size();
+        m->ax_blocks_int = (int32_t)bi.size();
         m->ax_blocks_back = (int32_t)bb.size();
+        // host copies for the serving batches: both condensation parts in one launch
         m->h_ax_desc_cond = dc;
+        m->h_ax_desc_cond.insert(m->h_ax_desc_cond.end(), di.begin(), di.end());
         m->h_ax_desc_back = db;
-        m->ax_kmax_cond = 1;
-        m->ax_kmax_back = 1;
+        m->ax_kmax_cond = m->ax_kmax_int = m->ax_kmax_back = 1;
         for (const auto& a : dc) m->ax_kmax_cond = std::max(m->ax_kmax_cond, a.K);
+        for (const auto& a : di) m->ax_kmax_int = std::max(m->ax_kmax_int, a.K);
         for (const auto& a : db) m->ax_kmax_back = std::max(m->ax_kmax_back, a.K);
         (void)VN;
     }
     m->n_tc = tcr;
     m->d_tc.alloc(std::max(tcr, 1));
-    m->rows_cond2.n_blocks = m->rows_back2.n_blocks = 0;
+    m->rows_cond2.n_blocks = m->rows_int2.n_blocks = m->rows_back2.n_blocks = 0;
     m->rows_cond2.host.clear();
+    m->rows_int2.host.clear();
     m->rows_back2.host.clear();
     if (two) {
-        std::vector<RowDesc> dc, db;
+        // [S_II^-1; Psi2^T] split by rows: the Psi2^T rows give the top-level
+        // condensation c2 (on the path to the coarse solve), the S_II^-1 rows
+        // the interior part t2 (needed only by the second-level back-substitution)
+        std::vector<RowDesc> dc, di, db;
         for (int g = 0; g < G; ++g) {
             const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
             if (n2 == 0) continue;
-            RowDesc c{};
-            c.a_off = h2_off[g];
-            c.rows = n2 + nb;
-            c.cols = n2;
-            c.ld = ldH2[g];
-            c.x_off = i2_off[g];
-            c.xidx_off = -1;
-            c.add_off = -1;
-            c.out_off = tc2_off[g];
-            dc.push_back(c);
+            RowDesc t{};
+            t.a_off = h2_off[g];
+            t.rows = n2;
+            t.cols = n2;
+            t.ld = ldH2[g];
+            t.x_off = i2_off[g];
+            t.xidx_off = -1;
+            t.add_off = -1;
+            t.out_off = tc2_off[g];
+            di.push_back(t);
             if (nb == 0) continue;
+            RowDesc c = t;
+            c.a_off = h2_off[g] + (int64_t)n2 * ldH2[g];
+            c.rows = nb;
+            c.out_off = tc2_off[g] + n2;
+            dc.push_back(c);
             RowDesc b{};
             b.a_off = t2_off[g];
             b.rows = n2;
@@ -986,6 +1028,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             db.push_back(b);
         }
         build_row_plan(m->rows_cond2, dc, m->prec, s);
+        build_row_plan(m->rows_int2, di, m->prec, s);
         build_row_plan(m->rows_back2, db, m->prec, s);
         upload(m->d_bidx2, b2all, s);
         // top-level gather lists (groups in increasing order)
@@ -1033,8 +1076,13 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     // ---- algorithmic bytes per launch of each phase (each array counted once)
     {
         const int64_t es = (m->prec == PD_PREC_BF16) ? 2 : 4;
-        int64_t mat_c = 0, mat_b = 0, nbd_tot = 0;
-        for (const auto& a : m->h_ax_desc_cond) mat_c += (int64_t)a.K * round_up(a.n_out, VN) * es;
+        int64_t mat_c = 0, mat_i = 0, mat_b = 0, nbd_tot = 0;
+        for (int32_t d = 0; d < n_dom; ++d) {
+            const int64_t ni = m->dom_n_int[d], nbd = (int64_t)m->dom_bnd[d].size();
+            if (ni == 0) continue;
+            mat_c += ni * round_up(nbd, VN) * es;
+            mat_i += ni * round_up(ni, VN) * es;
+        }
         for (const auto& a : m->h_ax_desc_back) mat_b += (int64_t)a.K * round_up(a.n_out, VN) * es;
         for (int32_t d = 0; d < n_dom; ++d)
             if (m->dom_n_int[d] > 0) nbd_tot += (int64_t)m->dom_bnd[d].size();
@@ -1042,28 +1090,34 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         const int64_t nkfp = (int64_t)m->Kfp_col.size(), nk = (int64_t)m->K_col.size();
         const int64_t ngat = nbd_tot;
         const int64_t colsS = (int64_t)round_up(std::max(m->cs_n, 1), VN);
-        int64_t mat_c2 = 0, mat_b2 = 0;
+        int64_t mat_c2 = 0, mat_i2 = 0, mat_b2 = 0;
         for (const auto& d : m->rows_cond2.host) mat_c2 += (int64_t)d.rows * d.ld * es;
+        for (const auto& d : m->rows_int2.host) mat_i2 += (int64_t)d.rows * d.ld * es;
         for (const auto& d : m->rows_back2.host) mat_b2 += (int64_t)d.rows * d.ld * es;
         for (int k = 0; k < 16; ++k) m->phase_bytes[k] = 0;
         m->phase_bytes[PH_INERTIA] = nv * 48 + nf * (16 + 4 + 16 + 4) + nkfp * 8 + (int64_t)m->n_pin * 16;
         m->phase_bytes[PH_LOCAL] = nt * (16 + 48 + 64) + nv * 16;
         m->phase_bytes[PH_ASSEMBLE] = nf * (4 + 16 + 16) + ninc * (4 + 16);
-        m->phase_bytes[PH_CONDENSE] = mat_c + (int64_t)n_int * 16 + (int64_t)tcr * 16;
+        m->phase_bytes[PH_CONDENSE] = mat_c + (int64_t)n_int * 16 + nbd_tot * 16;
+        m->phase_bytes[PH_INTERIOR] = mat_i + (int64_t)n_int * 32;
         m->phase_bytes[PH_GATHER] = (int64_t)n_B * (4 + 16 + 16) + ngat * (4 + 16);
         const int64_t ncs = m->cs_n;
         m->phase_bytes[PH_COARSE] = ncs * colsS * es + ncs * 16 + (int64_t)m->coarse_nchunks * ncs * 16;
         m->phase_bytes[PH_REDUCE] = (int64_t)m->coarse_nchunks * ncs * 16 + ncs * 16;
         if (two) {
-            m->phase_bytes[PH_CONDENSE2] = mat_c2 + (int64_t)(n_B - nT) * 16 + (int64_t)m->n_tc2 * 16;
+            m->phase_bytes[PH_CONDENSE2] = mat_c2 + (int64_t)(n_B - nT) * 16 + (int64_t)b2all.size() * 16;
+            m->phase_bytes[PH_INTERIOR2] = mat_i2 + (int64_t)(n_B - nT) * 32;
             m->phase_bytes[PH_GATHER2] = (int64_t)nT * (4 + 16 + 16) + (int64_t)m->n_gat2 * (4 + 16);
             m->phase_bytes[PH_BACKSUB2] = mat_b2 + (int64_t)b2all.size() * (4 + 16) + (int64_t)(n_B - nT) * 32;
         }
         m->phase_bytes[PH_BACKSUB] = mat_b + nbd_tot * (4 + 16) + (int64_t)n_int * 32;
         m->phase_bytes[PH_RESIDUAL] = nk * (4 + 8 + 16) + nf * (4 + 16 + 16);
         m->phase_bytes[PH_VELOCITY] = nv * 48;
-        int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (n_B > 0 ? 3 : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
-        if (two) dd += (m->rows_cond2.n_blocks > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) + (m->rows_back2.n_blocks > 0 ? 1 : 0);
+        int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (m->ax_blocks_int > 0 ? 1 : 0) + (n_B > 0 ? 3 : 0) +
+                 (m->ax_blocks_back > 0 ? 1 : 0);
+        if (two)
+            dd += (m->rows_cond2.n_blocks > 0 ? 1 : 0) + (m->rows_int2.n_blocks > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) +
+                  (m->rows_back2.n_blocks > 0 ? 1 : 0);
         m->launches_per_iter = 2 + dd + (m->correction ? 2 : 0) + m->refine * (2 + dd);
     }
 
@@ -1246,6 +1300,7 @@ pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
     bytes += m->d_inc_ptr.bytes() + m->d_inc.bytes() + m->d_kfp_ptr.bytes() + m->d_kfp_col.bytes();
     bytes += m->d_kfp_val.bytes() + m->d_old_of_new.bytes() + m->d_mat32.bytes() + m->d_mat16.bytes();
     bytes += m->d_ax_desc_cond.bytes() + m->d_ax_desc_back.bytes() + m->d_ax_blk_cond.bytes();
+    bytes += m->d_ax_desc_int.bytes() + m->d_ax_blk_int.bytes() + m->rows_int2.descs.bytes() + m->rows_int2.blk_u.bytes();
     bytes += m->d_ax_blk_back.bytes() + m->d_tc.bytes() + m->d_bidx.bytes();
     bytes += m->d_gat_ptr.bytes() + m->d_gat.bytes() + m->d_cB.bytes() + m->d_part.bytes();
     bytes += m->d_K_ptr.bytes() + m->d_K_col.bytes() + m->d_K_val.bytes() + m->d_r.bytes() + m->d_dx.bytes();

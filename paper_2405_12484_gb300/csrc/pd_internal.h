@@ -142,7 +142,8 @@ struct CoarseDescB {
 
 enum Phase : int {
     PH_INERTIA = 0, PH_LOCAL, PH_ASSEMBLE, PH_CONDENSE, PH_GATHER, PH_COARSE, PH_REDUCE,
-    PH_BACKSUB, PH_RESIDUAL, PH_VELOCITY, PH_CONDENSE2, PH_GATHER2, PH_BACKSUB2, PH_COUNT
+    PH_BACKSUB, PH_RESIDUAL, PH_VELOCITY, PH_CONDENSE2, PH_GATHER2, PH_BACKSUB2, PH_INTERIOR, PH_INTERIOR2,
+    PH_COUNT
 };
 
 // ---------------------------------------------------------------- mesh
@@ -155,6 +156,10 @@ struct pd_mesh {
     int32_t n_v = 0, n_t = 0, n_dom = 0, n_pin = 0, n_free = 0, n_int = 0, n_B = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+    // side streams of the subspace solve: the interior parts of the two
+    // condensations run beside the interface solve (fork/join by events)
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
 
     // host-side topology (new vertex numbering: [domain internals][interface][pinned])
     std::vector<int32_t> new_of_old, old_of_new;  // vertex maps
@@ -201,14 +206,16 @@ struct pd_mesh {
     pdg::DBuf<__nv_bfloat16> d_mat16;       // matrix pool (BF16)
     int64_t off_S = 0;                      // pool offset of S^-1
     int32_t ld_S = 0;
-    pdg::DBuf<pdg::AxDesc> d_ax_desc_cond, d_ax_desc_back;   // per-domain products (axpy form)
-    pdg::DBuf<pdg::AxBlock> d_ax_blk_cond, d_ax_blk_back;
-    int32_t ax_blocks_cond = 0, ax_blocks_back = 0;
-    int32_t ax_kmax_cond = 1, ax_kmax_back = 1;             // largest K (shared-memory vector size)
+    // per-domain products (axpy form): boundary modes, interior part, back-substitution
+    pdg::DBuf<pdg::AxDesc> d_ax_desc_cond, d_ax_desc_int, d_ax_desc_back;
+    pdg::DBuf<pdg::AxBlock> d_ax_blk_cond, d_ax_blk_int, d_ax_blk_back;
+    int32_t ax_blocks_cond = 0, ax_blocks_int = 0, ax_blocks_back = 0;
+    int32_t ax_kmax_cond = 1, ax_kmax_int = 1, ax_kmax_back = 1;   // largest K (shared-memory vector size)
     // second level (groups of domains): condensation onto the top-level interface
     bool two_level = false;
     int32_t cs_n = 0;                                       // rows of the dense coarse inverse in the pool
     pdg::RowPlan rows_cond2, rows_back2;   // row-form launches of the second level
+    pdg::RowPlan rows_int2;                // second-level interior part S_II^-1 c_I
     pdg::DBuf<int32_t> d_bidx2, d_gat2_ptr, d_gat2;
     pdg::DBuf<float4> d_tc2, d_cT;
     int32_t n_tc2 = 0, n_gat2 = 0;

@@ -294,7 +294,7 @@ def project(F: torch.Tensor, with_sigma=True):
 
 
 PHASES = ["inertia", "local", "assemble", "dd_condense", "dd_gather", "dd_coarse", "dd_reduce", "dd_backsub",
-          "residual", "velocity", "dd_condense2", "dd_gather2", "dd_backsub2"]
+          "residual", "velocity", "dd_condense2", "dd_gather2", "dd_backsub2", "dd_interior", "dd_interior2"]
 
 
 def phase_bit(name: str) -> int:
