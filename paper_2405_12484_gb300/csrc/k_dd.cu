@@ -18,6 +18,9 @@
 
 namespace pdg {
 
+void launch_stream_rows(const StreamPlan& P, int prec, const void* pool, const float4* x, const int* xidx,
+                        const float4* add, float4* out, int* err, cudaStream_t s);
+
 namespace {
 
 template <class T>
@@ -603,6 +606,55 @@ struct DDBufs {
 };
 
 // One subspace solve: x (free vertices of xout) = K_ff^-1 b.
+// The same solve with every product in the streaming row form (one launch per
+// product, in dependency order on one stream).
+void dd_solve_stream(pd_mesh* m, const void* pool, const float4* b, float4* xout, const DDBufs& w, cudaStream_t s) {
+    const int pr = m->prec;
+    int* err = m->d_err.p;
+    phase_begin(m, PH_CONDENSE, s);
+    launch_stream_rows(m->st_cond, pr, pool, b, nullptr, nullptr, w.tc, err, s);
+    phase_end(m, s);
+    phase_begin(m, PH_INTERIOR, s);
+    launch_stream_rows(m->st_int, pr, pool, b, nullptr, nullptr, w.tc, err, s);
+    phase_end(m, s);
+    if (m->n_B > 0) {
+        phase_begin(m, PH_GATHER, s);
+        k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, w.tc, w.cB);
+        PDG_CHECK_LAUNCH();
+        phase_end(m, s);
+        const float4* cin = w.cB;
+        float4* xcs = xout + m->n_int;
+        const int T0 = m->n_B - m->n_top;
+        if (m->two_level) {
+            phase_begin(m, PH_CONDENSE2, s);
+            launch_stream_rows(m->st_cond2, pr, pool, w.cB, nullptr, nullptr, w.tc2, err, s);
+            phase_end(m, s);
+            phase_begin(m, PH_INTERIOR2, s);
+            launch_stream_rows(m->st_int2, pr, pool, w.cB, nullptr, nullptr, w.tc2, err, s);
+            phase_end(m, s);
+            phase_begin(m, PH_GATHER2, s);
+            k_gather<<<nblk(m->n_top, 256), 256, 0, s>>>(m->n_top, m->d_gat2_ptr.p, m->d_gat2.p, w.cB + T0, w.tc2,
+                                                         w.cT);
+            PDG_CHECK_LAUNCH();
+            phase_end(m, s);
+            cin = w.cT;
+            xcs = xout + m->n_int + T0;
+        }
+        phase_begin(m, PH_COARSE, s);
+        launch_stream_rows(m->st_coarse, pr, pool, cin, nullptr, nullptr, xcs, err, s);
+        phase_end(m, s);
+        if (m->two_level) {
+            phase_begin(m, PH_BACKSUB2, s);
+            launch_stream_rows(m->st_back2, pr, pool, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int, err,
+                               s);
+            phase_end(m, s);
+        }
+    }
+    phase_begin(m, PH_BACKSUB, s);
+    launch_stream_rows(m->st_back, pr, pool, xout + m->n_int, m->d_bidx.p, w.tc, xout, err, s);
+    phase_end(m, s);
+}
+
 template <class T>
 void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, const DDBufs& w, cudaStream_t s) {
     // the interior part t = K_ii^-1 b_i runs on a side stream beside the
@@ -682,7 +734,10 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
 void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* tc, float4* cB, float4* part,
                              float4* tc2, float4* cT, cudaStream_t s) {
     const DDBufs w{tc, cB, part, tc2, cT};
-    if (m->prec == PD_PREC_BF16) dd_solve_impl<__nv_bfloat16>(m, m->d_mat16.p, b, xout, w, s);
+    if (m->use_stream)
+        dd_solve_stream(m, m->prec == PD_PREC_BF16 ? (const void*)m->d_mat16.p : (const void*)m->d_mat32.p, b, xout,
+                        w, s);
+    else if (m->prec == PD_PREC_BF16) dd_solve_impl<__nv_bfloat16>(m, m->d_mat16.p, b, xout, w, s);
     else dd_solve_impl<float>(m, m->d_mat32.p, b, xout, w, s);
 }
 
@@ -698,13 +753,8 @@ int ax_outputs_per_block(int prec) { return 32 * kAxM * (prec == PD_PREC_BF16 ? 
 
 // Returns false when the largest interface vector does not fit in shared memory.
 bool configure_coarse_b(int max_cols) {
-    int dev = 0, optin = 0;
-    PDG_CUDA(cudaGetDevice(&dev));
-    PDG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const size_t smem = sizeof(float) * 3 * (size_t)max_cols;
-    if (smem > (size_t)optin) return false;
-    PDG_CUDA(cudaFuncSetAttribute(k_coarse_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    return true;
+    return smem <= (size_t)allow_max_dynamic_smem(k_coarse_b);
 }
 
 void launch_coarse_b(const CoarseDescB* cd, int n_desc, int64_t U, int max_cols, int blocks, cudaStream_t s) {
@@ -719,14 +769,12 @@ int dd_max_sub_cols() { return kMaxSubCols; }
 // interface vector does not fit in shared memory and the chunked kernel is used.
 int dd_configure_coarse(int ld_S) {
     const size_t smem = sizeof(float) * 3 * (size_t)ld_S;
-    int dev = 0, sms = 0, optin = 0;
+    int dev = 0, sms = 0;
     PDG_CUDA(cudaGetDevice(&dev));
     PDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    PDG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int optin = std::min(allow_max_dynamic_smem(k_coarse_bal<float>),
+                               allow_max_dynamic_smem(k_coarse_bal<__nv_bfloat16>));
     if (smem > (size_t)optin || sms <= 0) return 0;
-    PDG_CUDA(cudaFuncSetAttribute(k_coarse_bal<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PDG_CUDA(cudaFuncSetAttribute(k_coarse_bal<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
     const int bps = (smem * kCoarseBps <= (size_t)optin) ? kCoarseBps : 1;
     return sms * bps;
 }
@@ -770,10 +818,10 @@ void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream
         }
     }
     const size_t smem = sizeof(float) * 3 * (size_t)xcap;
-    if (smem > 48 * 1024) {
-        PDG_CUDA(cudaFuncSetAttribute(k_rowdot<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        PDG_CUDA(cudaFuncSetAttribute(k_rowdot<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+    const int optin = std::min(allow_max_dynamic_smem(k_rowdot<float>), allow_max_dynamic_smem(k_rowdot<__nv_bfloat16>));
+    if (smem > (size_t)optin) {
+        set_error("row-form product: the x vector does not fit in shared memory");
+        throw Fail{PD_ERR_UNSUPPORTED};
     }
     upload(P.descs, descs, s);
     upload(P.blk_u, cut, s);

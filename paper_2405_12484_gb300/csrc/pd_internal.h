@@ -26,14 +26,30 @@ struct Fail {
         cudaError_t e_ = (call);                                                              \
         if (e_ != cudaSuccess) {                                                              \
             ::pdg::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));              \
+            (void)cudaGetLastError(); /* reported here: not left for the next check */          \
             throw ::pdg::Fail{e_ == cudaErrorMemoryAllocation ? PD_ERR_NO_MEMORY : PD_ERR_CUDA}; \
         }                                                                                     \
     } while (0)
 
 #define PDG_CHECK_LAUNCH() PDG_CUDA(cudaGetLastError())
 
+// Lets a kernel use all the dynamic shared memory the device allows per block
+// (the attribute is per kernel and shared by every mesh and plan).  Returns
+// that limit in bytes.
+template <class K>
+inline int allow_max_dynamic_smem(K* kernel) {
+    int dev = 0, optin = 0;
+    PDG_CUDA(cudaGetDevice(&dev));
+    PDG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    PDG_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    PDG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    return lim;
+}
+
 // Device error flag bits (d_err).
-enum : int { ERR_NONFINITE = 1, ERR_NOT_SPD = 2 };
+enum : int { ERR_NONFINITE = 1, ERR_NOT_SPD = 2, ERR_TIMEOUT = 4 };
 
 // ---------------------------------------------------------------- device buffer
 template <class T>
@@ -110,6 +126,20 @@ struct RowPlan {
     DBuf<int64_t> blk_u;
     int n_desc = 0, n_blocks = 0, xcap = 8;
     std::vector<RowDesc> host;     // host copy (byte accounting)
+};
+
+// Streaming row-form launch (bulk-copy pipeline): tiles of whole rows of one
+// descriptor, and the contiguous tile range of every CTA.
+struct StreamTile {
+    int32_t desc, r0, nr, q;   // descriptor, first row, rows, column chunks per row
+};
+struct StreamPlan {
+    DBuf<RowDesc> descs;
+    DBuf<StreamTile> tiles;
+    DBuf<int32_t> cta_tiles;
+    int n_ctas = 0, xcap = 8;
+    size_t smem = 0;
+    std::vector<RowDesc> host;
 };
 
 // One resident request of the serving loop, as the batched kernels see it.
@@ -216,6 +246,10 @@ struct pd_mesh {
     int32_t cs_n = 0;                                       // rows of the dense coarse inverse in the pool
     pdg::RowPlan rows_cond2, rows_back2;   // row-form launches of the second level
     pdg::RowPlan rows_int2;                // second-level interior part S_II^-1 c_I
+    // streaming (bulk-copy) launches of every product of the solve; used when
+    // all of them could be planned (every row fits one pipeline stage)
+    bool use_stream = false;
+    pdg::StreamPlan st_cond, st_int, st_back, st_cond2, st_int2, st_back2, st_coarse;
     pdg::DBuf<int32_t> d_bidx2, d_gat2_ptr, d_gat2;
     pdg::DBuf<float4> d_tc2, d_cT;
     int32_t n_tc2 = 0, n_gat2 = 0;
