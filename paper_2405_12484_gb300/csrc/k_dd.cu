@@ -18,7 +18,7 @@
 
 namespace pdg {
 
-void launch_stream_rows(const StreamPlan& P, int prec, const void* pool, const float4* x, const int* xidx,
+void launch_stream_cols(const StreamPlan& P, int prec, const void* pool, const float4* x, const int* xidx,
                         const float4* add, float4* out, int* err, cudaStream_t s);
 
 namespace {
@@ -606,16 +606,17 @@ struct DDBufs {
 };
 
 // One subspace solve: x (free vertices of xout) = K_ff^-1 b.
-// The same solve with every product in the streaming row form (one launch per
+// The same solve with every product in the streaming column form (one launch per
 // product, in dependency order on one stream).
-void dd_solve_stream(pd_mesh* m, const void* pool, const float4* b, float4* xout, const DDBufs& w, cudaStream_t s) {
+template <class T>
+void dd_solve_stream(pd_mesh* m, const T* pool, const float4* b, float4* xout, const DDBufs& w, cudaStream_t s) {
     const int pr = m->prec;
     int* err = m->d_err.p;
     phase_begin(m, PH_CONDENSE, s);
-    launch_stream_rows(m->st_cond, pr, pool, b, nullptr, nullptr, w.tc, err, s);
+    launch_stream_cols(m->st_cond, pr, pool, b, nullptr, nullptr, w.tc, err, s);
     phase_end(m, s);
     phase_begin(m, PH_INTERIOR, s);
-    launch_stream_rows(m->st_int, pr, pool, b, nullptr, nullptr, w.tc, err, s);
+    launch_stream_cols(m->st_int, pr, pool, b, nullptr, nullptr, w.tc, err, s);
     phase_end(m, s);
     if (m->n_B > 0) {
         phase_begin(m, PH_GATHER, s);
@@ -627,10 +628,10 @@ void dd_solve_stream(pd_mesh* m, const void* pool, const float4* b, float4* xout
         const int T0 = m->n_B - m->n_top;
         if (m->two_level) {
             phase_begin(m, PH_CONDENSE2, s);
-            launch_stream_rows(m->st_cond2, pr, pool, w.cB, nullptr, nullptr, w.tc2, err, s);
+            launch_stream_cols(m->st_cond2, pr, pool, w.cB, nullptr, nullptr, w.tc2, err, s);
             phase_end(m, s);
             phase_begin(m, PH_INTERIOR2, s);
-            launch_stream_rows(m->st_int2, pr, pool, w.cB, nullptr, nullptr, w.tc2, err, s);
+            launch_stream_cols(m->st_int2, pr, pool, w.cB, nullptr, nullptr, w.tc2, err, s);
             phase_end(m, s);
             phase_begin(m, PH_GATHER2, s);
             k_gather<<<nblk(m->n_top, 256), 256, 0, s>>>(m->n_top, m->d_gat2_ptr.p, m->d_gat2.p, w.cB + T0, w.tc2,
@@ -641,17 +642,21 @@ void dd_solve_stream(pd_mesh* m, const void* pool, const float4* b, float4* xout
             xcs = xout + m->n_int + T0;
         }
         phase_begin(m, PH_COARSE, s);
-        launch_stream_rows(m->st_coarse, pr, pool, cin, nullptr, nullptr, xcs, err, s);
+        launch_coarse<T>(m, pool, cin, w.part, s);
+        phase_end(m, s);
+        phase_begin(m, PH_REDUCE, s);
+        k_reduce<<<nblk(m->cs_n, 256), 256, 0, s>>>(m->cs_n, m->coarse_nchunks, w.part, xcs);
+        PDG_CHECK_LAUNCH();
         phase_end(m, s);
         if (m->two_level) {
             phase_begin(m, PH_BACKSUB2, s);
-            launch_stream_rows(m->st_back2, pr, pool, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int, err,
+            launch_stream_cols(m->st_back2, pr, pool, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int, err,
                                s);
             phase_end(m, s);
         }
     }
     phase_begin(m, PH_BACKSUB, s);
-    launch_stream_rows(m->st_back, pr, pool, xout + m->n_int, m->d_bidx.p, w.tc, xout, err, s);
+    launch_stream_cols(m->st_back, pr, pool, xout + m->n_int, m->d_bidx.p, w.tc, xout, err, s);
     phase_end(m, s);
 }
 
@@ -734,10 +739,10 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
 void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* tc, float4* cB, float4* part,
                              float4* tc2, float4* cT, cudaStream_t s) {
     const DDBufs w{tc, cB, part, tc2, cT};
-    if (m->use_stream)
-        dd_solve_stream(m, m->prec == PD_PREC_BF16 ? (const void*)m->d_mat16.p : (const void*)m->d_mat32.p, b, xout,
-                        w, s);
-    else if (m->prec == PD_PREC_BF16) dd_solve_impl<__nv_bfloat16>(m, m->d_mat16.p, b, xout, w, s);
+    if (m->use_stream) {
+        if (m->prec == PD_PREC_BF16) dd_solve_stream<__nv_bfloat16>(m, m->d_mat16.p, b, xout, w, s);
+        else dd_solve_stream<float>(m, m->d_mat32.p, b, xout, w, s);
+    } else if (m->prec == PD_PREC_BF16) dd_solve_impl<__nv_bfloat16>(m, m->d_mat16.p, b, xout, w, s);
     else dd_solve_impl<float>(m, m->d_mat32.p, b, xout, w, s);
 }
 

@@ -1,24 +1,30 @@
-// Streaming row-form products of the subspace solve (Sec. 7.2) on sm_103a:
-// out[r] = add[r] + A[r, 0:cols] . x for every row of a list of dense blocks
-// (RowDesc), x being three right-hand sides (K = K_s (x) I_3).
+// Streaming products of the subspace solve (Sec. 7.2) on sm_103a in the
+// column ("axpy") form: out[o] = add[o] + sum_k A[k][o] x_k for o < n_out,
+// the rows k of A contiguous in memory, x_k three right-hand sides
+// (K = K_s (x) I_3).  Every product of the solve has this form with the
+// factors the pool holds: K_ii^-1 (symmetric), Psi_d, Psi_d^T, and the same
+// for the second level and the coarse inverse.
 //
-// The matrices are read once per solve and are far larger than L2, so the
-// launch is bound by HBM.  Plain per-warp loads leave too few bytes in flight
-// (long-scoreboard stalls); here one producer thread per CTA streams
-// contiguous row tiles into a shared-memory ring with bulk asynchronous copies
-// (cp.async.bulk, completion counted in bytes on an mbarrier), so up to
-// kStages x kStageBytes per SM are in flight independently of the compute
-// warps.  Eight consumer warps take (row, column chunk) units of a tile, dot
-// them with x staged in shared memory as three float planes, and combine the
-// lanes with a fixed shuffle tree; the chunk sums of a row are added in chunk
-// order.  Results are bitwise reproducible and do not depend on the tile
-// schedule.  One CTA per SM; the host cuts the tile list into equal byte
-// ranges, one per CTA.
+// The matrices are read once per solve and are far larger than L2: the
+// launch is bound by HBM.  One producer thread per CTA streams whole-row
+// tiles into a shared-memory ring with bulk asynchronous copies
+// (cp.async.bulk, completion counted in bytes on an mbarrier), keeping
+// kStages x kStageBytes per SM in flight whatever the compute warps do.
+// Sixteen consumer warps own (output slab, row group) pairs: a warp adds
+// A[k][slab] * x_k for the rows k of its group, with x_k a shared-memory
+// broadcast and the accumulators in registers (no cross-lane reductions).
+// The row groups of a slab are combined in group order through shared memory.
+//
+// Work split: the rows of all blocks are cut into pieces, one contiguous
+// byte range of about the same size per CTA (a block may span CTAs).  A block
+// cut into several pieces writes per-piece partial sums; the CTA that
+// finishes the block's last piece (an atomic counter, no waiting) adds them in
+// piece order.  Results are bitwise reproducible for a given plan.
 //
 // Every wait is bounded: a wait that runs out sets ERR_TIMEOUT in the mesh's
-// error word, marks the CTA aborted (no further copies are issued, consumers
-// stop waiting), and the producer waits, again bounded, for its copies in
-// flight before the CTA exits.
+// error word and marks the CTA aborted (no further copies are issued,
+// consumers stop waiting); the producer waits, again bounded, for its copies
+// in flight before it exits.
 #include <algorithm>
 
 #include "pd_internal.h"
@@ -27,14 +33,13 @@ namespace pdg {
 
 namespace {
 
-constexpr int kStreamWarps = 8;                           // consumer warps
-constexpr int kStreamThreads = 32 * (kStreamWarps + 1);   // + one producer warp
+constexpr int kColWarps = 16;                            // consumer warps
+constexpr int kColThreads = 32 * (kColWarps + 1);        // + one producer warp
 constexpr int kStages = 4;
-constexpr int kStageBytes = 32 * 1024;
-constexpr int kMaxTileRows = 256;
-constexpr int kMaxUnits = 512;                            // (row, chunk) units of one tile
-constexpr int kChunkLoads = 4;                            // 16-byte loads per lane per unit
-constexpr long long kWaitLimit = 1LL << 24;               // try_wait polls before giving up
+constexpr int kStageBytes = 24 * 1024;
+constexpr int kMaxGroups = 8;                            // row groups per slab
+constexpr int kMaxPieceRows = 1024;                      // x slice of a piece in shared memory
+constexpr long long kWaitLimit = 1LL << 24;              // try_wait polls before giving up
 
 template <class T>
 struct SVec;
@@ -92,7 +97,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 __device__ __forceinline__ void consumer_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kStreamWarps) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kColWarps) : "memory");
 }
 
 __device__ __forceinline__ void vec_from_smem(const float* p, float (&v)[4]) {
@@ -111,221 +116,307 @@ __device__ __forceinline__ void vec_from_smem(const __nv_bfloat16* p, float (&v)
     }
 }
 
+// outputs of one warp's slab: M sub-slabs of 32 lanes x VN consecutive outputs
 template <class T>
-__global__ void __launch_bounds__(kStreamThreads, 1)
-    k_stream_rows(const RowDesc* __restrict__ descs, const StreamTile* __restrict__ tiles,
-                  const int32_t* __restrict__ cta_tiles, AxBases B, int xcap, int* __restrict__ err) {
-    constexpr int VN = SVec<T>::N;
-    constexpr int CW = 32 * VN * kChunkLoads;   // columns of one unit
+struct Slab {
+    static constexpr int VN = SVec<T>::N;
+    static constexpr int M = (VN == 4) ? 2 : 1;
+    static constexpr int OUT = 32 * VN * M;
+};
+
+__host__ __device__ inline int col_rows_per_tile(int ld, int es) {
+    const int r = kStageBytes / (ld * es);
+    return r > 0 ? r : 1;
+}
+
+__host__ __device__ inline void col_layout(int n_out, int slab_out, int& S, int& G) {
+    S = (n_out + slab_out - 1) / slab_out;
+    if (S < 1) S = 1;
+    G = kColWarps / S;
+    if (G > kMaxGroups) G = kMaxGroups;
+    if (G < 1) G = 1;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kColThreads, 1)
+    k_stream_cols(const ColDesc* __restrict__ descs, const ColPiece* __restrict__ pieces,
+                  const int32_t* __restrict__ cta_pieces, AxBases B, float4* __restrict__ part,
+                  int* __restrict__ cnt, int* __restrict__ err) {
+    constexpr int VN = Slab<T>::VN, M = Slab<T>::M, SO = Slab<T>::OUT;
+    constexpr int ES = (int)sizeof(T);
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned char* ring = sm;
-    float* x0 = reinterpret_cast<float*>(sm + (size_t)kStages * kStageBytes);
-    float* x1 = x0 + xcap;
-    float* x2 = x1 + xcap;
-    float* part = x2 + xcap;                                            // [kMaxUnits][3]
-    uint64_t* full = reinterpret_cast<uint64_t*>(part + 3 * kMaxUnits);  // [kStages]
-    uint64_t* empty = full + kStages;                                   // [kStages]
-    __shared__ int abort_flag;
+    float4* xs = reinterpret_cast<float4*>(sm + (size_t)kStages * kStageBytes);    // [kMaxPieceRows]
+    float* red = reinterpret_cast<float*>(xs + kMaxPieceRows);                      // [(kMaxGroups-1)*kColWarps... ]
+    uint64_t* full = reinterpret_cast<uint64_t*>(red + (size_t)(kMaxGroups - 1) * 2 * SO * 3);
+    uint64_t* empty = full + kStages;
+    __shared__ int abort_flag, last_flag;
 
-    const int t0 = cta_tiles[blockIdx.x], t1 = cta_tiles[blockIdx.x + 1];
+    const int p0 = cta_pieces[blockIdx.x], p1 = cta_pieces[blockIdx.x + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int k = 0; k < kStages; ++k) {
             mbar_init(&full[k], 1);
-            mbar_init(&empty[k], kStreamWarps);
+            mbar_init(&empty[k], kColWarps);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (t1 <= t0) return;
+    if (p1 <= p0) return;
     const T* pool = reinterpret_cast<const T*>(B.pool);
 
-    if (warp == kStreamWarps) {
-        // ---- producer: one thread issues the bulk copies of this CTA's tiles
+    if (warp == kColWarps) {
+        // ---- producer: one thread issues the bulk copies of every tile of this CTA
         if (lane != 0) return;
-        int issued = 0;
-        for (int i = 0; i < t1 - t0; ++i) {
-            if (*reinterpret_cast<volatile int*>(&abort_flag)) break;
-            const int slot = i % kStages;
-            if (i >= kStages && !mbar_wait(&empty[slot], (uint32_t)((i / kStages) - 1) & 1u)) {
-                atomicOr(err, ERR_TIMEOUT);
-                atomicExch(&abort_flag, 1);
-                break;
+        int i = 0, issued = 0;
+        bool stop = false;
+        for (int p = p0; p < p1 && !stop; ++p) {
+            const ColPiece pc = pieces[p];
+            const ColDesc D = descs[pc.desc];
+            const int rpt = col_rows_per_tile(D.ld, ES);
+            for (int k = pc.k0; k < pc.k1; k += rpt, ++i) {
+                if (*reinterpret_cast<volatile int*>(&abort_flag)) {
+                    stop = true;
+                    break;
+                }
+                const int slot = i % kStages;
+                if (i >= kStages && !mbar_wait(&empty[slot], (uint32_t)((i / kStages) - 1) & 1u)) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    atomicExch(&abort_flag, 1);
+                    stop = true;
+                    break;
+                }
+                const int nr = min(rpt, pc.k1 - k);
+                const uint32_t bytes = (uint32_t)nr * (uint32_t)D.ld * (uint32_t)ES;
+                mbar_arrive_expect_tx(&full[slot], bytes);
+                bulk_g2s(ring + (size_t)slot * kStageBytes, pool + D.a_off + (int64_t)k * D.ld, bytes, &full[slot]);
+                issued = i + 1;
             }
-            const StreamTile tl = tiles[t0 + i];
-            const RowDesc D = descs[tl.desc];
-            const uint32_t bytes = (uint32_t)tl.nr * (uint32_t)D.ld * (uint32_t)sizeof(T);
-            mbar_arrive_expect_tx(&full[slot], bytes);
-            bulk_g2s(ring + (size_t)slot * kStageBytes, pool + D.a_off + (int64_t)tl.r0 * D.ld, bytes, &full[slot]);
-            issued = i + 1;
         }
-        // before exit: every issued copy has landed (normally already consumed)
-        for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
-            if (!mbar_wait(&full[i % kStages], (uint32_t)(i / kStages) & 1u)) atomicOr(err, ERR_TIMEOUT);
+        for (int j = (issued > kStages ? issued - kStages : 0); j < issued; ++j)
+            if (!mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u)) atomicOr(err, ERR_TIMEOUT);
         return;
     }
 
-    // ---- consumers (warps 0 .. kStreamWarps-1)
-    int cur_desc = -1;
-    for (int i = 0; i < t1 - t0; ++i) {
-        const StreamTile tl = tiles[t0 + i];
-        const RowDesc D = descs[tl.desc];
-        if (tl.desc != cur_desc) {
-            // the previous tile ended with a consumer barrier: nobody reads the old x
-            for (int k = threadIdx.x; k < D.ld; k += 32 * kStreamWarps) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (k < D.cols) v = (D.xidx_off >= 0) ? B.x[B.bidx[D.xidx_off + k]] : B.x[D.x_off + k];
-                x0[k] = v.x;
-                x1[k] = v.y;
-                x2[k] = v.z;
+    // ---- consumers
+    const int tid = threadIdx.x;
+    int i = 0;   // tile counter (same sequence as the producer's)
+    for (int p = p0; p < p1; ++p) {
+        const ColPiece pc = pieces[p];
+        const ColDesc D = descs[pc.desc];
+        const int rpt = col_rows_per_tile(D.ld, ES);
+        int S, G;
+        col_layout(D.n_out, SO, S, G);
+        // x slice of the piece (the previous piece ended with a consumer barrier)
+        for (int k = tid; k < pc.k1 - pc.k0; k += 32 * kColWarps) {
+            const int kk = pc.k0 + k;
+            xs[k] = (D.xidx_off >= 0) ? B.x[B.bidx[D.xidx_off + kk]] : B.x[D.x_off + kk];
+        }
+        consumer_sync();
+        const bool active = warp < S * G;
+        const int slab = warp % S, grp = warp / S;
+        const int o_base = slab * SO + lane * VN;
+        float acc[M][VN][3];
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm)
+#pragma unroll
+            for (int j = 0; j < VN; ++j) acc[mm][j][0] = acc[mm][j][1] = acc[mm][j][2] = 0.f;
+        bool valid[M];
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm) valid[mm] = active && (o_base + mm * 32 * VN < D.n_out);
+        for (int k = pc.k0; k < pc.k1; k += rpt, ++i) {
+            const int slot = i % kStages;
+            if (!*reinterpret_cast<volatile int*>(&abort_flag) &&
+                !mbar_wait(&full[slot], (uint32_t)(i / kStages) & 1u)) {
+                atomicOr(err, ERR_TIMEOUT);
+                atomicExch(&abort_flag, 1);
             }
-            cur_desc = tl.desc;
-            consumer_sync();
-        }
-        const int slot = i % kStages;
-        if (!*reinterpret_cast<volatile int*>(&abort_flag) && !mbar_wait(&full[slot], (uint32_t)(i / kStages) & 1u)) {
-            atomicOr(err, ERR_TIMEOUT);
-            atomicExch(&abort_flag, 1);
-        }
-        const T* A = reinterpret_cast<const T*>(ring + (size_t)slot * kStageBytes);
-        const int units = tl.nr * tl.q;
-        for (int u = warp; u < units; u += kStreamWarps) {
-            const int r = u / tl.q, ch = u - r * tl.q;
-            const T* row = A + (int64_t)r * D.ld;
-            const int cb = ch * CW, ce = min(D.ld, cb + CW);
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+            const T* A = reinterpret_cast<const T*>(ring + (size_t)slot * kStageBytes);
+            const int nr = min(rpt, pc.k1 - k);
+            if (valid[0]) {
+                // rows r of the tile with (k - k0 + r) = grp (mod G)
+                int r = grp - ((k - pc.k0) % G);
+                if (r < 0) r += G;
+#pragma unroll 2
+                for (; r < nr; r += G) {
+                    const float4 xk = xs[k - pc.k0 + r];
+                    const T* a = A + (int64_t)r * D.ld + o_base;
 #pragma unroll
-            for (int l = 0; l < kChunkLoads; ++l) {
-                const int c = cb + (l * 32 + lane) * VN;
-                if (c < ce) {
-                    float v[VN];
-                    vec_from_smem(row + c, v);
+                    for (int mm = 0; mm < M; ++mm) {
+                        if (!valid[mm]) continue;
+                        float v[VN];
+                        vec_from_smem(a + mm * 32 * VN, v);
 #pragma unroll
-                    for (int j = 0; j < VN; j += 4) {
-                        const float4 p0 = *reinterpret_cast<const float4*>(x0 + c + j);
-                        const float4 p1 = *reinterpret_cast<const float4*>(x1 + c + j);
-                        const float4 p2 = *reinterpret_cast<const float4*>(x2 + c + j);
-                        a0 = fmaf(v[j], p0.x, a0); a0 = fmaf(v[j + 1], p0.y, a0);
-                        a0 = fmaf(v[j + 2], p0.z, a0); a0 = fmaf(v[j + 3], p0.w, a0);
-                        a1 = fmaf(v[j], p1.x, a1); a1 = fmaf(v[j + 1], p1.y, a1);
-                        a1 = fmaf(v[j + 2], p1.z, a1); a1 = fmaf(v[j + 3], p1.w, a1);
-                        a2 = fmaf(v[j], p2.x, a2); a2 = fmaf(v[j + 1], p2.y, a2);
-                        a2 = fmaf(v[j + 2], p2.z, a2); a2 = fmaf(v[j + 3], p2.w, a2);
+                        for (int j = 0; j < VN; ++j) {
+                            acc[mm][j][0] = fmaf(v[j], xk.x, acc[mm][j][0]);
+                            acc[mm][j][1] = fmaf(v[j], xk.y, acc[mm][j][1]);
+                            acc[mm][j][2] = fmaf(v[j], xk.z, acc[mm][j][2]);
+                        }
                     }
                 }
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+        // combine the row groups of each slab in group order
+        if (active && grp > 0) {
+            float* rb = red + ((size_t)(grp - 1) * S + slab) * SO * 3;
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                a0 += __shfl_xor_sync(0xffffffffu, a0, off);
-                a1 += __shfl_xor_sync(0xffffffffu, a1, off);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, off);
-            }
-            if (lane == 0) {
-                part[3 * u] = a0;
-                part[3 * u + 1] = a1;
-                part[3 * u + 2] = a2;
+            for (int mm = 0; mm < M; ++mm)
+#pragma unroll
+                for (int j = 0; j < VN; ++j) {
+                    const int lo = mm * 32 * VN + lane * VN + j;
+                    rb[3 * lo] = acc[mm][j][0];
+                    rb[3 * lo + 1] = acc[mm][j][1];
+                    rb[3 * lo + 2] = acc[mm][j][2];
+                }
+        }
+        consumer_sync();
+        const bool single = D.n_pieces == 1;
+        if (active && grp == 0) {
+#pragma unroll
+            for (int mm = 0; mm < M; ++mm)
+#pragma unroll
+                for (int j = 0; j < VN; ++j) {
+                    const int lo = mm * 32 * VN + lane * VN + j;
+                    const int o = slab * SO + lo;
+                    if (o >= D.n_out) continue;
+                    float s0 = acc[mm][j][0], s1 = acc[mm][j][1], s2 = acc[mm][j][2];
+                    for (int g = 1; g < G; ++g) {
+                        const float* rb = red + ((size_t)(g - 1) * S + slab) * SO * 3;
+                        s0 += rb[3 * lo];
+                        s1 += rb[3 * lo + 1];
+                        s2 += rb[3 * lo + 2];
+                    }
+                    if (single) {
+                        const float4 ad =
+                            (D.add_off >= 0) ? B.add[D.add_off + o] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        B.out[D.out_off + o] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
+                    } else {
+                        part[D.part_off + (int64_t)pc.piece * D.n_out + o] = make_float4(s0, s1, s2, 0.f);
+                    }
+                }
+        }
+        if (!single) {
+            // the CTA that completes the block's last piece adds the pieces in order
+            __threadfence();
+            consumer_sync();
+            if (tid == 0) last_flag = (atomicAdd(&cnt[pc.desc], 1) == D.n_pieces - 1);
+            consumer_sync();
+            if (last_flag) {
+                __threadfence();
+                for (int o = tid; o < D.n_out; o += 32 * kColWarps) {
+                    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+                    for (int q = 0; q < D.n_pieces; ++q) {
+                        const float4 v = __ldcg(&part[D.part_off + (int64_t)q * D.n_out + o]);
+                        s0 += v.x;
+                        s1 += v.y;
+                        s2 += v.z;
+                    }
+                    const float4 ad = (D.add_off >= 0) ? B.add[D.add_off + o] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    B.out[D.out_off + o] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
+                }
+                if (tid == 0) cnt[pc.desc] = 0;   // ready for the next launch
             }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the tile's bytes
-        consumer_sync();                             // every unit's partial sum is in part[]
-        for (int r = threadIdx.x; r < tl.nr; r += 32 * kStreamWarps) {
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-            for (int ch = 0; ch < tl.q; ++ch) {
-                s0 += part[3 * (r * tl.q + ch)];
-                s1 += part[3 * (r * tl.q + ch) + 1];
-                s2 += part[3 * (r * tl.q + ch) + 2];
-            }
-            const int gr = tl.r0 + r;
-            const float4 ad = (D.add_off >= 0) ? B.add[D.add_off + gr] : make_float4(0.f, 0.f, 0.f, 0.f);
-            B.out[D.out_off + gr] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
-        }
-        consumer_sync();                             // part[] free for the next tile
+        consumer_sync();   // xs and red are free for the next piece
     }
 }
 
-size_t stream_smem_bytes(int xcap) {
-    return (size_t)kStages * kStageBytes + sizeof(float) * (3 * (size_t)xcap + 3 * (size_t)kMaxUnits) +
-           sizeof(uint64_t) * 2 * kStages;
+template <class T>
+size_t col_smem_bytes() {
+    return (size_t)kStages * kStageBytes + sizeof(float4) * kMaxPieceRows +
+           sizeof(float) * (size_t)(kMaxGroups - 1) * 2 * Slab<T>::OUT * 3 + sizeof(uint64_t) * 2 * kStages;
 }
 
 }  // namespace
 
-// Tiles of whole rows (at most kStageBytes, kMaxTileRows rows and kMaxUnits
-// units each) for every descriptor in order, and the cut of the tile list into
-// one contiguous range per CTA with about the same number of bytes.  Returns
-// false (plan left empty) when a row does not fit in one stage or x does not
-// fit in shared memory.
-bool build_stream_plan(StreamPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s) {
+// Pieces of whole rows for every block in order, cut so that every CTA gets a
+// contiguous range of about the same number of bytes (at most kMaxPieceRows
+// rows per piece).  Returns false (plan left empty) when a row does not fit in
+// one stage or a block has more outputs than the consumer warps cover.
+bool build_stream_plan(StreamPlan& P, std::vector<ColDesc> descs, int prec, cudaStream_t s) {
     P.n_ctas = 0;
     P.host.clear();
     const int es = (prec == PD_PREC_BF16) ? 2 : 4;
-    const int VN = (prec == PD_PREC_BF16) ? 8 : 4;
-    const int CW = 32 * VN * kChunkLoads;
-    int xcap = 8;
-    std::vector<StreamTile> tiles;
-    std::vector<int64_t> tbytes;
-    for (int d = 0; d < (int)descs.size(); ++d) {
-        const RowDesc& D = descs[d];
-        if (D.rows <= 0) continue;
-        const int64_t row_bytes = (int64_t)D.ld * es;
-        if (row_bytes > kStageBytes || D.ld % 8 != 0 || D.a_off % 8 != 0) return false;
-        xcap = std::max(xcap, D.ld);
-        const int q = (D.ld + CW - 1) / CW;
-        int nr = (int)std::min<int64_t>(kStageBytes / row_bytes, kMaxTileRows);
-        nr = std::max(1, std::min(nr, kMaxUnits / q));
-        for (int r0 = 0; r0 < D.rows; r0 += nr) {
-            const int n = std::min(nr, D.rows - r0);
-            tiles.push_back(StreamTile{d, r0, n, q});
-            tbytes.push_back((int64_t)n * row_bytes + 1024);   // + a fixed per-tile cost
-        }
-    }
+    const int SO = (prec == PD_PREC_BF16) ? Slab<__nv_bfloat16>::OUT : Slab<float>::OUT;
     int dev = 0, sms = 0;
     PDG_CUDA(cudaGetDevice(&dev));
     PDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int lim = std::min(allow_max_dynamic_smem(k_stream_rows<float>),
-                             allow_max_dynamic_smem(k_stream_rows<__nv_bfloat16>));
-    const size_t smem = stream_smem_bytes(xcap);
-    if (smem > (size_t)lim) return false;
-    if (tiles.empty()) {
-        P.xcap = xcap;
-        return true;
-    }
     const int C = std::max(1, sms);
     int64_t W = 0;
-    for (auto b : tbytes) W += b;
-    std::vector<int32_t> cut(C + 1, (int32_t)tiles.size());
-    cut[0] = 0;
-    int64_t acc = 0;
-    int c = 1;
-    for (int t = 0; t < (int)tiles.size(); ++t) {
-        while (c < C && acc * C >= W * c) cut[c++] = t;
-        acc += tbytes[t];
+    for (const auto& D : descs) {
+        if ((int64_t)D.ld * es > kStageBytes || D.ld % 8 != 0 || D.a_off % 8 != 0) return false;
+        if ((D.n_out + SO - 1) / SO > kColWarps) return false;
+        W += (int64_t)D.K * D.ld * es + (int64_t)D.n_out * 64;
     }
+    // walk the blocks, closing a CTA's range when its byte budget is reached
+    std::vector<ColPiece> pcs;
+    std::vector<int32_t> cut(1, 0);
+    int64_t acc = 0;
+    int c = 0;
+    for (int d = 0; d < (int)descs.size(); ++d) {
+        ColDesc& D = descs[d];
+        const int64_t row_b = (int64_t)D.ld * es;
+        int k = 0, piece = 0;
+        acc += (int64_t)D.n_out * 64;
+        do {
+            // rows that fit in what is left of this CTA's budget
+            const int64_t budget = W * (c + 1) / C - acc;
+            int take = (int)std::min<int64_t>(D.K - k, std::max<int64_t>(1, budget / std::max<int64_t>(row_b, 1)));
+            take = std::min(take, kMaxPieceRows);
+            if (D.K == 0) take = 0;
+            pcs.push_back(ColPiece{d, k, k + take, piece++});
+            k += take;
+            acc += (int64_t)take * row_b;
+            if (c + 1 < C && acc * C >= W * (c + 1)) {
+                cut.push_back((int32_t)pcs.size());
+                ++c;
+            }
+        } while (k < D.K);
+        D.n_pieces = piece;
+    }
+    while ((int)cut.size() < C + 1) cut.push_back((int32_t)pcs.size());
+    int64_t po = 0;
+    for (auto& D : descs) {
+        D.part_off = po;
+        if (D.n_pieces > 1) po += (int64_t)D.n_pieces * D.n_out;
+    }
+    const size_t smem = (prec == PD_PREC_BF16) ? col_smem_bytes<__nv_bfloat16>() : col_smem_bytes<float>();
+    const int lim = std::min(allow_max_dynamic_smem(k_stream_cols<float>),
+                             allow_max_dynamic_smem(k_stream_cols<__nv_bfloat16>));
+    if (smem > (size_t)lim) return false;
     upload(P.descs, descs, s);
-    upload(P.tiles, tiles, s);
-    upload(P.cta_tiles, cut, s);
+    upload(P.pieces, pcs, s);
+    upload(P.cta_pieces, cut, s);
+    P.part.alloc((size_t)std::max<int64_t>(po, 1));
+    P.cnt.alloc(std::max<size_t>(descs.size(), 1));
+    PDG_CUDA(cudaMemsetAsync(P.cnt.p, 0, P.cnt.bytes(), s));
     PDG_CUDA(cudaStreamSynchronize(s));
     P.host = std::move(descs);
-    P.xcap = xcap;
-    P.n_ctas = C;
+    P.n_ctas = pcs.empty() ? 0 : C;
     P.smem = smem;
     return true;
 }
 
-void launch_stream_rows(const StreamPlan& P, int prec, const void* pool, const float4* x, const int* xidx,
+void launch_stream_cols(const StreamPlan& P, int prec, const void* pool, const float4* x, const int* xidx,
                         const float4* add, float4* out, int* err, cudaStream_t s) {
     if (P.n_ctas <= 0) return;
     const AxBases B{pool, x, xidx, add, out};
     if (prec == PD_PREC_BF16)
-        k_stream_rows<__nv_bfloat16><<<P.n_ctas, kStreamThreads, P.smem, s>>>(P.descs.p, P.tiles.p, P.cta_tiles.p, B,
-                                                                              P.xcap, err);
+        k_stream_cols<__nv_bfloat16><<<P.n_ctas, kColThreads, P.smem, s>>>(P.descs.p, P.pieces.p, P.cta_pieces.p, B,
+                                                                           P.part.p, P.cnt.p, err);
     else
-        k_stream_rows<float><<<P.n_ctas, kStreamThreads, P.smem, s>>>(P.descs.p, P.tiles.p, P.cta_tiles.p, B, P.xcap,
-                                                                      err);
+        k_stream_cols<float><<<P.n_ctas, kColThreads, P.smem, s>>>(P.descs.p, P.pieces.p, P.cta_pieces.p, B, P.part.p,
+                                                                   P.cnt.p, err);
     PDG_CHECK_LAUNCH();
+}
+
+// After a wait ran out the block counters may be left mid-count: clear them.
+void reset_stream_plan(StreamPlan& P, cudaStream_t s) {
+    if (P.cnt.p) PDG_CUDA(cudaMemsetAsync(P.cnt.p, 0, P.cnt.bytes(), s));
 }
 
 }  // namespace pdg

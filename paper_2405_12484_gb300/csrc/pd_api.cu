@@ -26,7 +26,8 @@ int dd_coarse_chunk();
 int dd_configure_coarse(int ld_S);
 int ax_outputs_per_block(int prec);
 void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s);
-bool build_stream_plan(StreamPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s);
+bool build_stream_plan(StreamPlan& P, std::vector<ColDesc> descs, int prec, cudaStream_t s);
+void reset_stream_plan(StreamPlan& P, cudaStream_t s);
 void launch_prefactor_helpers_scatter_coo(double* S, int ld, const int* r, const int* c, const double* v, int n,
                                           cudaStream_t s);
 void launch_prefactor_add_block(double* S, int ldS, const double* Sd, int ldSd, const int* bidx, int nb,
@@ -1074,59 +1075,48 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     m->d_part.alloc((size_t)std::max(m->cs_n, 1) * m->coarse_nchunks);
     m->coarse_blocks = (m->cs_n > 0) ? dd_configure_coarse(m->ld_S) : 0;
 
-    // ---- streaming plans: every product as rows (x_i parts of the back-substitution
-    // as rows of Psi_d, the boundary modes as rows of Psi_d^T, K_ii^-1 symmetric)
+    // ---- streaming plans (column form): t = K_ii^-1 b_i over the rows of K_ii^-1,
+    // c_d = Psi_d^T b_i over the rows of Psi_d, x_i = t + Psi_d x_B over the rows
+    // of Psi_d^T; the second level likewise; the coarse inverse is symmetric
     {
-        std::vector<RowDesc> rc, ri, rb;
+        auto col = [](int64_t a_off, int32_t K, int32_t n_out, int32_t ld, int32_t x_off, int32_t xidx_off,
+                      int32_t add_off, int32_t out_off) {
+            ColDesc c{};
+            c.a_off = a_off;
+            c.K = K;
+            c.n_out = n_out;
+            c.ld = ld;
+            c.x_off = x_off;
+            c.xidx_off = xidx_off;
+            c.add_off = add_off;
+            c.out_off = out_off;
+            c.n_pieces = 1;
+            return c;
+        };
+        std::vector<ColDesc> cc, ci, cb, c2, i2, b2v;
         for (int32_t d = 0; d < n_dom; ++d) {
             const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
             if (ni == 0) continue;
-            RowDesc c{};
-            c.a_off = t_off[d];
-            c.rows = nbd;
-            c.cols = ni;
-            c.ld = ldT[d];
-            c.x_off = m->dom_int_off[d];
-            c.xidx_off = -1;
-            c.add_off = -1;
-            c.out_off = tc_off[d] + ni;
-            if (nbd > 0) rc.push_back(c);
-            RowDesc t = c;
-            t.a_off = h_off[d];
-            t.rows = ni;
-            t.ld = ldH[d];
-            t.out_off = tc_off[d];
-            ri.push_back(t);
-            RowDesc b{};
-            b.a_off = p_off[d];
-            b.rows = ni;
-            b.cols = nbd;
-            b.ld = ldP[d];
-            b.x_off = 0;
-            b.xidx_off = bidx_off[d];
-            b.add_off = tc_off[d];
-            b.out_off = m->dom_int_off[d];
-            rb.push_back(b);
+            if (nbd > 0) cc.push_back(col(p_off[d], ni, nbd, ldP[d], m->dom_int_off[d], -1, -1, tc_off[d] + ni));
+            ci.push_back(col(h_off[d], ni, ni, ldH[d], m->dom_int_off[d], -1, -1, tc_off[d]));
+            cb.push_back(col(t_off[d], nbd, ni, ldT[d], 0, bidx_off[d], tc_off[d], m->dom_int_off[d]));
         }
-        std::vector<RowDesc> rs;
-        if (m->cs_n > 0) {
-            RowDesc c{};
-            c.a_off = m->off_S;
-            c.rows = m->cs_n;
-            c.cols = m->cs_n;
-            c.ld = m->ld_S;
-            c.x_off = 0;
-            c.xidx_off = -1;
-            c.add_off = -1;
-            c.out_off = 0;
-            rs.push_back(c);
+        if (two) {
+            for (int g = 0; g < G; ++g) {
+                const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
+                if (n2 == 0) continue;
+                i2.push_back(col(h2_off[g], n2, n2, ldH2[g], i2_off[g], -1, -1, tc2_off[g]));
+                if (nb == 0) continue;
+                c2.push_back(col(t2_off[g], n2, nb, ldT2[g], i2_off[g], -1, -1, tc2_off[g] + n2));
+                b2v.push_back(col(h2_off[g] + (int64_t)n2 * ldH2[g], nb, n2, ldH2[g], 0, b2_off[g], tc2_off[g],
+                                  i2_off[g]));
+            }
         }
-        bool ok = build_stream_plan(m->st_cond, rc, m->prec, s) && build_stream_plan(m->st_int, ri, m->prec, s) &&
-                  build_stream_plan(m->st_back, rb, m->prec, s) && build_stream_plan(m->st_coarse, rs, m->prec, s);
+        bool ok = build_stream_plan(m->st_cond, cc, m->prec, s) && build_stream_plan(m->st_int, ci, m->prec, s) &&
+                  build_stream_plan(m->st_back, cb, m->prec, s);
         if (ok && two)
-            ok = build_stream_plan(m->st_cond2, m->rows_cond2.host, m->prec, s) &&
-                 build_stream_plan(m->st_int2, m->rows_int2.host, m->prec, s) &&
-                 build_stream_plan(m->st_back2, m->rows_back2.host, m->prec, s);
+            ok = build_stream_plan(m->st_cond2, c2, m->prec, s) && build_stream_plan(m->st_int2, i2, m->prec, s) &&
+                 build_stream_plan(m->st_back2, b2v, m->prec, s);
         m->use_stream = ok;
     }
 
@@ -1171,7 +1161,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->phase_bytes[PH_RESIDUAL] = nk * (4 + 8 + 16) + nf * (4 + 16 + 16);
         m->phase_bytes[PH_VELOCITY] = nv * 48;
         int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (m->ax_blocks_int > 0 ? 1 : 0) +
-                 (n_B > 0 ? (m->use_stream ? 2 : 3) : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
+                 (n_B > 0 ? 3 : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
         if (two)
             dd += (m->rows_cond2.n_blocks > 0 ? 1 : 0) + (m->rows_int2.n_blocks > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) +
                   (m->rows_back2.n_blocks > 0 ? 1 : 0);
@@ -1327,7 +1317,13 @@ pd_status pd_sync(pd_mesh* m) {
     if (herr) {
         PDG_CUDA(cudaMemset(m->d_err.p, 0, sizeof(int32_t)));
         if (herr & ERR_NONFINITE) return fail(PD_ERR_NONFINITE, "non-finite positions or velocities");
-        if (herr & ERR_TIMEOUT) return fail(PD_ERR_TIMEOUT, "a pipeline wait in the subspace solve ran out");
+        if (herr & ERR_TIMEOUT) {
+            for (StreamPlan* P : {&m->st_cond, &m->st_int, &m->st_back, &m->st_cond2, &m->st_int2, &m->st_back2,
+                                  &m->st_coarse})
+                reset_stream_plan(*P, m->stream);
+            PDG_CUDA(cudaStreamSynchronize(m->stream));
+            return fail(PD_ERR_TIMEOUT, "a pipeline wait in the subspace solve ran out");
+        }
         return fail(PD_ERR_NOT_SPD, "a Cholesky pivot was not positive");
     }
     return PD_OK;

@@ -128,18 +128,32 @@ struct RowPlan {
     std::vector<RowDesc> host;     // host copy (byte accounting)
 };
 
-// Streaming row-form launch (bulk-copy pipeline): tiles of whole rows of one
-// descriptor, and the contiguous tile range of every CTA.
-struct StreamTile {
-    int32_t desc, r0, nr, q;   // descriptor, first row, rows, column chunks per row
+// Streaming column-form product out[o] = add[o] + sum_k A[k][o] x_k of one
+// dense block (offsets into AxBases as for AxDesc), and a piece of its rows.
+struct ColDesc {
+    int64_t a_off;         // pool offset of row 0
+    int64_t part_off;      // partial-sum offset (blocks cut into several pieces)
+    int32_t K, n_out, ld;  // rows, outputs, row stride
+    int32_t x_off;         // x offset (contiguous source)
+    int32_t xidx_off;      // >= 0: x_k = x[bidx[xidx_off + k]]
+    int32_t add_off;       // >= 0: add offset
+    int32_t out_off;
+    int32_t n_pieces;
 };
+struct ColPiece {
+    int32_t desc, k0, k1, piece;
+};
+// One streaming launch: descriptors, pieces, the piece range of every CTA,
+// partial sums and per-block completion counters.
 struct StreamPlan {
-    DBuf<RowDesc> descs;
-    DBuf<StreamTile> tiles;
-    DBuf<int32_t> cta_tiles;
-    int n_ctas = 0, xcap = 8;
+    DBuf<ColDesc> descs;
+    DBuf<ColPiece> pieces;
+    DBuf<int32_t> cta_pieces;
+    DBuf<float4> part;
+    DBuf<int32_t> cnt;
+    int n_ctas = 0;
     size_t smem = 0;
-    std::vector<RowDesc> host;
+    std::vector<ColDesc> host;
 };
 
 // One resident request of the serving loop, as the batched kernels see it.
