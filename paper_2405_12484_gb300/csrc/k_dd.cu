@@ -615,9 +615,6 @@ void dd_solve_stream(pd_mesh* m, const T* pool, const float4* b, float4* xout, c
     phase_begin(m, PH_CONDENSE, s);
     launch_stream_cols(m->st_cond, pr, pool, b, nullptr, nullptr, w.tc, err, s);
     phase_end(m, s);
-    phase_begin(m, PH_INTERIOR, s);
-    launch_stream_cols(m->st_int, pr, pool, b, nullptr, nullptr, w.tc, err, s);
-    phase_end(m, s);
     if (m->n_B > 0) {
         phase_begin(m, PH_GATHER, s);
         k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, w.tc, w.cB);
@@ -629,9 +626,6 @@ void dd_solve_stream(pd_mesh* m, const T* pool, const float4* b, float4* xout, c
         if (m->two_level) {
             phase_begin(m, PH_CONDENSE2, s);
             launch_stream_cols(m->st_cond2, pr, pool, w.cB, nullptr, nullptr, w.tc2, err, s);
-            phase_end(m, s);
-            phase_begin(m, PH_INTERIOR2, s);
-            launch_stream_cols(m->st_int2, pr, pool, w.cB, nullptr, nullptr, w.tc2, err, s);
             phase_end(m, s);
             phase_begin(m, PH_GATHER2, s);
             k_gather<<<nblk(m->n_top, 256), 256, 0, s>>>(m->n_top, m->d_gat2_ptr.p, m->d_gat2.p, w.cB + T0, w.tc2,

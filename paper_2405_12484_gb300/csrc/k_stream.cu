@@ -9,8 +9,10 @@
 // launch is bound by HBM.  One producer thread per CTA streams whole-row
 // tiles into a shared-memory ring with bulk asynchronous copies
 // (cp.async.bulk, completion counted in bytes on an mbarrier), keeping
-// kStages x kStageBytes per SM in flight whatever the compute warps do.
-// Sixteen consumer warps own (output slab, row group) pairs: a warp adds
+// kStages x kStageBytes per SM in flight whatever the compute warps do; a
+// second warp loads the x slice of the next piece (gathered where the block
+// says so) into a double buffer.  Sixteen consumer warps own (output slab,
+// row group) pairs: a warp adds
 // A[k][slab] * x_k for the rows k of its group, with x_k a shared-memory
 // broadcast and the accumulators in registers (no cross-lane reductions).
 // The row groups of a slab are combined in group order through shared memory.
@@ -34,7 +36,7 @@ namespace pdg {
 namespace {
 
 constexpr int kColWarps = 16;                            // consumer warps
-constexpr int kColThreads = 32 * (kColWarps + 1);        // + one producer warp
+constexpr int kColThreads = 32 * (kColWarps + 2);        // + copy producer and x loader warps
 constexpr int kStages = 4;
 constexpr int kStageBytes = 24 * 1024;
 constexpr int kMaxGroups = 8;                            // row groups per slab
@@ -137,6 +139,18 @@ __host__ __device__ inline void col_layout(int n_out, int slab_out, int& S, int&
     if (G < 1) G = 1;
 }
 
+// largest (G - 1) * S over the slab counts S (the row-group partials kept in red[])
+__host__ __device__ constexpr int red_slabs() {
+    int best = 0;
+    for (int S = 1; S <= kColWarps; ++S) {
+        int G = kColWarps / S;
+        if (G > kMaxGroups) G = kMaxGroups;
+        if (G < 1) G = 1;
+        if ((G - 1) * S > best) best = (G - 1) * S;
+    }
+    return best;
+}
+
 template <class T>
 __global__ void __launch_bounds__(kColThreads, 1)
     k_stream_cols(const ColDesc* __restrict__ descs, const ColPiece* __restrict__ pieces,
@@ -146,10 +160,12 @@ __global__ void __launch_bounds__(kColThreads, 1)
     constexpr int ES = (int)sizeof(T);
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned char* ring = sm;
-    float4* xs = reinterpret_cast<float4*>(sm + (size_t)kStages * kStageBytes);    // [kMaxPieceRows]
-    float* red = reinterpret_cast<float*>(xs + kMaxPieceRows);                      // [(kMaxGroups-1)*kColWarps... ]
-    uint64_t* full = reinterpret_cast<uint64_t*>(red + (size_t)(kMaxGroups - 1) * 2 * SO * 3);
+    float4* xs = reinterpret_cast<float4*>(sm + (size_t)kStages * kStageBytes);    // [2][kMaxPieceRows]
+    float* red = reinterpret_cast<float*>(xs + 2 * kMaxPieceRows);                  // [red_slabs()][SO][3]
+    uint64_t* full = reinterpret_cast<uint64_t*>(red + (size_t)red_slabs() * SO * 3);
     uint64_t* empty = full + kStages;
+    uint64_t* xfull = empty + kStages;   // [2]
+    uint64_t* xempty = xfull + 2;        // [2]
     __shared__ int abort_flag, last_flag;
 
     const int p0 = cta_pieces[blockIdx.x], p1 = cta_pieces[blockIdx.x + 1];
@@ -158,6 +174,10 @@ __global__ void __launch_bounds__(kColThreads, 1)
         for (int k = 0; k < kStages; ++k) {
             mbar_init(&full[k], 1);
             mbar_init(&empty[k], kColWarps);
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&xfull[k], 1);
+            mbar_init(&xempty[k], kColWarps);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -199,22 +219,51 @@ __global__ void __launch_bounds__(kColThreads, 1)
             if (!mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u)) atomicOr(err, ERR_TIMEOUT);
         return;
     }
+    if (warp == kColWarps + 1) {
+        // ---- x loader: the x slice of every piece (gathered where the block says
+        // so) into a double buffer, ahead of the consumers
+        for (int p = p0; p < p1; ++p) {
+            const int pp = p - p0, buf = pp & 1;
+            if (pp >= 2) {
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait(&xempty[buf], (uint32_t)((pp / 2) - 1) & 1u);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) {
+                    if (lane == 0) {
+                        atomicOr(err, ERR_TIMEOUT);
+                        atomicExch(&abort_flag, 1);
+                    }
+                    return;
+                }
+            }
+            const ColPiece pc = pieces[p];
+            const ColDesc D = descs[pc.desc];
+            float4* xb = xs + buf * kMaxPieceRows;
+            for (int k = lane; k < pc.k1 - pc.k0; k += 32) {
+                const int kk = pc.k0 + k;
+                xb[k] = (D.xidx_off >= 0) ? B.x[B.bidx[D.xidx_off + kk]] : B.x[D.x_off + kk];
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xfull[buf]);   // release: the warp's writes above
+        }
+        return;
+    }
 
     // ---- consumers
     const int tid = threadIdx.x;
     int i = 0;   // tile counter (same sequence as the producer's)
     for (int p = p0; p < p1; ++p) {
+        const int pp = p - p0, buf = pp & 1;
         const ColPiece pc = pieces[p];
         const ColDesc D = descs[pc.desc];
         const int rpt = col_rows_per_tile(D.ld, ES);
         int S, G;
         col_layout(D.n_out, SO, S, G);
-        // x slice of the piece (the previous piece ended with a consumer barrier)
-        for (int k = tid; k < pc.k1 - pc.k0; k += 32 * kColWarps) {
-            const int kk = pc.k0 + k;
-            xs[k] = (D.xidx_off >= 0) ? B.x[B.bidx[D.xidx_off + kk]] : B.x[D.x_off + kk];
+        if (!*reinterpret_cast<volatile int*>(&abort_flag) && !mbar_wait(&xfull[buf], (uint32_t)(pp / 2) & 1u)) {
+            atomicOr(err, ERR_TIMEOUT);
+            atomicExch(&abort_flag, 1);
         }
-        consumer_sync();
+        const float4* xb = xs + buf * kMaxPieceRows;
         const bool active = warp < S * G;
         const int slab = warp % S, grp = warp / S;
         const int o_base = slab * SO + lane * VN;
@@ -241,7 +290,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 if (r < 0) r += G;
 #pragma unroll 2
                 for (; r < nr; r += G) {
-                    const float4 xk = xs[k - pc.k0 + r];
+                    const float4 xk = xb[k - pc.k0 + r];
                     const T* a = A + (int64_t)r * D.ld + o_base;
 #pragma unroll
                     for (int mm = 0; mm < M; ++mm) {
@@ -260,6 +309,8 @@ __global__ void __launch_bounds__(kColThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[slot]);
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&xempty[buf]);   // this warp no longer reads the x slice
         // combine the row groups of each slab in group order
         if (active && grp > 0) {
             float* rb = red + ((size_t)(grp - 1) * S + slab) * SO * 3;
@@ -273,7 +324,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
                     rb[3 * lo + 2] = acc[mm][j][2];
                 }
         }
-        consumer_sync();
+        if (G > 1) consumer_sync();
         const bool single = D.n_pieces == 1;
         if (active && grp == 0) {
 #pragma unroll
@@ -300,13 +351,18 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 }
         }
         if (!single) {
-            // the CTA that completes the block's last piece adds the pieces in order
-            __threadfence();
+            // the CTA that completes the block's last piece adds the pieces in
+            // order: one release (fence + counter) per CTA after a CTA barrier,
+            // an acquire fence on the counter's result
             consumer_sync();
-            if (tid == 0) last_flag = (atomicAdd(&cnt[pc.desc], 1) == D.n_pieces - 1);
+            if (tid == 0) {
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                const int prev = atomicAdd(&cnt[pc.desc], 1);
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                last_flag = (prev == D.n_pieces - 1);
+            }
             consumer_sync();
             if (last_flag) {
-                __threadfence();
                 for (int o = tid; o < D.n_out; o += 32 * kColWarps) {
                     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
                     for (int q = 0; q < D.n_pieces; ++q) {
@@ -321,14 +377,14 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 if (tid == 0) cnt[pc.desc] = 0;   // ready for the next launch
             }
         }
-        consumer_sync();   // xs and red are free for the next piece
+        if (G > 1 || !single) consumer_sync();   // red[] (and last_flag) free for the next piece
     }
 }
 
 template <class T>
 size_t col_smem_bytes() {
-    return (size_t)kStages * kStageBytes + sizeof(float4) * kMaxPieceRows +
-           sizeof(float) * (size_t)(kMaxGroups - 1) * 2 * Slab<T>::OUT * 3 + sizeof(uint64_t) * 2 * kStages;
+    return (size_t)kStages * kStageBytes + sizeof(float4) * 2 * kMaxPieceRows +
+           sizeof(float) * (size_t)red_slabs() * Slab<T>::OUT * 3 + sizeof(uint64_t) * (2 * kStages + 4);
 }
 
 }  // namespace

@@ -1112,11 +1112,11 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
                                   i2_off[g]));
             }
         }
-        bool ok = build_stream_plan(m->st_cond, cc, m->prec, s) && build_stream_plan(m->st_int, ci, m->prec, s) &&
-                  build_stream_plan(m->st_back, cb, m->prec, s);
-        if (ok && two)
-            ok = build_stream_plan(m->st_cond2, c2, m->prec, s) && build_stream_plan(m->st_int2, i2, m->prec, s) &&
-                 build_stream_plan(m->st_back2, b2v, m->prec, s);
+        // both parts of a condensation read the same x: one launch each level
+        cc.insert(cc.end(), ci.begin(), ci.end());
+        c2.insert(c2.end(), i2.begin(), i2.end());
+        bool ok = build_stream_plan(m->st_cond, cc, m->prec, s) && build_stream_plan(m->st_back, cb, m->prec, s);
+        if (ok && two) ok = build_stream_plan(m->st_cond2, c2, m->prec, s) && build_stream_plan(m->st_back2, b2v, m->prec, s);
         m->use_stream = ok;
     }
 
@@ -1147,6 +1147,10 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->phase_bytes[PH_ASSEMBLE] = nf * (4 + 16 + 16) + ninc * (4 + 16);
         m->phase_bytes[PH_CONDENSE] = mat_c + (int64_t)n_int * 16 + nbd_tot * 16;
         m->phase_bytes[PH_INTERIOR] = mat_i + (int64_t)n_int * 32;
+        if (m->use_stream) {   // one launch reads b_i once for both parts
+            m->phase_bytes[PH_CONDENSE] = mat_c + mat_i + (int64_t)n_int * 16 + (int64_t)tcr * 16;
+            m->phase_bytes[PH_INTERIOR] = 0;
+        }
         m->phase_bytes[PH_GATHER] = (int64_t)n_B * (4 + 16 + 16) + ngat * (4 + 16);
         const int64_t ncs = m->cs_n;
         m->phase_bytes[PH_COARSE] = ncs * colsS * es + ncs * 16 + (int64_t)m->coarse_nchunks * ncs * 16;
@@ -1154,6 +1158,10 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         if (two) {
             m->phase_bytes[PH_CONDENSE2] = mat_c2 + (int64_t)(n_B - nT) * 16 + (int64_t)b2all.size() * 16;
             m->phase_bytes[PH_INTERIOR2] = mat_i2 + (int64_t)(n_B - nT) * 32;
+            if (m->use_stream) {
+                m->phase_bytes[PH_CONDENSE2] = mat_c2 + mat_i2 + (int64_t)(n_B - nT) * 16 + (int64_t)m->n_tc2 * 16;
+                m->phase_bytes[PH_INTERIOR2] = 0;
+            }
             m->phase_bytes[PH_GATHER2] = (int64_t)nT * (4 + 16 + 16) + (int64_t)m->n_gat2 * (4 + 16);
             m->phase_bytes[PH_BACKSUB2] = mat_b2 + (int64_t)b2all.size() * (4 + 16) + (int64_t)(n_B - nT) * 32;
         }
@@ -1165,6 +1173,11 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         if (two)
             dd += (m->rows_cond2.n_blocks > 0 ? 1 : 0) + (m->rows_int2.n_blocks > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) +
                   (m->rows_back2.n_blocks > 0 ? 1 : 0);
+        if (m->use_stream) {
+            // condensation (both parts), gather, coarse, reduce, back-substitution; per level
+            dd = (m->st_cond.n_ctas > 0 ? 1 : 0) + (n_B > 0 ? 3 : 0) + (m->st_back.n_ctas > 0 ? 1 : 0);
+            if (two) dd += (m->st_cond2.n_ctas > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) + (m->st_back2.n_ctas > 0 ? 1 : 0);
+        }
         m->launches_per_iter = 2 + dd + (m->correction ? 2 : 0) + m->refine * (2 + dd);
     }
 
