@@ -18,8 +18,8 @@
 
 namespace pdg {
 
-void launch_stream_cols(const StreamPlan& P, int prec, const void* pool, const float4* x, const int* xidx,
-                        const float4* add, float4* out, int* err, cudaStream_t s);
+void launch_stream_cols(const StreamPlan& P, const float4* x, const int* xidx, const float4* add, float4* out,
+                        int* err, cudaStream_t s);
 
 namespace {
 
@@ -610,10 +610,9 @@ struct DDBufs {
 // product, in dependency order on one stream).
 template <class T>
 void dd_solve_stream(pd_mesh* m, const T* pool, const float4* b, float4* xout, const DDBufs& w, cudaStream_t s) {
-    const int pr = m->prec;
     int* err = m->d_err.p;
     phase_begin(m, PH_CONDENSE, s);
-    launch_stream_cols(m->st_cond, pr, pool, b, nullptr, nullptr, w.tc, err, s);
+    launch_stream_cols(m->st_cond, b, nullptr, nullptr, w.tc, err, s);
     phase_end(m, s);
     if (m->n_B > 0) {
         phase_begin(m, PH_GATHER, s);
@@ -625,7 +624,7 @@ void dd_solve_stream(pd_mesh* m, const T* pool, const float4* b, float4* xout, c
         const int T0 = m->n_B - m->n_top;
         if (m->two_level) {
             phase_begin(m, PH_CONDENSE2, s);
-            launch_stream_cols(m->st_cond2, pr, pool, w.cB, nullptr, nullptr, w.tc2, err, s);
+            launch_stream_cols(m->st_cond2, w.cB, nullptr, nullptr, w.tc2, err, s);
             phase_end(m, s);
             phase_begin(m, PH_GATHER2, s);
             k_gather<<<nblk(m->n_top, 256), 256, 0, s>>>(m->n_top, m->d_gat2_ptr.p, m->d_gat2.p, w.cB + T0, w.tc2,
@@ -644,13 +643,13 @@ void dd_solve_stream(pd_mesh* m, const T* pool, const float4* b, float4* xout, c
         phase_end(m, s);
         if (m->two_level) {
             phase_begin(m, PH_BACKSUB2, s);
-            launch_stream_cols(m->st_back2, pr, pool, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int, err,
+            launch_stream_cols(m->st_back2, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int, err,
                                s);
             phase_end(m, s);
         }
     }
     phase_begin(m, PH_BACKSUB, s);
-    launch_stream_cols(m->st_back, pr, pool, xout + m->n_int, m->d_bidx.p, w.tc, xout, err, s);
+    launch_stream_cols(m->st_back, xout + m->n_int, m->d_bidx.p, w.tc, xout, err, s);
     phase_end(m, s);
 }
 

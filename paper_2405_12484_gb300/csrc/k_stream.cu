@@ -1,32 +1,36 @@
 // Streaming products of the subspace solve (Sec. 7.2) on sm_103a in the
 // column ("axpy") form: out[o] = add[o] + sum_k A[k][o] x_k for o < n_out,
-// the rows k of A contiguous in memory, x_k three right-hand sides
-// (K = K_s (x) I_3).  Every product of the solve has this form with the
-// factors the pool holds: K_ii^-1 (symmetric), Psi_d, Psi_d^T, and the same
-// for the second level and the coarse inverse.
+// x_k three right-hand sides (K = K_s (x) I_3).  Every product of the solve
+// has this form with the factors of the pool: K_ii^-1 (symmetric), Psi_d,
+// Psi_d^T, and the same for the second level.
+//
+// Layout: the plan copies each block into column panels of at most 256
+// outputs, every panel contiguous (rows k of the panel back to back), so a
+// unit of work (a panel, or a range of its rows) is one contiguous stream.
 //
 // The matrices are read once per solve and are far larger than L2: the
 // launch is bound by HBM.  One producer thread per CTA streams whole-row
 // tiles into a shared-memory ring with bulk asynchronous copies
 // (cp.async.bulk, completion counted in bytes on an mbarrier), keeping
 // kStages x kStageBytes per SM in flight whatever the compute warps do; a
-// second warp loads the x slice of the next piece (gathered where the block
-// says so) into a double buffer.  Sixteen consumer warps own (output slab,
-// row group) pairs: a warp adds
-// A[k][slab] * x_k for the rows k of its group, with x_k a shared-memory
-// broadcast and the accumulators in registers (no cross-lane reductions).
-// The row groups of a slab are combined in group order through shared memory.
+// second warp loads the x slice of the next piece (one bulk copy, or
+// gathered loads where the block says so) into a double buffer.  Sixteen
+// consumer warps split the rows of a tile (row groups); each lane owns a few
+// outputs of the panel and adds A[k][o] x_k with x_k a shared-memory
+// broadcast and paired FMAs, accumulators in registers, no cross-lane
+// reductions.  At the end of a piece all consumer threads add the row
+// groups in group order through shared memory.
 //
-// Work split: the rows of all blocks are cut into pieces, one contiguous
-// byte range of about the same size per CTA (a block may span CTAs).  A block
-// cut into several pieces writes per-piece partial sums; the CTA that
-// finishes the block's last piece (an atomic counter, no waiting) adds them in
-// piece order.  Results are bitwise reproducible for a given plan.
+// Work split: the panels' rows are cut into pieces, one contiguous byte range
+// of about the same size per CTA (a panel may span CTAs).  A panel cut into
+// several pieces writes per-piece partial sums; the CTA that finishes the
+// panel's last piece (an atomic counter, no waiting) adds them in piece
+// order.  Results are bitwise reproducible for a given plan.
 //
 // Every wait is bounded: a wait that runs out sets ERR_TIMEOUT in the mesh's
 // error word and marks the CTA aborted (no further copies are issued,
-// consumers stop waiting); the producer waits, again bounded, for its copies
-// in flight before it exits.
+// consumers stop waiting); the producer and the x loader wait, again
+// bounded, for their copies in flight before they exit.
 #include <algorithm>
 
 #include "pd_internal.h"
@@ -36,11 +40,15 @@ namespace pdg {
 namespace {
 
 constexpr int kColWarps = 16;                            // consumer warps
-constexpr int kColThreads = 32 * (kColWarps + 2);        // + copy producer and x loader warps
-constexpr int kStages = 4;
-constexpr int kStageBytes = 24 * 1024;
-constexpr int kMaxGroups = 8;                            // row groups per slab
-constexpr int kMaxPieceRows = 1024;                      // x slice of a piece in shared memory
+constexpr int kEpiWarps = 4;                             // epilogue warps
+constexpr int kColThreads = 32 * (kColWarps + 2 + kEpiWarps);   // + copy producer, x loader, epilogue
+constexpr int kPanel = 256;                              // outputs of one panel
+constexpr int kStages = 3;
+constexpr int kStageBytes = 32 * 1024;
+constexpr int kMaxGroups = 16;                           // row groups per slab
+constexpr int kMaxPieceRows = 512;                       // x slice of a piece in shared memory
+constexpr int kMaxCtaPieces = 64;                        // piece records of one CTA in shared memory
+static_assert(sizeof(ColPieceRec) % 16 == 0, "piece records are copied in 16-byte words");
 constexpr long long kWaitLimit = 1LL << 24;              // try_wait polls before giving up
 
 template <class T>
@@ -98,8 +106,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-__device__ __forceinline__ void consumer_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kColWarps) : "memory");
+
+__device__ __forceinline__ void epi_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
 }
 
 __device__ __forceinline__ void vec_from_smem(const float* p, float (&v)[4]) {
@@ -122,8 +131,9 @@ __device__ __forceinline__ void vec_from_smem(const __nv_bfloat16* p, float (&v)
 template <class T>
 struct Slab {
     static constexpr int VN = SVec<T>::N;
-    static constexpr int M = (VN == 4) ? 2 : 1;
+    static constexpr int M = 1;
     static constexpr int OUT = 32 * VN * M;
+    static constexpr int RB = (OUT <= 128) ? 3 : 2;   // row-group partial buffers (epilogue lag in pieces)
 };
 
 __host__ __device__ inline int col_rows_per_tile(int ld, int es) {
@@ -139,37 +149,36 @@ __host__ __device__ inline void col_layout(int n_out, int slab_out, int& S, int&
     if (G < 1) G = 1;
 }
 
-// largest (G - 1) * S over the slab counts S (the row-group partials kept in red[])
-__host__ __device__ constexpr int red_slabs() {
-    int best = 0;
-    for (int S = 1; S <= kColWarps; ++S) {
-        int G = kColWarps / S;
-        if (G > kMaxGroups) G = kMaxGroups;
-        if (G < 1) G = 1;
-        if ((G - 1) * S > best) best = (G - 1) * S;
-    }
-    return best;
-}
-
 template <class T>
 __global__ void __launch_bounds__(kColThreads, 1)
-    k_stream_cols(const ColDesc* __restrict__ descs, const ColPiece* __restrict__ pieces,
-                  const int32_t* __restrict__ cta_pieces, AxBases B, float4* __restrict__ part,
+    k_stream_cols(const ColPieceRec* __restrict__ recs, const int32_t* __restrict__ cta_pieces, AxBases B,
+                  float4* __restrict__ part,
                   int* __restrict__ cnt, int* __restrict__ err) {
     constexpr int VN = Slab<T>::VN, M = Slab<T>::M, SO = Slab<T>::OUT;
     constexpr int ES = (int)sizeof(T);
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned char* ring = sm;
     float4* xs = reinterpret_cast<float4*>(sm + (size_t)kStages * kStageBytes);    // [2][kMaxPieceRows]
-    float* red = reinterpret_cast<float*>(xs + 2 * kMaxPieceRows);                  // [red_slabs()][SO][3]
-    uint64_t* full = reinterpret_cast<uint64_t*>(red + (size_t)red_slabs() * SO * 3);
+    float* red = reinterpret_cast<float*>(xs + 2 * kMaxPieceRows);                  // [2][kColWarps][SO][3]
+    constexpr int RB = Slab<T>::RB;
+    uint64_t* full = reinterpret_cast<uint64_t*>(red + (size_t)RB * kColWarps * SO * 3);
     uint64_t* empty = full + kStages;
     uint64_t* xfull = empty + kStages;   // [2]
     uint64_t* xempty = xfull + 2;        // [2]
+    uint64_t* rfull = xempty + 2;        // [RB]
+    uint64_t* rempty = rfull + RB;       // [RB]
     __shared__ int abort_flag, last_flag;
+    __shared__ __align__(16) ColPieceRec srec[kMaxCtaPieces];
 
     const int p0 = cta_pieces[blockIdx.x], p1 = cta_pieces[blockIdx.x + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        // every piece record of this CTA into shared memory (16-byte words)
+        const int nw = (p1 - p0) * (int)(sizeof(ColPieceRec) / 16);
+        const int4* src = reinterpret_cast<const int4*>(recs + p0);
+        int4* dst = reinterpret_cast<int4*>(srec);
+        for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = src[k];
+    }
     if (threadIdx.x == 0) {
         for (int k = 0; k < kStages; ++k) {
             mbar_init(&full[k], 1);
@@ -178,6 +187,10 @@ __global__ void __launch_bounds__(kColThreads, 1)
         for (int k = 0; k < 2; ++k) {
             mbar_init(&xfull[k], 1);
             mbar_init(&xempty[k], kColWarps);
+        }
+        for (int k = 0; k < RB; ++k) {
+            mbar_init(&rfull[k], kColWarps);
+            mbar_init(&rempty[k], 1);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -193,8 +206,8 @@ __global__ void __launch_bounds__(kColThreads, 1)
         int i = 0, issued = 0;
         bool stop = false;
         for (int p = p0; p < p1 && !stop; ++p) {
-            const ColPiece pc = pieces[p];
-            const ColDesc D = descs[pc.desc];
+            const ColPiece pc = srec[p - p0].p;
+            const ColDesc D = srec[p - p0].d;
             const int rpt = col_rows_per_tile(D.ld, ES);
             for (int k = pc.k0; k < pc.k1; k += rpt, ++i) {
                 if (*reinterpret_cast<volatile int*>(&abort_flag)) {
@@ -222,6 +235,8 @@ __global__ void __launch_bounds__(kColThreads, 1)
     if (warp == kColWarps + 1) {
         // ---- x loader: the x slice of every piece (gathered where the block says
         // so) into a double buffer, ahead of the consumers
+        int bulk_mask = 0;   // bit b: the last slice written to buffer b came by bulk copy
+        int done = 0;        // pieces whose slice was issued
         for (int p = p0; p < p1; ++p) {
             const int pp = p - p0, buf = pp & 1;
             if (pp >= 2) {
@@ -233,29 +248,126 @@ __global__ void __launch_bounds__(kColThreads, 1)
                         atomicOr(err, ERR_TIMEOUT);
                         atomicExch(&abort_flag, 1);
                     }
-                    return;
+                    break;
                 }
             }
-            const ColPiece pc = pieces[p];
-            const ColDesc D = descs[pc.desc];
+            const ColPiece pc = srec[p - p0].p;
+            const ColDesc D = srec[p - p0].d;
             float4* xb = xs + buf * kMaxPieceRows;
-            for (int k = lane; k < pc.k1 - pc.k0; k += 32) {
-                const int kk = pc.k0 + k;
-                xb[k] = (D.xidx_off >= 0) ? B.x[B.bidx[D.xidx_off + kk]] : B.x[D.x_off + kk];
+            const int n = pc.k1 - pc.k0;
+            if (D.xidx_off < 0 && n > 0) {
+                // contiguous slice: one bulk copy, completion counted on xfull
+                if (lane == 0) {
+                    const uint32_t bytes = (uint32_t)n * 16u;
+                    mbar_arrive_expect_tx(&xfull[buf], bytes);
+                    bulk_g2s(xb, B.x + D.x_off + pc.k0, bytes, &xfull[buf]);
+                }
+                bulk_mask |= 1 << buf;
+            } else {
+                bulk_mask &= ~(1 << buf);
+                // gathered slice: eight independent loads in flight per lane
+                for (int k0 = 0; k0 < n; k0 += 32 * 8) {
+                    float4 v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int k = k0 + u * 32 + lane;
+                        if (k < n) v[u] = B.x[B.bidx[D.xidx_off + pc.k0 + k]];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int k = k0 + u * 32 + lane;
+                        if (k < n) xb[k] = v[u];
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&xfull[buf]);   // release: the warp's writes above
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&xfull[buf]);   // release: the warp's writes above
+            done = pp + 1;
+        }
+        // before exit: the last bulk copies have landed (normally long since consumed)
+        for (int pp = (done > 2 ? done - 2 : 0); pp < done; ++pp)
+            if (lane == 0 && (bulk_mask >> (pp & 1) & 1) && !mbar_wait(&xfull[pp & 1], (uint32_t)(pp / 2) & 1u))
+                atomicOr(err, ERR_TIMEOUT);
+        return;
+    }
+
+    if (warp >= kColWarps + 2) {
+        // ---- epilogue warps: add the row groups of every output in group order,
+        // write the outputs or the piece's partial sums, and for a panel cut into
+        // several pieces let the CTA completing the last piece add them in order;
+        // runs beside the consumers, which go on with the next piece
+        const int et = threadIdx.x - 32 * (kColWarps + 2);
+        for (int p = p0; p < p1; ++p) {
+            const int pp = p - p0, rbuf = pp % RB;
+            const ColPiece pc = srec[pp].p;
+            const ColDesc D = srec[pp].d;
+            int S, G;
+            col_layout(D.n_out, SO, S, G);
+            if (et == 0 && !*reinterpret_cast<volatile int*>(&abort_flag) &&
+                !mbar_wait(&rfull[rbuf], (uint32_t)(pp / RB) & 1u)) {
+                atomicOr(err, ERR_TIMEOUT);
+                atomicExch(&abort_flag, 1);
+            }
+            epi_sync();
+            const float* rb = red + (size_t)rbuf * kColWarps * SO * 3;
+            const bool single = D.n_pieces == 1;
+            for (int o = et; o < D.n_out; o += 32 * kEpiWarps) {
+                const int sl = o / SO, lo = o - sl * SO;
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+                for (int g = 0; g < G; ++g) {
+                    const float* q = rb + ((size_t)(g * S + sl) * SO + lo) * 3;
+                    s0 += q[0];
+                    s1 += q[1];
+                    s2 += q[2];
+                }
+                if (single) {
+                    const float4 ad = (D.add_off >= 0) ? B.add[D.add_off + o] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    B.out[D.out_off + o] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
+                } else {
+                    part[D.part_off + (int64_t)pc.piece * D.n_out + o] = make_float4(s0, s1, s2, 0.f);
+                }
+            }
+            epi_sync();   // red[rbuf] read by every epilogue thread
+            if (et == 0) mbar_arrive(&rempty[rbuf]);
+            if (!single) {
+                // release the partial sums (barrier, then one gpu-scope fence) and
+                // count the piece
+                if (et == 0) {
+                    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                    const int prev = atomicAdd(&cnt[pc.desc], 1);
+                    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                    last_flag = (prev == D.n_pieces - 1);
+                }
+                epi_sync();
+                if (last_flag) {
+                    for (int o = et; o < D.n_out; o += 32 * kEpiWarps) {
+                        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
+                        for (int q = 0; q < D.n_pieces; ++q) {
+                            const float4 v = __ldcg(&part[D.part_off + (int64_t)q * D.n_out + o]);
+                            s0 += v.x;
+                            s1 += v.y;
+                            s2 += v.z;
+                        }
+                        const float4 ad =
+                            (D.add_off >= 0) ? B.add[D.add_off + o] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        B.out[D.out_off + o] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
+                    }
+                    if (et == 0) cnt[pc.desc] = 0;   // ready for the next launch
+                }
+                epi_sync();   // last_flag free for the next piece
+            }
         }
         return;
     }
 
-    // ---- consumers
-    const int tid = threadIdx.x;
+    // ---- consumers: hand the row-group partials of a piece to the epilogue
+    // warps and go on with the next piece
     int i = 0;   // tile counter (same sequence as the producer's)
     for (int p = p0; p < p1; ++p) {
         const int pp = p - p0, buf = pp & 1;
-        const ColPiece pc = pieces[p];
-        const ColDesc D = descs[pc.desc];
+        const ColPiece pc = srec[pp].p;
+        const ColDesc D = srec[pp].d;
         const int rpt = col_rows_per_tile(D.ld, ES);
         int S, G;
         col_layout(D.n_out, SO, S, G);
@@ -267,148 +379,153 @@ __global__ void __launch_bounds__(kColThreads, 1)
         const bool active = warp < S * G;
         const int slab = warp % S, grp = warp / S;
         const int o_base = slab * SO + lane * VN;
-        float acc[M][VN][3];
+        // accumulators of output pairs (2jp, 2jp+1), one per right-hand side:
+        // paired FMAs (FFMA2), each lane of the pair rounded like fmaf
+        float2 acc[M][VN / 2][3];
 #pragma unroll
         for (int mm = 0; mm < M; ++mm)
 #pragma unroll
-            for (int j = 0; j < VN; ++j) acc[mm][j][0] = acc[mm][j][1] = acc[mm][j][2] = 0.f;
+            for (int j = 0; j < VN / 2; ++j) acc[mm][j][0] = acc[mm][j][1] = acc[mm][j][2] = make_float2(0.f, 0.f);
         bool valid[M];
 #pragma unroll
         for (int mm = 0; mm < M; ++mm) valid[mm] = active && (o_base + mm * 32 * VN < D.n_out);
+        int ph = 0;   // (k - k0) mod G at the start of the tile
         for (int k = pc.k0; k < pc.k1; k += rpt, ++i) {
             const int slot = i % kStages;
-            if (!*reinterpret_cast<volatile int*>(&abort_flag) &&
+            // one lane of each warp polls the stage barrier; the warp barrier then
+            // orders the other lanes after it (fewer polls competing with the copies)
+            if (lane == 0 && !*reinterpret_cast<volatile int*>(&abort_flag) &&
                 !mbar_wait(&full[slot], (uint32_t)(i / kStages) & 1u)) {
                 atomicOr(err, ERR_TIMEOUT);
                 atomicExch(&abort_flag, 1);
             }
+            __syncwarp();
             const T* A = reinterpret_cast<const T*>(ring + (size_t)slot * kStageBytes);
             const int nr = min(rpt, pc.k1 - k);
             if (valid[0]) {
                 // rows r of the tile with (k - k0 + r) = grp (mod G)
-                int r = grp - ((k - pc.k0) % G);
+                int r = grp - ph;
                 if (r < 0) r += G;
 #pragma unroll 2
                 for (; r < nr; r += G) {
                     const float4 xk = xb[k - pc.k0 + r];
-                    const T* a = A + (int64_t)r * D.ld + o_base;
+                    const float2 xx = make_float2(xk.x, xk.x), xy = make_float2(xk.y, xk.y);
+                    const float2 xz = make_float2(xk.z, xk.z);
+                    const T* a = A + r * D.ld + o_base;
 #pragma unroll
                     for (int mm = 0; mm < M; ++mm) {
                         if (!valid[mm]) continue;
                         float v[VN];
                         vec_from_smem(a + mm * 32 * VN, v);
 #pragma unroll
-                        for (int j = 0; j < VN; ++j) {
-                            acc[mm][j][0] = fmaf(v[j], xk.x, acc[mm][j][0]);
-                            acc[mm][j][1] = fmaf(v[j], xk.y, acc[mm][j][1]);
-                            acc[mm][j][2] = fmaf(v[j], xk.z, acc[mm][j][2]);
+                        for (int j = 0; j < VN / 2; ++j) {
+                            const float2 vv = make_float2(v[2 * j], v[2 * j + 1]);
+                            acc[mm][j][0] = __ffma2_rn(vv, xx, acc[mm][j][0]);
+                            acc[mm][j][1] = __ffma2_rn(vv, xy, acc[mm][j][1]);
+                            acc[mm][j][2] = __ffma2_rn(vv, xz, acc[mm][j][2]);
                         }
                     }
                 }
             }
+            ph += nr;
+            while (ph >= G) ph -= G;
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[slot]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&xempty[buf]);   // this warp no longer reads the x slice
-        // combine the row groups of each slab in group order
-        if (active && grp > 0) {
-            float* rb = red + ((size_t)(grp - 1) * S + slab) * SO * 3;
+        const int rbuf = pp % RB;
+        if (pp >= RB) {
+            // red[rbuf] was last filled for piece pp - RB: the epilogue must be done with it
+            if (lane == 0 && !*reinterpret_cast<volatile int*>(&abort_flag) &&
+                !mbar_wait(&rempty[rbuf], (uint32_t)((pp / RB) - 1) & 1u)) {
+                atomicOr(err, ERR_TIMEOUT);
+                atomicExch(&abort_flag, 1);
+            }
+            __syncwarp();
+        }
+        if (active) {
+            float* rb = red + ((size_t)rbuf * kColWarps + (size_t)(grp * S + slab)) * SO * 3;
 #pragma unroll
             for (int mm = 0; mm < M; ++mm)
 #pragma unroll
                 for (int j = 0; j < VN; ++j) {
                     const int lo = mm * 32 * VN + lane * VN + j;
-                    rb[3 * lo] = acc[mm][j][0];
-                    rb[3 * lo + 1] = acc[mm][j][1];
-                    rb[3 * lo + 2] = acc[mm][j][2];
+                    rb[3 * lo] = (j & 1) ? acc[mm][j / 2][0].y : acc[mm][j / 2][0].x;
+                    rb[3 * lo + 1] = (j & 1) ? acc[mm][j / 2][1].y : acc[mm][j / 2][1].x;
+                    rb[3 * lo + 2] = (j & 1) ? acc[mm][j / 2][2].y : acc[mm][j / 2][2].x;
                 }
         }
-        if (G > 1) consumer_sync();
-        const bool single = D.n_pieces == 1;
-        if (active && grp == 0) {
-#pragma unroll
-            for (int mm = 0; mm < M; ++mm)
-#pragma unroll
-                for (int j = 0; j < VN; ++j) {
-                    const int lo = mm * 32 * VN + lane * VN + j;
-                    const int o = slab * SO + lo;
-                    if (o >= D.n_out) continue;
-                    float s0 = acc[mm][j][0], s1 = acc[mm][j][1], s2 = acc[mm][j][2];
-                    for (int g = 1; g < G; ++g) {
-                        const float* rb = red + ((size_t)(g - 1) * S + slab) * SO * 3;
-                        s0 += rb[3 * lo];
-                        s1 += rb[3 * lo + 1];
-                        s2 += rb[3 * lo + 2];
-                    }
-                    if (single) {
-                        const float4 ad =
-                            (D.add_off >= 0) ? B.add[D.add_off + o] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        B.out[D.out_off + o] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
-                    } else {
-                        part[D.part_off + (int64_t)pc.piece * D.n_out + o] = make_float4(s0, s1, s2, 0.f);
-                    }
-                }
-        }
-        if (!single) {
-            // the CTA that completes the block's last piece adds the pieces in
-            // order: one release (fence + counter) per CTA after a CTA barrier,
-            // an acquire fence on the counter's result
-            consumer_sync();
-            if (tid == 0) {
-                asm volatile("fence.acq_rel.gpu;" ::: "memory");
-                const int prev = atomicAdd(&cnt[pc.desc], 1);
-                asm volatile("fence.acq_rel.gpu;" ::: "memory");
-                last_flag = (prev == D.n_pieces - 1);
-            }
-            consumer_sync();
-            if (last_flag) {
-                for (int o = tid; o < D.n_out; o += 32 * kColWarps) {
-                    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-                    for (int q = 0; q < D.n_pieces; ++q) {
-                        const float4 v = __ldcg(&part[D.part_off + (int64_t)q * D.n_out + o]);
-                        s0 += v.x;
-                        s1 += v.y;
-                        s2 += v.z;
-                    }
-                    const float4 ad = (D.add_off >= 0) ? B.add[D.add_off + o] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    B.out[D.out_off + o] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
-                }
-                if (tid == 0) cnt[pc.desc] = 0;   // ready for the next launch
-            }
-        }
-        if (G > 1 || !single) consumer_sync();   // red[] (and last_flag) free for the next piece
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rfull[rbuf]);   // release: this warp's partials
+    }
+}
+
+// Panel copies: dst panel (K rows x width, zero beyond `valid` columns) from
+// columns [c0, c0 + valid) of a row-major block of the pool.
+struct PanelCopy {
+    int64_t src_off, dst_off;
+    int32_t K, src_ld, c0, width, valid, pad;
+};
+
+template <class T>
+__global__ void k_copy_panels(const PanelCopy* __restrict__ pc, const T* __restrict__ src, T* __restrict__ dst) {
+    const PanelCopy P = pc[blockIdx.x];
+    const int64_t n = (int64_t)P.K * P.width;
+    for (int64_t l = threadIdx.x; l < n; l += blockDim.x) {
+        const int k = (int)(l / P.width), j = (int)(l - (int64_t)k * P.width);
+        dst[P.dst_off + l] = (j < P.valid) ? src[P.src_off + (int64_t)k * P.src_ld + P.c0 + j] : T(0.f);
     }
 }
 
 template <class T>
 size_t col_smem_bytes() {
     return (size_t)kStages * kStageBytes + sizeof(float4) * 2 * kMaxPieceRows +
-           sizeof(float) * (size_t)red_slabs() * Slab<T>::OUT * 3 + sizeof(uint64_t) * (2 * kStages + 4);
+           sizeof(float) * (size_t)Slab<T>::RB * kColWarps * Slab<T>::OUT * 3 +
+           sizeof(uint64_t) * (2 * kStages + 4 + 2 * Slab<T>::RB);
 }
 
 }  // namespace
 
-// Pieces of whole rows for every block in order, cut so that every CTA gets a
-// contiguous range of about the same number of bytes (at most kMaxPieceRows
-// rows per piece).  Returns false (plan left empty) when a row does not fit in
-// one stage or a block has more outputs than the consumer warps cover.
-bool build_stream_plan(StreamPlan& P, std::vector<ColDesc> descs, int prec, cudaStream_t s) {
+// Copies every block (a_off into the row-major pool src) into the plan's own
+// pool as contiguous column panels of at most kPanel outputs, cuts the
+// panels' rows into pieces so that every CTA gets a contiguous range of about
+// the same number of bytes (at most kMaxPieceRows rows per piece and
+// kMaxCtaPieces pieces per CTA), and uploads the piece records.  Returns
+// false (plan left empty) when a panel row does not fit in one stage.
+bool build_stream_plan(StreamPlan& P, const std::vector<ColDesc>& blocks, int prec, const void* src, cudaStream_t s) {
     P.n_ctas = 0;
     P.host.clear();
     const int es = (prec == PD_PREC_BF16) ? 2 : 4;
-    const int SO = (prec == PD_PREC_BF16) ? Slab<__nv_bfloat16>::OUT : Slab<float>::OUT;
+    // panels
+    std::vector<ColDesc> descs;
+    std::vector<PanelCopy> copies;
+    int64_t pool = 0;
+    for (const auto& D : blocks) {
+        if (D.n_out <= 0) continue;
+        for (int c0 = 0; c0 < D.n_out; c0 += kPanel) {
+            const int valid = std::min(kPanel, D.n_out - c0);
+            const int width = (valid + 7) / 8 * 8;
+            if ((int64_t)width * es > kStageBytes) return false;
+            ColDesc p = D;
+            p.a_off = pool;
+            p.ld = width;
+            p.n_out = valid;
+            p.out_off = D.out_off + c0;
+            p.add_off = (D.add_off >= 0) ? D.add_off + c0 : -1;
+            p.n_pieces = 1;
+            descs.push_back(p);
+            if (D.K > 0) copies.push_back(PanelCopy{D.a_off, pool, D.K, D.ld, c0, width, valid, 0});
+            pool += (int64_t)D.K * width;
+        }
+    }
     int dev = 0, sms = 0;
     PDG_CUDA(cudaGetDevice(&dev));
     PDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int C = std::max(1, sms);
     int64_t W = 0;
-    for (const auto& D : descs) {
-        if ((int64_t)D.ld * es > kStageBytes || D.ld % 8 != 0 || D.a_off % 8 != 0) return false;
-        if ((D.n_out + SO - 1) / SO > kColWarps) return false;
-        W += (int64_t)D.K * D.ld * es + (int64_t)D.n_out * 64;
-    }
-    // walk the blocks, closing a CTA's range when its byte budget is reached
+    for (const auto& D : descs) W += (int64_t)D.K * D.ld * es + (int64_t)D.n_out * 64;
+    // walk the panels, closing a CTA's range when its byte budget is reached
     std::vector<ColPiece> pcs;
     std::vector<int32_t> cut(1, 0);
     int64_t acc = 0;
@@ -419,7 +536,6 @@ bool build_stream_plan(StreamPlan& P, std::vector<ColDesc> descs, int prec, cuda
         int k = 0, piece = 0;
         acc += (int64_t)D.n_out * 64;
         do {
-            // rows that fit in what is left of this CTA's budget
             const int64_t budget = W * (c + 1) / C - acc;
             int take = (int)std::min<int64_t>(D.K - k, std::max<int64_t>(1, budget / std::max<int64_t>(row_b, 1)));
             take = std::min(take, kMaxPieceRows);
@@ -435,38 +551,60 @@ bool build_stream_plan(StreamPlan& P, std::vector<ColDesc> descs, int prec, cuda
         D.n_pieces = piece;
     }
     while ((int)cut.size() < C + 1) cut.push_back((int32_t)pcs.size());
+    for (int c2 = 0; c2 < C; ++c2)
+        if (cut[c2 + 1] - cut[c2] > kMaxCtaPieces) return false;
     int64_t po = 0;
     for (auto& D : descs) {
         D.part_off = po;
         if (D.n_pieces > 1) po += (int64_t)D.n_pieces * D.n_out;
     }
+    std::vector<ColPieceRec> recs(pcs.size());
+    for (size_t q = 0; q < pcs.size(); ++q) recs[q] = ColPieceRec{descs[pcs[q].desc], pcs[q]};
     const size_t smem = (prec == PD_PREC_BF16) ? col_smem_bytes<__nv_bfloat16>() : col_smem_bytes<float>();
     const int lim = std::min(allow_max_dynamic_smem(k_stream_cols<float>),
                              allow_max_dynamic_smem(k_stream_cols<__nv_bfloat16>));
     if (smem > (size_t)lim) return false;
-    upload(P.descs, descs, s);
-    upload(P.pieces, pcs, s);
+    // the panel pool
+    P.pan32.free();
+    P.pan16.free();
+    DBuf<PanelCopy> dcp;
+    upload(dcp, copies, s);
+    if (prec == PD_PREC_BF16) {
+        P.pan16.alloc((size_t)std::max<int64_t>(pool, 8));
+        if (!copies.empty())
+            k_copy_panels<__nv_bfloat16><<<(int)copies.size(), 256, 0, s>>>(
+                dcp.p, static_cast<const __nv_bfloat16*>(src), P.pan16.p);
+    } else {
+        P.pan32.alloc((size_t)std::max<int64_t>(pool, 8));
+        if (!copies.empty())
+            k_copy_panels<float><<<(int)copies.size(), 256, 0, s>>>(dcp.p, static_cast<const float*>(src), P.pan32.p);
+    }
+    PDG_CHECK_LAUNCH();
+    upload(P.recs, recs, s);
     upload(P.cta_pieces, cut, s);
     P.part.alloc((size_t)std::max<int64_t>(po, 1));
     P.cnt.alloc(std::max<size_t>(descs.size(), 1));
     PDG_CUDA(cudaMemsetAsync(P.cnt.p, 0, P.cnt.bytes(), s));
     PDG_CUDA(cudaStreamSynchronize(s));
     P.host = std::move(descs);
+    P.prec = prec;
     P.n_ctas = pcs.empty() ? 0 : C;
     P.smem = smem;
     return true;
 }
 
-void launch_stream_cols(const StreamPlan& P, int prec, const void* pool, const float4* x, const int* xidx,
-                        const float4* add, float4* out, int* err, cudaStream_t s) {
+void launch_stream_cols(const StreamPlan& P, const float4* x, const int* xidx, const float4* add, float4* out,
+                        int* err, cudaStream_t s) {
     if (P.n_ctas <= 0) return;
-    const AxBases B{pool, x, xidx, add, out};
-    if (prec == PD_PREC_BF16)
-        k_stream_cols<__nv_bfloat16><<<P.n_ctas, kColThreads, P.smem, s>>>(P.descs.p, P.pieces.p, P.cta_pieces.p, B,
-                                                                           P.part.p, P.cnt.p, err);
-    else
-        k_stream_cols<float><<<P.n_ctas, kColThreads, P.smem, s>>>(P.descs.p, P.pieces.p, P.cta_pieces.p, B, P.part.p,
-                                                                   P.cnt.p, err);
+    if (P.prec == PD_PREC_BF16) {
+        const AxBases B{P.pan16.p, x, xidx, add, out};
+        k_stream_cols<__nv_bfloat16><<<P.n_ctas, kColThreads, P.smem, s>>>(P.recs.p, P.cta_pieces.p, B, P.part.p,
+                                                                           P.cnt.p, err);
+    } else {
+        const AxBases B{P.pan32.p, x, xidx, add, out};
+        k_stream_cols<float><<<P.n_ctas, kColThreads, P.smem, s>>>(P.recs.p, P.cta_pieces.p, B, P.part.p, P.cnt.p,
+                                                                   err);
+    }
     PDG_CHECK_LAUNCH();
 }
 

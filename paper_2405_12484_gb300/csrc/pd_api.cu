@@ -26,7 +26,8 @@ int dd_coarse_chunk();
 int dd_configure_coarse(int ld_S);
 int ax_outputs_per_block(int prec);
 void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s);
-bool build_stream_plan(StreamPlan& P, std::vector<ColDesc> descs, int prec, cudaStream_t s);
+bool build_stream_plan(StreamPlan& P, const std::vector<ColDesc>& blocks, int prec, const void* src,
+                       cudaStream_t s);
 void reset_stream_plan(StreamPlan& P, cudaStream_t s);
 void launch_prefactor_helpers_scatter_coo(double* S, int ld, const int* r, const int* c, const double* v, int n,
                                           cudaStream_t s);
@@ -1115,8 +1116,11 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         // both parts of a condensation read the same x: one launch each level
         cc.insert(cc.end(), ci.begin(), ci.end());
         c2.insert(c2.end(), i2.begin(), i2.end());
-        bool ok = build_stream_plan(m->st_cond, cc, m->prec, s) && build_stream_plan(m->st_back, cb, m->prec, s);
-        if (ok && two) ok = build_stream_plan(m->st_cond2, c2, m->prec, s) && build_stream_plan(m->st_back2, b2v, m->prec, s);
+        const void* src = (m->prec == PD_PREC_BF16) ? (const void*)m->d_mat16.p : (const void*)m->d_mat32.p;
+        bool ok = !m->batched_only && build_stream_plan(m->st_cond, cc, m->prec, src, s) && build_stream_plan(m->st_back, cb, m->prec, src, s);
+        if (ok && two)
+            ok = build_stream_plan(m->st_cond2, c2, m->prec, src, s) &&
+                 build_stream_plan(m->st_back2, b2v, m->prec, src, s);
         m->use_stream = ok;
     }
 
@@ -1374,6 +1378,8 @@ pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
     bytes += m->rows_cond2.descs.bytes() + m->rows_cond2.blk_u.bytes() + m->rows_back2.descs.bytes();
     bytes += m->rows_back2.blk_u.bytes() + m->d_bidx2.bytes() + m->d_gat2_ptr.bytes() + m->d_gat2.bytes();
     bytes += m->d_tc2.bytes() + m->d_cT.bytes();
+    for (const StreamPlan* P : {&m->st_cond, &m->st_back, &m->st_cond2, &m->st_back2})
+        bytes += P->pan32.bytes() + P->pan16.bytes() + P->recs.bytes() + P->part.bytes() + P->cnt.bytes();
     out->device_bytes = bytes;
     out->prefactor_seconds = m->prefactor_seconds;
     out->launches_per_iter = m->launches_per_iter;

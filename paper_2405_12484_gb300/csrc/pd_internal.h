@@ -143,14 +143,22 @@ struct ColDesc {
 struct ColPiece {
     int32_t desc, k0, k1, piece;
 };
+// A piece with a copy of its block's descriptor (64 bytes): a CTA loads all of
+// its records into shared memory once.
+struct ColPieceRec {
+    ColDesc d;
+    ColPiece p;
+};
 // One streaming launch: descriptors, pieces, the piece range of every CTA,
 // partial sums and per-block completion counters.
 struct StreamPlan {
-    DBuf<ColDesc> descs;
-    DBuf<ColPiece> pieces;
+    DBuf<ColPieceRec> recs;
     DBuf<int32_t> cta_pieces;
     DBuf<float4> part;
     DBuf<int32_t> cnt;
+    DBuf<float> pan32;             // the blocks as column panels (the plan's own copy)
+    DBuf<__nv_bfloat16> pan16;
+    int prec = 0;
     int n_ctas = 0;
     size_t smem = 0;
     std::vector<ColDesc> host;
@@ -263,6 +271,7 @@ struct pd_mesh {
     // streaming (bulk-copy) launches of every product of the solve; used when
     // all of them could be planned (every row fits one pipeline stage)
     bool use_stream = false;
+    bool batched_only = false;             // set by the serving loop: no streaming plans
     pdg::StreamPlan st_cond, st_int, st_back, st_cond2, st_int2, st_back2, st_coarse;
     pdg::DBuf<int32_t> d_bidx2, d_gat2_ptr, d_gat2;
     pdg::DBuf<float4> d_tc2, d_cT;

@@ -280,6 +280,7 @@ static bool admit(pd_server* S, Request& R) {
     }
     st = pd_set_materials(m, R.gs.data(), R.gv.data());
     pd_solver_opts o{PD_PREC_FP32, 0, 0, PD_SOLVE_SINGLE_LEVEL};  // the batched coarse kernel is single-level
+    m->batched_only = true;   // the serving loop runs its own batched kernels: no streaming copies
     if (st == PD_OK) st = pd_prefactor(m, R.dt, &o);
     if (st != PD_OK) {
         pd_destroy_mesh(m);
