@@ -38,6 +38,8 @@ def parse():
     p.add_argument("--refine", type=int, default=0)
     p.add_argument("--correction", action="store_true",
                    help="solve each PD iteration for the correction b - K x (FP64 residual)")
+    p.add_argument("--streaming", action="store_true",
+                   help="the whole subspace solve as one cooperative streaming launch")
     p.add_argument("--single-level", action="store_true",
                    help="one dense S^-1 for the interface instead of the two-level interface solve")
     p.add_argument("--iters", type=int, default=20, help="PD iterations per frame")
@@ -335,7 +337,7 @@ def main():
     m.set_materials(w.gamma_s, w.gamma_v)
     t0 = time.perf_counter()
     m.prefactor(w.dt, precision=args.precision, refine_steps=args.refine, use_graphs=True,
-                correction=args.correction, single_level=args.single_level)
+                correction=args.correction, single_level=args.single_level, streaming=args.streaming)
     prefactor_s = time.perf_counter() - t0
     info = m.info()
     K, W = args.steps, max(3, args.warmup)

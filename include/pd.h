@@ -79,7 +79,13 @@ enum {
     /* Solve the interface system with one dense S^-1 even when the mesh has
      * enough domains for the two-level interface solve (groups of domains
      * condensed onto a top-level interface first; chosen automatically). */
-    PD_SOLVE_SINGLE_LEVEL = 2
+    PD_SOLVE_SINGLE_LEVEL = 2,
+    /* Run the whole subspace solve as one cooperative persistent launch that
+     * streams every factor through shared memory with bulk asynchronous copies
+     * (phases separated by bounded grid-wide counters).  Same results up to
+     * FP32 summation order; off by default (the separate launches are faster
+     * on the meshes measured so far). */
+    PD_SOLVE_STREAMING = 4
 };
 
 typedef struct pd_solver_opts {

@@ -30,6 +30,7 @@ PD_PREC_TF32 = 2
 
 PD_SOLVE_CORRECTION = 1
 PD_SOLVE_SINGLE_LEVEL = 2
+PD_SOLVE_STREAMING = 4
 
 
 class pd_solver_opts(C.Structure):

@@ -18,8 +18,7 @@
 
 namespace pdg {
 
-void launch_stream_cols(const StreamPlan& P, const float4* x, const int* xidx, const float4* add, float4* out,
-                        int* err, cudaStream_t s);
+void launch_stream_solve(const StreamPlan& P, FusedArgs F, cudaStream_t s);
 
 namespace {
 
@@ -602,54 +601,42 @@ void launch_rowdot(const RowPlan& P, const AxBases& B, cudaStream_t s) {
 }
 
 struct DDBufs {
-    float4 *tc, *cB, *part, *tc2, *cT;
+    float4 *tc, *cB, *part, *tc2, *cT, *xg2, *xgB;
 };
 
 // One subspace solve: x (free vertices of xout) = K_ff^-1 b.
-// The same solve with every product in the streaming column form (one launch per
-// product, in dependency order on one stream).
-template <class T>
-void dd_solve_stream(pd_mesh* m, const T* pool, const float4* b, float4* xout, const DDBufs& w, cudaStream_t s) {
-    int* err = m->d_err.p;
-    phase_begin(m, PH_CONDENSE, s);
-    launch_stream_cols(m->st_cond, b, nullptr, nullptr, w.tc, err, s);
-    phase_end(m, s);
-    if (m->n_B > 0) {
-        phase_begin(m, PH_GATHER, s);
-        k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, w.tc, w.cB);
-        PDG_CHECK_LAUNCH();
-        phase_end(m, s);
-        const float4* cin = w.cB;
-        float4* xcs = xout + m->n_int;
-        const int T0 = m->n_B - m->n_top;
-        if (m->two_level) {
-            phase_begin(m, PH_CONDENSE2, s);
-            launch_stream_cols(m->st_cond2, w.cB, nullptr, nullptr, w.tc2, err, s);
-            phase_end(m, s);
-            phase_begin(m, PH_GATHER2, s);
-            k_gather<<<nblk(m->n_top, 256), 256, 0, s>>>(m->n_top, m->d_gat2_ptr.p, m->d_gat2.p, w.cB + T0, w.tc2,
-                                                         w.cT);
-            PDG_CHECK_LAUNCH();
-            phase_end(m, s);
-            cin = w.cT;
-            xcs = xout + m->n_int + T0;
-        }
-        phase_begin(m, PH_COARSE, s);
-        launch_coarse<T>(m, pool, cin, w.part, s);
-        phase_end(m, s);
-        phase_begin(m, PH_REDUCE, s);
-        k_reduce<<<nblk(m->cs_n, 256), 256, 0, s>>>(m->cs_n, m->coarse_nchunks, w.part, xcs);
-        PDG_CHECK_LAUNCH();
-        phase_end(m, s);
-        if (m->two_level) {
-            phase_begin(m, PH_BACKSUB2, s);
-            launch_stream_cols(m->st_back2, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int, err,
-                               s);
-            phase_end(m, s);
-        }
-    }
-    phase_begin(m, PH_BACKSUB, s);
-    launch_stream_cols(m->st_back, xout + m->n_int, m->d_bidx.p, w.tc, xout, err, s);
+// The same solve as one fused streaming launch (every product, both levels).
+void dd_solve_stream(pd_mesh* m, const float4* b, float4* xout, const DDBufs& w, cudaStream_t s) {
+    FusedArgs F{};
+    F.b = b;
+    F.x = xout;
+    F.tc = w.tc;
+    F.tc2 = w.tc2;
+    F.gat_ptr = m->d_gat_ptr.p;
+    F.gat = m->d_gat.p;
+    F.gat2_ptr = m->d_gat2_ptr.p;
+    F.gat2 = m->d_gat2.p;
+    F.bidx = m->d_bidx.p;
+    F.bidx2 = m->d_bidx2.p;
+    F.cB = w.cB;
+    F.cT = w.cT;
+    F.xg2 = w.xg2;
+    F.xgB = w.xgB;
+    F.invB_ptr = m->d_invB_ptr.p;
+    F.invB = m->d_invB.p;
+    F.inv2_ptr = m->d_inv2_ptr.p;
+    F.inv2 = m->d_inv2.p;
+    F.cb0 = m->d_cb0.p;
+    F.ct0 = m->d_ct0.p;
+    F.n_cb0 = m->n_cb0;
+    F.n_ct0 = m->n_ct0;
+    F.cnt_cb = m->st_solve.cnt_cb.p;
+    F.cnt_ct = m->st_solve.cnt_ct.p;
+    F.err = m->d_err.p;
+    F.n_int = m->n_int;
+    F.T0 = m->n_B - m->n_top;
+    phase_begin(m, PH_SOLVE, s);
+    launch_stream_solve(m->st_solve, F, s);
     phase_end(m, s);
 }
 
@@ -730,11 +717,10 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
 }  // namespace
 
 void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* tc, float4* cB, float4* part,
-                             float4* tc2, float4* cT, cudaStream_t s) {
-    const DDBufs w{tc, cB, part, tc2, cT};
+                             float4* tc2, float4* cT, float4* xg2, float4* xgB, cudaStream_t s) {
+    const DDBufs w{tc, cB, part, tc2, cT, xg2, xgB};
     if (m->use_stream) {
-        if (m->prec == PD_PREC_BF16) dd_solve_stream<__nv_bfloat16>(m, m->d_mat16.p, b, xout, w, s);
-        else dd_solve_stream<float>(m, m->d_mat32.p, b, xout, w, s);
+        dd_solve_stream(m, b, xout, w, s);
     } else if (m->prec == PD_PREC_BF16) dd_solve_impl<__nv_bfloat16>(m, m->d_mat16.p, b, xout, w, s);
     else dd_solve_impl<float>(m, m->d_mat32.p, b, xout, w, s);
 }
@@ -829,7 +815,8 @@ void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream
 }
 
 void launch_dd_solve(pd_mesh* m, const float4* b, float4* xout, cudaStream_t s, bool /*timed*/) {
-    launch_dd_solve_scratch(m, b, xout, m->d_tc.p, m->d_cB.p, m->d_part.p, m->d_tc2.p, m->d_cT.p, s);
+    launch_dd_solve_scratch(m, b, xout, m->d_tc.p, m->d_cB.p, m->d_part.p, m->d_tc2.p, m->d_cT.p, m->d_xg2.p,
+                            m->d_xgB.p, s);
 }
 
 void launch_residual(const pd_mesh* m, const float4* b, const float4* x, float4* r, cudaStream_t s) {

@@ -149,18 +149,139 @@ __host__ __device__ inline void col_layout(int n_out, int slab_out, int& S, int&
     if (G < 1) G = 1;
 }
 
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, 0.f); }
+
+__device__ __forceinline__ const float4* xvec_of(const FusedArgs& F, int kind) {
+    switch (kind) {
+        case XK_B: return F.b;
+        case XK_CB: return F.cB;
+        case XK_CT: return F.cT;
+        case XK_G2: return F.xg2;
+        default: return F.xgB;
+    }
+}
+
+// atomic add with acquire-release semantics at gpu scope (publishes this
+// thread's earlier stores; the last contributor sees everyone's)
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// what follows the store of a final output v at index o of a block
+__device__ __forceinline__ void post_output(const FusedArgs& F, const ColDesc& D, int o, float4 v) {
+    switch (D.post_kind) {
+        case PK_CB: {
+            const int j = __ldg(F.bidx + D.post_off + o);
+            const int q0 = __ldg(F.gat_ptr + j), q1 = __ldg(F.gat_ptr + j + 1);
+            if (atom_add_acq_rel(F.cnt_cb + j, 1) == q1 - q0 - 1) {
+                float4 acc = F.b[F.n_int + j];
+                for (int q = q0; q < q1; ++q) acc = f4add(acc, __ldcg(F.tc + __ldg(F.gat + q)));
+                F.cB[j] = acc;
+                F.cnt_cb[j] = 0;   // ready for the next launch
+            }
+            break;
+        }
+        case PK_CT: {
+            const int t = __ldg(F.bidx2 + D.post_off + o);
+            const int q0 = __ldg(F.gat2_ptr + t), q1 = __ldg(F.gat2_ptr + t + 1);
+            if (atom_add_acq_rel(F.cnt_ct + t, 1) == q1 - q0 - 1) {
+                float4 acc = __ldcg(F.cB + F.T0 + t);
+                for (int q = q0; q < q1; ++q) acc = f4add(acc, __ldcg(F.tc2 + __ldg(F.gat2 + q)));
+                F.cT[t] = acc;
+                F.cnt_ct[t] = 0;
+            }
+            break;
+        }
+        case PK_XT: {
+            const int t = D.post_off + o;
+            for (int q = __ldg(F.inv2_ptr + t), e = __ldg(F.inv2_ptr + t + 1); q < e; ++q) F.xg2[__ldg(F.inv2 + q)] = v;
+            const int j = F.T0 + t;
+            for (int q = __ldg(F.invB_ptr + j), e = __ldg(F.invB_ptr + j + 1); q < e; ++q) F.xgB[__ldg(F.invB + q)] = v;
+            break;
+        }
+        case PK_XB: {
+            const int j = D.post_off + o;
+            for (int q = __ldg(F.invB_ptr + j), e = __ldg(F.invB_ptr + j + 1); q < e; ++q) F.xgB[__ldg(F.invB + q)] = v;
+            break;
+        }
+        default: break;
+    }
+}
+
+__device__ __forceinline__ float4* vec_of(const FusedArgs& F, int kind) {
+    return kind == VK_TC ? F.tc : (kind == VK_TC2 ? F.tc2 : F.x);
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// bounded wait for every CTA to have completed phase ph (false when the limit ran out)
+__device__ __forceinline__ bool phase_wait(const FusedArgs& F, int ph) {
+    for (long long k = 0; k < (kWaitLimit >> 4); ++k) {
+        if (ld_acquire(F.phase_cnt + ph) >= F.n_ctas) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void phase_arrive(const FusedArgs& F, int ph) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    atomicAdd(F.phase_cnt + ph, 1);
+}
+
+// the final count: every CTA's x loader (past all its waits) and epilogue
+// (past all its stores); the last of the 2 n_ctas arrivals clears the
+// counters for the next launch
+__device__ __forceinline__ void final_arrive(const FusedArgs& F) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    if (atomicAdd(F.phase_cnt + F.n_phases, 1) == 2 * F.n_ctas - 1)
+        for (int k = 0; k <= F.n_phases; ++k) F.phase_cnt[k] = 0;
+}
+
+// Work of CTA 0's epilogue threads before it signals phase ph: the entries
+// of c_B (phase 0) and c_T (phase 1, after every CTA completed phase 0) that
+// no block contributes to.
+__device__ __forceinline__ void epi_extra(const FusedArgs& F, int ph, int et) {
+    if (blockIdx.x != 0) return;
+    if (ph == 0) {
+        for (int k = et; k < F.n_cb0; k += 32 * kEpiWarps) {
+            const int j = __ldg(F.cb0 + k);
+            F.cB[j] = F.b[F.n_int + j];
+        }
+    } else if (ph == 1 && F.n_ct0 > 0) {
+        bool ok = true;
+        if (et == 0) ok = phase_wait(F, 0);
+        if (et == 0 && !ok) atomicOr(F.err, ERR_TIMEOUT);
+        epi_sync();
+        for (int k = et; k < F.n_ct0; k += 32 * kEpiWarps) {
+            const int t = __ldg(F.ct0 + k);
+            F.cT[t] = __ldcg(F.cB + F.T0 + t);
+        }
+    }
+}
+
+// One launch runs the products of the solve as phases: the copy producer
+// streams every tile of this CTA's pieces in order (the matrices do not
+// depend on the solve's data, so the stream runs ahead across phases); the x
+// loader of a piece in phase p waits until every CTA has completed phase
+// p - 1; the epilogue warps signal the completion of each phase.  Launched
+// cooperatively (all CTAs resident).
 template <class T>
-__global__ void __launch_bounds__(kColThreads, 1)
-    k_stream_cols(const ColPieceRec* __restrict__ recs, const int32_t* __restrict__ cta_pieces, AxBases B,
-                  float4* __restrict__ part,
-                  int* __restrict__ cnt, int* __restrict__ err) {
+__global__ void __launch_bounds__(kColThreads, 1) k_stream_solve(const ColPieceRec* __restrict__ recs,
+                                                                 const int32_t* __restrict__ cta_pieces,
+                                                                 FusedArgs F) {
     constexpr int VN = Slab<T>::VN, M = Slab<T>::M, SO = Slab<T>::OUT;
     constexpr int ES = (int)sizeof(T);
+    constexpr int RB = Slab<T>::RB;
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned char* ring = sm;
     float4* xs = reinterpret_cast<float4*>(sm + (size_t)kStages * kStageBytes);    // [2][kMaxPieceRows]
-    float* red = reinterpret_cast<float*>(xs + 2 * kMaxPieceRows);                  // [2][kColWarps][SO][3]
-    constexpr int RB = Slab<T>::RB;
+    float* red = reinterpret_cast<float*>(xs + 2 * kMaxPieceRows);                  // [RB][kColWarps][SO][3]
     uint64_t* full = reinterpret_cast<uint64_t*>(red + (size_t)RB * kColWarps * SO * 3);
     uint64_t* empty = full + kStages;
     uint64_t* xfull = empty + kStages;   // [2]
@@ -197,8 +318,22 @@ __global__ void __launch_bounds__(kColThreads, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (p1 <= p0) return;
-    const T* pool = reinterpret_cast<const T*>(B.pool);
+    if (p1 <= p0) {
+        // no work here: complete every phase and the final count at once
+        if (threadIdx.x < 32 * kEpiWarps) {
+            for (int ph = 0; ph < F.n_phases; ++ph) {
+                epi_extra(F, ph, threadIdx.x);
+                epi_sync();
+                if (threadIdx.x == 0) phase_arrive(F, ph);
+            }
+            if (threadIdx.x == 0) {
+                final_arrive(F);
+                final_arrive(F);
+            }
+        }
+        return;
+    }
+    const T* pool = reinterpret_cast<const T*>(F.pool);
 
     if (warp == kColWarps) {
         // ---- producer: one thread issues the bulk copies of every tile of this CTA
@@ -216,7 +351,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 }
                 const int slot = i % kStages;
                 if (i >= kStages && !mbar_wait(&empty[slot], (uint32_t)((i / kStages) - 1) & 1u)) {
-                    atomicOr(err, ERR_TIMEOUT);
+                    atomicOr(F.err, ERR_TIMEOUT);
                     atomicExch(&abort_flag, 1);
                     stop = true;
                     break;
@@ -229,88 +364,91 @@ __global__ void __launch_bounds__(kColThreads, 1)
             }
         }
         for (int j = (issued > kStages ? issued - kStages : 0); j < issued; ++j)
-            if (!mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u)) atomicOr(err, ERR_TIMEOUT);
+            if (!mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u)) atomicOr(F.err, ERR_TIMEOUT);
         return;
     }
     if (warp == kColWarps + 1) {
-        // ---- x loader: the x slice of every piece (gathered where the block says
-        // so) into a double buffer, ahead of the consumers
+        // ---- x loader: the x slice of every piece into a double buffer, ahead
+        // of the consumers; before the first piece of a phase p > 0 it waits
+        // until every CTA has completed phase p - 1
         int bulk_mask = 0;   // bit b: the last slice written to buffer b came by bulk copy
         int done = 0;        // pieces whose slice was issued
+        int ready = 0;       // phases whose inputs are known complete
         for (int p = p0; p < p1; ++p) {
             const int pp = p - p0, buf = pp & 1;
-            if (pp >= 2) {
-                bool ok = true;
-                if (lane == 0) ok = mbar_wait(&xempty[buf], (uint32_t)((pp / 2) - 1) & 1u);
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                if (!ok) {
-                    if (lane == 0) {
-                        atomicOr(err, ERR_TIMEOUT);
-                        atomicExch(&abort_flag, 1);
-                    }
-                    break;
+            const ColPiece pc = srec[pp].p;
+            const ColDesc D = srec[pp].d;
+            bool ok = true;
+            if (pp >= 2 && lane == 0) ok = mbar_wait(&xempty[buf], (uint32_t)((pp / 2) - 1) & 1u);
+            if (ok && D.phase > ready) {
+                if (lane == 0 && !*reinterpret_cast<volatile int*>(&abort_flag)) {
+                    ok = phase_wait(F, D.phase - 1);
+                    // the bulk copies below read what other CTAs stored (generic proxy)
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
                 }
+                ready = D.phase;
             }
-            const ColPiece pc = srec[p - p0].p;
-            const ColDesc D = srec[p - p0].d;
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            __syncwarp();   // orders every lane's loads below after lane 0's acquire
+            if (!ok) {
+                if (lane == 0) {
+                    atomicOr(F.err, ERR_TIMEOUT);
+                    atomicExch(&abort_flag, 1);
+                }
+                break;
+            }
             float4* xb = xs + buf * kMaxPieceRows;
             const int n = pc.k1 - pc.k0;
-            if (D.xidx_off < 0 && n > 0) {
-                // contiguous slice: one bulk copy, completion counted on xfull
+            if (n > 0) {
+                // contiguous slice of a vector: one bulk copy, completion counted on xfull
                 if (lane == 0) {
                     const uint32_t bytes = (uint32_t)n * 16u;
                     mbar_arrive_expect_tx(&xfull[buf], bytes);
-                    bulk_g2s(xb, B.x + D.x_off + pc.k0, bytes, &xfull[buf]);
+                    bulk_g2s(xb, xvec_of(F, D.xkind) + D.x_off + pc.k0, bytes, &xfull[buf]);
                 }
                 bulk_mask |= 1 << buf;
             } else {
                 bulk_mask &= ~(1 << buf);
-                // gathered slice: eight independent loads in flight per lane
-                for (int k0 = 0; k0 < n; k0 += 32 * 8) {
-                    float4 v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int k = k0 + u * 32 + lane;
-                        if (k < n) v[u] = B.x[B.bidx[D.xidx_off + pc.k0 + k]];
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int k = k0 + u * 32 + lane;
-                        if (k < n) xb[k] = v[u];
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&xfull[buf]);   // release: the warp's writes above
+                if (lane == 0) mbar_arrive(&xfull[buf]);
             }
             done = pp + 1;
         }
         // before exit: the last bulk copies have landed (normally long since consumed)
         for (int pp = (done > 2 ? done - 2 : 0); pp < done; ++pp)
             if (lane == 0 && (bulk_mask >> (pp & 1) & 1) && !mbar_wait(&xfull[pp & 1], (uint32_t)(pp / 2) & 1u))
-                atomicOr(err, ERR_TIMEOUT);
+                atomicOr(F.err, ERR_TIMEOUT);
+        if (lane == 0) final_arrive(F);
         return;
     }
-
     if (warp >= kColWarps + 2) {
         // ---- epilogue warps: add the row groups of every output in group order,
-        // write the outputs or the piece's partial sums, and for a panel cut into
-        // several pieces let the CTA completing the last piece add them in order;
-        // runs beside the consumers, which go on with the next piece
+        // write the outputs or the piece's partial sums (a panel cut into several
+        // pieces is completed by the CTA finishing its last piece, adding the
+        // pieces in order), and signal the completion of each phase
         const int et = threadIdx.x - 32 * (kColWarps + 2);
+        int arrived = 0;   // phases signalled
         for (int p = p0; p < p1; ++p) {
             const int pp = p - p0, rbuf = pp % RB;
             const ColPiece pc = srec[pp].p;
             const ColDesc D = srec[pp].d;
+            // all of this CTA's pieces of earlier phases are done
+            for (; arrived < D.phase; ++arrived) {
+                epi_extra(F, arrived, et);
+                epi_sync();
+                if (et == 0) phase_arrive(F, arrived);
+            }
             int S, G;
             col_layout(D.n_out, SO, S, G);
             if (et == 0 && !*reinterpret_cast<volatile int*>(&abort_flag) &&
                 !mbar_wait(&rfull[rbuf], (uint32_t)(pp / RB) & 1u)) {
-                atomicOr(err, ERR_TIMEOUT);
+                atomicOr(F.err, ERR_TIMEOUT);
                 atomicExch(&abort_flag, 1);
             }
             epi_sync();
             const float* rb = red + (size_t)rbuf * kColWarps * SO * 3;
             const bool single = D.n_pieces == 1;
+            float4* outv = vec_of(F, D.okind);
+            const float4* addv = (D.akind == VK_NONE) ? nullptr : vec_of(F, D.akind);
             for (int o = et; o < D.n_out; o += 32 * kEpiWarps) {
                 const int sl = o / SO, lo = o - sl * SO;
                 float s0 = 0.f, s1 = 0.f, s2 = 0.f;
@@ -321,20 +459,20 @@ __global__ void __launch_bounds__(kColThreads, 1)
                     s2 += q[2];
                 }
                 if (single) {
-                    const float4 ad = (D.add_off >= 0) ? B.add[D.add_off + o] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    B.out[D.out_off + o] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
+                    const float4 ad = addv ? __ldcg(addv + D.add_off + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 v = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
+                    outv[D.out_off + o] = v;
+                    post_output(F, D, o, v);
                 } else {
-                    part[D.part_off + (int64_t)pc.piece * D.n_out + o] = make_float4(s0, s1, s2, 0.f);
+                    F.part[D.part_off + (int64_t)pc.piece * D.n_out + o] = make_float4(s0, s1, s2, 0.f);
                 }
             }
             epi_sync();   // red[rbuf] read by every epilogue thread
             if (et == 0) mbar_arrive(&rempty[rbuf]);
             if (!single) {
-                // release the partial sums (barrier, then one gpu-scope fence) and
-                // count the piece
                 if (et == 0) {
                     asm volatile("fence.acq_rel.gpu;" ::: "memory");
-                    const int prev = atomicAdd(&cnt[pc.desc], 1);
+                    const int prev = atomicAdd(&F.cnt[pc.desc], 1);
                     asm volatile("fence.acq_rel.gpu;" ::: "memory");
                     last_flag = (prev == D.n_pieces - 1);
                 }
@@ -344,20 +482,27 @@ __global__ void __launch_bounds__(kColThreads, 1)
                         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll 4
                         for (int q = 0; q < D.n_pieces; ++q) {
-                            const float4 v = __ldcg(&part[D.part_off + (int64_t)q * D.n_out + o]);
+                            const float4 v = __ldcg(&F.part[D.part_off + (int64_t)q * D.n_out + o]);
                             s0 += v.x;
                             s1 += v.y;
                             s2 += v.z;
                         }
-                        const float4 ad =
-                            (D.add_off >= 0) ? B.add[D.add_off + o] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        B.out[D.out_off + o] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
+                        const float4 ad = addv ? __ldcg(addv + D.add_off + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 v = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
+                        outv[D.out_off + o] = v;
+                        post_output(F, D, o, v);
                     }
-                    if (et == 0) cnt[pc.desc] = 0;   // ready for the next launch
+                    if (et == 0) F.cnt[pc.desc] = 0;   // ready for the next launch
                 }
                 epi_sync();   // last_flag free for the next piece
             }
         }
+        for (; arrived < F.n_phases; ++arrived) {
+            epi_extra(F, arrived, et);
+            epi_sync();
+            if (et == 0) phase_arrive(F, arrived);
+        }
+        if (et == 0) final_arrive(F);
         return;
     }
 
@@ -372,7 +517,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
         int S, G;
         col_layout(D.n_out, SO, S, G);
         if (!*reinterpret_cast<volatile int*>(&abort_flag) && !mbar_wait(&xfull[buf], (uint32_t)(pp / 2) & 1u)) {
-            atomicOr(err, ERR_TIMEOUT);
+            atomicOr(F.err, ERR_TIMEOUT);
             atomicExch(&abort_flag, 1);
         }
         const float4* xb = xs + buf * kMaxPieceRows;
@@ -392,11 +537,9 @@ __global__ void __launch_bounds__(kColThreads, 1)
         int ph = 0;   // (k - k0) mod G at the start of the tile
         for (int k = pc.k0; k < pc.k1; k += rpt, ++i) {
             const int slot = i % kStages;
-            // one lane of each warp polls the stage barrier; the warp barrier then
-            // orders the other lanes after it (fewer polls competing with the copies)
             if (lane == 0 && !*reinterpret_cast<volatile int*>(&abort_flag) &&
                 !mbar_wait(&full[slot], (uint32_t)(i / kStages) & 1u)) {
-                atomicOr(err, ERR_TIMEOUT);
+                atomicOr(F.err, ERR_TIMEOUT);
                 atomicExch(&abort_flag, 1);
             }
             __syncwarp();
@@ -439,7 +582,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
             // red[rbuf] was last filled for piece pp - RB: the epilogue must be done with it
             if (lane == 0 && !*reinterpret_cast<volatile int*>(&abort_flag) &&
                 !mbar_wait(&rempty[rbuf], (uint32_t)((pp / RB) - 1) & 1u)) {
-                atomicOr(err, ERR_TIMEOUT);
+                atomicOr(F.err, ERR_TIMEOUT);
                 atomicExch(&abort_flag, 1);
             }
             __syncwarp();
@@ -487,19 +630,25 @@ size_t col_smem_bytes() {
 
 }  // namespace
 
-// Copies every block (a_off into the row-major pool src) into the plan's own
-// pool as contiguous column panels of at most kPanel outputs, cuts the
-// panels' rows into pieces so that every CTA gets a contiguous range of about
-// the same number of bytes (at most kMaxPieceRows rows per piece and
-// kMaxCtaPieces pieces per CTA), and uploads the piece records.  Returns
-// false (plan left empty) when a panel row does not fit in one stage.
+// Builds the fused solve: copies every block (a_off into the row-major pool
+// src; phase, x/add/out kinds set by the caller) into the plan's own pool as
+// contiguous column panels of at most kPanel outputs, cuts the rows of each
+// phase's panels into pieces so that every CTA gets a contiguous range of
+// about the same number of bytes of every phase (at most kMaxPieceRows rows
+// per piece), and lays out each CTA's pieces phase by phase.  Returns false
+// (plan left empty) when a panel row does not fit in one stage or a CTA would
+// hold more than kMaxCtaPieces pieces.
 bool build_stream_plan(StreamPlan& P, const std::vector<ColDesc>& blocks, int prec, const void* src, cudaStream_t s) {
     P.n_ctas = 0;
+    P.n_phases = 0;
     P.host.clear();
     const int es = (prec == PD_PREC_BF16) ? 2 : 4;
-    // panels
+    int n_ph = 0;
+    for (const auto& D : blocks) n_ph = std::max(n_ph, D.phase + 1);
+    // panels, phase by phase
     std::vector<ColDesc> descs;
     std::vector<PanelCopy> copies;
+    std::vector<std::vector<int>> ph_descs(n_ph);
     int64_t pool = 0;
     for (const auto& D : blocks) {
         if (D.n_out <= 0) continue;
@@ -512,8 +661,10 @@ bool build_stream_plan(StreamPlan& P, const std::vector<ColDesc>& blocks, int pr
             p.ld = width;
             p.n_out = valid;
             p.out_off = D.out_off + c0;
-            p.add_off = (D.add_off >= 0) ? D.add_off + c0 : -1;
+            p.add_off = (D.akind != VK_NONE) ? D.add_off + c0 : -1;
+            p.post_off = D.post_off + c0;
             p.n_pieces = 1;
+            ph_descs[D.phase].push_back((int)descs.size());
             descs.push_back(p);
             if (D.K > 0) copies.push_back(PanelCopy{D.a_off, pool, D.K, D.ld, c0, width, valid, 0});
             pool += (int64_t)D.K * width;
@@ -523,36 +674,40 @@ bool build_stream_plan(StreamPlan& P, const std::vector<ColDesc>& blocks, int pr
     PDG_CUDA(cudaGetDevice(&dev));
     PDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int C = std::max(1, sms);
-    int64_t W = 0;
-    for (const auto& D : descs) W += (int64_t)D.K * D.ld * es + (int64_t)D.n_out * 64;
-    // walk the panels, closing a CTA's range when its byte budget is reached
-    std::vector<ColPiece> pcs;
-    std::vector<int32_t> cut(1, 0);
-    int64_t acc = 0;
-    int c = 0;
-    for (int d = 0; d < (int)descs.size(); ++d) {
-        ColDesc& D = descs[d];
-        const int64_t row_b = (int64_t)D.ld * es;
-        int k = 0, piece = 0;
-        acc += (int64_t)D.n_out * 64;
-        do {
-            const int64_t budget = W * (c + 1) / C - acc;
-            int take = (int)std::min<int64_t>(D.K - k, std::max<int64_t>(1, budget / std::max<int64_t>(row_b, 1)));
-            take = std::min(take, kMaxPieceRows);
-            if (D.K == 0) take = 0;
-            pcs.push_back(ColPiece{d, k, k + take, piece++});
-            k += take;
-            acc += (int64_t)take * row_b;
-            if (c + 1 < C && acc * C >= W * (c + 1)) {
-                cut.push_back((int32_t)pcs.size());
-                ++c;
-            }
-        } while (k < D.K);
-        D.n_pieces = piece;
+    // per phase: walk its panels, closing a CTA's range when its byte budget is reached
+    std::vector<std::vector<ColPiece>> per_cta(C);
+    for (int ph = 0; ph < n_ph; ++ph) {
+        int64_t W = 0;
+        for (int d : ph_descs[ph]) W += (int64_t)descs[d].K * descs[d].ld * es + (int64_t)descs[d].n_out * 64;
+        int64_t acc = 0;
+        int c = 0;
+        for (int d : ph_descs[ph]) {
+            ColDesc& D = descs[d];
+            const int64_t row_b = (int64_t)D.ld * es;
+            int k = 0, piece = 0;
+            acc += (int64_t)D.n_out * 64;
+            do {
+                const int64_t budget = W * (c + 1) / C - acc;
+                int take =
+                    (int)std::min<int64_t>(D.K - k, std::max<int64_t>(1, budget / std::max<int64_t>(row_b, 1)));
+                take = std::min(take, kMaxPieceRows);
+                if (D.K == 0) take = 0;
+                per_cta[c].push_back(ColPiece{d, k, k + take, piece++});
+                k += take;
+                acc += (int64_t)take * row_b;
+                if (c + 1 < C && acc * C >= W * (c + 1)) ++c;
+            } while (k < D.K);
+            D.n_pieces = piece;
+        }
     }
-    while ((int)cut.size() < C + 1) cut.push_back((int32_t)pcs.size());
-    for (int c2 = 0; c2 < C; ++c2)
-        if (cut[c2 + 1] - cut[c2] > kMaxCtaPieces) return false;
+    std::vector<int32_t> cut(C + 1, 0);
+    std::vector<ColPiece> pcs;
+    for (int c = 0; c < C; ++c) {
+        if ((int)per_cta[c].size() > kMaxCtaPieces) return false;
+        cut[c] = (int32_t)pcs.size();
+        pcs.insert(pcs.end(), per_cta[c].begin(), per_cta[c].end());
+    }
+    cut[C] = (int32_t)pcs.size();
     int64_t po = 0;
     for (auto& D : descs) {
         D.part_off = po;
@@ -561,9 +716,17 @@ bool build_stream_plan(StreamPlan& P, const std::vector<ColDesc>& blocks, int pr
     std::vector<ColPieceRec> recs(pcs.size());
     for (size_t q = 0; q < pcs.size(); ++q) recs[q] = ColPieceRec{descs[pcs[q].desc], pcs[q]};
     const size_t smem = (prec == PD_PREC_BF16) ? col_smem_bytes<__nv_bfloat16>() : col_smem_bytes<float>();
-    const int lim = std::min(allow_max_dynamic_smem(k_stream_cols<float>),
-                             allow_max_dynamic_smem(k_stream_cols<__nv_bfloat16>));
+    const int lim = std::min(allow_max_dynamic_smem(k_stream_solve<float>),
+                             allow_max_dynamic_smem(k_stream_solve<__nv_bfloat16>));
     if (smem > (size_t)lim) return false;
+    // all CTAs resident at once (the phases wait on one another)
+    int per_sm = 0;
+    if (prec == PD_PREC_BF16)
+        PDG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_solve<__nv_bfloat16>, kColThreads,
+                                                               smem));
+    else
+        PDG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_solve<float>, kColThreads, smem));
+    if (per_sm < 1) return false;
     // the panel pool
     P.pan32.free();
     P.pan16.free();
@@ -585,32 +748,46 @@ bool build_stream_plan(StreamPlan& P, const std::vector<ColDesc>& blocks, int pr
     P.part.alloc((size_t)std::max<int64_t>(po, 1));
     P.cnt.alloc(std::max<size_t>(descs.size(), 1));
     PDG_CUDA(cudaMemsetAsync(P.cnt.p, 0, P.cnt.bytes(), s));
+    P.phase_cnt.alloc((size_t)n_ph + 1);
+    PDG_CUDA(cudaMemsetAsync(P.phase_cnt.p, 0, P.phase_cnt.bytes(), s));
     PDG_CUDA(cudaStreamSynchronize(s));
     P.host = std::move(descs);
     P.prec = prec;
+    P.n_phases = n_ph;
     P.n_ctas = pcs.empty() ? 0 : C;
     P.smem = smem;
     return true;
 }
 
-void launch_stream_cols(const StreamPlan& P, const float4* x, const int* xidx, const float4* add, float4* out,
-                        int* err, cudaStream_t s) {
+// One fused solve: every phase of the plan in one cooperative launch.
+void launch_stream_solve(const StreamPlan& P, FusedArgs F, cudaStream_t s) {
     if (P.n_ctas <= 0) return;
-    if (P.prec == PD_PREC_BF16) {
-        const AxBases B{P.pan16.p, x, xidx, add, out};
-        k_stream_cols<__nv_bfloat16><<<P.n_ctas, kColThreads, P.smem, s>>>(P.recs.p, P.cta_pieces.p, B, P.part.p,
-                                                                           P.cnt.p, err);
-    } else {
-        const AxBases B{P.pan32.p, x, xidx, add, out};
-        k_stream_cols<float><<<P.n_ctas, kColThreads, P.smem, s>>>(P.recs.p, P.cta_pieces.p, B, P.part.p, P.cnt.p,
-                                                                   err);
-    }
-    PDG_CHECK_LAUNCH();
+    F.pool = (P.prec == PD_PREC_BF16) ? (const void*)P.pan16.p : (const void*)P.pan32.p;
+    F.part = P.part.p;
+    F.cnt = P.cnt.p;
+    F.phase_cnt = P.phase_cnt.p;
+    F.n_phases = P.n_phases;
+    F.n_ctas = P.n_ctas;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(P.n_ctas);
+    cfg.blockDim = dim3(kColThreads);
+    cfg.dynamicSmemBytes = P.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const ColPieceRec* recs = P.recs.p;
+    const int32_t* cuts = P.cta_pieces.p;
+    if (P.prec == PD_PREC_BF16) PDG_CUDA(cudaLaunchKernelEx(&cfg, k_stream_solve<__nv_bfloat16>, recs, cuts, F));
+    else PDG_CUDA(cudaLaunchKernelEx(&cfg, k_stream_solve<float>, recs, cuts, F));
 }
 
-// After a wait ran out the block counters may be left mid-count: clear them.
+// After a wait ran out the counters may be left mid-count: clear them.
 void reset_stream_plan(StreamPlan& P, cudaStream_t s) {
     if (P.cnt.p) PDG_CUDA(cudaMemsetAsync(P.cnt.p, 0, P.cnt.bytes(), s));
+    if (P.phase_cnt.p) PDG_CUDA(cudaMemsetAsync(P.phase_cnt.p, 0, P.phase_cnt.bytes(), s));
 }
 
 }  // namespace pdg

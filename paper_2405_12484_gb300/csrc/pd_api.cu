@@ -230,7 +230,7 @@ const char* pd_last_error(void) { return g_last_error.c_str(); }
 static const char* kPhaseNames[PH_COUNT] = {"inertia",      "local",      "assemble",   "dd_condense", "dd_gather",
                                             "dd_coarse",    "dd_reduce",  "dd_backsub", "residual",    "velocity",
                                             "dd_condense2", "dd_gather2", "dd_backsub2", "dd_interior",
-                                            "dd_interior2"};
+                                            "dd_interior2", "dd_solve"};
 
 const char* pd_phase_name(int32_t k) { return (k >= 0 && k < PH_COUNT) ? kPhaseNames[k] : "?"; }
 
@@ -613,7 +613,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     pd_solver_opts o{PD_PREC_FP32, 0, 1, 0};
     if (opts) o = *opts;
     if (o.precision < PD_PREC_FP32 || o.precision > PD_PREC_TF32 || o.refine_steps < 0 || o.refine_steps > 2 ||
-        (o.flags & ~(PD_SOLVE_CORRECTION | PD_SOLVE_SINGLE_LEVEL)) != 0)
+        (o.flags & ~(PD_SOLVE_CORRECTION | PD_SOLVE_SINGLE_LEVEL | PD_SOLVE_STREAMING)) != 0)
         return fail(PD_ERR_INVALID_ARG, "bad solver options");
     PD_API_BEGIN
     auto t0 = std::chrono::steady_clock::now();
@@ -1076,12 +1076,15 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     m->d_part.alloc((size_t)std::max(m->cs_n, 1) * m->coarse_nchunks);
     m->coarse_blocks = (m->cs_n > 0) ? dd_configure_coarse(m->ld_S) : 0;
 
-    // ---- streaming plans (column form): t = K_ii^-1 b_i over the rows of K_ii^-1,
-    // c_d = Psi_d^T b_i over the rows of Psi_d, x_i = t + Psi_d x_B over the rows
-    // of Psi_d^T; the second level likewise; the coarse inverse is symmetric
+    // ---- fused streaming solve (column form), phase by phase:
+    //   0: c_d = Psi_d^T b_i over the rows of Psi_d, t_d = K_ii^-1 b_i over the rows of K_ii^-1
+    //   1: (two levels) c2, t2 over the rows of Psi2 and S_II^-1, x = c_B formed on the fly
+    //   2: x_T = S2^-1 c_T (or x_B = S^-1 c_B on one level), S symmetric
+    //   3: (two levels) x_I = t2 + Psi2 x_T over the rows of Psi2^T
+    //   4: x_i = t_d + Psi_d x_B over the rows of Psi_d^T
     {
-        auto col = [](int64_t a_off, int32_t K, int32_t n_out, int32_t ld, int32_t x_off, int32_t xidx_off,
-                      int32_t add_off, int32_t out_off) {
+        auto col = [](int phase, int64_t a_off, int32_t K, int32_t n_out, int32_t ld, int32_t xkind, int32_t x_off,
+                      int32_t xidx_off, int32_t akind, int32_t add_off, int32_t okind, int32_t out_off) {
             ColDesc c{};
             c.a_off = a_off;
             c.K = K;
@@ -1092,36 +1095,117 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             c.add_off = add_off;
             c.out_off = out_off;
             c.n_pieces = 1;
+            c.phase = phase;
+            c.xkind = xkind;
+            c.akind = akind;
+            c.okind = okind;
             return c;
         };
-        std::vector<ColDesc> cc, ci, cb, c2, i2, b2v;
+        auto post = [](ColDesc c, int32_t kind, int32_t off) {
+            c.post_kind = kind;
+            c.post_off = off;
+            return c;
+        };
+        std::vector<ColDesc> bl;
         for (int32_t d = 0; d < n_dom; ++d) {
             const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
             if (ni == 0) continue;
-            if (nbd > 0) cc.push_back(col(p_off[d], ni, nbd, ldP[d], m->dom_int_off[d], -1, -1, tc_off[d] + ni));
-            ci.push_back(col(h_off[d], ni, ni, ldH[d], m->dom_int_off[d], -1, -1, tc_off[d]));
-            cb.push_back(col(t_off[d], nbd, ni, ldT[d], 0, bidx_off[d], tc_off[d], m->dom_int_off[d]));
+            if (nbd > 0)
+                bl.push_back(post(col(0, p_off[d], ni, nbd, ldP[d], XK_B, m->dom_int_off[d], -1, VK_NONE, -1, VK_TC,
+                                      tc_off[d] + ni),
+                                  PK_CB, bidx_off[d]));
+            bl.push_back(col(0, h_off[d], ni, ni, ldH[d], XK_B, m->dom_int_off[d], -1, VK_NONE, -1, VK_TC, tc_off[d]));
         }
+        const int ph_coarse = two ? 2 : 1, ph_back = two ? 4 : (n_B > 0 ? 2 : 1);
         if (two) {
             for (int g = 0; g < G; ++g) {
                 const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
                 if (n2 == 0) continue;
-                i2.push_back(col(h2_off[g], n2, n2, ldH2[g], i2_off[g], -1, -1, tc2_off[g]));
-                if (nb == 0) continue;
-                c2.push_back(col(t2_off[g], n2, nb, ldT2[g], i2_off[g], -1, -1, tc2_off[g] + n2));
-                b2v.push_back(col(h2_off[g] + (int64_t)n2 * ldH2[g], nb, n2, ldH2[g], 0, b2_off[g], tc2_off[g],
-                                  i2_off[g]));
+                if (nb > 0)
+                    bl.push_back(post(col(1, t2_off[g], n2, nb, ldT2[g], XK_CB, i2_off[g], -1, VK_NONE, -1, VK_TC2,
+                                          tc2_off[g] + n2),
+                                      PK_CT, b2_off[g]));
+                bl.push_back(col(1, h2_off[g], n2, n2, ldH2[g], XK_CB, i2_off[g], -1, VK_NONE, -1, VK_TC2, tc2_off[g]));
             }
+            bl.push_back(post(col(2, m->off_S, nT, nT, m->ld_S, XK_CT, 0, -1, VK_NONE, -1, VK_X, n_int + T0), PK_XT, 0));
+            for (int g = 0; g < G; ++g) {
+                const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
+                if (n2 == 0 || nb == 0) continue;
+                bl.push_back(post(col(3, h2_off[g] + (int64_t)n2 * ldH2[g], nb, n2, ldH2[g], XK_G2, b2_off[g], -1,
+                                      VK_TC2, tc2_off[g], VK_X, n_int + i2_off[g]),
+                                  PK_XB, i2_off[g]));
+            }
+        } else if (n_B > 0) {
+            bl.push_back(post(col(ph_coarse, m->off_S, n_B, n_B, m->ld_S, XK_CB, 0, -1, VK_NONE, -1, VK_X, n_int), PK_XB,
+                              0));
         }
-        // both parts of a condensation read the same x: one launch each level
-        cc.insert(cc.end(), ci.begin(), ci.end());
-        c2.insert(c2.end(), i2.begin(), i2.end());
+        for (int32_t d = 0; d < n_dom; ++d) {
+            const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
+            if (ni == 0) continue;
+            bl.push_back(col(ph_back, t_off[d], nbd, ni, ldT[d], XK_GB, bidx_off[d], -1, VK_TC, tc_off[d], VK_X,
+                             m->dom_int_off[d]));
+        }
+        // inverse gather lists (positions of every interface / top entry in the
+        // per-domain and per-group lists) and the entries nobody contributes to
+        {
+            const int32_t nq = (int32_t)bidx.size();
+            std::vector<int32_t> ip(n_B + 1, 0), il(nq);
+            for (int32_t q = 0; q < nq; ++q) ip[bidx[q] + 1]++;
+            for (int32_t j = 0; j < n_B; ++j) ip[j + 1] += ip[j];
+            std::vector<int32_t> fill(ip.begin(), ip.end() - 1);
+            for (int32_t q = 0; q < nq; ++q) il[fill[bidx[q]]++] = q;
+            upload(m->d_invB_ptr, ip, s);
+            upload(m->d_invB, il, s);
+            m->n_xgB = nq;
+            m->d_xgB.alloc(std::max(nq, 1));
+            // c_B entries: the contributing domains are those with internal vertices
+            std::vector<int32_t> ncb(std::max(n_B, 1), 0);
+            for (int32_t d = 0; d < n_dom; ++d)
+                if (m->dom_n_int[d] > 0)
+                    for (int32_t j : m->dom_bnd[d]) ncb[j]++;
+            std::vector<int32_t> z;
+            for (int32_t j = 0; j < n_B; ++j)
+                if (ncb[j] == 0) z.push_back(j);
+            upload(m->d_cb0, z, s);
+            m->n_cb0 = (int32_t)z.size();
+            const int32_t nq2 = two ? (int32_t)b2all.size() : 0;
+            std::vector<int32_t> ip2(nT + 1, 0), il2(std::max(nq2, 0));
+            for (int32_t q = 0; q < nq2; ++q) ip2[b2all[q] + 1]++;
+            for (int32_t t = 0; t < nT; ++t) ip2[t + 1] += ip2[t];
+            std::vector<int32_t> fill2(ip2.begin(), ip2.end() - 1);
+            for (int32_t q = 0; q < nq2; ++q) il2[fill2[b2all[q]]++] = q;
+            upload(m->d_inv2_ptr, ip2, s);
+            upload(m->d_inv2, il2, s);
+            m->n_xg2 = nq2;
+            m->d_xg2.alloc(std::max(nq2, 1));
+            std::vector<int32_t> z2;
+            if (two) {
+                // the contributing groups are those with internal interface vertices
+                std::vector<int32_t> nct(std::max(nT, 1), 0);
+                for (int g = 0; g < G; ++g)
+                    if (m->grp_n2[g] > 0)
+                        for (int32_t t : b2[g]) nct[t]++;
+                for (int32_t t = 0; t < nT; ++t)
+                    if (nct[t] == 0) z2.push_back(t);
+            }
+            upload(m->d_ct0, z2, s);
+            m->n_ct0 = (int32_t)z2.size();
+        }
         const void* src = (m->prec == PD_PREC_BF16) ? (const void*)m->d_mat16.p : (const void*)m->d_mat32.p;
-        bool ok = !m->batched_only && build_stream_plan(m->st_cond, cc, m->prec, src, s) && build_stream_plan(m->st_back, cb, m->prec, src, s);
-        if (ok && two)
-            ok = build_stream_plan(m->st_cond2, c2, m->prec, src, s) &&
-                 build_stream_plan(m->st_back2, b2v, m->prec, src, s);
-        m->use_stream = ok;
+        m->use_stream = (o.flags & PD_SOLVE_STREAMING) && !m->batched_only &&
+                        build_stream_plan(m->st_solve, bl, m->prec, src, s);
+        if (!m->use_stream) {
+            // release what an earlier streaming plan held
+            m->st_solve.pan32.free();
+            m->st_solve.pan16.free();
+            m->st_solve.n_ctas = 0;
+        }
+        if (m->use_stream) {
+            m->st_solve.cnt_cb.alloc(std::max(n_B, 1));
+            PDG_CUDA(cudaMemsetAsync(m->st_solve.cnt_cb.p, 0, m->st_solve.cnt_cb.bytes(), s));
+            m->st_solve.cnt_ct.alloc(std::max(nT, 1));
+            PDG_CUDA(cudaMemsetAsync(m->st_solve.cnt_ct.p, 0, m->st_solve.cnt_ct.bytes(), s));
+        }
     }
 
     // ---- algorithmic bytes per launch of each phase (each array counted once)
@@ -1151,10 +1235,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->phase_bytes[PH_ASSEMBLE] = nf * (4 + 16 + 16) + ninc * (4 + 16);
         m->phase_bytes[PH_CONDENSE] = mat_c + (int64_t)n_int * 16 + nbd_tot * 16;
         m->phase_bytes[PH_INTERIOR] = mat_i + (int64_t)n_int * 32;
-        if (m->use_stream) {   // one launch reads b_i once for both parts
-            m->phase_bytes[PH_CONDENSE] = mat_c + mat_i + (int64_t)n_int * 16 + (int64_t)tcr * 16;
-            m->phase_bytes[PH_INTERIOR] = 0;
-        }
+
         m->phase_bytes[PH_GATHER] = (int64_t)n_B * (4 + 16 + 16) + ngat * (4 + 16);
         const int64_t ncs = m->cs_n;
         m->phase_bytes[PH_COARSE] = ncs * colsS * es + ncs * 16 + (int64_t)m->coarse_nchunks * ncs * 16;
@@ -1162,26 +1243,26 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         if (two) {
             m->phase_bytes[PH_CONDENSE2] = mat_c2 + (int64_t)(n_B - nT) * 16 + (int64_t)b2all.size() * 16;
             m->phase_bytes[PH_INTERIOR2] = mat_i2 + (int64_t)(n_B - nT) * 32;
-            if (m->use_stream) {
-                m->phase_bytes[PH_CONDENSE2] = mat_c2 + mat_i2 + (int64_t)(n_B - nT) * 16 + (int64_t)m->n_tc2 * 16;
-                m->phase_bytes[PH_INTERIOR2] = 0;
-            }
+
             m->phase_bytes[PH_GATHER2] = (int64_t)nT * (4 + 16 + 16) + (int64_t)m->n_gat2 * (4 + 16);
             m->phase_bytes[PH_BACKSUB2] = mat_b2 + (int64_t)b2all.size() * (4 + 16) + (int64_t)(n_B - nT) * 32;
         }
         m->phase_bytes[PH_BACKSUB] = mat_b + nbd_tot * (4 + 16) + (int64_t)n_int * 32;
         m->phase_bytes[PH_RESIDUAL] = nk * (4 + 8 + 16) + nf * (4 + 16 + 16);
         m->phase_bytes[PH_VELOCITY] = nv * 48;
+        if (m->use_stream) {
+            // matrices once, every x slice read, every output written (and its add read)
+            int64_t sb = 0;
+            for (const auto& D : m->st_solve.host)
+                sb += (int64_t)D.K * D.ld * es + (int64_t)D.K * 16 + (int64_t)D.n_out * (D.akind >= 0 ? 32 : 16);
+            m->phase_bytes[PH_SOLVE] = sb;
+        }
         int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (m->ax_blocks_int > 0 ? 1 : 0) +
                  (n_B > 0 ? 3 : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
         if (two)
             dd += (m->rows_cond2.n_blocks > 0 ? 1 : 0) + (m->rows_int2.n_blocks > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) +
                   (m->rows_back2.n_blocks > 0 ? 1 : 0);
-        if (m->use_stream) {
-            // condensation (both parts), gather, coarse, reduce, back-substitution; per level
-            dd = (m->st_cond.n_ctas > 0 ? 1 : 0) + (n_B > 0 ? 3 : 0) + (m->st_back.n_ctas > 0 ? 1 : 0);
-            if (two) dd += (m->st_cond2.n_ctas > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) + (m->st_back2.n_ctas > 0 ? 1 : 0);
-        }
+        if (m->use_stream) dd = 1;   // the fused solve
         m->launches_per_iter = 2 + dd + (m->correction ? 2 : 0) + m->refine * (2 + dd);
     }
 
@@ -1335,9 +1416,7 @@ pd_status pd_sync(pd_mesh* m) {
         PDG_CUDA(cudaMemset(m->d_err.p, 0, sizeof(int32_t)));
         if (herr & ERR_NONFINITE) return fail(PD_ERR_NONFINITE, "non-finite positions or velocities");
         if (herr & ERR_TIMEOUT) {
-            for (StreamPlan* P : {&m->st_cond, &m->st_int, &m->st_back, &m->st_cond2, &m->st_int2, &m->st_back2,
-                                  &m->st_coarse})
-                reset_stream_plan(*P, m->stream);
+            reset_stream_plan(m->st_solve, m->stream);
             PDG_CUDA(cudaStreamSynchronize(m->stream));
             return fail(PD_ERR_TIMEOUT, "a pipeline wait in the subspace solve ran out");
         }
@@ -1378,8 +1457,8 @@ pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
     bytes += m->rows_cond2.descs.bytes() + m->rows_cond2.blk_u.bytes() + m->rows_back2.descs.bytes();
     bytes += m->rows_back2.blk_u.bytes() + m->d_bidx2.bytes() + m->d_gat2_ptr.bytes() + m->d_gat2.bytes();
     bytes += m->d_tc2.bytes() + m->d_cT.bytes();
-    for (const StreamPlan* P : {&m->st_cond, &m->st_back, &m->st_cond2, &m->st_back2})
-        bytes += P->pan32.bytes() + P->pan16.bytes() + P->recs.bytes() + P->part.bytes() + P->cnt.bytes();
+    bytes += m->st_solve.pan32.bytes() + m->st_solve.pan16.bytes() + m->st_solve.recs.bytes() +
+             m->st_solve.part.bytes() + m->st_solve.cnt.bytes();
     out->device_bytes = bytes;
     out->prefactor_seconds = m->prefactor_seconds;
     out->launches_per_iter = m->launches_per_iter;

@@ -129,37 +129,95 @@ struct RowPlan {
 };
 
 // Streaming column-form product out[o] = add[o] + sum_k A[k][o] x_k of one
-// dense block (offsets into AxBases as for AxDesc), and a piece of its rows.
+// dense block (a column panel of a factor), and a piece of its rows.  The
+// fused solve runs several such products as phases of one launch; x, add
+// and out name vectors of the solve (XK_*, VK_*) plus offsets into them.
+enum : int32_t {
+    XK_B = 0,      // x_k = b[x_off + k]      (input of the solve)
+    XK_CB = 1,     // x_k = c_B[x_off + k]    (interface right-hand side)
+    XK_CT = 2,     // x_k = c_T[x_off + k]    (top-level right-hand side)
+    XK_G2 = 3,     // x_k = xg2[x_off + k]    (x_T gathered per group)
+    XK_GB = 4,     // x_k = xgB[x_off + k]    (x_B gathered per domain)
+};
+enum : int32_t { VK_NONE = -1, VK_TC = 0, VK_TC2 = 1, VK_X = 2 };
+// what the epilogue does with a final output besides storing it
+enum : int32_t {
+    PK_NONE = 0,
+    PK_CB = 1,     // contribution to c_B[bidx[post_off + o]]: the last contributor forms the entry
+    PK_CT = 2,     // contribution to c_T[bidx2[post_off + o]]: likewise
+    PK_XT = 3,     // x_T[post_off + o]: copies into xg2 and xgB
+    PK_XB = 4,     // x_B[post_off + o]: copies into xgB
+};
 struct ColDesc {
     int64_t a_off;         // pool offset of row 0
     int64_t part_off;      // partial-sum offset (blocks cut into several pieces)
     int32_t K, n_out, ld;  // rows, outputs, row stride
-    int32_t x_off;         // x offset (contiguous source)
-    int32_t xidx_off;      // >= 0: x_k = x[bidx[xidx_off + k]]
-    int32_t add_off;       // >= 0: add offset
+    int32_t x_off;         // offset of x_0 in the XK_* vector
+    int32_t xidx_off;      // (unused by the fused solve)
+    int32_t add_off;       // >= 0: add offset (into the add vector)
     int32_t out_off;
     int32_t n_pieces;
+    int32_t phase;         // phase of the fused solve (0 = first)
+    int32_t xkind;         // XK_*
+    int32_t akind, okind;  // VK_* of the add and out vectors
+    int32_t post_kind;     // PK_*
+    int32_t post_off;
+    int32_t pad0, pad1;
 };
 struct ColPiece {
     int32_t desc, k0, k1, piece;
 };
-// A piece with a copy of its block's descriptor (64 bytes): a CTA loads all of
-// its records into shared memory once.
+// A piece with a copy of its block's descriptor: a CTA loads all of its
+// records into shared memory once.
 struct ColPieceRec {
     ColDesc d;
     ColPiece p;
 };
-// One streaming launch: descriptors, pieces, the piece range of every CTA,
-// partial sums and per-block completion counters.
+// Vectors and index lists of one fused solve (kernel argument).
+struct FusedArgs {
+    const void* pool;
+    const float4* b;
+    float4* x;
+    float4* tc;
+    float4* tc2;
+    float4* cB;
+    float4* cT;
+    float4* xg2;
+    float4* xgB;
+    float4* part;
+    const int* gat_ptr;    // c_B[j] = b_B[j] + sum tc[gat[gat_ptr[j] ..]]
+    const int* gat;
+    const int* gat2_ptr;   // c_T[t] = c_B[T0 + t] + sum tc2[gat2[gat2_ptr[t] ..]]
+    const int* gat2;
+    const int* bidx;       // interface index of every (domain, boundary mode)
+    const int* bidx2;      // top index of every (group, boundary mode)
+    const int* invB_ptr;   // positions q with bidx[q] = j
+    const int* invB;
+    const int* inv2_ptr;   // positions q with bidx2[q] = t
+    const int* inv2;
+    const int* cb0;        // interface entries without a contribution
+    const int* ct0;        // top entries without a contribution
+    int* cnt;              // per panel: pieces done
+    int* cnt_cb;           // per c_B entry: contributions done
+    int* cnt_ct;           // per c_T entry
+    int* phase_cnt;        // per phase: CTAs done; [n_phases]: final count (loaders and epilogues)
+    int* err;
+    int n_int, T0, n_phases, n_ctas, n_cb0, n_ct0;
+};
+// One fused streaming solve: piece records, the piece range of every CTA,
+// partial sums, counters and the panel pool.
 struct StreamPlan {
     DBuf<ColPieceRec> recs;
     DBuf<int32_t> cta_pieces;
     DBuf<float4> part;
     DBuf<int32_t> cnt;
+    DBuf<int32_t> phase_cnt;
+    DBuf<int32_t> cnt_cb, cnt_ct;
     DBuf<float> pan32;             // the blocks as column panels (the plan's own copy)
     DBuf<__nv_bfloat16> pan16;
     int prec = 0;
     int n_ctas = 0;
+    int n_phases = 0;
     size_t smem = 0;
     std::vector<ColDesc> host;
 };
@@ -195,7 +253,7 @@ struct CoarseDescB {
 enum Phase : int {
     PH_INERTIA = 0, PH_LOCAL, PH_ASSEMBLE, PH_CONDENSE, PH_GATHER, PH_COARSE, PH_REDUCE,
     PH_BACKSUB, PH_RESIDUAL, PH_VELOCITY, PH_CONDENSE2, PH_GATHER2, PH_BACKSUB2, PH_INTERIOR, PH_INTERIOR2,
-    PH_COUNT
+    PH_SOLVE, PH_COUNT
 };
 
 // ---------------------------------------------------------------- mesh
@@ -268,13 +326,18 @@ struct pd_mesh {
     int32_t cs_n = 0;                                       // rows of the dense coarse inverse in the pool
     pdg::RowPlan rows_cond2, rows_back2;   // row-form launches of the second level
     pdg::RowPlan rows_int2;                // second-level interior part S_II^-1 c_I
-    // streaming (bulk-copy) launches of every product of the solve; used when
-    // all of them could be planned (every row fits one pipeline stage)
+    // the fused streaming solve (one cooperative launch per solve); used when it
+    // could be planned (every panel row fits one pipeline stage)
     bool use_stream = false;
     bool batched_only = false;             // set by the serving loop: no streaming plans
-    pdg::StreamPlan st_cond, st_int, st_back, st_cond2, st_int2, st_back2, st_coarse;
+    pdg::StreamPlan st_solve;
     pdg::DBuf<int32_t> d_bidx2, d_gat2_ptr, d_gat2;
     pdg::DBuf<float4> d_tc2, d_cT;
+    // fused solve: gathered copies of x_T (per group) and x_B (per domain), the
+    // inverse gather lists, and the entries without any contribution
+    pdg::DBuf<float4> d_xg2, d_xgB;
+    pdg::DBuf<int32_t> d_invB_ptr, d_invB, d_inv2_ptr, d_inv2, d_cb0, d_ct0;
+    int32_t n_cb0 = 0, n_ct0 = 0, n_xg2 = 0, n_xgB = 0;
     int32_t n_tc2 = 0, n_gat2 = 0;
     std::vector<pdg::AxDesc> h_ax_desc_cond, h_ax_desc_back;   // host copies (serving batches)
     pdg::DBuf<float4> d_tc;                 // stacked [t_d; c_d] rows of every domain

@@ -92,8 +92,10 @@ class Mesh:
         p_v = gv.ctypes.data if isinstance(gv, np.ndarray) else gv.data_ptr()
         _check(lib().pd_set_materials(self._h, C.c_void_p(p_s), C.c_void_p(p_v)), "pd_set_materials")
 
-    def prefactor(self, dt, precision="fp32", refine_steps=0, use_graphs=True, correction=False, single_level=False):
-        flags = (_lib.PD_SOLVE_CORRECTION if correction else 0) | (_lib.PD_SOLVE_SINGLE_LEVEL if single_level else 0)
+    def prefactor(self, dt, precision="fp32", refine_steps=0, use_graphs=True, correction=False, single_level=False,
+                  streaming=False):
+        flags = ((_lib.PD_SOLVE_CORRECTION if correction else 0) | (_lib.PD_SOLVE_SINGLE_LEVEL if single_level else 0)
+                 | (_lib.PD_SOLVE_STREAMING if streaming else 0))
         o = _lib.pd_solver_opts(PRECISIONS[precision], int(refine_steps), 1 if use_graphs else 0, flags)
         _check(lib().pd_prefactor(self._h, float(dt), C.byref(o)), "pd_prefactor")
 
@@ -294,7 +296,8 @@ def project(F: torch.Tensor, with_sigma=True):
 
 
 PHASES = ["inertia", "local", "assemble", "dd_condense", "dd_gather", "dd_coarse", "dd_reduce", "dd_backsub",
-          "residual", "velocity", "dd_condense2", "dd_gather2", "dd_backsub2", "dd_interior", "dd_interior2"]
+          "residual", "velocity", "dd_condense2", "dd_gather2", "dd_backsub2", "dd_interior", "dd_interior2",
+          "dd_solve"]
 
 
 def phase_bit(name: str) -> int:

@@ -317,6 +317,36 @@ def test_one_step_error_mixed_precision(slab_traj, prec, refine, correction, tol
     assert max(errs.values()) < tol, errs
 
 
+@pytest.mark.parametrize("prec,refine,tol", [("fp32", 0, 1e-5), ("bf16", 2, 1e-5)])
+def test_streaming_solve_slab(slab_traj, prec, refine, tol):
+    """The fused streaming solve (one cooperative launch per solve): the
+    subspace solve against the full Cholesky solve, and one-step errors."""
+    w, xs, vs = slab_traj
+    from oracle.pd_oracle import PDOracle
+    from paper_2405_12484_gb300.sim import Mesh
+    m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density)
+    m.set_materials(w.gamma_s, w.gamma_v)
+    m.prefactor(w.dt, precision=prec, refine_steps=refine, streaming=True)
+    o = PDOracle(w.rest, w.tets, w.pinned, f32(w.gamma_s), f32(w.gamma_v), w.density, w.dt)
+    rng = np.random.default_rng(9)
+    x = _deformed(w, rng)
+    R, V = o.local(x)
+    b = o.rhs(x + 1e-3 * rng.standard_normal(x.shape), R, V).astype(np.float32)
+    xg = m.solve(torch.as_tensor(b)).cpu().numpy()
+    e_solve = rel(xg[o.free], o.chol.solve(b.astype(np.float64)[o.free]))
+    out = torch.empty((w.n_v, 3), device="cuda")
+    errs = {}
+    for n in (1, 50, 100):
+        m.set_state(torch.as_tensor(xs[n - 1], dtype=torch.float32), torch.as_tensor(vs[n - 1], dtype=torch.float32))
+        m.step(torch.as_tensor(w.pin_targets(n - 1), dtype=torch.float32), w.gravity, w.n_iter, x_out=out)
+        m.sync()
+        errs[n] = rel(out.cpu().numpy(), xs[n])
+    _record(f"streaming_slab_{prec}_r{refine}", {"solve": e_solve, "one_step": {str(k): v for k, v in errs.items()}})
+    m.close()
+    assert e_solve < tol
+    assert max(errs.values()) < tol, errs
+
+
 def test_shell_full_size_mixed_precision():
     """The 390K-tet shell, BF16 matrices in the correction form, 2 PD iterations
     against the oracle (the FP32 run of the same frame is in the test above)."""

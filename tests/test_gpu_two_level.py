@@ -43,11 +43,13 @@ def _rhs(w, o, seed):
     return b.astype(np.float32)
 
 
-@pytest.mark.parametrize("prec,refine,single_level,tol", [("fp32", 0, False, 1e-5), ("fp32", 0, True, 1e-5),
-                                                           ("bf16", 2, False, 1e-5), ("tf32", 2, False, 1e-5)])
-def test_shell_interface_solve(shell_pair, prec, refine, single_level, tol):
+@pytest.mark.parametrize("prec,refine,single_level,streaming,tol", [
+    ("fp32", 0, False, False, 1e-5), ("fp32", 0, True, False, 1e-5), ("bf16", 2, False, False, 1e-5),
+    ("tf32", 2, False, False, 1e-5), ("fp32", 0, False, True, 1e-5), ("fp32", 0, True, True, 1e-5),
+    ("bf16", 2, False, True, 1e-5)])
+def test_shell_interface_solve(shell_pair, prec, refine, single_level, streaming, tol):
     w, m, o = shell_pair
-    m.prefactor(w.dt, precision=prec, refine_steps=refine, single_level=single_level)
+    m.prefactor(w.dt, precision=prec, refine_steps=refine, single_level=single_level, streaming=streaming)
     info = m.info()
     assert info["n_groups"] >= 8
     assert info["two_level"] == (0 if single_level else 1)
@@ -57,7 +59,8 @@ def test_shell_interface_solve(shell_pair, prec, refine, single_level, tol):
     e = rel(xg[o.free], xo)
     try:
         os.makedirs(OUT, exist_ok=True)
-        with open(os.path.join(OUT, f"two_level_{prec}_r{refine}_single{int(single_level)}.json"), "w") as f:
+        with open(os.path.join(OUT, f"two_level_{prec}_r{refine}_single{int(single_level)}_stream{int(streaming)}.json"),
+                  "w") as f:
             json.dump({"rel_err": e, "n_groups": info["n_groups"], "n_top": info["n_top_interface"],
                        "n_interface": info["n_interface"], "prefactor_s": info["prefactor_seconds"],
                        "device_bytes": info["device_bytes"]}, f, indent=1)
