@@ -231,6 +231,17 @@ pd_status pd_enable_timing(pd_mesh* mesh, int32_t enable);
 pd_status pd_phase_times(pd_mesh* mesh, float* out, int32_t n_out, int32_t* n_phases);
 const char* pd_phase_name(int32_t k);
 
+/*
+ * pd_test_offset_phase_counter -- testing hook for failure detection (no
+ * counterpart in the paper).  Adds `delta` to the completion counter of
+ * phase `phase` of the streaming solve (PD_SOLVE_STREAMING), so that the
+ * next solve's wait on that phase can never be satisfied: the wait runs out
+ * after its iteration limit, the launch finishes without a fault, and the
+ * next pd_sync returns PD_ERR_TIMEOUT (and clears the counters, leaving the
+ * mesh usable).  Errors: INVALID_ARG (no streaming plan, phase out of range).
+ */
+pd_status pd_test_offset_phase_counter(pd_mesh* mesh, int32_t phase, int32_t delta);
+
 /* ---- Differentiation: equilibrium steps and the adjoint step (Sec. 6.1) ---- */
 
 typedef struct pd_adjoint pd_adjoint;   /* opaque workspace: CG vectors and the adjoint states */

@@ -49,7 +49,7 @@ constexpr int kMaxGroups = 16;                           // row groups per slab
 constexpr int kMaxPieceRows = 512;                       // x slice of a piece in shared memory
 constexpr int kMaxCtaPieces = 64;                        // piece records of one CTA in shared memory
 static_assert(sizeof(ColPieceRec) % 16 == 0, "piece records are copied in 16-byte words");
-constexpr long long kWaitLimit = 1LL << 24;              // try_wait polls before giving up
+constexpr unsigned long long kWaitNs = 1000000000ull;    // a wait gives up after 1 s
 
 template <class T>
 struct SVec;
@@ -91,11 +91,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait; false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long k = 0; k < kWaitLimit; ++k)
+__device__ __forceinline__ unsigned long long gtime_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false when it ran out (1 s) or, if `abort` is given, when the
+// CTA was marked aborted meanwhile.  Waits for copies still in flight pass no
+// abort flag: they must not end early.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int* abort = nullptr) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtime_ns();
+    for (unsigned k = 1;; ++k) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if ((k & 63u) == 0) {
+            if (abort && *reinterpret_cast<const volatile int*>(abort)) return false;
+            if (gtime_ns() - t0 > kWaitNs) return false;
+        }
+    }
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -220,13 +234,16 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     return v;
 }
 
-// bounded wait for every CTA to have completed phase ph (false when the limit ran out)
-__device__ __forceinline__ bool phase_wait(const FusedArgs& F, int ph) {
-    for (long long k = 0; k < (kWaitLimit >> 4); ++k) {
+// bounded wait for every CTA to have completed phase ph (false when it ran
+// out, 1 s, or the CTA was marked aborted)
+__device__ __forceinline__ bool phase_wait(const FusedArgs& F, int ph, const int* abort) {
+    const unsigned long long t0 = gtime_ns();
+    for (;;) {
         if (ld_acquire(F.phase_cnt + ph) >= F.n_ctas) return true;
+        if (*reinterpret_cast<const volatile int*>(abort)) return false;
+        if (gtime_ns() - t0 > kWaitNs) return false;
         __nanosleep(64);
     }
-    return false;
 }
 
 __device__ __forceinline__ void phase_arrive(const FusedArgs& F, int ph) {
@@ -246,7 +263,7 @@ __device__ __forceinline__ void final_arrive(const FusedArgs& F) {
 // Work of CTA 0's epilogue threads before it signals phase ph: the entries
 // of c_B (phase 0) and c_T (phase 1, after every CTA completed phase 0) that
 // no block contributes to.
-__device__ __forceinline__ void epi_extra(const FusedArgs& F, int ph, int et) {
+__device__ __forceinline__ void epi_extra(const FusedArgs& F, int ph, int et, const int* abort) {
     if (blockIdx.x != 0) return;
     if (ph == 0) {
         for (int k = et; k < F.n_cb0; k += 32 * kEpiWarps) {
@@ -255,7 +272,7 @@ __device__ __forceinline__ void epi_extra(const FusedArgs& F, int ph, int et) {
         }
     } else if (ph == 1 && F.n_ct0 > 0) {
         bool ok = true;
-        if (et == 0) ok = phase_wait(F, 0);
+        if (et == 0) ok = phase_wait(F, 0, abort);
         if (et == 0 && !ok) atomicOr(F.err, ERR_TIMEOUT);
         epi_sync();
         for (int k = et; k < F.n_ct0; k += 32 * kEpiWarps) {
@@ -322,7 +339,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_stream_solve(const ColPieceR
         // no work here: complete every phase and the final count at once
         if (threadIdx.x < 32 * kEpiWarps) {
             for (int ph = 0; ph < F.n_phases; ++ph) {
-                epi_extra(F, ph, threadIdx.x);
+                epi_extra(F, ph, threadIdx.x, &abort_flag);
                 epi_sync();
                 if (threadIdx.x == 0) phase_arrive(F, ph);
             }
@@ -350,7 +367,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_stream_solve(const ColPieceR
                     break;
                 }
                 const int slot = i % kStages;
-                if (i >= kStages && !mbar_wait(&empty[slot], (uint32_t)((i / kStages) - 1) & 1u)) {
+                if (i >= kStages && !mbar_wait(&empty[slot], (uint32_t)((i / kStages) - 1) & 1u, &abort_flag)) {
                     atomicOr(F.err, ERR_TIMEOUT);
                     atomicExch(&abort_flag, 1);
                     stop = true;
@@ -379,10 +396,10 @@ __global__ void __launch_bounds__(kColThreads, 1) k_stream_solve(const ColPieceR
             const ColPiece pc = srec[pp].p;
             const ColDesc D = srec[pp].d;
             bool ok = true;
-            if (pp >= 2 && lane == 0) ok = mbar_wait(&xempty[buf], (uint32_t)((pp / 2) - 1) & 1u);
+            if (pp >= 2 && lane == 0) ok = mbar_wait(&xempty[buf], (uint32_t)((pp / 2) - 1) & 1u, &abort_flag);
             if (ok && D.phase > ready) {
                 if (lane == 0 && !*reinterpret_cast<volatile int*>(&abort_flag)) {
-                    ok = phase_wait(F, D.phase - 1);
+                    ok = phase_wait(F, D.phase - 1, &abort_flag);
                     // the bulk copies below read what other CTAs stored (generic proxy)
                     asm volatile("fence.proxy.async.global;" ::: "memory");
                 }
@@ -433,14 +450,14 @@ __global__ void __launch_bounds__(kColThreads, 1) k_stream_solve(const ColPieceR
             const ColDesc D = srec[pp].d;
             // all of this CTA's pieces of earlier phases are done
             for (; arrived < D.phase; ++arrived) {
-                epi_extra(F, arrived, et);
+                epi_extra(F, arrived, et, &abort_flag);
                 epi_sync();
                 if (et == 0) phase_arrive(F, arrived);
             }
             int S, G;
             col_layout(D.n_out, SO, S, G);
             if (et == 0 && !*reinterpret_cast<volatile int*>(&abort_flag) &&
-                !mbar_wait(&rfull[rbuf], (uint32_t)(pp / RB) & 1u)) {
+                !mbar_wait(&rfull[rbuf], (uint32_t)(pp / RB) & 1u, &abort_flag)) {
                 atomicOr(F.err, ERR_TIMEOUT);
                 atomicExch(&abort_flag, 1);
             }
@@ -498,7 +515,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_stream_solve(const ColPieceR
             }
         }
         for (; arrived < F.n_phases; ++arrived) {
-            epi_extra(F, arrived, et);
+            epi_extra(F, arrived, et, &abort_flag);
             epi_sync();
             if (et == 0) phase_arrive(F, arrived);
         }
@@ -516,7 +533,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_stream_solve(const ColPieceR
         const int rpt = col_rows_per_tile(D.ld, ES);
         int S, G;
         col_layout(D.n_out, SO, S, G);
-        if (!*reinterpret_cast<volatile int*>(&abort_flag) && !mbar_wait(&xfull[buf], (uint32_t)(pp / 2) & 1u)) {
+        if (!*reinterpret_cast<volatile int*>(&abort_flag) && !mbar_wait(&xfull[buf], (uint32_t)(pp / 2) & 1u, &abort_flag)) {
             atomicOr(F.err, ERR_TIMEOUT);
             atomicExch(&abort_flag, 1);
         }
@@ -538,7 +555,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_stream_solve(const ColPieceR
         for (int k = pc.k0; k < pc.k1; k += rpt, ++i) {
             const int slot = i % kStages;
             if (lane == 0 && !*reinterpret_cast<volatile int*>(&abort_flag) &&
-                !mbar_wait(&full[slot], (uint32_t)(i / kStages) & 1u)) {
+                !mbar_wait(&full[slot], (uint32_t)(i / kStages) & 1u, &abort_flag)) {
                 atomicOr(F.err, ERR_TIMEOUT);
                 atomicExch(&abort_flag, 1);
             }
@@ -581,7 +598,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_stream_solve(const ColPieceR
         if (pp >= RB) {
             // red[rbuf] was last filled for piece pp - RB: the epilogue must be done with it
             if (lane == 0 && !*reinterpret_cast<volatile int*>(&abort_flag) &&
-                !mbar_wait(&rempty[rbuf], (uint32_t)((pp / RB) - 1) & 1u)) {
+                !mbar_wait(&rempty[rbuf], (uint32_t)((pp / RB) - 1) & 1u, &abort_flag)) {
                 atomicOr(F.err, ERR_TIMEOUT);
                 atomicExch(&abort_flag, 1);
             }
@@ -788,6 +805,8 @@ void launch_stream_solve(const StreamPlan& P, FusedArgs F, cudaStream_t s) {
 void reset_stream_plan(StreamPlan& P, cudaStream_t s) {
     if (P.cnt.p) PDG_CUDA(cudaMemsetAsync(P.cnt.p, 0, P.cnt.bytes(), s));
     if (P.phase_cnt.p) PDG_CUDA(cudaMemsetAsync(P.phase_cnt.p, 0, P.phase_cnt.bytes(), s));
+    if (P.cnt_cb.p) PDG_CUDA(cudaMemsetAsync(P.cnt_cb.p, 0, P.cnt_cb.bytes(), s));
+    if (P.cnt_ct.p) PDG_CUDA(cudaMemsetAsync(P.cnt_ct.p, 0, P.cnt_ct.bytes(), s));
 }
 
 }  // namespace pdg

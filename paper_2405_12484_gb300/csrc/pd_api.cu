@@ -1414,12 +1414,12 @@ pd_status pd_sync(pd_mesh* m) {
     PDG_CUDA(cudaMemcpy(&herr, m->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (herr) {
         PDG_CUDA(cudaMemset(m->d_err.p, 0, sizeof(int32_t)));
-        if (herr & ERR_NONFINITE) return fail(PD_ERR_NONFINITE, "non-finite positions or velocities");
-        if (herr & ERR_TIMEOUT) {
+        if (herr & ERR_TIMEOUT) {   // the root cause: the solve's values are not meaningful
             reset_stream_plan(m->st_solve, m->stream);
             PDG_CUDA(cudaStreamSynchronize(m->stream));
             return fail(PD_ERR_TIMEOUT, "a pipeline wait in the subspace solve ran out");
         }
+        if (herr & ERR_NONFINITE) return fail(PD_ERR_NONFINITE, "non-finite positions or velocities");
         return fail(PD_ERR_NOT_SPD, "a Cholesky pivot was not positive");
     }
     return PD_OK;
@@ -1531,6 +1531,19 @@ pd_status pd_enable_timing(pd_mesh* m, int32_t mask) {
     if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
     m->timing_mask = mask < 0 ? ((1 << PH_COUNT) - 1) : (mask & ((1 << PH_COUNT) - 1));
     return PD_OK;
+}
+
+pd_status pd_test_offset_phase_counter(pd_mesh* m, int32_t phase, int32_t delta) {
+    if (!m || !m->use_stream || phase < 0 || phase >= m->st_solve.n_phases)
+        return fail(PD_ERR_INVALID_ARG, "no streaming plan or phase out of range");
+    PD_API_BEGIN
+    PDG_CUDA(cudaStreamSynchronize(m->stream));
+    int32_t v = 0;
+    PDG_CUDA(cudaMemcpy(&v, m->st_solve.phase_cnt.p + phase, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    v += delta;
+    PDG_CUDA(cudaMemcpy(m->st_solve.phase_cnt.p + phase, &v, sizeof(int32_t), cudaMemcpyHostToDevice));
+    return PD_OK;
+    PD_API_END
 }
 
 pd_status pd_phase_times(pd_mesh* m, float* out, int32_t n_out, int32_t* n_phases) {

@@ -159,6 +159,10 @@ class Mesh:
         _check(lib().pd_phase_times(self._h, out, 16, C.byref(n)), "pd_phase_times")
         return {lib().pd_phase_name(k).decode(): float(out[k]) for k in range(n.value)}
 
+    def test_offset_phase_counter(self, phase, delta):
+        """Testing hook: makes the next streaming solve's wait on `phase` run out."""
+        _check(lib().pd_test_offset_phase_counter(self._h, int(phase), int(delta)), "pd_test_offset_phase_counter")
+
 
 class Adjoint:
     """Workspace for equilibrium steps and backward adjoint steps on one mesh."""

@@ -362,3 +362,33 @@ def test_shell_full_size_mixed_precision():
                                                 "e_disp": float(np.linalg.norm(x.cpu().numpy() - xo)
                                                                 / np.linalg.norm(xo - w.rest))})
     assert e < 1e-5
+
+
+def test_streaming_wait_runs_out_and_reports_timeout():
+    """Failure detection without a fault: a phase counter that can never reach
+    its target makes the streaming solve's bounded wait run out; the launch
+    ends, pd_sync reports PD_ERR_TIMEOUT, and the mesh works again afterwards."""
+    from paper_2405_12484_gb300 import _lib
+    from paper_2405_12484_gb300.sim import Mesh
+    w = parity_slab()
+    m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density)
+    m.set_materials(w.gamma_s, w.gamma_v)
+    m.prefactor(w.dt, streaming=True, use_graphs=False)
+    x0 = torch.as_tensor(w.rest, dtype=torch.float32)
+    v0 = torch.zeros_like(x0)
+    ref = torch.empty((w.n_v, 3), device="cuda")
+    m.set_state(x0, v0)
+    m.step(torch.as_tensor(w.pin_targets(0), dtype=torch.float32), w.gravity, 2, x_out=ref)
+    m.sync()
+    m.test_offset_phase_counter(0, -100000)
+    m.set_state(x0, v0)
+    m.step(torch.as_tensor(w.pin_targets(0), dtype=torch.float32), w.gravity, 1)
+    with pytest.raises(_lib.PDError) as e:
+        m.sync()
+    assert e.value.status == _lib.PD_ERR_TIMEOUT
+    out = torch.empty_like(ref)
+    m.set_state(x0, v0)
+    m.step(torch.as_tensor(w.pin_targets(0), dtype=torch.float32), w.gravity, 2, x_out=out)
+    m.sync()
+    assert torch.equal(out, ref)
+    m.close()
