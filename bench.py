@@ -40,6 +40,10 @@ def parse():
                    help="solve each PD iteration for the correction b - K x (FP64 residual)")
     p.add_argument("--streaming", action="store_true",
                    help="the whole subspace solve as one cooperative streaming launch")
+    p.add_argument("--modal", action="store_true",
+                   help="the paper's own global step: normal modes per domain + Chebyshev-Jacobi sweeps")
+    p.add_argument("--modes", type=int, default=20)
+    p.add_argument("--sweeps", type=int, default=20)
     p.add_argument("--single-level", action="store_true",
                    help="one dense S^-1 for the interface instead of the two-level interface solve")
     p.add_argument("--iters", type=int, default=20, help="PD iterations per frame")
@@ -338,7 +342,8 @@ def main():
     m.set_materials(w.gamma_s, w.gamma_v)
     t0 = time.perf_counter()
     m.prefactor(w.dt, precision=args.precision, refine_steps=args.refine, use_graphs=True,
-                correction=args.correction, single_level=args.single_level, streaming=args.streaming)
+                correction=args.correction, single_level=args.single_level, streaming=args.streaming,
+                modal=args.modal, modes=args.modes, jacobi_sweeps=args.sweeps if args.modal else 0)
     prefactor_s = time.perf_counter() - t0
     info = m.info()
     K, W = args.steps, max(3, args.warmup)
@@ -451,6 +456,8 @@ def main():
                        if not args.small else f"{w.name} (small profiling case)",
                        "pd_iters_per_frame": n_iter, "dt": w.dt, "precision": args.precision,
                        "refine_steps": args.refine, "correction_form": args.correction,
+                       "solver": ("modal, %d modes, %d Chebyshev-Jacobi sweeps" % (args.modes, args.sweeps)
+                                  if args.modal else "exact subspace solve"),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "per-iteration working set > 129 MB L2 (the solve's matrices alone > 0.3 GB): "
                              "no flush needed",

@@ -85,7 +85,13 @@ enum {
      * (phases separated by bounded grid-wide counters).  Same results up to
      * FP32 summation order; off by default (the separate launches are faster
      * on the meshes measured so far). */
-    PD_SOLVE_STREAMING = 4
+    PD_SOLVE_STREAMING = 4,
+    /* The paper's own global step (Sec. 7.2 and its solver set-up): per domain
+     * only the `modes` fixed-interface normal modes of K_ii with the smallest
+     * eigenvalues (besides the exact boundary modes), then `jacobi_sweeps`
+     * full-space Jacobi sweeps with Chebyshev weights.  Approximate: the error
+     * falls with the sweeps.  Not with PD_SOLVE_STREAMING. */
+    PD_SOLVE_MODAL = 8
 };
 
 typedef struct pd_solver_opts {
@@ -93,6 +99,10 @@ typedef struct pd_solver_opts {
     int32_t refine_steps;  /* 0..2 extra refinement steps per PD iteration with an FP64 residual r = b - K x */
     int32_t use_graphs;    /* 1: replay each frame as a captured CUDA graph (default), 0: plain launches */
     int32_t flags;         /* PD_SOLVE_* bits; 0 = direct solve x = S(b) */
+    int32_t modes;         /* PD_SOLVE_MODAL: normal modes per domain (1..64; 0 = 20) */
+    int32_t jacobi_sweeps; /* PD_SOLVE_MODAL: Chebyshev-Jacobi sweeps after the subspace solve (0..1000) */
+    double jacobi_rho;     /* PD_SOLVE_MODAL: spectral radius of I - D^-1 K for the Chebyshev
+                              weights (0 < rho < 1), or <= 0: estimated by power iteration */
 } pd_solver_opts;
 
 typedef struct pd_mesh pd_mesh;   /* opaque, library-owned */
@@ -107,7 +117,7 @@ typedef struct pd_mesh_info {
     double prefactor_seconds;      /* wall time of the last pd_prefactor */
     int32_t launches_per_iter;     /* kernels launched per PD iteration (after pd_prefactor) */
     int32_t launches_per_frame;    /* kernels launched per frame besides the iterations (pin copy, inertia, velocity) */
-    int64_t phase_bytes[16];       /* algorithmic bytes moved by one launch of each phase (pd_phase_name order) */
+    int64_t phase_bytes[24];       /* algorithmic bytes moved by one launch of each phase (pd_phase_name order) */
     int32_t n_groups;              /* domain groups of the two-level interface solve (0 = single level) */
     int32_t n_top_interface;       /* interface vertices shared by two or more groups */
     int32_t two_level;             /* 1 when the last pd_prefactor built the two-level interface solve */

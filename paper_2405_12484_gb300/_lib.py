@@ -31,11 +31,12 @@ PD_PREC_TF32 = 2
 PD_SOLVE_CORRECTION = 1
 PD_SOLVE_SINGLE_LEVEL = 2
 PD_SOLVE_STREAMING = 4
+PD_SOLVE_MODAL = 8
 
 
 class pd_solver_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("refine_steps", C.c_int32), ("use_graphs", C.c_int32),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("modes", C.c_int32), ("jacobi_sweeps", C.c_int32), ("jacobi_rho", C.c_double)]
 
 
 class pd_mesh_info(C.Structure):
@@ -44,7 +45,7 @@ class pd_mesh_info(C.Structure):
                 ("max_domain_internal", C.c_int32), ("max_domain_boundary", C.c_int32),
                 ("device_bytes", C.c_int64), ("prefactor_seconds", C.c_double),
                 ("launches_per_iter", C.c_int32), ("launches_per_frame", C.c_int32),
-                ("phase_bytes", C.c_int64 * 16), ("n_groups", C.c_int32), ("n_top_interface", C.c_int32),
+                ("phase_bytes", C.c_int64 * 24), ("n_groups", C.c_int32), ("n_top_interface", C.c_int32),
                 ("two_level", C.c_int32)]
 
 

@@ -569,6 +569,30 @@ __global__ void k_axpy(int n, const float4* __restrict__ dx, float4* __restrict_
     x[i] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w);
 }
 
+// One Jacobi sweep with Chebyshev weight omega over the free vertices:
+// x_hat = x + D^-1 (b - K x) (FP64 accumulation), out = omega (x_hat - x_prev) + x_prev.
+__global__ void k_cheb_jacobi(int n_free, const int* __restrict__ ptr, const int* __restrict__ col,
+                              const double* __restrict__ val, const double* __restrict__ dinv,
+                              const float4* __restrict__ b, const float4* __restrict__ x,
+                              const float4* __restrict__ x_prev, float omega, float4* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_free) return;
+    const float4 bb = b[i];
+    double rx = bb.x, ry = bb.y, rz = bb.z;
+    for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const double kv = val[k];
+        const float4 xv = x[col[k]];
+        rx -= kv * (double)xv.x;
+        ry -= kv * (double)xv.y;
+        rz -= kv * (double)xv.z;
+    }
+    const float4 xi = x[i], xp = x_prev[i];
+    const double di = dinv[i];
+    const float hx = (float)((double)xi.x + di * rx), hy = (float)((double)xi.y + di * ry),
+                hz = (float)((double)xi.z + di * rz);
+    out[i] = make_float4(fmaf(omega, hx - xp.x, xp.x), fmaf(omega, hy - xp.y, xp.y), fmaf(omega, hz - xp.z, xp.z), 0.f);
+}
+
 inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
 template <class T>
@@ -601,7 +625,7 @@ void launch_rowdot(const RowPlan& P, const AxBases& B, cudaStream_t s) {
 }
 
 struct DDBufs {
-    float4 *tc, *cB, *part, *tc2, *cT, *xg2, *xgB;
+    float4 *tc, *cB, *part, *tc2, *cT, *xg2, *xgB, *pm, *jx1, *jx2;
 };
 
 // One subspace solve: x (free vertices of xout) = K_ff^-1 b.
@@ -644,14 +668,24 @@ template <class T>
 void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, const DDBufs& w, cudaStream_t s) {
     // the interior part t = K_ii^-1 b_i runs on a side stream beside the
     // interface solve and is joined before the back-substitution
-    const bool fork1 = m->ax_blocks_int > 0;
+    const bool fork1 = m->ax_blocks_int > 0 || m->ax_blocks_m1 > 0;
     if (fork1) {
         PDG_CUDA(cudaEventRecord(m->ev_fork[0], s));
         PDG_CUDA(cudaStreamWaitEvent(m->side[0], m->ev_fork[0], 0));
-        phase_begin(m, PH_INTERIOR, m->side[0]);
-        launch_ax<T>(m->d_ax_desc_int.p, m->d_ax_blk_int.p, m->ax_blocks_int, m->ax_kmax_int,
-                     AxBases{pool, b, nullptr, nullptr, w.tc}, m->side[0]);
-        phase_end(m, m->side[0]);
+        if (m->modal) {
+            // t = (Phi Lambda^-1)(Phi^T b_i): the truncated interior response
+            phase_begin(m, PH_MODAL, m->side[0]);
+            launch_ax<T>(m->d_ax_desc_m1.p, m->d_ax_blk_m1.p, m->ax_blocks_m1, m->ax_kmax_m1,
+                         AxBases{pool, b, nullptr, nullptr, w.pm}, m->side[0]);
+            launch_ax<T>(m->d_ax_desc_m2.p, m->d_ax_blk_m2.p, m->ax_blocks_m2, m->ax_kmax_m2,
+                         AxBases{pool, w.pm, nullptr, nullptr, w.tc}, m->side[0]);
+            phase_end(m, m->side[0]);
+        } else {
+            phase_begin(m, PH_INTERIOR, m->side[0]);
+            launch_ax<T>(m->d_ax_desc_int.p, m->d_ax_blk_int.p, m->ax_blocks_int, m->ax_kmax_int,
+                         AxBases{pool, b, nullptr, nullptr, w.tc}, m->side[0]);
+            phase_end(m, m->side[0]);
+        }
         PDG_CUDA(cudaEventRecord(m->ev_join[0], m->side[0]));
     }
     if (m->ax_blocks_cond > 0) {
@@ -712,13 +746,33 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
                      AxBases{pool, xout + m->n_int, m->d_bidx.p, w.tc, xout}, s);
         phase_end(m, s);
     }
+    const int S = (int)m->jacobi_omega.size();
+    if (S > 0 && m->n_free > 0) {
+        // full-space Chebyshev-weighted Jacobi sweeps; iterate k+1 goes to buffer
+        // (k+1) mod 3 of {xout, jx1, jx2}, the last one is copied back to xout
+        float4* buf[3] = {xout, w.jx1, w.jx2};
+        phase_begin(m, PH_JACOBI, s);
+        for (int k = 1; k <= S; ++k) {
+            const float4* cur = buf[(k - 1) % 3];
+            const float4* prev = buf[(k >= 2 ? k - 2 : 0) % 3];
+            k_cheb_jacobi<<<nblk(m->n_free, 256), 256, 0, s>>>(m->n_free, m->d_K_ptr.p, m->d_K_col.p, m->d_K_val.p,
+                                                              m->d_Dinv.p, b, cur, prev, m->jacobi_omega[k - 1],
+                                                              buf[k % 3]);
+            PDG_CHECK_LAUNCH();
+        }
+        if (S % 3 != 0)
+            PDG_CUDA(cudaMemcpyAsync(xout, buf[S % 3], sizeof(float4) * (size_t)m->n_free, cudaMemcpyDeviceToDevice,
+                                     s));
+        phase_end(m, s);
+    }
 }
 
 }  // namespace
 
 void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* tc, float4* cB, float4* part,
-                             float4* tc2, float4* cT, float4* xg2, float4* xgB, cudaStream_t s) {
-    const DDBufs w{tc, cB, part, tc2, cT, xg2, xgB};
+                             float4* tc2, float4* cT, float4* xg2, float4* xgB, float4* pm, float4* jx1, float4* jx2,
+                             cudaStream_t s) {
+    const DDBufs w{tc, cB, part, tc2, cT, xg2, xgB, pm, jx1, jx2};
     if (m->use_stream) {
         dd_solve_stream(m, b, xout, w, s);
     } else if (m->prec == PD_PREC_BF16) dd_solve_impl<__nv_bfloat16>(m, m->d_mat16.p, b, xout, w, s);
@@ -816,7 +870,7 @@ void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream
 
 void launch_dd_solve(pd_mesh* m, const float4* b, float4* xout, cudaStream_t s, bool /*timed*/) {
     launch_dd_solve_scratch(m, b, xout, m->d_tc.p, m->d_cB.p, m->d_part.p, m->d_tc2.p, m->d_cT.p, m->d_xg2.p,
-                            m->d_xgB.p, s);
+                            m->d_xgB.p, m->d_pm.p, m->d_jx1.p, m->d_jx2.p, s);
 }
 
 void launch_residual(const pd_mesh* m, const float4* b, const float4* x, float4* r, cudaStream_t s) {

@@ -40,6 +40,77 @@ void launch_copy_block_idx(const double* S, int ldS, int r0, int nr, const int* 
 
 static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// ---- small dense helpers of the modal prefactorisation (q x q, q <= 64, FP64)
+
+// G = R^T R (R upper triangular) and the inverse of R; false if G is not SPD.
+static bool chol_upper_inverse(const double* G, int q, int ld, std::vector<double>& Rinv) {
+    std::vector<double> R((size_t)q * q, 0.0);
+    for (int j = 0; j < q; ++j) {
+        double s = G[(size_t)j * ld + j];
+        for (int k = 0; k < j; ++k) s -= R[(size_t)k * q + j] * R[(size_t)k * q + j];
+        if (!(s > 0.0)) return false;
+        const double rjj = std::sqrt(s);
+        R[(size_t)j * q + j] = rjj;
+        for (int i = j + 1; i < q; ++i) {
+            double t = G[(size_t)j * ld + i];
+            for (int k = 0; k < j; ++k) t -= R[(size_t)k * q + j] * R[(size_t)k * q + i];
+            R[(size_t)j * q + i] = t / rjj;
+        }
+    }
+    // back substitution on the identity: R X = I, X upper triangular
+    Rinv.assign((size_t)q * q, 0.0);
+    for (int c = 0; c < q; ++c)
+        for (int i = c; i >= 0; --i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= c; ++k) t -= R[(size_t)i * q + k] * Rinv[(size_t)k * q + c];
+            Rinv[(size_t)i * q + c] = t / R[(size_t)i * q + i];
+        }
+    return true;
+}
+
+// Cyclic Jacobi eigenvalue algorithm for a symmetric q x q matrix (Golub &
+// Van Loan, Sec. 8.5): A is overwritten; on return w holds the eigenvalues and
+// the columns of V the eigenvectors (unsorted).
+static void jacobi_eig(std::vector<double>& A, int q, std::vector<double>& w, std::vector<double>& V) {
+    V.assign((size_t)q * q, 0.0);
+    for (int i = 0; i < q; ++i) V[(size_t)i * q + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < q; ++i)
+            for (int j = 0; j < q; ++j) {
+                const double a = A[(size_t)i * q + j];
+                tot += a * a;
+                if (i != j) off += a * a;
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < q - 1; ++p)
+            for (int r = p + 1; r < q; ++r) {
+                const double apr = A[(size_t)p * q + r];
+                if (apr == 0.0) continue;
+                const double theta = (A[(size_t)r * q + r] - A[(size_t)p * q + p]) / (2.0 * apr);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < q; ++k) {   // A <- J^T A J
+                    const double akp = A[(size_t)k * q + p], akr = A[(size_t)k * q + r];
+                    A[(size_t)k * q + p] = c * akp - sn * akr;
+                    A[(size_t)k * q + r] = sn * akp + c * akr;
+                }
+                for (int k = 0; k < q; ++k) {
+                    const double apk = A[(size_t)p * q + k], ark = A[(size_t)r * q + k];
+                    A[(size_t)p * q + k] = c * apk - sn * ark;
+                    A[(size_t)r * q + k] = sn * apk + c * ark;
+                }
+                for (int k = 0; k < q; ++k) {
+                    const double vkp = V[(size_t)k * q + p], vkr = V[(size_t)k * q + r];
+                    V[(size_t)k * q + p] = c * vkp - sn * vkr;
+                    V[(size_t)k * q + r] = sn * vkp + c * vkr;
+                }
+            }
+    }
+    w.resize(q);
+    for (int i = 0; i < q; ++i) w[i] = A[(size_t)i * q + i];
+}
+
 void phase_begin(pd_mesh* m, int phase, cudaStream_t s) {
     if (!m->timing_armed || !m->ev_rec || !(m->timing_mask & (1 << phase))) return;
     pd_mesh::TimingSet& T = *m->ev_rec;
@@ -230,7 +301,7 @@ const char* pd_last_error(void) { return g_last_error.c_str(); }
 static const char* kPhaseNames[PH_COUNT] = {"inertia",      "local",      "assemble",   "dd_condense", "dd_gather",
                                             "dd_coarse",    "dd_reduce",  "dd_backsub", "residual",    "velocity",
                                             "dd_condense2", "dd_gather2", "dd_backsub2", "dd_interior",
-                                            "dd_interior2", "dd_solve"};
+                                            "dd_interior2", "dd_solve", "dd_modal", "dd_jacobi"};
 
 const char* pd_phase_name(int32_t k) { return (k >= 0 && k < PH_COUNT) ? kPhaseNames[k] : "?"; }
 
@@ -613,8 +684,12 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     pd_solver_opts o{PD_PREC_FP32, 0, 1, 0};
     if (opts) o = *opts;
     if (o.precision < PD_PREC_FP32 || o.precision > PD_PREC_TF32 || o.refine_steps < 0 || o.refine_steps > 2 ||
-        (o.flags & ~(PD_SOLVE_CORRECTION | PD_SOLVE_SINGLE_LEVEL | PD_SOLVE_STREAMING)) != 0)
+        (o.flags & ~(PD_SOLVE_CORRECTION | PD_SOLVE_SINGLE_LEVEL | PD_SOLVE_STREAMING | PD_SOLVE_MODAL)) != 0)
         return fail(PD_ERR_INVALID_ARG, "bad solver options");
+    if ((o.flags & PD_SOLVE_MODAL) &&
+        ((o.flags & PD_SOLVE_STREAMING) || o.modes < 0 || o.modes > 64 || o.jacobi_sweeps < 0 ||
+         o.jacobi_sweeps > 1000 || !(o.jacobi_rho < 1.0) || !std::isfinite(o.jacobi_rho)))
+        return fail(PD_ERR_INVALID_ARG, "bad modal-solve options");
     PD_API_BEGIN
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = m->stream;
@@ -722,6 +797,98 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
                false, s);
     dKii.free();
     dKib.free();
+
+    // ---- the paper's normal modes (PD_SOLVE_MODAL): per domain the r
+    // eigenvectors of K_ii with the smallest eigenvalues (the largest of
+    // K_ii^-1), by subspace iteration with K_ii^-1 (batched FP64 GEMMs on the
+    // device) re-orthonormalised by Cholesky QR, then Rayleigh-Ritz; only the
+    // q x q Gram and Ritz matrices (q <= 64) are factored on the host.
+    const bool modal = (o.flags & PD_SOLVE_MODAL) != 0;
+    const int r_req = modal ? (o.modes > 0 ? o.modes : 20) : 0;
+    const int NR = modal ? (int)round_up(r_req, 8) : 8;
+    std::vector<int32_t> r_dom(n_dom, 0);
+    DBuf<double> dPhi, dPhiS;   // Phi and Phi Lambda^-1, n_dom blocks of NI x NR
+    if (modal) {
+        const int NQ = (int)round_up(std::min(r_req + 8, 64), 8);
+        const int64_t sZ = (int64_t)NI * NQ, sG = (int64_t)NQ * NQ, sP = (int64_t)NI * NR, sV = (int64_t)NQ * NR;
+        std::vector<int32_t> q_dom(n_dom, 0);
+        for (int32_t d = 0; d < n_dom; ++d) {
+            q_dom[d] = std::min(NQ, m->dom_n_int[d]);
+            r_dom[d] = std::min(r_req, m->dom_n_int[d]);
+        }
+        // start block: fixed pseudo-random entries (64-bit LCG) on each domain's
+        // rows and first q columns, zero elsewhere
+        std::vector<double> hz((size_t)n_dom * sZ, 0.0);
+        uint64_t st = 0x9e3779b97f4a7c15ull;
+        for (int32_t d = 0; d < n_dom; ++d)
+            for (int32_t k = 0; k < m->dom_n_int[d]; ++k)
+                for (int j = 0; j < q_dom[d]; ++j) {
+                    st = st * 6364136223846793005ull + 1442695040888963407ull;
+                    hz[(size_t)d * sZ + (size_t)k * NQ + j] = (double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+                }
+        DBuf<double> dZ, dY, dG;
+        upload(dZ, hz, s);
+        dY.alloc((size_t)n_dom * sZ);
+        dG.alloc((size_t)n_dom * sG);
+        std::vector<double> hG((size_t)n_dom * sG), hR((size_t)n_dom * sG);
+        std::vector<double> Rinv;
+        constexpr int kModalIters = 60;
+        for (int it = 0; it <= kModalIters; ++it) {
+            dense_gemm(false, false, NI, NQ, NI, 1.0, dXii.p, NI, sKii, dZ.p, NQ, sZ, 0.0, dY.p, NQ, sZ, n_dom, false,
+                       s);
+            if (it == kModalIters) break;
+            dense_gemm(true, false, NQ, NQ, NI, 1.0, dY.p, NQ, sZ, dY.p, NQ, sZ, 0.0, dG.p, NQ, sG, n_dom, false, s);
+            PDG_CUDA(cudaMemcpyAsync(hG.data(), dG.p, sizeof(double) * hG.size(), cudaMemcpyDeviceToHost, s));
+            PDG_CUDA(cudaStreamSynchronize(s));
+            std::fill(hR.begin(), hR.end(), 0.0);
+            for (int32_t d = 0; d < n_dom; ++d) {
+                const int q = q_dom[d];
+                if (q == 0) continue;
+                if (!chol_upper_inverse(&hG[(size_t)d * sG], q, NQ, Rinv))
+                    return fail(PD_ERR_NOT_SPD, "modal subspace iteration lost rank");
+                for (int i = 0; i < q; ++i)
+                    for (int j = 0; j < q; ++j) hR[(size_t)d * sG + (size_t)i * NQ + j] = Rinv[(size_t)i * q + j];
+            }
+            PDG_CUDA(cudaMemcpyAsync(dG.p, hR.data(), sizeof(double) * hR.size(), cudaMemcpyHostToDevice, s));
+            dense_gemm(false, false, NI, NQ, NQ, 1.0, dY.p, NQ, sZ, dG.p, NQ, sG, 0.0, dZ.p, NQ, sZ, n_dom, false, s);
+        }
+        // Rayleigh-Ritz with K_ii^-1: T = Z^T (K_ii^-1 Z), eigenvalues mu = 1 / lambda
+        dense_gemm(true, false, NQ, NQ, NI, 1.0, dZ.p, NQ, sZ, dY.p, NQ, sZ, 0.0, dG.p, NQ, sG, n_dom, false, s);
+        PDG_CUDA(cudaMemcpyAsync(hG.data(), dG.p, sizeof(double) * hG.size(), cudaMemcpyDeviceToHost, s));
+        PDG_CUDA(cudaStreamSynchronize(s));
+        std::vector<double> hV((size_t)n_dom * sV, 0.0), hVs((size_t)n_dom * sV, 0.0), T, w, V;
+        m->modal_lambda_min = 1e300;
+        for (int32_t d = 0; d < n_dom; ++d) {
+            const int q = q_dom[d];
+            if (q == 0) continue;
+            T.assign((size_t)q * q, 0.0);
+            for (int i = 0; i < q; ++i)
+                for (int j = 0; j < q; ++j)
+                    T[(size_t)i * q + j] =
+                        0.5 * (hG[(size_t)d * sG + (size_t)i * NQ + j] + hG[(size_t)d * sG + (size_t)j * NQ + i]);
+            jacobi_eig(T, q, w, V);
+            std::vector<int> idx(q);
+            std::iota(idx.begin(), idx.end(), 0);
+            std::sort(idx.begin(), idx.end(), [&](int a, int b) { return w[a] > w[b]; });
+            for (int j = 0; j < r_dom[d]; ++j) {
+                const double mu = w[idx[j]];
+                if (!(mu > 0.0)) return fail(PD_ERR_NOT_SPD, "modal Rayleigh-Ritz value not positive");
+                m->modal_lambda_min = std::min(m->modal_lambda_min, 1.0 / mu);
+                for (int i = 0; i < q; ++i) {
+                    hV[(size_t)d * sV + (size_t)i * NR + j] = V[(size_t)i * q + idx[j]];
+                    hVs[(size_t)d * sV + (size_t)i * NR + j] = V[(size_t)i * q + idx[j]] * mu;   // / lambda
+                }
+            }
+        }
+        DBuf<double> dV, dVs;
+        upload(dV, hV, s);
+        upload(dVs, hVs, s);
+        dPhi.alloc((size_t)n_dom * sP);
+        dPhiS.alloc((size_t)n_dom * sP);
+        dense_gemm(false, false, NI, NR, NQ, 1.0, dZ.p, NQ, sZ, dV.p, NR, sV, 0.0, dPhi.p, NR, sP, n_dom, false, s);
+        dense_gemm(false, false, NI, NR, NQ, 1.0, dZ.p, NQ, sZ, dVs.p, NR, sV, 0.0, dPhiS.p, NR, sP, n_dom, false, s);
+        PDG_CUDA(cudaStreamSynchronize(s));
+    }
 
     // ---- boundary index lists and the reduced interface matrix S = K_BB + sum_d S_d
     std::vector<int32_t> sbidx_off(n_dom + 1, 0), sbidx;
@@ -842,17 +1009,27 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     // per domain: K_ii^-1 (n_i x n_i), Psi_d (n_i x n_bd, row k = coefficients of
     // b_k for every boundary mode) and Psi_d^T (n_bd x n_i); row strides rounded
     // to 8 entries so every row starts on a 16-byte boundary
-    std::vector<int64_t> h_off(n_dom), p_off(n_dom), t_off(n_dom);
-    std::vector<int32_t> ldH(n_dom), ldP(n_dom), ldT(n_dom), tc_off(n_dom);
+    std::vector<int64_t> h_off(n_dom), p_off(n_dom), t_off(n_dom), m1_off(n_dom), m2_off(n_dom);
+    std::vector<int32_t> ldH(n_dom), ldP(n_dom), ldT(n_dom), tc_off(n_dom), pm_off(n_dom);
     int64_t pool = 0;
-    int32_t tcr = 0;
+    int32_t tcr = 0, pmr = 0;
     for (int32_t d = 0; d < n_dom; ++d) {
         const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
         ldH[d] = (int32_t)round_up(std::max(ni, 1), 8);
         ldP[d] = (int32_t)round_up(std::max(nbd, 1), 8);
         ldT[d] = ldH[d];
         h_off[d] = pool;
-        pool += (int64_t)ni * ldH[d];
+        if (modal) {
+            // Phi (n_i x r) and (Phi Lambda^-1)^T (r x n_i) in place of K_ii^-1
+            m1_off[d] = pool;
+            pool += (int64_t)ni * NR;
+            m2_off[d] = pool;
+            pool += (int64_t)r_dom[d] * ldH[d];
+            pm_off[d] = pmr;
+            pmr += r_dom[d];
+        } else {
+            pool += (int64_t)ni * ldH[d];
+        }
         p_off[d] = pool;
         pool += (int64_t)ni * ldP[d];
         t_off[d] = pool;
@@ -896,7 +1073,17 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         if (ni == 0) continue;
         const double* Xd = dXii.p + (size_t)d * sKii;
         const double* Pd = dPsi.p + (size_t)d * sKib;
-        launch_cast_block(Xd, NI, ni, ni, 0, m->prec, m->d_mat32.p, m->d_mat16.p, h_off[d], ldH[d], s);
+        if (modal) {
+            const int64_t sP = (int64_t)NI * NR;
+            if (r_dom[d] > 0) {
+                launch_cast_block(dPhi.p + d * sP, NR, ni, r_dom[d], 0, m->prec, m->d_mat32.p, m->d_mat16.p, m1_off[d],
+                                  NR, s);
+                launch_cast_block(dPhiS.p + d * sP, NR, r_dom[d], ni, 1, m->prec, m->d_mat32.p, m->d_mat16.p, m2_off[d],
+                                  ldH[d], s);
+            }
+        } else {
+            launch_cast_block(Xd, NI, ni, ni, 0, m->prec, m->d_mat32.p, m->d_mat16.p, h_off[d], ldH[d], s);
+        }
         if (nbd > 0) {
             launch_cast_block(Pd, NBp, ni, nbd, 0, m->prec, m->d_mat32.p, m->d_mat16.p, p_off[d], ldP[d], s);
             launch_cast_block(Pd, NBp, nbd, ni, 1, m->prec, m->d_mat32.p, m->d_mat16.p, t_off[d], ldT[d], s);
@@ -933,8 +1120,8 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         // (on the path to the interface solve) and the interior part
         // t_d = K_ii^-1 b_i (needed only by the back-substitution)
         const int OW = ax_outputs_per_block(m->prec);
-        std::vector<AxDesc> dc, di, db;
-        std::vector<AxBlock> bc, bi, bb;
+        std::vector<AxDesc> dc, di, db, dm1, dm2;
+        std::vector<AxBlock> bc, bi, bb, bm1, bm2;
         for (int32_t d = 0; d < n_dom; ++d) {
             const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
             if (ni == 0) continue;
@@ -951,13 +1138,39 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
                 for (int32_t o0 = 0; o0 < c.n_out; o0 += OW) bc.push_back(AxBlock{(int32_t)dc.size(), o0});
                 dc.push_back(c);
             }
-            AxDesc t = c;
-            t.a_off = h_off[d];
-            t.out_off = tc_off[d];
-            t.ld = ldH[d];
-            t.n_out = ni;
-            for (int32_t o0 = 0; o0 < t.n_out; o0 += OW) bi.push_back(AxBlock{(int32_t)di.size(), o0});
-            di.push_back(t);
+            if (!modal) {
+                AxDesc t = c;
+                t.a_off = h_off[d];
+                t.out_off = tc_off[d];
+                t.ld = ldH[d];
+                t.n_out = ni;
+                for (int32_t o0 = 0; o0 < t.n_out; o0 += OW) bi.push_back(AxBlock{(int32_t)di.size(), o0});
+                di.push_back(t);
+            } else if (r_dom[d] > 0) {
+                // p = Phi^T b_i (rows k of Phi), then t = (Phi Lambda^-1) p (rows j of its transpose)
+                AxDesc a1{};
+                a1.a_off = m1_off[d];
+                a1.x_off = m->dom_int_off[d];
+                a1.bidx_off = -1;
+                a1.add_off = -1;
+                a1.out_off = pm_off[d];
+                a1.K = ni;
+                a1.ld = NR;
+                a1.n_out = r_dom[d];
+                for (int32_t o0 = 0; o0 < a1.n_out; o0 += OW) bm1.push_back(AxBlock{(int32_t)dm1.size(), o0});
+                dm1.push_back(a1);
+                AxDesc a2{};
+                a2.a_off = m2_off[d];
+                a2.x_off = pm_off[d];
+                a2.bidx_off = -1;
+                a2.add_off = -1;
+                a2.out_off = tc_off[d];
+                a2.K = r_dom[d];
+                a2.ld = ldH[d];
+                a2.n_out = ni;
+                for (int32_t o0 = 0; o0 < a2.n_out; o0 += OW) bm2.push_back(AxBlock{(int32_t)dm2.size(), o0});
+                dm2.push_back(a2);
+            }
             AxDesc b{};
             b.a_off = t_off[d];
             b.x_off = 0;
@@ -983,6 +1196,15 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->h_ax_desc_cond = dc;
         m->h_ax_desc_cond.insert(m->h_ax_desc_cond.end(), di.begin(), di.end());
         m->h_ax_desc_back = db;
+        upload(m->d_ax_desc_m1, dm1, s);
+        upload(m->d_ax_desc_m2, dm2, s);
+        upload(m->d_ax_blk_m1, bm1, s);
+        upload(m->d_ax_blk_m2, bm2, s);
+        m->ax_blocks_m1 = (int32_t)bm1.size();
+        m->ax_blocks_m2 = (int32_t)bm2.size();
+        m->ax_kmax_m1 = m->ax_kmax_m2 = 1;
+        for (const auto& a : dm1) m->ax_kmax_m1 = std::max(m->ax_kmax_m1, a.K);
+        for (const auto& a : dm2) m->ax_kmax_m2 = std::max(m->ax_kmax_m2, a.K);
         m->ax_kmax_cond = m->ax_kmax_int = m->ax_kmax_back = 1;
         for (const auto& a : dc) m->ax_kmax_cond = std::max(m->ax_kmax_cond, a.K);
         for (const auto& a : di) m->ax_kmax_int = std::max(m->ax_kmax_int, a.K);
@@ -990,6 +1212,59 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         (void)VN;
     }
     m->n_tc = tcr;
+    m->modal = modal;
+    m->modes = r_req;
+    m->jacobi_sweeps = modal ? o.jacobi_sweeps : 0;
+    m->n_pm = pmr;
+    m->d_pm.alloc(std::max(pmr, 1));
+    m->jacobi_omega.clear();
+    if (modal && m->jacobi_sweeps > 0) {
+        // the Jacobi diagonal and the Chebyshev weights (Wang 2015) for the
+        // spectral radius rho of I - D^-1 K (given, or from 300 power
+        // iterations on the similar symmetric I - D^-1/2 K D^-1/2, raised by 1 %)
+        std::vector<double> dinv(std::max(n_free, 1), 1.0), sq(std::max(n_free, 1), 1.0);
+        for (int32_t i = 0; i < n_free; ++i)
+            for (int32_t k = m->K_rowptr[i]; k < m->K_rowptr[i + 1]; ++k)
+                if (m->K_col[k] == i) {
+                    dinv[i] = 1.0 / m->K_val[k];
+                    sq[i] = std::sqrt(dinv[i]);
+                }
+        upload(m->d_Dinv, dinv, s);
+        double rho = o.jacobi_rho;
+        if (!(rho > 0.0)) {
+            std::vector<double> v(n_free), w(n_free);
+            uint64_t st = 0x2545f4914f6cdd1dull;
+            for (auto& e : v) {
+                st = st * 6364136223846793005ull + 1442695040888963407ull;
+                e = (double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+            }
+            double lam = 0.0;
+            for (int it = 0; it < 300; ++it) {
+                double nrm = 0.0;
+                for (int32_t i = 0; i < n_free; ++i) {
+                    double kv = 0.0;
+                    for (int32_t k = m->K_rowptr[i]; k < m->K_rowptr[i + 1]; ++k)
+                        kv += m->K_val[k] * sq[m->K_col[k]] * v[m->K_col[k]];
+                    w[i] = v[i] - sq[i] * kv;
+                    nrm += w[i] * w[i];
+                }
+                nrm = std::sqrt(nrm);
+                if (!(nrm > 0.0)) break;
+                lam = nrm;   // |v| = 1 after the first iteration: ||A v|| -> |lambda|max
+                for (int32_t i = 0; i < n_free; ++i) v[i] = w[i] / nrm;
+            }
+            rho = std::min(0.9999, 1.01 * lam);
+        }
+        if (!(rho < 1.0)) return fail(PD_ERR_UNSUPPORTED, "Jacobi sweeps do not converge on this matrix");
+        m->jacobi_rho = rho;
+        double om = 1.0;
+        for (int k = 1; k <= m->jacobi_sweeps; ++k) {
+            om = (k == 1) ? 1.0 : (k == 2 ? 2.0 / (2.0 - rho * rho) : 4.0 / (4.0 - rho * rho * om));
+            m->jacobi_omega.push_back((float)om);
+        }
+        m->d_jx1.alloc(std::max(n_free, 1));
+        m->d_jx2.alloc(std::max(n_free, 1));
+    }
     m->d_tc.alloc(std::max(tcr, 1));
     m->rows_cond2.n_blocks = m->rows_int2.n_blocks = m->rows_back2.n_blocks = 0;
     m->rows_cond2.host.clear();
@@ -1229,12 +1504,21 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         for (const auto& d : m->rows_cond2.host) mat_c2 += (int64_t)d.rows * d.ld * es;
         for (const auto& d : m->rows_int2.host) mat_i2 += (int64_t)d.rows * d.ld * es;
         for (const auto& d : m->rows_back2.host) mat_b2 += (int64_t)d.rows * d.ld * es;
-        for (int k = 0; k < 16; ++k) m->phase_bytes[k] = 0;
+        for (int k = 0; k < 24; ++k) m->phase_bytes[k] = 0;
         m->phase_bytes[PH_INERTIA] = nv * 48 + nf * (16 + 4 + 16 + 4) + nkfp * 8 + (int64_t)m->n_pin * 16;
         m->phase_bytes[PH_LOCAL] = nt * (16 + 48 + 64) + nv * 16;
         m->phase_bytes[PH_ASSEMBLE] = nf * (4 + 16 + 16) + ninc * (4 + 16);
         m->phase_bytes[PH_CONDENSE] = mat_c + (int64_t)n_int * 16 + nbd_tot * 16;
         m->phase_bytes[PH_INTERIOR] = mat_i + (int64_t)n_int * 32;
+        if (modal) {
+            int64_t mb = 0;
+            for (int32_t d = 0; d < n_dom; ++d)
+                mb += ((int64_t)m->dom_n_int[d] * NR + (int64_t)r_dom[d] * ldH[d]) * es;
+            m->phase_bytes[PH_INTERIOR] = 0;
+            m->phase_bytes[PH_MODAL] = mb + (int64_t)n_int * 32 + (int64_t)pmr * 32;
+            m->phase_bytes[PH_JACOBI] = (int64_t)m->jacobi_omega.size() *
+                                        ((int64_t)m->K_col.size() * (4 + 8 + 16) + (int64_t)n_free * (4 + 8 + 16 * 4));
+        }
 
         m->phase_bytes[PH_GATHER] = (int64_t)n_B * (4 + 16 + 16) + ngat * (4 + 16);
         const int64_t ncs = m->cs_n;
@@ -1259,6 +1543,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         }
         int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (m->ax_blocks_int > 0 ? 1 : 0) +
                  (n_B > 0 ? 3 : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
+        if (modal) dd += (m->ax_blocks_m1 > 0 ? 2 : 0) + (int)m->jacobi_omega.size();
         if (two)
             dd += (m->rows_cond2.n_blocks > 0 ? 1 : 0) + (m->rows_int2.n_blocks > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) +
                   (m->rows_back2.n_blocks > 0 ? 1 : 0);
@@ -1463,7 +1748,7 @@ pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
     out->prefactor_seconds = m->prefactor_seconds;
     out->launches_per_iter = m->launches_per_iter;
     out->launches_per_frame = 3;   // pin copy (or hold), inertia, velocity
-    for (int k = 0; k < 16; ++k) out->phase_bytes[k] = m->phase_bytes[k];
+    for (int k = 0; k < 24; ++k) out->phase_bytes[k] = m->phase_bytes[k];
     return PD_OK;
 }
 

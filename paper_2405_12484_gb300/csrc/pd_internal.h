@@ -253,7 +253,7 @@ struct CoarseDescB {
 enum Phase : int {
     PH_INERTIA = 0, PH_LOCAL, PH_ASSEMBLE, PH_CONDENSE, PH_GATHER, PH_COARSE, PH_REDUCE,
     PH_BACKSUB, PH_RESIDUAL, PH_VELOCITY, PH_CONDENSE2, PH_GATHER2, PH_BACKSUB2, PH_INTERIOR, PH_INTERIOR2,
-    PH_SOLVE, PH_COUNT
+    PH_SOLVE, PH_MODAL, PH_JACOBI, PH_COUNT
 };
 
 // ---------------------------------------------------------------- mesh
@@ -329,6 +329,20 @@ struct pd_mesh {
     // the fused streaming solve (one cooperative launch per solve); used when it
     // could be planned (every panel row fits one pipeline stage)
     bool use_stream = false;
+    // the paper's own global step (PD_SOLVE_MODAL): rank-r interior response
+    // t = (Phi Lambda^-1)(Phi^T b_i), then Chebyshev-weighted Jacobi sweeps
+    bool modal = false;
+    int32_t modes = 0, jacobi_sweeps = 0;
+    double jacobi_rho = 0.0;
+    double modal_lambda_min = 0.0;          // smallest kept normal-mode eigenvalue (diagnostics)
+    pdg::DBuf<pdg::AxDesc> d_ax_desc_m1, d_ax_desc_m2;
+    pdg::DBuf<pdg::AxBlock> d_ax_blk_m1, d_ax_blk_m2;
+    int32_t ax_blocks_m1 = 0, ax_blocks_m2 = 0, ax_kmax_m1 = 1, ax_kmax_m2 = 1;
+    pdg::DBuf<float4> d_pm;                 // modal coordinates p (sum of the domains' r)
+    int32_t n_pm = 0;
+    pdg::DBuf<double> d_Dinv;               // 1 / diag K_ff
+    pdg::DBuf<float4> d_jx1, d_jx2;         // Jacobi iterates
+    std::vector<float> jacobi_omega;        // Chebyshev weights of the sweeps
     bool batched_only = false;             // set by the serving loop: no streaming plans
     pdg::StreamPlan st_solve;
     pdg::DBuf<int32_t> d_bidx2, d_gat2_ptr, d_gat2;
@@ -359,7 +373,7 @@ struct pd_mesh {
     double dt = 0.0;
     bool use_graphs = true;
     double prefactor_seconds = 0.0;
-    int64_t phase_bytes[16] = {0};
+    int64_t phase_bytes[24] = {0};
     int32_t launches_per_iter = 0;
 
     // per-phase timing: the event pairs recorded by one captured graph (or by

@@ -21,7 +21,8 @@
 namespace pdg {
 
 void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* tc, float4* cB, float4* part,
-                             float4* tc2, float4* cT, float4* xg2, float4* xgB, cudaStream_t s);
+                             float4* tc2, float4* cT, float4* xg2, float4* xgB, float4* pm, float4* jx1, float4* jx2,
+                             cudaStream_t s);
 
 namespace {
 
@@ -69,7 +70,12 @@ extern "C" pd_status pd_solve_noalloc(pd_mesh* m, const float* r, float* x) {
     const size_t nxg2 = (size_t)(m->n_xg2 > 0 ? m->n_xg2 : 1), nxgb = (size_t)(m->n_xgB > 0 ? m->n_xgB : 1);
     const size_t off_xg2 = off_ct + align256(ntop * sizeof(float4));
     const size_t off_xgb = off_xg2 + align256(nxg2 * sizeof(float4));
-    const size_t total = off_xgb + align256(nxgb * sizeof(float4));
+    const size_t npm = (size_t)(m->n_pm > 0 ? m->n_pm : 1);
+    const size_t njx = m->jacobi_omega.empty() ? 1 : nf;
+    const size_t off_pm = off_xgb + align256(nxgb * sizeof(float4));
+    const size_t off_jx1 = off_pm + align256(npm * sizeof(float4));
+    const size_t off_jx2 = off_jx1 + align256(njx * sizeof(float4));
+    const size_t total = off_jx2 + align256(njx * sizeof(float4));
     if (total > kNoallocBytes) {
         set_error("pd_solve_noalloc: this mesh needs " + std::to_string(total) +
                   " bytes of scratch, more than the fixed 16 MiB (16777216 bytes); use pd_solve");
@@ -107,14 +113,17 @@ extern "C" pd_status pd_solve_noalloc(pd_mesh* m, const float* r, float* x) {
         float4* cT = reinterpret_cast<float4*>(base + off_ct);
         float4* xg2 = reinterpret_cast<float4*>(base + off_xg2);
         float4* xgb = reinterpret_cast<float4*>(base + off_xgb);
+        float4* pm = reinterpret_cast<float4*>(base + off_pm);
+        float4* jx1 = reinterpret_cast<float4*>(base + off_jx1);
+        float4* jx2 = reinterpret_cast<float4*>(base + off_jx2);
         cudaStream_t s = m->stream;
         // the solution buffer keeps the previous call's contents: clear it
         PDG_CUDA(cudaMemsetAsync(xi, 0, nv * sizeof(float4), s));
         launch_gather_in(m, r, ri, s);
-        launch_dd_solve_scratch(m, ri, xi, tc, cB, part, tc2, cT, xg2, xgb, s);
+        launch_dd_solve_scratch(m, ri, xi, tc, cB, part, tc2, cT, xg2, xgb, pm, jx1, jx2, s);
         for (int k = 0; k < m->refine; ++k) {
             launch_residual(m, ri, xi, rr, s);
-            launch_dd_solve_scratch(m, rr, dx, tc, cB, part, tc2, cT, xg2, xgb, s);
+            launch_dd_solve_scratch(m, rr, dx, tc, cB, part, tc2, cT, xg2, xgb, pm, jx1, jx2, s);
             launch_axpy_free(m, dx, xi, s);
         }
         launch_scatter_out(m, xi, x, 1, s);

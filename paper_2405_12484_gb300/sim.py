@@ -93,10 +93,11 @@ class Mesh:
         _check(lib().pd_set_materials(self._h, C.c_void_p(p_s), C.c_void_p(p_v)), "pd_set_materials")
 
     def prefactor(self, dt, precision="fp32", refine_steps=0, use_graphs=True, correction=False, single_level=False,
-                  streaming=False):
+                  streaming=False, modal=False, modes=20, jacobi_sweeps=0, jacobi_rho=0.0):
         flags = ((_lib.PD_SOLVE_CORRECTION if correction else 0) | (_lib.PD_SOLVE_SINGLE_LEVEL if single_level else 0)
-                 | (_lib.PD_SOLVE_STREAMING if streaming else 0))
-        o = _lib.pd_solver_opts(PRECISIONS[precision], int(refine_steps), 1 if use_graphs else 0, flags)
+                 | (_lib.PD_SOLVE_STREAMING if streaming else 0) | (_lib.PD_SOLVE_MODAL if modal else 0))
+        o = _lib.pd_solver_opts(PRECISIONS[precision], int(refine_steps), 1 if use_graphs else 0, flags, int(modes),
+                                int(jacobi_sweeps), float(jacobi_rho))
         _check(lib().pd_prefactor(self._h, float(dt), C.byref(o)), "pd_prefactor")
 
     # -- state -----------------------------------------------------------------
@@ -154,9 +155,9 @@ class Mesh:
         _check(lib().pd_enable_timing(self._h, int(mask)), "pd_enable_timing")
 
     def phase_times(self) -> dict:
-        out = (C.c_float * 16)()
+        out = (C.c_float * 24)()
         n = C.c_int32()
-        _check(lib().pd_phase_times(self._h, out, 16, C.byref(n)), "pd_phase_times")
+        _check(lib().pd_phase_times(self._h, out, 24, C.byref(n)), "pd_phase_times")
         return {lib().pd_phase_name(k).decode(): float(out[k]) for k in range(n.value)}
 
     def test_offset_phase_counter(self, phase, delta):
@@ -301,7 +302,7 @@ def project(F: torch.Tensor, with_sigma=True):
 
 PHASES = ["inertia", "local", "assemble", "dd_condense", "dd_gather", "dd_coarse", "dd_reduce", "dd_backsub",
           "residual", "velocity", "dd_condense2", "dd_gather2", "dd_backsub2", "dd_interior", "dd_interior2",
-          "dd_solve"]
+          "dd_solve", "dd_modal", "dd_jacobi"]
 
 
 def phase_bit(name: str) -> int:

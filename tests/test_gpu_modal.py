@@ -1,0 +1,113 @@
+"""The paper's own global step (PD_SOLVE_MODAL: fixed-interface normal modes
+plus Chebyshev-weighted Jacobi sweeps, Sec. 7.2 and the solver set-up of
+Sec. 8) through the C ABI against its FP64 oracle (oracle/modal.py), and its
+accuracy against the exact solve on the 390K-tet shell."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_helpers import f32, rel  # noqa: E402
+
+from oracle.modal import ModalDD  # noqa: E402
+from oracle.pd_oracle import PDOracle  # noqa: E402
+from workloads.meshes import parity_slab, sweater_shell  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+
+
+def _record(name, payload):
+    try:
+        os.makedirs(OUT, exist_ok=True)
+        with open(os.path.join(OUT, f"modal_{name}.json"), "w") as f:
+            json.dump(payload, f, indent=1)
+    except OSError:
+        pass
+
+
+@pytest.fixture(scope="module")
+def slab():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_12484_gb300.sim import Mesh
+    w = parity_slab()
+    o = PDOracle(w.rest, w.tets, w.pinned, f32(w.gamma_s), f32(w.gamma_v), w.density, w.dt)
+    dd = ModalDD(o.K_ff, o.free, w.n_v, w.tets, w.tet_domain, w.n_domains, w.pinned, modes=20)
+    m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density)
+    m.set_materials(w.gamma_s, w.gamma_v)
+    yield w, o, dd, m
+    m.close()
+
+
+def _rhs(w, o, seed):
+    rng = np.random.default_rng(seed)
+    x = w.rest + 0.003 * rng.standard_normal(w.rest.shape)
+    R, V = o.local(x)
+    return o.rhs(x, R, V).astype(np.float32)
+
+
+@pytest.mark.parametrize("sweeps", [0, 10, 40])
+def test_modal_solve_matches_oracle(slab, sweeps):
+    w, o, dd, m = slab
+    rho = dd.jacobi_rho()
+    m.prefactor(w.dt, modal=True, modes=20, jacobi_sweeps=sweeps, jacobi_rho=rho)
+    b = _rhs(w, o, 4 + sweeps)
+    xg = m.solve(torch.as_tensor(b)).cpu().numpy()[o.free]
+    bf = b.astype(np.float64)[o.free]
+    xo = dd.solve(bf, sweeps, rho)
+    exact = o.chol.solve(bf)
+    e = rel(xg, xo)
+    _record(f"slab_s{sweeps}", {"gpu_vs_oracle": e, "oracle_vs_exact": rel(xo, exact), "gpu_vs_exact": rel(xg, exact),
+                                "rho": rho})
+    assert e < 1e-5
+
+
+def test_modal_pd_step_matches_oracle(slab):
+    """One PD frame (10 iterations) with the modal solve on both sides."""
+    w, o, dd, m = slab
+    rho = dd.jacobi_rho()
+    sweeps = 20
+    m.prefactor(w.dt, modal=True, modes=20, jacobi_sweeps=sweeps, jacobi_rho=rho)
+
+    def modal_global(b, x_pin):
+        return dd.solve(b[o.free] - o.K_fp @ x_pin, sweeps, rho)
+
+    o.global_solve = modal_global
+    x = torch.empty((w.n_v, 3), device="cuda")
+    m.set_state(torch.as_tensor(w.rest, dtype=torch.float32), torch.zeros((w.n_v, 3)))
+    m.step(torch.as_tensor(w.pin_targets(0), dtype=torch.float32), w.gravity, w.n_iter, x_out=x)
+    m.sync()
+    xo, _ = o.step(w.rest, np.zeros_like(w.rest), w.pin_targets(0), w.gravity, w.n_iter)
+    del o.global_solve
+    e = rel(x.cpu().numpy(), xo)
+    _record("slab_pd_step", {"e_n": e})
+    assert e < 1e-5
+
+
+def test_modal_accuracy_on_the_shell():
+    """Error of the paper's solve against the exact solve as the sweeps grow
+    (390K-tet shell, 20 modes per domain; the estimate of rho is the library's)."""
+    from paper_2405_12484_gb300.sim import Mesh
+    w = sweater_shell()
+    m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density)
+    m.set_materials(w.gamma_s, w.gamma_v)
+    rng = np.random.default_rng(2)
+    x = w.rest + 0.003 * rng.standard_normal(w.rest.shape)
+    b = torch.as_tensor(((1.0 / w.dt ** 2) * x).astype(np.float32))
+    m.prefactor(w.dt)
+    exact = m.solve(b).cpu().numpy().astype(np.float64)
+    free = ~w.pinned.astype(bool)
+    errs = {}
+    for s in (0, 10, 40, 160):
+        m.prefactor(w.dt, modal=True, modes=20, jacobi_sweeps=s)
+        xs = m.solve(b).cpu().numpy().astype(np.float64)
+        errs[s] = rel(xs[free], exact[free])
+    _record("shell_accuracy", {str(k): v for k, v in errs.items()})
+    m.close()
+    assert errs[40] < errs[0] and errs[160] < errs[40]
