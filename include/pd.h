@@ -303,6 +303,115 @@ pd_status pd_hessian_vec(pd_mesh* mesh, const float* x, const float* v, float* H
 pd_status pd_residual(pd_mesh* mesh, const float* x, const float* x_prev, const float* v_prev,
                       const float* gravity, float* g);
 
+/* ---- Material fitting: adjoint Gauss-Newton (Sec. 6.2) and its loop (Sec. 6.3) ----
+ *
+ * One sample pose is fitted at a time.  It starts from a known state
+ * (x_prev, v_prev), so its inertial target y is known and the equilibrium
+ * constraint of Eq. g is g(x, gamma) = (M/dt^2)(x - y) + grad E(x; gamma) = 0
+ * (what pd_equilibrium_step solves).  Its loss is the misfit
+ * eps = sum over free vertices of ||x - xhat||^2, so G = d^2 eps/dx^2 = 2 I.
+ *
+ * Parameter vectors hold 2 n_t floats, gamma = [gamma_s | gamma_v]: gamma_s
+ * of every tet, then gamma_v of every tet, in the caller's tet order (the
+ * 2 n_E material vector of Sec. 6).  Activity masks are 2 n_t uint8 in the
+ * same layout: nonzero = the parameter takes part, zero = pivoted (removed
+ * from the Gauss-Newton solve, Sec. 6.3).
+ */
+
+/*
+ * pd_pose_misfit -- eps and d eps/dx = 2 (x - xhat) (0 on pinned vertices).
+ *   x, target [device] n_v x 3.   dL_dx [device] n_v x 3 out, or NULL.
+ *   loss      [device] one double out.
+ * Asynchronous.  Errors: INVALID_ARG.
+ */
+pd_status pd_pose_misfit(pd_mesh* mesh, const float* x, const float* target, float* dL_dx, double* loss);
+
+/*
+ * pd_gn_product -- P v, P = J^T G J with J = dx/dgamma = -H^-1 B
+ * (Eq. pxpgamma; H = dg/dx, B = dg/dgamma) and G = g_scale I: the matrix of
+ * Eq. gn, applied through the eliminated block system of Eq. agn:
+ * mu = H^-1 B v, nu = H^-1 G mu, P v = B^T nu, the two solves by
+ * preconditioned CG with the workspace's cg_iters (the rows of each solve
+ * are scaled to unit norm first, so that no FP32 vector underflows).
+ *   x      [device] n_v x 3 equilibrium positions of the pose.
+ *   v, Pv  [device] 2 n_t.  active [device] 2 n_t or NULL (all active):
+ *          inactive entries of v are ignored and those of Pv are 0.
+ * Asynchronous.  Errors: INVALID_ARG, NOT_PREFACTORED, CUDA.
+ */
+pd_status pd_gn_product(pd_mesh* mesh, pd_adjoint* adj, const float* x, const float* v, const uint8_t* active,
+                        float g_scale, float* Pv);
+
+/*
+ * pd_gn_direction -- the Gauss-Newton direction of Eq. gn with the
+ * Levenberg-Marquardt shift, (P + kappa I) d = -grad on the active
+ * parameters and d = 0 on the rest, by outer_iters CG iterations over the
+ * parameters (one pd_gn_product each).  kappa = kappa_rel g^T P g / g^T g
+ * with g = grad on the active set (the curvature along the gradient),
+ * evaluated on the device in the first iteration.
+ *   x         [device] n_v x 3 equilibrium positions.
+ *   grad      [device] 2 n_t, d eps/d gamma (pd_adjoint_step gives it).
+ *   active    [device] 2 n_t or NULL.
+ *   d         [device] 2 n_t out.   kappa_out [device] one double, or NULL.
+ * Asynchronous.  Errors: INVALID_ARG (outer_iters outside 1..1000,
+ * kappa_rel < 0 or not finite), NOT_PREFACTORED, CUDA.
+ */
+pd_status pd_gn_direction(pd_mesh* mesh, pd_adjoint* adj, const float* x, const float* grad, const uint8_t* active,
+                          double kappa_rel, float g_scale, int32_t outer_iters, float* d, double* kappa_out);
+
+typedef struct pd_fit_opts {
+    int32_t n_gd;          /* gradient-descent iterations first (Sec. 6.3 uses 10-15) */
+    int32_t n_gn;          /* Gauss-Newton iterations after them (20-30) */
+    float gd_step;         /* initial GD step (0.01): the GD direction -grad is scaled so that
+                              max_j |d_j| / gamma_j = 1, so a step moves no parameter by more
+                              than that fraction of its value */
+    float gn_step;         /* initial GN step (1.0) */
+    double kappa_rel;      /* Levenberg-Marquardt shift, relative as in pd_gn_direction */
+    float floor;           /* value given to a parameter pushed below zero (1e-3) */
+    int32_t max_halvings;  /* step halvings of one line search (12) */
+    int32_t max_pivots;    /* pivots added in one iteration (8) */
+    int32_t n_pd_iter;     /* PD iterations of each equilibrium solve */
+    int32_t n_newton;      /* Newton steps after them (Sec. 8: three to five) */
+    int32_t outer_iters;   /* CG iterations of each Gauss-Newton direction */
+    double dt;             /* time step (> 0) */
+    const pd_solver_opts* solver;  /* pd_prefactor options after each material change (NULL = defaults) */
+} pd_fit_opts;
+
+typedef struct pd_fit_report {
+    int32_t iterations;    /* iterations whose line search lowered the loss */
+    int32_t trials;        /* equilibrium solves of the line searches */
+    int32_t clamped;       /* parameters cached as clamped at the end */
+    int32_t pivots;        /* parameters pivoted at the end */
+    double loss0, loss;    /* pose loss before and after */
+    double seconds;        /* wall time */
+} pd_fit_report;
+
+/*
+ * pd_fit_pose -- the two-stage fitting loop of Sec. 6.3 on one pose: n_gd
+ * gradient-descent iterations, then n_gn Gauss-Newton iterations.  Each
+ * iteration: gradient by the adjoint (pd_adjoint_step); direction; a cached
+ * (clamped) parameter may not decrease (its component is zeroed); a
+ * Gauss-Newton direction that is then not a descent direction pivots the
+ * cached parameter at the floor whose tentative value gamma_j + d_j is most
+ * negative and is recomputed without it (at most max_pivots times); line
+ * search from the initial step, halving until the loss decreases; a
+ * negative component of the accepted step is set to the floor and cached.
+ * Every trial re-assembles and re-factors the PD matrix (pd_set_materials,
+ * pd_prefactor) and solves the pose to equilibrium (pd_set_state(x_prev,
+ * v_prev), pd_equilibrium_step).  The loop stops early when a line search
+ * fails.  On return the mesh holds the fitted materials, prefactored.
+ *   x_prev, v_prev [device] n_v x 3 state the pose starts from.
+ *   pin_targets    [device] n_pinned x 3, or NULL.   gravity [host] 3 floats or NULL.
+ *   target         [device] n_v x 3 pose to match.
+ *   gamma          [device] 2 n_t, in: initial materials, out: fitted.
+ *   losses         [host] n_gd + n_gn + 1 doubles, or NULL: the loss before the
+ *                  loop and after each iteration (repeated after an early stop).
+ *   report         [host] or NULL.
+ * Synchronous.  Errors: INVALID_ARG, BAD_MATERIAL, NOT_SPD, NONFINITE, CUDA.
+ */
+pd_status pd_fit_pose(pd_mesh* mesh, pd_adjoint* adj, const pd_fit_opts* opts, const float* x_prev,
+                      const float* v_prev, const float* pin_targets, const float* gravity, const float* target,
+                      float* gamma, double* losses, pd_fit_report* report);
+
 /* ---- Serving: many garment simulations resident on one GPU ---- */
 
 typedef struct pd_server pd_server;   /* opaque */

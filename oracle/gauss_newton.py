@@ -52,7 +52,8 @@ Readings taken here (each listed in the design notes):
     descent direction, the cached component whose tentative value
     gamma_j + d_j is most negative (among the cached ones still at the
     floor) is pivoted -- fixed at the floor and removed from the solve --
-    and the direction recomputed, one component at a time.
+    and the direction (and its relative shift) recomputed, one component
+    at a time.
 """
 from __future__ import annotations
 
@@ -253,6 +254,7 @@ def fit_pose(rest, tets, pinned, density, dt, x_prev, v_prev, pins, target, gamm
                 break
             pivot[j] = True
             pivots_added += 1
+            kappa = gn.kappa(x, grad, kappa_rel, active=~pivot)
             raw = gn.direction(x, grad, kappa, active=~pivot)
             d = clamp_direction(raw, clamped)
         accepted = False

@@ -49,6 +49,18 @@ class pd_mesh_info(C.Structure):
                 ("two_level", C.c_int32)]
 
 
+class pd_fit_opts(C.Structure):
+    _fields_ = [("n_gd", C.c_int32), ("n_gn", C.c_int32), ("gd_step", C.c_float), ("gn_step", C.c_float),
+                ("kappa_rel", C.c_double), ("floor", C.c_float), ("max_halvings", C.c_int32),
+                ("max_pivots", C.c_int32), ("n_pd_iter", C.c_int32), ("n_newton", C.c_int32),
+                ("outer_iters", C.c_int32), ("dt", C.c_double), ("solver", C.POINTER(pd_solver_opts))]
+
+
+class pd_fit_report(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("trials", C.c_int32), ("clamped", C.c_int32), ("pivots", C.c_int32),
+                ("loss0", C.c_double), ("loss", C.c_double), ("seconds", C.c_double)]
+
+
 PD_REQ_QUEUED, PD_REQ_ACTIVE, PD_REQ_DONE, PD_REQ_FAILED = 0, 1, 2, 3
 
 
@@ -90,6 +102,14 @@ SIGNATURES = [
     ("pd_adjoint_step", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pd_hessian_vec", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pd_residual", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_pose_misfit", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_gn_product", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
+                                  C.c_void_p]),
+    ("pd_gn_direction", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                    C.c_float, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("pd_fit_pose", C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(pd_fit_opts), C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.POINTER(pd_fit_report)]),
     ("pd_server_create", C.c_int32, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("pd_server_destroy", None, [C.c_void_p]),
     ("pd_submit", C.c_int32, [C.c_void_p, C.POINTER(pd_request), C.POINTER(C.c_int64)]),

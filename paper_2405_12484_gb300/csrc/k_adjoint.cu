@@ -328,6 +328,344 @@ __global__ void k_adj_rhs(int n, const float4* __restrict__ dldx, const float* _
                          0.f);
 }
 
+// ---- Gauss-Newton (Sec. 6.2, Eq. gn / Eq. agn): dg/dgamma and its transpose
+// With x fixed, the columns of B = dg/dgamma of element e are
+// V_e (F - R) g_c (gamma_s) and V_e (F - V) g_c (gamma_v) at its corners c.
+// k_gn_setup stores Ts = V_e (F - R), Tv = V_e (F - V) once per direction
+// (9 planes of n_t floats each, plane k = row-major entry k), so that every
+// product B v and B^T nu is a memory-bound pass without an SVD.
+__global__ void __launch_bounds__(128) k_gn_setup(int n_t, const int4* __restrict__ tets,
+                                                  const float4* __restrict__ geo, const float* __restrict__ vol,
+                                                  const float4* __restrict__ x, float* __restrict__ Ts,
+                                                  float* __restrict__ Tv) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_t) return;
+    const Tet T = load_tet(e, n_t, tets, geo);
+    float F[3][3], U[3][3], W[3][3], s[3], d[3], Ps[3][3], Pv[3][3];
+    tet_grad(T, x, F);
+    svd3(F, U, s, W);
+    volume_targets(s, d);
+    const float ve = vol[e];
+    const float cs[3] = {ve * (s[0] - 1.f), ve * (s[1] - 1.f), ve * (s[2] - 1.f)};
+    const float cv[3] = {ve * (s[0] - d[0]), ve * (s[1] - d[1]), ve * (s[2] - d[2])};
+    udwt(U, cs, W, Ps);
+    udwt(U, cv, W, Pv);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            Ts[(int64_t)(3 * i + j) * n_t + e] = Ps[i][j];
+            Tv[(int64_t)(3 * i + j) * n_t + e] = Pv[i][j];
+        }
+}
+
+// corner forces of B v: (v_s Ts + v_v Tv) g_c; v = [v_s | v_v] in the caller's tet order.
+__global__ void __launch_bounds__(128) k_gn_bv(int n_t, const float4* __restrict__ geo, const float* __restrict__ Ts,
+                                               const float* __restrict__ Tv, const int* __restrict__ user_of_tet,
+                                               const float* __restrict__ v, float4* __restrict__ force) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_t) return;
+    Tet T;
+    const float4 r1 = __ldg(&geo[e]);
+    const float4 r2 = __ldg(&geo[n_t + e]);
+    const float4 r3 = __ldg(&geo[2 * (int64_t)n_t + e]);
+    T.g[1][0] = r1.x; T.g[1][1] = r1.y; T.g[1][2] = r1.z;
+    T.g[2][0] = r2.x; T.g[2][1] = r2.y; T.g[2][2] = r2.z;
+    T.g[3][0] = r3.x; T.g[3][1] = r3.y; T.g[3][2] = r3.z;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) T.g[0][j] = -(T.g[1][j] + T.g[2][j] + T.g[3][j]);
+    const int u = user_of_tet[e];
+    const float vs = v[u], vv = v[n_t + u];
+    float P[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            P[i][j] = vs * Ts[(int64_t)(3 * i + j) * n_t + e] + vv * Tv[(int64_t)(3 * i + j) * n_t + e];
+    store_corners(P, T, force + 4 * (int64_t)e);
+}
+
+// out_i = sum_inc force (free vertices)
+__global__ void __launch_bounds__(256) k_assemble_sum(int n_free, const int* __restrict__ inc_ptr,
+                                                         const int* __restrict__ inc, const float4* __restrict__ force,
+                                                         float4* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_free) return;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    for (int k = inc_ptr[i]; k < inc_ptr[i + 1]; ++k) {
+        const float4 f = force[inc[k]];
+        ax += f.x; ay += f.y; az += f.z;
+    }
+    out[i] = make_float4(ax, ay, az, 0.f);
+}
+
+// x *= 1 / sqrt(sc[idx]) (x = 0 when sc[idx] <= 0); free vertices
+__global__ void k_normalize_f4(int n, const double* __restrict__ sc, int idx, float4* __restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double nn = sc[idx];
+    const float f = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+    float4 a = x[i];
+    x[i] = make_float4(a.x * f, a.y * f, a.z * f, 0.f);
+}
+
+// B^T nu: out_s[u] = c <Ts, N>, out_v[u] = c <Tv, N>, N = sum_c nu_c (outer) g_c,
+// c = gs * sqrt(sc[i1] sc[i2]); entries of inactive parameters are 0.
+__global__ void __launch_bounds__(128) k_gn_btv(int n_t, const int4* __restrict__ tets, const float4* __restrict__ geo,
+                                                const float* __restrict__ Ts, const float* __restrict__ Tv,
+                                                const int* __restrict__ user_of_tet, const float4* __restrict__ nu,
+                                                const uint8_t* __restrict__ active, const double* __restrict__ sc,
+                                                int i1, int i2, float gs, float* __restrict__ out) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_t) return;
+    const Tet T = load_tet(e, n_t, tets, geo);
+    float N[3][3];
+    tet_grad(T, nu, N);
+    float as = 0.f, av = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            as += Ts[(int64_t)(3 * i + j) * n_t + e] * N[i][j];
+            av += Tv[(int64_t)(3 * i + j) * n_t + e] * N[i][j];
+        }
+    const double p = sc[i1] * sc[i2];
+    const float c = gs * (p > 0.0 ? (float)sqrt(p) : 0.f);
+    const int u = user_of_tet[e];
+    out[u] = (active && !active[u]) ? 0.f : c * as;
+    out[n_t + u] = (active && !active[n_t + u]) ? 0.f : c * av;
+}
+
+// ---- parameter-space vectors (2 n_t floats) of the outer CG and the fitting loop
+// Scalars (FP64, one array): see GnScalar.
+enum GnScalar : int { G_RR = 0, G_PAP, G_ALPHA, G_BETA, G_KAPPA, G_GG, G_N1, G_N2, G_TMP, G_MAX, G_COUNT };
+
+constexpr int kPBlocks = 256;
+
+// partial sums of a.b (FP64) or, with mode 1, of max_j |a_j| / b_j over b_j > 0
+__global__ void __launch_bounds__(256) k_pdot_partial(int n, const float* __restrict__ a, const float* __restrict__ b,
+                                                      const uint8_t* __restrict__ mask, int mode,
+                                                      double* __restrict__ partial) {
+    __shared__ double sm[256];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (mask && !mask[i]) continue;
+        if (mode == 0) {
+            acc += (double)a[i] * (double)b[i];
+        } else {
+            const double r = b[i] > 0.f ? fabs((double)a[i]) / (double)b[i] : 0.0;
+            acc = r > acc ? r : acc;
+        }
+    }
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            sm[threadIdx.x] = mode == 0 ? sm[threadIdx.x] + sm[threadIdx.x + w]
+                                        : (sm[threadIdx.x + w] > sm[threadIdx.x] ? sm[threadIdx.x + w] : sm[threadIdx.x]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+// op 0: sc[dst] = v; op 1 (alpha): sc[PAP] = v, sc[ALPHA] = sc[RR] / v (0 unless v > 0);
+// op 2 (beta): sc[BETA] = v / sc[RR] (0 unless sc[RR] > 0), sc[RR] = v;
+// op 3 (kappa): sc[KAPPA] = kr * v / sc[RR] (0 unless sc[RR] > 0)
+__global__ void __launch_bounds__(256) k_pdot_final(int nb, const double* __restrict__ partial, int mode, int op,
+                                                    int dst, double kr, double* __restrict__ sc) {
+    __shared__ double sm[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const double v = partial[i];
+        acc = mode == 0 ? acc + v : (v > acc ? v : acc);
+    }
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            sm[threadIdx.x] = mode == 0 ? sm[threadIdx.x] + sm[threadIdx.x + w]
+                                        : (sm[threadIdx.x + w] > sm[threadIdx.x] ? sm[threadIdx.x + w] : sm[threadIdx.x]);
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double v = sm[0];
+    if (op == 0) {
+        sc[dst] = v;
+    } else if (op == 1) {
+        sc[G_PAP] = v;
+        sc[G_ALPHA] = (v > 0.0 && isfinite(v)) ? sc[G_RR] / v : 0.0;
+    } else if (op == 2) {
+        sc[G_BETA] = sc[G_RR] > 0.0 ? v / sc[G_RR] : 0.0;
+        sc[G_RR] = v;
+    } else {
+        sc[G_KAPPA] = sc[G_RR] > 0.0 ? kr * v / sc[G_RR] : 0.0;
+    }
+}
+
+// r = p = -g / |g| on the active parameters (0 elsewhere); d = 0
+__global__ void k_gn_init(int n, const float* __restrict__ g, const uint8_t* __restrict__ active,
+                          const double* __restrict__ sc, float* __restrict__ r, float* __restrict__ p,
+                          float* __restrict__ d) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double gg = sc[G_GG];
+    const float f = gg > 0.0 ? (float)(-1.0 / sqrt(gg)) : 0.f;
+    const float v = (active && !active[i]) ? 0.f : f * g[i];
+    r[i] = v;
+    p[i] = v;
+    d[i] = 0.f;
+}
+
+// Ap = q + kappa p
+__global__ void k_gn_ap(int n, const double* __restrict__ sc, const float* __restrict__ q, const float* __restrict__ p,
+                        float* __restrict__ ap) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ap[i] = q[i] + (float)sc[G_KAPPA] * p[i];
+}
+
+// d += alpha p ; r -= alpha Ap
+__global__ void k_gn_update(int n, const double* __restrict__ sc, const float* __restrict__ p,
+                            const float* __restrict__ ap, float* __restrict__ d, float* __restrict__ r) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float al = (float)sc[G_ALPHA];
+    d[i] += al * p[i];
+    r[i] -= al * ap[i];
+}
+
+// p = r + beta p
+__global__ void k_gn_pdir(int n, const double* __restrict__ sc, const float* __restrict__ r, float* __restrict__ p) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    p[i] = r[i] + (float)sc[G_BETA] * p[i];
+}
+
+// x *= sqrt(sc[idx]) (mode 0) or x *= -1 / sc[idx] (mode 1, 0 when sc[idx] <= 0); masked entries -> 0
+__global__ void k_pscale(int n, const double* __restrict__ sc, int idx, int mode, const uint8_t* __restrict__ active,
+                         const float* __restrict__ src, float* __restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = sc[idx];
+    const float f = mode == 0 ? (v > 0.0 ? (float)sqrt(v) : 0.f) : (v > 0.0 ? (float)(-1.0 / v) : 0.f);
+    x[i] = (active && !active[i]) ? 0.f : f * src[i];
+}
+
+// d = raw, with components of cached (clamped) parameters that would decrease set to 0
+__global__ void k_clamp_dir(int n, const float* __restrict__ raw, const uint8_t* __restrict__ clamped,
+                            float* __restrict__ d) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float r = raw[i];
+    d[i] = (clamped[i] && r < 0.f) ? 0.f : r;
+}
+
+// trial = gamma + alpha d; negative components -> floor, neg = 1 there
+__global__ void k_project(int n, const float* __restrict__ gamma, const float* __restrict__ d, float alpha, float fl,
+                          float* __restrict__ trial, uint8_t* __restrict__ neg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float t = gamma[i] + alpha * d[i];
+    const bool ng = t < 0.f;
+    trial[i] = ng ? fl : t;
+    neg[i] = ng ? 1 : 0;
+}
+
+// gamma = trial; clamped |= neg
+__global__ void k_accept(int n, const float* __restrict__ trial, const uint8_t* __restrict__ neg,
+                         float* __restrict__ gamma, uint8_t* __restrict__ clamped) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    gamma[i] = trial[i];
+    clamped[i] = (clamped[i] || neg[i]) ? 1 : 0;
+}
+
+// pivot candidate: clamped, not pivoted, raw < 0, gamma at the floor; key = gamma + raw.
+// Partial argmin per block (ties -> smaller index); index -1 when none.
+__global__ void __launch_bounds__(256) k_pivot_partial(int n, const float* __restrict__ gamma,
+                                                       const float* __restrict__ raw,
+                                                       const uint8_t* __restrict__ clamped,
+                                                       const uint8_t* __restrict__ active, float fl,
+                                                       double* __restrict__ pval, int* __restrict__ pidx) {
+    __shared__ double sv[256];
+    __shared__ int si[256];
+    double best = 0.0;
+    int bi = -1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool cand = clamped[i] && active[i] && raw[i] < 0.f && gamma[i] <= fl * (1.f + 1e-6f);
+        if (!cand) continue;
+        const double key = (double)gamma[i] + (double)raw[i];
+        if (bi < 0 || key < best || (key == best && i < bi)) {
+            best = key;
+            bi = i;
+        }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            const int j = si[threadIdx.x + w];
+            const int k = si[threadIdx.x];
+            if (j >= 0 && (k < 0 || sv[threadIdx.x + w] < sv[threadIdx.x] ||
+                           (sv[threadIdx.x + w] == sv[threadIdx.x] && j < k))) {
+                sv[threadIdx.x] = sv[threadIdx.x + w];
+                si[threadIdx.x] = j;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pval[blockIdx.x] = sv[0];
+        pidx[blockIdx.x] = si[0];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pivot_final(int nb, const double* __restrict__ pval,
+                                                     const int* __restrict__ pidx, int* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double best = 0.0;
+    int bi = -1;
+    for (int b = 0; b < nb; ++b) {
+        const int j = pidx[b];
+        if (j < 0) continue;
+        if (bi < 0 || pval[b] < best || (pval[b] == best && j < bi)) {
+            best = pval[b];
+            bi = j;
+        }
+    }
+    *out = bi;
+}
+
+// out[i] = sign * a[i], 0 on inactive parameters (parameter vectors)
+__global__ void k_pcopy(int n, float sign, const float* __restrict__ a, const uint8_t* __restrict__ active,
+                        float* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = (active && !active[i]) ? 0.f : sign * a[i];
+}
+
+// pose misfit: diff = x - xhat on free vertices -> dL/dx = 2 diff, partial sums of |diff|^2
+__global__ void __launch_bounds__(256) k_misfit(int n_free, const float4* __restrict__ x,
+                                                const float4* __restrict__ xhat, float4* __restrict__ dldx,
+                                                double* __restrict__ partial) {
+    __shared__ double sm[256];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_free; i += gridDim.x * blockDim.x) {
+        const float4 a = x[i], b = xhat[i];
+        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        if (dldx) dldx[i] = make_float4(2.f * dx, 2.f * dy, 2.f * dz, 0.f);
+        acc += (double)dx * dx + (double)dy * dy + (double)dz * dz;
+    }
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
 inline int nb(int n, int b) { return (n + b - 1) / b; }
 
 }  // namespace
@@ -389,6 +727,115 @@ void launch_adj_rhs(int n, const float4* dldx, const float* mh2, const float4* l
                     cudaStream_t s) {
     if (n <= 0) return;
     k_adj_rhs<<<nb(n, 256), 256, 0, s>>>(n, dldx, mh2, lam1, lam2, rhs);
+    PDG_CHECK_LAUNCH();
+}
+
+// ---- Gauss-Newton launchers
+int gn_scalar_count() { return G_COUNT; }
+int gn_partial_blocks() { return kPBlocks; }
+
+void launch_gn_setup(const pd_mesh* m, const float* vol, const float4* x, float* Ts, float* Tv, cudaStream_t s) {
+    k_gn_setup<<<nb(m->n_t, 128), 128, 0, s>>>(m->n_t, m->d_tets.p, m->d_geo.p, vol, x, Ts, Tv);
+    PDG_CHECK_LAUNCH();
+}
+
+// out (free vertices) = B v
+void launch_gn_bv(const pd_mesh* m, const float* Ts, const float* Tv, const int* user_of_tet, const float* v,
+                  float4* force, float4* out, cudaStream_t s) {
+    k_gn_bv<<<nb(m->n_t, 128), 128, 0, s>>>(m->n_t, m->d_geo.p, Ts, Tv, user_of_tet, v, force);
+    PDG_CHECK_LAUNCH();
+    if (m->n_free <= 0) return;
+    k_assemble_sum<<<nb(m->n_free, 256), 256, 0, s>>>(m->n_free, m->d_inc_ptr.p, m->d_inc.p, force, out);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_normalize_f4(int n, const double* sc, int idx, float4* x, cudaStream_t s) {
+    if (n <= 0) return;
+    k_normalize_f4<<<nb(n, 256), 256, 0, s>>>(n, sc, idx, x);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_gn_btv(const pd_mesh* m, const float* Ts, const float* Tv, const int* user_of_tet, const float4* nu,
+                   const uint8_t* active, const double* sc, int i1, int i2, float gs, float* out, cudaStream_t s) {
+    k_gn_btv<<<nb(m->n_t, 128), 128, 0, s>>>(m->n_t, m->d_tets.p, m->d_geo.p, Ts, Tv, user_of_tet, nu, active, sc,
+                                             i1, i2, gs, out);
+    PDG_CHECK_LAUNCH();
+}
+
+// parameter-space reduction into sc: op as k_pdot_final; mode 0 = dot, 1 = max |a|/b
+void launch_pdot(int n, const float* a, const float* b, const uint8_t* mask, int mode, int op, int dst, double kr,
+                 double* partial, double* sc, cudaStream_t s) {
+    const int blocks = std::max(1, std::min(kPBlocks, nb(n, 256)));
+    k_pdot_partial<<<blocks, 256, 0, s>>>(n, a, b, mask, mode, partial);
+    PDG_CHECK_LAUNCH();
+    k_pdot_final<<<1, 256, 0, s>>>(blocks, partial, mode, op, dst, kr, sc);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_gn_init(int n, const float* g, const uint8_t* active, const double* sc, float* r, float* p, float* d,
+                    cudaStream_t s) {
+    k_gn_init<<<nb(n, 256), 256, 0, s>>>(n, g, active, sc, r, p, d);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_gn_ap(int n, const double* sc, const float* q, const float* p, float* ap, cudaStream_t s) {
+    k_gn_ap<<<nb(n, 256), 256, 0, s>>>(n, sc, q, p, ap);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_gn_update(int n, const double* sc, const float* p, const float* ap, float* d, float* r, cudaStream_t s) {
+    k_gn_update<<<nb(n, 256), 256, 0, s>>>(n, sc, p, ap, d, r);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_gn_pdir(int n, const double* sc, const float* r, float* p, cudaStream_t s) {
+    k_gn_pdir<<<nb(n, 256), 256, 0, s>>>(n, sc, r, p);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_pscale(int n, const double* sc, int idx, int mode, const uint8_t* active, const float* src, float* x,
+                   cudaStream_t s) {
+    k_pscale<<<nb(n, 256), 256, 0, s>>>(n, sc, idx, mode, active, src, x);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_clamp_dir(int n, const float* raw, const uint8_t* clamped, float* d, cudaStream_t s) {
+    k_clamp_dir<<<nb(n, 256), 256, 0, s>>>(n, raw, clamped, d);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_project(int n, const float* gamma, const float* d, float alpha, float fl, float* trial, uint8_t* neg,
+                    cudaStream_t s) {
+    k_project<<<nb(n, 256), 256, 0, s>>>(n, gamma, d, alpha, fl, trial, neg);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_accept(int n, const float* trial, const uint8_t* neg, float* gamma, uint8_t* clamped, cudaStream_t s) {
+    k_accept<<<nb(n, 256), 256, 0, s>>>(n, trial, neg, gamma, clamped);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_pick_pivot(int n, const float* gamma, const float* raw, const uint8_t* clamped, const uint8_t* active,
+                       float fl, double* pval, int* pidx, int* out, cudaStream_t s) {
+    const int blocks = std::max(1, std::min(kPBlocks, nb(n, 256)));
+    k_pivot_partial<<<blocks, 256, 0, s>>>(n, gamma, raw, clamped, active, fl, pval, pidx);
+    PDG_CHECK_LAUNCH();
+    k_pivot_final<<<1, 32, 0, s>>>(blocks, pval, pidx, out);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_pcopy(int n, float sign, const float* a, const uint8_t* active, float* out, cudaStream_t s) {
+    k_pcopy<<<nb(n, 256), 256, 0, s>>>(n, sign, a, active, out);
+    PDG_CHECK_LAUNCH();
+}
+
+// loss partial sums into partial[0..blocks), then sc[dst] = loss
+void launch_misfit(int n_free, const float4* x, const float4* xhat, float4* dldx, double* partial, double* sc, int dst,
+                   cudaStream_t s) {
+    const int blocks = std::max(1, std::min(kPBlocks, nb(n_free, 256)));
+    k_misfit<<<blocks, 256, 0, s>>>(n_free, x, xhat, dldx, partial);
+    PDG_CHECK_LAUNCH();
+    k_pdot_final<<<1, 256, 0, s>>>(blocks, partial, 0, 0, dst, 0.0, sc);
     PDG_CHECK_LAUNCH();
 }
 

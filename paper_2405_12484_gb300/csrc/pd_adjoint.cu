@@ -32,22 +32,15 @@ void launch_adj_rhs(int n, const float4* dldx, const float* mh2, const float4* l
 
 using namespace pdg;
 
-struct pd_adjoint {
-    pd_mesh* mesh = nullptr;
-    int32_t cg_iters = 30;
-    DBuf<float4> xeq, vprev, g, rhs, lam, lam1, lam2, r, z, p, Ap, dx;
-    DBuf<double> partial, sc;
-    DBuf<float> vol;
-    DBuf<int32_t> user_of_tet;
-};
-
 static pd_status afail(pd_status c, const char* msg) {
     set_error(msg);
     return c;
 }
 
+namespace pdg {
+
 // x = H(x_lin)^-1 b by PCG (fixed iteration count), preconditioner = PD subspace solve.
-static void pcg(pd_mesh* m, pd_adjoint* a, const float4* x_lin, const float4* b, float4* x, cudaStream_t s) {
+void adjoint_pcg(pd_mesh* m, pd_adjoint* a, const float4* x_lin, const float4* b, float4* x, cudaStream_t s) {
     const int n = m->n_free;
     PDG_CUDA(cudaMemsetAsync(x, 0, sizeof(float4) * m->n_v, s));
     if (n <= 0) return;
@@ -64,6 +57,8 @@ static void pcg(pd_mesh* m, pd_adjoint* a, const float4* x_lin, const float4* b,
         launch_cg_direction(n, a->sc.p, a->z.p, a->p.p, 0, s);
     }
 }
+
+}  // namespace pdg
 
 extern "C" {
 
@@ -140,7 +135,7 @@ pd_status pd_equilibrium_step(pd_mesh* m, pd_adjoint* a, const float* pin_target
         for (int k = 0; k < n_newton; ++k) {
             launch_grad_local(m, m->d_x.p, m->d_force.p, s);
             launch_assemble_residual(m, m->d_force.p, m->d_x.p, m->d_xprev.p, a->vprev.p, h, g, -1.f, a->rhs.p, s);
-            pcg(m, a, m->d_x.p, a->rhs.p, a->dx.p, s);
+            adjoint_pcg(m, a, m->d_x.p, a->rhs.p, a->dx.p, s);
             launch_axpy_free(m, a->dx.p, m->d_x.p, s);
         }
         launch_velocity(m, 1.0f / h, s);
@@ -161,7 +156,7 @@ pd_status pd_adjoint_step(pd_mesh* m, pd_adjoint* a, const float* x_n, const flo
         launch_gather_in(m, x_n, a->xeq.p, s);
         launch_gather_in(m, dL_dx, a->g.p, s);
         launch_adj_rhs(m->n_free, a->g.p, m->d_mh2.p, a->lam1.p, a->lam2.p, a->rhs.p, s);
-        pcg(m, a, a->xeq.p, a->rhs.p, a->lam.p, s);
+        adjoint_pcg(m, a, a->xeq.p, a->rhs.p, a->lam.p, s);
         launch_grad_gamma(m, a->vol.p, a->user_of_tet.p, a->xeq.p, a->lam.p, dL_dgamma_s, dL_dgamma_v, s);
         const size_t bytes = sizeof(float4) * m->n_v;
         PDG_CUDA(cudaMemcpyAsync(a->lam2.p, a->lam1.p, bytes, cudaMemcpyDeviceToDevice, s));

@@ -405,7 +405,27 @@ struct pd_mesh {
     ~pd_mesh();
 };
 
+// Workspace of the adjoint path (equilibrium steps, adjoint steps, Gauss-Newton).
+struct pd_adjoint {
+    pd_mesh* mesh = nullptr;
+    int32_t cg_iters = 30;
+    pdg::DBuf<float4> xeq, vprev, g, rhs, lam, lam1, lam2, r, z, p, Ap, dx;
+    pdg::DBuf<double> partial, sc;
+    pdg::DBuf<float> vol;
+    pdg::DBuf<int32_t> user_of_tet;
+    // Gauss-Newton (allocated on first use): per-tet V_e (F - R), V_e (F - V)
+    // (9 planes of n_t each), parameter-space CG vectors (2 n_t), vertex
+    // vectors of the two inner solves, and the outer scalars.
+    pdg::DBuf<float> gn_Ts, gn_Tv, gn_r, gn_p, gn_q, gn_ap, gn_tmp;
+    pdg::DBuf<float4> gn_b, gn_mu, gn_nu;
+    pdg::DBuf<double> gn_sc, gn_partial;
+    pdg::DBuf<int32_t> gn_ipartial;
+    bool gn_ready = false;
+};
+
 namespace pdg {
+
+void adjoint_pcg(pd_mesh* m, pd_adjoint* a, const float4* x_lin, const float4* b, float4* x, cudaStream_t s);
 
 // ---------------------------------------------------------------- kernels (launchers)
 void launch_project(const float* F, int n, float* R, float* V, float* sig, cudaStream_t s);

@@ -69,6 +69,7 @@ class Mesh:
         _check(st, "pd_create_mesh")
         self._h = h
         self._keep = {}
+        self.dt = None
 
     # -- lifecycle -------------------------------------------------------------
     def close(self):
@@ -92,13 +93,18 @@ class Mesh:
         p_v = gv.ctypes.data if isinstance(gv, np.ndarray) else gv.data_ptr()
         _check(lib().pd_set_materials(self._h, C.c_void_p(p_s), C.c_void_p(p_v)), "pd_set_materials")
 
-    def prefactor(self, dt, precision="fp32", refine_steps=0, use_graphs=True, correction=False, single_level=False,
-                  streaming=False, modal=False, modes=20, jacobi_sweeps=0, jacobi_rho=0.0):
+    @staticmethod
+    def solver_opts(precision="fp32", refine_steps=0, use_graphs=True, correction=False, single_level=False,
+                    streaming=False, modal=False, modes=20, jacobi_sweeps=0, jacobi_rho=0.0):
         flags = ((_lib.PD_SOLVE_CORRECTION if correction else 0) | (_lib.PD_SOLVE_SINGLE_LEVEL if single_level else 0)
                  | (_lib.PD_SOLVE_STREAMING if streaming else 0) | (_lib.PD_SOLVE_MODAL if modal else 0))
-        o = _lib.pd_solver_opts(PRECISIONS[precision], int(refine_steps), 1 if use_graphs else 0, flags, int(modes),
-                                int(jacobi_sweeps), float(jacobi_rho))
+        return _lib.pd_solver_opts(PRECISIONS[precision], int(refine_steps), 1 if use_graphs else 0, flags,
+                                   int(modes), int(jacobi_sweeps), float(jacobi_rho))
+
+    def prefactor(self, dt, **solver):
+        o = self.solver_opts(**solver)
         _check(lib().pd_prefactor(self._h, float(dt), C.byref(o)), "pd_prefactor")
+        self.dt = float(dt)
 
     # -- state -----------------------------------------------------------------
     def set_state(self, x=None, v=None):
@@ -220,6 +226,65 @@ class Adjoint:
         xt, xpt, vpt = (_dev_f32(t, (m.n_v, 3)) for t in (x, x_prev, v_prev))   # held until the call returns
         _check(lib().pd_residual(m._h, _ptr(xt), _ptr(xpt), _ptr(vpt), g, _ptr(out)), "pd_residual")
         return out
+
+
+    # ---- material fitting (Sec. 6.2, 6.3) ----------------------------------------------
+    def pose_misfit(self, x, target, with_grad=True):
+        """(loss tensor (1,) float64 on the device, dL/dx or None)."""
+        m = self.mesh
+        xt, tt = _dev_f32(x, (m.n_v, 3)), _dev_f32(target, (m.n_v, 3))
+        loss = torch.empty(1, device="cuda", dtype=torch.float64)
+        g = torch.empty((m.n_v, 3), device="cuda", dtype=torch.float32) if with_grad else None
+        _check(lib().pd_pose_misfit(m._h, _ptr(xt), _ptr(tt), _ptr(g), _ptr(loss)), "pd_pose_misfit")
+        return loss, g
+
+    def gn_product(self, x, v, active=None, g_scale=2.0):
+        m = self.mesh
+        xt = _dev_f32(x, (m.n_v, 3))
+        vt = _dev_f32(v, (2 * m.n_t,))
+        at = None if active is None else torch.as_tensor(active).to(device="cuda", dtype=torch.uint8).contiguous()
+        out = torch.empty(2 * m.n_t, device="cuda", dtype=torch.float32)
+        _check(lib().pd_gn_product(m._h, self._h, _ptr(xt), _ptr(vt), _ptr(at), float(g_scale), _ptr(out)),
+               "pd_gn_product")
+        torch.cuda.synchronize()          # inputs converted here are held until the work is done
+        return out
+
+    def gn_direction(self, x, grad, active=None, kappa_rel=1e-2, outer_iters=50, g_scale=2.0):
+        """(d, kappa) of (P + kappa I) d = -grad."""
+        m = self.mesh
+        xt = _dev_f32(x, (m.n_v, 3))
+        gt = _dev_f32(grad, (2 * m.n_t,))
+        at = None if active is None else torch.as_tensor(active).to(device="cuda", dtype=torch.uint8).contiguous()
+        d = torch.empty(2 * m.n_t, device="cuda", dtype=torch.float32)
+        kap = torch.empty(1, device="cuda", dtype=torch.float64)
+        _check(lib().pd_gn_direction(m._h, self._h, _ptr(xt), _ptr(gt), _ptr(at), float(kappa_rel), float(g_scale),
+                                     int(outer_iters), _ptr(d), _ptr(kap)), "pd_gn_direction")
+        torch.cuda.synchronize()
+        return d, kap
+
+    def fit_pose(self, x_prev, v_prev, target, gamma, pin_targets=None, gravity=(0.0, 0.0, -9.81), n_gd=2, n_gn=3,
+                 gd_step=0.01, gn_step=1.0, kappa_rel=1e-2, floor=1e-3, max_halvings=12, max_pivots=8,
+                 n_pd_iter=30, n_newton=4, outer_iters=50, dt=None, **solver):
+        """Two-stage fit of one pose; gamma = [gamma_s | gamma_v] (2 n_t).  Returns
+        (gamma tensor, losses array, report dict).  `solver` holds the prefactor
+        options used after each material change."""
+        m = self.mesh
+        if dt is None and m.dt is None:
+            raise ValueError("fit_pose needs dt (or a prefactored mesh)")
+        xp, vp, tg = (_dev_f32(t, (m.n_v, 3)) for t in (x_prev, v_prev, target))
+        pt = _dev_f32(pin_targets, (m.n_pinned, 3)) if pin_targets is not None else None
+        gm = _dev_f32(gamma, (2 * m.n_t,)).clone()
+        so = m.solver_opts(**solver)
+        o = _lib.pd_fit_opts(int(n_gd), int(n_gn), float(gd_step), float(gn_step), float(kappa_rel), float(floor),
+                             int(max_halvings), int(max_pivots), int(n_pd_iter), int(n_newton), int(outer_iters),
+                             float(dt if dt is not None else m.dt), C.pointer(so))
+        losses = np.zeros(int(n_gd) + int(n_gn) + 1, np.float64)
+        rep = _lib.pd_fit_report()
+        g = (C.c_float * 3)(*[float(a) for a in gravity])
+        _check(lib().pd_fit_pose(m._h, self._h, C.byref(o), _ptr(xp), _ptr(vp), _ptr(pt), g, _ptr(tg), _ptr(gm),
+                                 losses.ctypes.data_as(C.c_void_p), C.byref(rep)), "pd_fit_pose")
+        info = {k: getattr(rep, k) for k, _ in _lib.pd_fit_report._fields_}
+        return gm, losses, info
 
 
 class Server:
