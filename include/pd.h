@@ -412,6 +412,48 @@ pd_status pd_fit_pose(pd_mesh* mesh, pd_adjoint* adj, const pd_fit_opts* opts, c
                       const float* v_prev, const float* pin_targets, const float* gravity, const float* target,
                       float* gamma, double* losses, pd_fit_report* report);
 
+/*
+ * pd_harmonic_basis -- harmonic material basis (Sec. 6, Harmonic
+ * Initialization): the r lowest eigenpairs of the graph Laplacian L = D - A
+ * of the tets' face adjacency (two tets are adjacent when they share a face),
+ * by Chebyshev-filtered subspace iteration in FP64 on the device (block of
+ * r + 8 vectors; the polynomial degree adapts to the ratio of the block's
+ * largest Ritz value to the bound 2 max-degree of lambda_max; until every
+ * residual |L h - lambda h| <= 1e-9 times that bound).
+ *   r          1 .. min(56, n_t).
+ *   H          [device] n_t x r float, column-major in the caller's tet order
+ *              (column k = h_{k+1}, n_t contiguous floats); orthonormal; the
+ *              entry of largest magnitude of each column is positive, so h_1
+ *              is the constant 1/sqrt(n_t) on a connected mesh.
+ *   lambda     [host] r doubles, ascending, or NULL.
+ *   iterations [host] filter iterations used, or NULL.
+ * Synchronous.  Errors: INVALID_ARG, NOT_SPD (the block lost rank), TIMEOUT
+ * (not converged in 500 iterations), CUDA.
+ */
+pd_status pd_harmonic_basis(pd_mesh* mesh, int32_t r, float* H, double* lambda, int32_t* iterations);
+
+/*
+ * pd_fit_pose_reduced -- Gauss-Newton iterations of one pose in the reduced
+ * coordinates q of gamma = diag(H, H) q (Eq. q2gamma): q starts as
+ * diag(H, H)^T gamma; each iteration forms P_q = D^T P D (2 r products
+ * pd_gn_product) and grad_q = D^T grad, solves (P_q + kappa I) d_q = -grad_q
+ * (kappa relative as in pd_gn_direction; the 2r x 2r system is solved on
+ * the host), and line-searches q + alpha d_q from gn_step with halving; a
+ * trial whose gamma has a component below `floor` is rejected (gamma stays
+ * in the span of H).  Uses n_gn, gn_step, kappa_rel, floor, max_halvings,
+ * n_pd_iter, n_newton, dt, solver of opts (n_gd, max_pivots, outer_iters,
+ * gd_step are not used).
+ *   H       [device] n_t x r, as written by pd_harmonic_basis (any
+ *           orthonormal columns work).
+ *   gamma   [device] 2 n_t, in: the guess, out: D q.
+ *   other arguments as pd_fit_pose.
+ * Synchronous.  Errors: INVALID_ARG, BAD_MATERIAL (the projected guess has a
+ * component below the floor), NOT_SPD, NONFINITE, CUDA.
+ */
+pd_status pd_fit_pose_reduced(pd_mesh* mesh, pd_adjoint* adj, const pd_fit_opts* opts, const float* H, int32_t r,
+                              const float* x_prev, const float* v_prev, const float* pin_targets, const float* gravity,
+                              const float* target, float* gamma, double* losses, pd_fit_report* report);
+
 /* ---- Serving: many garment simulations resident on one GPU ---- */
 
 typedef struct pd_server pd_server;   /* opaque */

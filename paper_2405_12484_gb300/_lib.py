@@ -110,6 +110,10 @@ SIGNATURES = [
     ("pd_fit_pose", C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(pd_fit_opts), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.POINTER(pd_fit_report)]),
+    ("pd_harmonic_basis", C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    ("pd_fit_pose_reduced", C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(pd_fit_opts), C.c_void_p, C.c_int32,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.POINTER(pd_fit_report)]),
     ("pd_server_create", C.c_int32, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("pd_server_destroy", None, [C.c_void_p]),
     ("pd_submit", C.c_int32, [C.c_void_p, C.POINTER(pd_request), C.POINTER(C.c_int64)]),

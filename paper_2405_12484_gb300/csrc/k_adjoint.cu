@@ -666,6 +666,52 @@ __global__ void __launch_bounds__(256) k_misfit(int n_free, const float4* __rest
     if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
 }
 
+// ---- reduced coordinates gamma = diag(H, H) q (Eq. q2gamma); H column-major n_t x r
+// out[b] = sum_t H[k][t] w[half n_t + t], b = half r + k; one block per output, fixed order
+__global__ void __launch_bounds__(256) k_basis_t(int n_t, int r, const float* __restrict__ H,
+                                                 const float* __restrict__ w, double* __restrict__ out) {
+    __shared__ double sm[256];
+    const int b = blockIdx.x, half = b / r, k = b % r;
+    const float* h = H + (int64_t)k * n_t;
+    const float* v = w + (int64_t)half * n_t;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < n_t; t += blockDim.x) acc += (double)h[t] * (double)v[t];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[b] = sm[0];
+}
+
+// out[half n_t + t] = sum_k H[k][t] q[half r + k]
+__global__ void k_basis_apply(int n_t, int r, const float* __restrict__ H, const double* __restrict__ q,
+                              float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * n_t) return;
+    const int half = i / n_t, t = i % n_t;
+    double acc = 0.0;
+    for (int k = 0; k < r; ++k) acc += (double)H[(int64_t)k * n_t + t] * q[half * r + k];
+    out[i] = (float)acc;
+}
+
+// out = column j of diag(H, H)
+__global__ void k_basis_col(int n_t, int r, const float* __restrict__ H, int j, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * n_t) return;
+    const int half = i / n_t, t = i % n_t;
+    out[i] = (half == j / r) ? H[(int64_t)(j % r) * n_t + t] : 0.f;
+}
+
+// *count += number of a[i] < fl
+__global__ void k_count_below(int n, const float* __restrict__ a, float fl, int* __restrict__ count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool below = i < n && a[i] < fl;
+    const unsigned m = __ballot_sync(0xffffffffu, below);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(count, __popc(m));
+}
+
 inline int nb(int n, int b) { return (n + b - 1) / b; }
 
 }  // namespace
@@ -826,6 +872,27 @@ void launch_pick_pivot(int n, const float* gamma, const float* raw, const uint8_
 
 void launch_pcopy(int n, float sign, const float* a, const uint8_t* active, float* out, cudaStream_t s) {
     k_pcopy<<<nb(n, 256), 256, 0, s>>>(n, sign, a, active, out);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_basis_t(int n_t, int r, const float* H, const float* w, double* out, cudaStream_t s) {
+    k_basis_t<<<2 * r, 256, 0, s>>>(n_t, r, H, w, out);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_basis_apply(int n_t, int r, const float* H, const double* q, float* out, cudaStream_t s) {
+    k_basis_apply<<<nb(2 * n_t, 256), 256, 0, s>>>(n_t, r, H, q, out);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_basis_col(int n_t, int r, const float* H, int j, float* out, cudaStream_t s) {
+    k_basis_col<<<nb(2 * n_t, 256), 256, 0, s>>>(n_t, r, H, j, out);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_count_below(int n, const float* a, float fl, int* count, cudaStream_t s) {
+    PDG_CUDA(cudaMemsetAsync(count, 0, sizeof(int), s));
+    k_count_below<<<nb(n, 256), 256, 0, s>>>(n, a, fl, count);
     PDG_CHECK_LAUNCH();
 }
 

@@ -40,10 +40,11 @@ void launch_copy_block_idx(const double* S, int ldS, int r0, int nr, const int* 
 
 static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
-// ---- small dense helpers of the modal prefactorisation (q x q, q <= 64, FP64)
+// ---- small dense helpers (q x q, q <= 64, FP64) of the modal prefactorisation and
+// the harmonic basis
 
 // G = R^T R (R upper triangular) and the inverse of R; false if G is not SPD.
-static bool chol_upper_inverse(const double* G, int q, int ld, std::vector<double>& Rinv) {
+bool chol_upper_inverse(const double* G, int q, int ld, std::vector<double>& Rinv) {
     std::vector<double> R((size_t)q * q, 0.0);
     for (int j = 0; j < q; ++j) {
         double s = G[(size_t)j * ld + j];
@@ -71,7 +72,7 @@ static bool chol_upper_inverse(const double* G, int q, int ld, std::vector<doubl
 // Cyclic Jacobi eigenvalue algorithm for a symmetric q x q matrix (Golub &
 // Van Loan, Sec. 8.5): A is overwritten; on return w holds the eigenvalues and
 // the columns of V the eigenvectors (unsorted).
-static void jacobi_eig(std::vector<double>& A, int q, std::vector<double>& w, std::vector<double>& V) {
+void jacobi_eig(std::vector<double>& A, int q, std::vector<double>& w, std::vector<double>& V) {
     V.assign((size_t)q * q, 0.0);
     for (int i = 0; i < q; ++i) V[(size_t)i * q + i] = 1.0;
     for (int sweep = 0; sweep < 100; ++sweep) {

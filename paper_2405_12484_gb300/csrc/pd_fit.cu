@@ -44,6 +44,10 @@ void launch_pick_pivot(int n, const float* gamma, const float* raw, const uint8_
 void launch_pcopy(int n, float sign, const float* a, const uint8_t* active, float* out, cudaStream_t s);
 void launch_misfit(int n_free, const float4* x, const float4* xhat, float4* dldx, double* partial, double* sc, int dst,
                    cudaStream_t s);
+void launch_basis_t(int n_t, int r, const float* H, const float* w, double* out, cudaStream_t s);
+void launch_basis_apply(int n_t, int r, const float* H, const double* q, float* out, cudaStream_t s);
+void launch_basis_col(int n_t, int r, const float* H, int j, float* out, cudaStream_t s);
+void launch_count_below(int n, const float* a, float fl, int* count, cudaStream_t s);
 
 // indices of the FP64 scalars of the outer CG (k_adjoint.cu, GnScalar)
 enum : int { S_RR = 0, S_PAP, S_ALPHA, S_BETA, S_KAPPA, S_GG, S_N1, S_N2, S_TMP, S_MAX };
@@ -322,6 +326,155 @@ pd_status pd_fit_pose(pd_mesh* m, pd_adjoint* a, const pd_fit_opts* o, const flo
         rep.loss = eps;
     } catch (const Fail& f) {
         cudaStreamSynchronize(s);
+        return f.code;
+    }
+    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (report) *report = rep;
+    return PD_OK;
+}
+
+pd_status pd_fit_pose_reduced(pd_mesh* m, pd_adjoint* a, const pd_fit_opts* o, const float* H, int32_t r,
+                              const float* x_prev, const float* v_prev, const float* pin_targets, const float* gravity,
+                              const float* target, float* gamma, double* losses, pd_fit_report* report) {
+    if (!check_mesh(m, a) || !o || !H || !x_prev || !v_prev || !target || !gamma)
+        return ffail(PD_ERR_INVALID_ARG, "null argument or mismatched workspace");
+    if (r < 1 || r > 56 || r > m->n_t) return ffail(PD_ERR_INVALID_ARG, "r out of range [1, min(56, n_t)]");
+    if (o->n_gn < 0 || o->n_gn > 10000 || !(o->gn_step > 0.f) || !(o->kappa_rel >= 0.0) ||
+        !std::isfinite(o->kappa_rel) || !(o->floor > 0.f) || o->max_halvings < 0 || o->max_halvings > 60 ||
+        !(o->dt > 0.0))
+        return ffail(PD_ERR_INVALID_ARG, "fit options out of range");
+    const auto t0 = std::chrono::steady_clock::now();
+    const int n_t = m->n_t, np = 2 * n_t, nq = 2 * r, nv3 = 3 * m->n_v;
+    cudaStream_t s = m->stream;
+    pd_fit_report rep{};
+    try {
+        gn_prepare(m, a);
+        DBuf<float> gam, trial, grad, x_acc, x_try, dl_acc, dl_try;
+        DBuf<double> loss_dev, dq, Pq;
+        DBuf<int32_t> cnt;
+        gam.alloc(np);
+        trial.alloc(np);
+        grad.alloc(np);
+        for (auto* b : {&x_acc, &x_try, &dl_acc, &dl_try}) b->alloc(nv3);
+        loss_dev.alloc(1);
+        dq.alloc(nq);
+        Pq.alloc((size_t)nq * nq);
+        cnt.alloc(1);
+        auto check = [](pd_status st) {
+            if (st != PD_OK) throw Fail{st};
+        };
+        const float* mesh_gamma = nullptr;
+        auto use = [&](const float* g) {
+            check(pd_set_materials(m, g, g + n_t));
+            check(pd_prefactor(m, o->dt, o->solver));
+            mesh_gamma = g;
+        };
+        auto evaluate = [&](const float* g, float* xo, float* dlo) -> double {
+            use(g);
+            check(pd_set_state(m, x_prev, v_prev));
+            check(pd_equilibrium_step(m, a, pin_targets, gravity, o->n_pd_iter, o->n_newton, xo));
+            check(pd_pose_misfit(m, xo, target, dlo, loss_dev.p));
+            double l = 0.0;
+            PDG_CUDA(cudaMemcpyAsync(&l, loss_dev.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+            check(pd_sync(m));
+            ++rep.trials;
+            return l;
+        };
+        // gamma = D q, and the number of its components below the floor
+        auto apply = [&](const std::vector<double>& q, float* out) {
+            PDG_CUDA(cudaMemcpyAsync(dq.p, q.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, s));
+            launch_basis_apply(n_t, r, H, dq.p, out, s);
+            launch_count_below(np, out, o->floor, cnt.p, s);
+            int below = 0;
+            PDG_CUDA(cudaMemcpyAsync(&below, cnt.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            PDG_CUDA(cudaStreamSynchronize(s));
+            return below;
+        };
+        auto project_t = [&](const float* w, std::vector<double>& out) {   // out = D^T w
+            launch_basis_t(n_t, r, H, w, dq.p, s);
+            out.resize(nq);
+            PDG_CUDA(cudaMemcpyAsync(out.data(), dq.p, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
+            PDG_CUDA(cudaStreamSynchronize(s));
+        };
+
+        std::vector<double> q, gq, qt(nq), hP((size_t)nq * nq), Rinv, dlt(nq);
+        project_t(gamma, q);
+        if (apply(q, gam.p) > 0) throw Fail{PD_ERR_BAD_MATERIAL};
+        double eps = evaluate(gam.p, x_acc.p, dl_acc.p);
+        rep.loss0 = eps;
+        if (losses) losses[0] = eps;
+        int done = 0;
+        for (int it = 0; it < o->n_gn; ++it) {
+            if (mesh_gamma != gam.p) use(gam.p);
+            PDG_CUDA(cudaMemsetAsync(grad.p, 0, sizeof(float) * np, s));
+            check(pd_adjoint_reset(a));
+            check(pd_adjoint_step(m, a, x_acc.p, dl_acc.p, grad.p, grad.p + n_t));
+            project_t(grad.p, gq);
+            // P_q = D^T P D, one column per basis vector (2 r products)
+            launch_gather_in(m, x_acc.p, a->xeq.p, s);
+            gn_setup(m, a, s);
+            for (int j = 0; j < nq; ++j) {
+                launch_basis_col(n_t, r, H, j, a->gn_p.p, s);
+                gn_apply(m, a, a->gn_p.p, nullptr, 2.f, a->gn_q.p, s);
+                launch_basis_t(n_t, r, H, a->gn_q.p, Pq.p + (size_t)j * nq, s);
+            }
+            PDG_CUDA(cudaMemcpyAsync(hP.data(), Pq.p, sizeof(double) * nq * nq, cudaMemcpyDeviceToHost, s));
+            PDG_CUDA(cudaStreamSynchronize(s));
+            // (P_q + kappa I) d = -g_q on the host (2 r <= 112 unknowns), kappa relative as in the full fit
+            double gg = 0.0, gPg = 0.0;
+            for (int i = 0; i < nq; ++i) {
+                gg += gq[i] * gq[i];
+                for (int j = 0; j < nq; ++j) gPg += gq[i] * 0.5 * (hP[(size_t)i * nq + j] + hP[(size_t)j * nq + i]) * gq[j];
+            }
+            const double kappa = gg > 0.0 ? o->kappa_rel * gPg / gg : 0.0;
+            std::vector<double> A((size_t)nq * nq);
+            for (int i = 0; i < nq; ++i)
+                for (int j = 0; j < nq; ++j)
+                    A[(size_t)i * nq + j] = 0.5 * (hP[(size_t)i * nq + j] + hP[(size_t)j * nq + i]) + (i == j ? kappa : 0.0);
+            if (!chol_upper_inverse(A.data(), nq, nq, Rinv)) throw Fail{PD_ERR_NOT_SPD};
+            // d = -R^-1 R^-T g
+            std::vector<double> y(nq, 0.0);
+            for (int i = 0; i < nq; ++i)
+                for (int k = 0; k < nq; ++k) y[i] += Rinv[(size_t)k * nq + i] * gq[k];
+            for (int i = 0; i < nq; ++i) {
+                double acc = 0.0;
+                for (int k = 0; k < nq; ++k) acc += Rinv[(size_t)i * nq + k] * y[k];
+                dlt[i] = -acc;
+            }
+            double alpha = o->gn_step;
+            bool accepted = false;
+            for (int h = 0; h <= o->max_halvings; ++h) {
+                for (int i = 0; i < nq; ++i) qt[i] = q[i] + alpha * dlt[i];
+                if (apply(qt, trial.p) == 0) {
+                    const double et = evaluate(trial.p, x_try.p, dl_try.p);
+                    if (et < eps) {
+                        PDG_CUDA(cudaMemcpyAsync(gam.p, trial.p, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
+                        PDG_CUDA(cudaMemcpyAsync(x_acc.p, x_try.p, sizeof(float) * nv3, cudaMemcpyDeviceToDevice, s));
+                        PDG_CUDA(cudaMemcpyAsync(dl_acc.p, dl_try.p, sizeof(float) * nv3, cudaMemcpyDeviceToDevice, s));
+                        mesh_gamma = gam.p;
+                        q = qt;
+                        eps = et;
+                        accepted = true;
+                        break;
+                    }
+                }
+                alpha *= 0.5;
+            }
+            if (losses) losses[it + 1] = eps;
+            if (!accepted) {
+                for (int k = it + 1; losses && k < o->n_gn; ++k) losses[k + 1] = eps;
+                break;
+            }
+            ++done;
+        }
+        if (mesh_gamma != gam.p) use(gam.p);
+        PDG_CUDA(cudaMemcpyAsync(gamma, gam.p, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
+        PDG_CUDA(cudaStreamSynchronize(s));
+        rep.iterations = done;
+        rep.loss = eps;
+    } catch (const Fail& f) {
+        cudaStreamSynchronize(s);
+        if (f.code == PD_ERR_BAD_MATERIAL) set_error("the projection of gamma onto the basis has a component below the floor");
         return f.code;
     }
     rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

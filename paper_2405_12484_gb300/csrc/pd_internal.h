@@ -427,6 +427,12 @@ namespace pdg {
 
 void adjoint_pcg(pd_mesh* m, pd_adjoint* a, const float4* x_lin, const float4* b, float4* x, cudaStream_t s);
 
+// Small dense FP64 helpers (host, q up to ~100; row-major q x q with leading dimension ld):
+// Cholesky G = R^T R and R^-1 (false if G is not SPD); cyclic Jacobi eigen-decomposition
+// (A overwritten, eigenvalues in w unsorted, eigenvectors in the columns of V).
+bool chol_upper_inverse(const double* G, int q, int ld, std::vector<double>& Rinv);
+void jacobi_eig(std::vector<double>& A, int q, std::vector<double>& w, std::vector<double>& V);
+
 // ---------------------------------------------------------------- kernels (launchers)
 void launch_project(const float* F, int n, float* R, float* V, float* sig, cudaStream_t s);
 void launch_local(const pd_mesh* m, const float4* x, float4* force, cudaStream_t s);

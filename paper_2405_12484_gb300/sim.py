@@ -287,6 +287,54 @@ class Adjoint:
         return gm, losses, info
 
 
+    def harmonic_basis(self, r):
+        """(H (r, n_t) float32 on the device: row k = h_{k+1}, lambdas (r,), iterations)."""
+        m = self.mesh
+        H = torch.empty((int(r), m.n_t), device="cuda", dtype=torch.float32)
+        lam = np.zeros(int(r), np.float64)
+        it = C.c_int32(0)
+        _check(lib().pd_harmonic_basis(m._h, int(r), _ptr(H), lam.ctypes.data_as(C.c_void_p), C.byref(it)),
+               "pd_harmonic_basis")
+        return H, lam, int(it.value)
+
+    def fit_pose_reduced(self, H, x_prev, v_prev, target, gamma, pin_targets=None, gravity=(0.0, 0.0, -9.81),
+                         n_gn=3, gn_step=1.0, kappa_rel=1e-2, floor=1e-3, max_halvings=12, n_pd_iter=30, n_newton=4,
+                         dt=None, **solver):
+        """Gauss-Newton in gamma = diag(H, H) q; H (r, n_t) as from harmonic_basis.
+        Returns (gamma tensor, losses array, report dict)."""
+        m = self.mesh
+        if dt is None and m.dt is None:
+            raise ValueError("fit_pose_reduced needs dt (or a prefactored mesh)")
+        Ht = _dev_f32(H).contiguous()
+        r = int(Ht.shape[0])
+        xp, vp, tg = (_dev_f32(t, (m.n_v, 3)) for t in (x_prev, v_prev, target))
+        pt = _dev_f32(pin_targets, (m.n_pinned, 3)) if pin_targets is not None else None
+        gm = _dev_f32(gamma, (2 * m.n_t,)).clone()
+        so = m.solver_opts(**solver)
+        o = _lib.pd_fit_opts(0, int(n_gn), 0.01, float(gn_step), float(kappa_rel), float(floor), int(max_halvings), 0,
+                             int(n_pd_iter), int(n_newton), 1, float(dt if dt is not None else m.dt), C.pointer(so))
+        losses = np.zeros(int(n_gn) + 1, np.float64)
+        rep = _lib.pd_fit_report()
+        g = (C.c_float * 3)(*[float(a) for a in gravity])
+        _check(lib().pd_fit_pose_reduced(m._h, self._h, C.byref(o), _ptr(Ht), r, _ptr(xp), _ptr(vp), _ptr(pt), g,
+                                         _ptr(tg), _ptr(gm), losses.ctypes.data_as(C.c_void_p), C.byref(rep)),
+               "pd_fit_pose_reduced")
+        info = {k: getattr(rep, k) for k, _ in _lib.pd_fit_report._fields_}
+        return gm, losses, info
+
+    def harmonic_initialization(self, x_prev, v_prev, target, gamma, ranks=(1, 10, 30), n_gn=3, **kw):
+        """Rank by rank (Sec. 6, Harmonic Initialization): the basis of the largest
+        rank once, then Gauss-Newton in its leading r columns for each r.
+        Returns (gamma, [(r, losses), ...])."""
+        H, _, _ = self.harmonic_basis(max(ranks))
+        out = []
+        g = gamma
+        for r in ranks:
+            g, losses, _ = self.fit_pose_reduced(H[:r], x_prev, v_prev, target, g, n_gn=n_gn, **kw)
+            out.append((r, losses))
+        return g, out
+
+
 class Server:
     """Serving loop: resident garment simulations advanced in shared batched launches."""
 

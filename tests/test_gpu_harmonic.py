@@ -1,0 +1,134 @@
+"""Harmonic initialization on the device (Sec. 6, Eq. q2gamma) through the C
+ABI: the element-Laplacian basis against the FP64 oracle (oracle/harmonic.py,
+pinned by a closed-form path spectrum), the reduced Gauss-Newton fit against
+the oracle's with the same basis, and the rank-by-rank progression."""
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_helpers import f32, rel  # noqa: E402
+
+from oracle.adjoint import AdjointOracle  # noqa: E402
+from oracle.gauss_newton import GaussNewtonOracle  # noqa: E402
+from oracle.harmonic import fit_reduced, harmonic_basis  # noqa: E402
+from oracle.pd_oracle import PDOracle  # noqa: E402
+from workloads.meshes import parity_slab, slab_workload, sweater_shell  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+
+
+def _record(name, payload):
+    try:
+        os.makedirs(OUT, exist_ok=True)
+        with open(os.path.join(OUT, f"harmonic_{name}.json"), "w") as f:
+            json.dump(payload, f, indent=1)
+    except OSError:
+        pass
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _small():
+    return slab_workload(4, 4, 2, 0.01, 5, (2, 2), seed=3, n_iter=10, name="harm-small")
+
+
+def _pair(w, cg_iters=150):
+    from paper_2405_12484_gb300.sim import Adjoint, Mesh
+    m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density)
+    m.set_materials(w.gamma_s, w.gamma_v)
+    m.prefactor(w.dt)
+    return m, Adjoint(m, cg_iters)
+
+
+@pytest.mark.parametrize("mesh,r", [("small", 12), ("parity", 30)])
+def test_basis_matches_oracle(mesh, r):
+    w = _small() if mesh == "small" else parity_slab()
+    m, a = _pair(w, 10)
+    t0 = time.perf_counter()
+    H, lam, its = a.harmonic_basis(r)
+    secs = time.perf_counter() - t0
+    H = H.cpu().numpy().astype(np.float64).T                     # n_t x r
+    lam_o, H_o = harmonic_basis(w.tets, r + 1)
+    el = float(np.max(np.abs(lam - lam_o[:r])))
+    # compare the spans up to the last gap (clusters of equal eigenvalues have no unique basis)
+    gaps = [k for k in range(1, r + 1) if lam_o[k] - lam_o[k - 1] > 1e-6]
+    k = max(gaps)
+    span = float(np.linalg.norm(H_o[:, :k] - H[:, :k] @ (H[:, :k].T @ H_o[:, :k])))
+    orth = float(np.abs(H.T @ H - np.eye(r)).max())
+    _record(f"basis_{mesh}", {"lambda_abs_err": el, "span_err": span, "span_rank": k, "orth_err": orth,
+                              "iterations": its, "seconds": secs, "lambda": lam.tolist()})
+    assert np.allclose(H[:, 0], 1.0 / np.sqrt(w.n_t), rtol=1e-5)
+    assert el < 1e-8 * 8
+    assert orth < 1e-5
+    assert span < 1e-4
+
+
+def _pose(w):
+    x0, v0, pins = w.rest, np.zeros_like(w.rest), w.pin_targets(0)
+    rng = np.random.default_rng(1)
+    gs_star = w.gamma_s * np.exp(0.3 * rng.standard_normal(w.n_t))
+    o = PDOracle(w.rest, w.tets, w.pinned, f32(gs_star), f32(10 * gs_star), w.density, w.dt)
+    return x0, v0, pins, GaussNewtonOracle(AdjointOracle(o)).equilibrium(x0, v0, pins)
+
+
+def test_reduced_fit_matches_oracle():
+    w = _small()
+    m, a = _pair(w)
+    x0, v0, pins, target = _pose(w)
+    _, H_o = harmonic_basis(w.tets, 10)
+    H = H_o.astype(np.float32)                                     # the same basis on both sides
+    gamma0 = np.concatenate([w.gamma_s, w.gamma_v]).astype(np.float32)
+    g_o, losses_o = fit_reduced(w.rest, w.tets, w.pinned, w.density, w.dt, x0, v0, pins, target,
+                                gamma0.astype(np.float64), H.astype(np.float64), n_gn=2, kappa_rel=1e-2)
+    g, losses, info = a.fit_pose_reduced(torch.as_tensor(H.T.copy()), x0, v0, target.astype(np.float32), gamma0,
+                                         pin_targets=pins, n_gn=2, kappa_rel=1e-2, dt=w.dt)
+    g = g.cpu().numpy()
+    lo = np.asarray(losses_o)
+    el = float(np.max(np.abs(losses - lo) / lo))
+    eg = rel(g, g_o)
+    _record("reduced_fit", {"losses": losses.tolist(), "oracle_losses": lo.tolist(), "loss_rel_err": el,
+                            "gamma_rel_err": eg, "report": info})
+    assert all(losses[k + 1] <= losses[k] for k in range(len(losses) - 1))
+    assert losses[-1] < losses[0]
+    assert el < 2e-2 and eg < 2e-2
+
+
+def test_rank_by_rank_progression():
+    w = _small()
+    m, a = _pair(w)
+    x0, v0, pins, target = _pose(w)
+    gamma0 = np.concatenate([w.gamma_s, w.gamma_v]).astype(np.float32)
+    g, stages = a.harmonic_initialization(x0, v0, target.astype(np.float32), gamma0, ranks=(1, 4, 10), n_gn=2,
+                                          pin_targets=pins, dt=w.dt)
+    _record("progression", {"stages": [(r, l.tolist()) for r, l in stages]})
+    for _, l in stages:
+        assert all(l[k + 1] <= l[k] for k in range(len(l) - 1))
+    # the bases are nested: each rank starts where the previous one ended
+    for (_, prev), (_, nxt) in zip(stages, stages[1:]):
+        assert abs(nxt[0] - prev[-1]) <= 1e-3 * prev[-1]
+    assert stages[-1][1][-1] < stages[0][1][0]
+
+
+def test_basis_time_on_the_shell():
+    """390K-tet shell, r = 30: wall time and filter iterations (recorded)."""
+    w = sweater_shell()
+    m, a = _pair(w, 10)
+    t0 = time.perf_counter()
+    H, lam, its = a.harmonic_basis(30)
+    secs = time.perf_counter() - t0
+    Hn = H.double()
+    orth = float((Hn @ Hn.T - torch.eye(30, device="cuda", dtype=torch.float64)).abs().max())
+    _record("basis_shell", {"seconds": secs, "iterations": its, "lambda": lam.tolist(), "orth_err": orth})
+    assert orth < 1e-5 and lam[0] < 1e-9 and np.all(np.diff(lam) >= -1e-12)
