@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "pd_internal.h"
+#include "tma.cuh"
 
 namespace pdg {
 
@@ -46,6 +47,75 @@ __device__ __forceinline__ void load_vec(const __nv_bfloat16* p, float (&v)[8]) 
         float2 f = __bfloat1622float2(h[k]);
         v[2 * k] = f.x;
         v[2 * k + 1] = f.y;
+    }
+}
+
+__device__ __forceinline__ void load_vec_shared(const float* p, float (&v)[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+
+__device__ __forceinline__ void load_vec_shared(const __nv_bfloat16* p, float (&v)[8]) {
+    const uint4 a = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&a);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float2 f = __bfloat1622float2(h[k]);
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
+    }
+}
+
+// Staging of a product's x vector in shared memory with many loads in flight:
+// each thread issues kStageU independent loads (indices first when indexed,
+// then values) before it stores any of them, so staging costs one or two
+// memory latencies per kStageU entries instead of one per entry.
+constexpr int kStageU = 8;
+
+// xs[k] = x[idx ? idx[k] : k] for k < n
+__device__ __forceinline__ void stage_f4(float4* __restrict__ xs, int n, const float4* __restrict__ x,
+                                         const int* __restrict__ idx, int tid, int nthreads) {
+    for (int base = tid; base < n; base += nthreads * kStageU) {
+        int id[kStageU];
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) {
+            const int k = base + u * nthreads;
+            id[u] = k < n ? (idx ? idx[k] : k) : -1;
+        }
+        float4 v[kStageU];
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) v[u] = id[u] >= 0 ? x[id[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) {
+            const int k = base + u * nthreads;
+            if (k < n) xs[k] = v[u];
+        }
+    }
+}
+
+// three float planes x0/x1/x2[k] = x[idx ? idx[k] : k] for k < n_valid, 0 for n_valid <= k < n
+__device__ __forceinline__ void stage_planes(float* __restrict__ x0, float* __restrict__ x1, float* __restrict__ x2,
+                                             int n_valid, int n, const float4* __restrict__ x,
+                                             const int* __restrict__ idx, int tid, int nthreads) {
+    for (int base = tid; base < n; base += nthreads * kStageU) {
+        int id[kStageU];
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) {
+            const int k = base + u * nthreads;
+            id[u] = k < n_valid ? (idx ? idx[k] : k) : -1;
+        }
+        float4 v[kStageU];
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) v[u] = id[u] >= 0 ? x[id[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) {
+            const int k = base + u * nthreads;
+            if (k < n) {
+                x0[k] = v[u].x;
+                x1[k] = v[u].y;
+                x2[k] = v[u].z;
+            }
+        }
     }
 }
 
@@ -168,8 +238,7 @@ __global__ void __launch_bounds__(32 * kAxWarps) k_axpy_form(const AxDesc* __res
     const AxDesc D = descs[bk.desc];
     const AxBases B = BATCHED ? multi[D.slot] : single;
     const T* A = reinterpret_cast<const T*>(B.pool) + D.a_off;
-    const float4* x = B.x + D.x_off;
-    for (int k = threadIdx.x; k < D.K; k += blockDim.x) xs[k] = (D.bidx_off >= 0) ? x[B.bidx[D.bidx_off + k]] : x[k];
+    stage_f4(xs, D.K, B.x + D.x_off, D.bidx_off >= 0 ? B.bidx + D.bidx_off : nullptr, threadIdx.x, blockDim.x);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k0 = D.K * warp / kAxWarps, k1 = D.K * (warp + 1) / kAxWarps;
@@ -178,11 +247,14 @@ __global__ void __launch_bounds__(32 * kAxWarps) k_axpy_form(const AxDesc* __res
     for (int j = 0; j < kAxM; ++j)
 #pragma unroll
         for (int i = 0; i < VN; ++i) acc[j][i][0] = acc[j][i][1] = acc[j][i][2] = 0.f;
+    // row stride: the matrix's ld, or the width of this block's tile (chunk width in ld)
+    const int ldr = D.tiled ? ax_tile_width(D.n_out, bk.o0, D.ld, VN) : D.ld;
     bool valid[kAxM];
 #pragma unroll
-    for (int j = 0; j < kAxM; ++j) valid[j] = bk.o0 + j * SW + lane * VN < D.n_out;
+    for (int j = 0; j < kAxM; ++j)
+        valid[j] = bk.o0 + j * SW + lane * VN < D.n_out && (!D.tiled || j * SW + lane * VN < ldr);
     if (valid[0]) {
-        const T* a = A + bk.o0 + lane * VN;
+        const T* a = A + (D.tiled ? (int64_t)bk.o0 * D.K : (int64_t)bk.o0) + lane * VN;
 #pragma unroll kAxUnroll
         for (int k = k0; k < k1; ++k) {
             const float4 xk = xs[k];
@@ -190,7 +262,7 @@ __global__ void __launch_bounds__(32 * kAxWarps) k_axpy_form(const AxDesc* __res
             for (int j = 0; j < kAxM; ++j) {
                 if (!valid[j]) continue;
                 float v[VN];
-                load_vec(a + (int64_t)k * D.ld + j * SW, v);
+                load_vec(a + (int64_t)k * ldr + j * SW, v);
 #pragma unroll
                 for (int i = 0; i < VN; ++i) {
                     acc[j][i][0] = fmaf(v[i], xk.x, acc[j][i][0]);
@@ -219,7 +291,8 @@ __global__ void __launch_bounds__(32 * kAxWarps) k_axpy_form(const AxDesc* __res
 #pragma unroll
             for (int i = 0; i < VN; ++i) {
                 const int oi = bk.o0 + j * SW + lane * VN + i;
-                if (oi >= D.n_out) break;
+                // outputs past this block's tile belong to the next block
+                if (oi >= D.n_out || (D.tiled && j * SW + lane * VN + i >= ldr)) break;
                 float r0 = acc[j][i][0], r1 = acc[j][i][1], r2 = acc[j][i][2];
 #pragma unroll
                 for (int w = 0; w < kAxWarps - 1; ++w) {
@@ -233,9 +306,167 @@ __global__ void __launch_bounds__(32 * kAxWarps) k_axpy_form(const AxDesc* __res
     }
 }
 
+// The same product streamed through shared memory with bulk asynchronous
+// copies (tiled layout only): one producer lane copies the block's tile in
+// stages of kAxtRows rows (one cp.async.bulk per stage, a ring of kAxtStages
+// stages of kAxtRows x w elements, completion counted in bytes on an
+// mbarrier), so the copies in flight do not depend on what the compute
+// warps do.  kAxtWarps consumer warps take the rows of a stage in turn (row
+// r to warp r mod kAxtWarps), each lane owning VN consecutive outputs with
+// x_k a shared-memory broadcast; after the last stage the warps' partial
+// sums go through the (then idle) ring and are added in warp order
+// (deterministic).  Every wait is bounded (1 s or the CTA's abort flag): a
+// wait that runs out sets ERR_TIMEOUT in `err`, the producer stops issuing
+// and drains the copies it has in flight.
+#ifndef PDG_AXT_STAGES
+#define PDG_AXT_STAGES 3
+#endif
+#ifndef PDG_AXT_ROWS
+#define PDG_AXT_ROWS 32
+#endif
+#ifndef PDG_AXT_WARPS
+#define PDG_AXT_WARPS 4
+#endif
+constexpr int kAxtStages = PDG_AXT_STAGES;
+constexpr int kAxtRows = PDG_AXT_ROWS;
+constexpr int kAxtWarps = PDG_AXT_WARPS;
+static_assert(kAxM == 1, "the tiled layout has one output chunk per block");
+
+// ring bytes of a launch whose widest tile has wmax outputs (a multiple of VN)
+template <class T>
+inline size_t axt_ring_bytes(int wmax) {
+    const size_t ring = (size_t)kAxtStages * kAxtRows * wmax * sizeof(T);
+    const size_t red = (size_t)(kAxtWarps - 1) * wmax * 3 * sizeof(float);
+    return (std::max(ring, red) + 15) / 16 * 16;
+}
+
+template <class T>
+__global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_tma(const AxDesc* __restrict__ descs,
+                                                                   const AxBlock* __restrict__ blocks, AxBases B,
+                                                                   int ring_bytes, int* __restrict__ err) {
+    using namespace tma;
+    constexpr int VN = VecN<T>::N;
+    constexpr int S = kAxtStages, R = kAxtRows;
+    extern __shared__ __align__(128) unsigned char axt_smem[];
+    T* ring = reinterpret_cast<T*>(axt_smem);
+    float* red = reinterpret_cast<float*>(axt_smem);     // reused after the last stage
+    float4* xs = reinterpret_cast<float4*>(axt_smem + ring_bytes);
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ int abort_flag;
+    const AxBlock bk = blocks[blockIdx.x];
+    const AxDesc D = descs[bk.desc];
+    const int w = ax_tile_width(D.n_out, bk.o0, D.ld, VN);
+    const T* tile = reinterpret_cast<const T*>(B.pool) + D.a_off + (int64_t)bk.o0 * D.K;
+    const int n_st = (D.K + R - 1) / R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    pdl_trigger();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kAxtWarps);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();   // barriers initialised: the producer starts at once, the consumers stage x meanwhile
+    if (warp == kAxtWarps) {
+        // producer
+        if (lane == 0) {
+            int issued = 0;
+            for (int i = 0; i < n_st; ++i) {
+                const int slot = i % S;
+                if (i >= S && !mbar_wait(&empty[slot], ((i / S) - 1) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    atomicOr(err, ERR_TIMEOUT);
+                    break;
+                }
+                const int rows = min(R, D.K - i * R);
+                const uint32_t bytes = (uint32_t)(rows * w * (int)sizeof(T));
+                mbar_arrive_expect_tx(&full[slot], bytes);
+                bulk_g2s(ring + (size_t)slot * R * w, tile + (int64_t)i * R * w, bytes, &full[slot]);
+                issued = i + 1;
+            }
+            // every copy issued has landed before the CTA may exit
+            for (int i = max(0, issued - S); i < issued; ++i)
+                if (!mbar_wait(&full[i % S], (i / S) & 1)) atomicOr(err, ERR_TIMEOUT);
+        }
+        return;
+    }
+    // consumers (the producer streams the constant tile without waiting for the predecessor)
+    pdl_wait();
+    stage_f4(xs, D.K, B.x + D.x_off, D.bidx_off >= 0 ? B.bidx + D.bidx_off : nullptr, threadIdx.x, 32 * kAxtWarps);
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kAxtWarps) : "memory");
+    float acc[VN][3];
+#pragma unroll
+    for (int i = 0; i < VN; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+    const int my = lane * VN;
+    const bool act = my < w;
+    for (int i = 0; i < n_st; ++i) {
+        const int slot = i % S;
+        if (!mbar_wait(&full[slot], (i / S) & 1, &abort_flag)) {
+            if (lane == 0) {
+                abort_flag = 1;
+                atomicOr(err, ERR_TIMEOUT);
+            }
+            break;
+        }
+        const int rows = min(R, D.K - i * R);
+        const T* st = ring + (size_t)slot * R * w;
+        if (act) {
+#pragma unroll 2
+            for (int r = warp; r < rows; r += kAxtWarps) {
+                const float4 xk = xs[i * R + r];
+                float v[VN];
+                load_vec_shared(st + r * w + my, v);
+#pragma unroll
+                for (int j = 0; j < VN; ++j) {
+                    acc[j][0] = fmaf(v[j], xk.x, acc[j][0]);
+                    acc[j][1] = fmaf(v[j], xk.y, acc[j][1]);
+                    acc[j][2] = fmaf(v[j], xk.z, acc[j][2]);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kAxtWarps) : "memory");   // every consumer is past the ring
+    if (warp > 0 && act) {
+#pragma unroll
+        for (int j = 0; j < VN; ++j) {
+            float* r = red + ((size_t)(warp - 1) * w + my + j) * 3;
+            r[0] = acc[j][0];
+            r[1] = acc[j][1];
+            r[2] = acc[j][2];
+        }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kAxtWarps) : "memory");
+    if (warp == 0 && act) {
+        float4* out = B.out + D.out_off;
+        const float4* add = (D.add_off >= 0) ? B.add + D.add_off : nullptr;
+#pragma unroll
+        for (int j = 0; j < VN; ++j) {
+            const int oi = bk.o0 + my + j;
+            if (oi >= D.n_out) break;
+            float r0 = acc[j][0], r1 = acc[j][1], r2 = acc[j][2];
+            for (int q = 0; q < kAxtWarps - 1; ++q) {
+                const float* r = red + ((size_t)q * w + my + j) * 3;
+                r0 += r[0];
+                r1 += r[1];
+                r2 += r[2];
+            }
+            const float4 b = add ? add[oi] : make_float4(0.f, 0.f, 0.f, 0.f);
+            out[oi] = make_float4(b.x + r0, b.y + r1, b.z + r2, 0.f);
+        }
+    }
+}
+
 // gather: c_B[j] = b_B[j] + sum over the domains touching j of their c_d entry (fixed order)
 __global__ void k_gather(int n_B, const int* __restrict__ ptr, const int* __restrict__ rows,
                          const float4* __restrict__ bB, const float4* __restrict__ tc, float4* __restrict__ cB) {
+    pdl_trigger();
+    pdl_wait();
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_B) return;
     float4 acc = bB[j];
@@ -292,12 +523,9 @@ __global__ void __launch_bounds__(512, kCoarseBps) k_coarse_bal(const T* __restr
     float* x0 = xsm;
     float* x1 = xsm + cols;
     float* x2 = xsm + 2 * cols;
-    for (int k = threadIdx.x; k < cols; k += blockDim.x) {
-        float4 v = (k < n_B) ? cB[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        x0[k] = v.x;
-        x1[k] = v.y;
-        x2[k] = v.z;
-    }
+    pdl_trigger();
+    pdl_wait();
+    stage_planes(x0, x1, x2, n_B, cols, cB, nullptr, threadIdx.x, blockDim.x);
     __syncthreads();
     constexpr int VN = VecN<T>::N;
     constexpr int RU = CoarseRows<T>::R;   // rows per unit: x values reused RU times
@@ -470,13 +698,8 @@ __global__ void __launch_bounds__(32 * kRowWarps, kRowBps) k_rowdot(const RowDes
         const int64_t hi = b1 < D.u0 + nu ? b1 : D.u0 + nu;
         if (hi <= lo) continue;
         __syncthreads();
-        for (int k = threadIdx.x; k < D.ld; k += blockDim.x) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (k < D.cols) v = (D.xidx_off >= 0) ? B.x[B.bidx[D.xidx_off + k]] : B.x[D.x_off + k];
-            x0[k] = v.x;
-            x1[k] = v.y;
-            x2[k] = v.z;
-        }
+        if (D.xidx_off >= 0) stage_planes(x0, x1, x2, D.cols, D.ld, B.x, B.bidx + D.xidx_off, threadIdx.x, blockDim.x);
+        else stage_planes(x0, x1, x2, D.cols, D.ld, B.x + D.x_off, nullptr, threadIdx.x, blockDim.x);
         __syncthreads();
         const int64_t n = hi - lo;
         const int64_t w0 = lo + n * warp / kRowWarps, w1 = lo + n * (warp + 1) / kRowWarps;
@@ -534,6 +757,8 @@ __global__ void __launch_bounds__(32 * kRowWarps, kRowBps) k_rowdot(const RowDes
 
 // reduce: x_B[j] = sum over chunks (fixed order) of part[ch][j]
 __global__ void k_reduce(int n_B, int n_chunks, const float4* __restrict__ part, float4* __restrict__ xB) {
+    pdl_trigger();
+    pdl_wait();
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_B) return;
     float4 acc = part[j];
@@ -593,6 +818,174 @@ __global__ void k_cheb_jacobi(int n_free, const int* __restrict__ ptr, const int
     out[i] = make_float4(fmaf(omega, hx - xp.x, xp.x), fmaf(omega, hy - xp.y, xp.y), fmaf(omega, hz - xp.z, xp.z), 0.f);
 }
 
+// Row-form products streamed through shared memory with bulk asynchronous
+// copies.  A block's rows of one descriptor are contiguous in the pool (row
+// stride ld), so one cp.async.bulk moves a whole stage of RS rows
+// (RS = kRowtStageBytes / row bytes); a ring of kRowtStages stages keeps them
+// in flight.  The rows go to the consumer warps in pairs (pair p to warp
+// p mod kRowtWarps), so every x value read from shared memory serves two
+// rows: lanes stride the rows with 16-byte shared-memory loads against x
+// staged as three float planes, a fixed-order shuffle tree combines them
+// (deterministic).  Every wait is bounded, as in k_axpy_tma.
+#ifndef PDG_ROWT_STAGE_BYTES
+#define PDG_ROWT_STAGE_BYTES 24576
+#endif
+#ifndef PDG_ROWT_STAGES
+#define PDG_ROWT_STAGES 3
+#endif
+#ifndef PDG_ROWT_WARPS
+#define PDG_ROWT_WARPS 4
+#endif
+constexpr int kRowtStageBytes = PDG_ROWT_STAGE_BYTES;
+constexpr int kRowtStages = PDG_ROWT_STAGES;
+constexpr int kRowtWarps = PDG_ROWT_WARPS;
+
+template <class T>
+__global__ void __launch_bounds__(32 * (kRowtWarps + 1)) k_rowdot_tma(const RowDesc* __restrict__ descs, int n_desc,
+                                                                      const int64_t* __restrict__ blk_u, AxBases B,
+                                                                      int xcap, int* __restrict__ err) {
+    using namespace tma;
+    constexpr int VN = VecN<T>::N;
+    constexpr int RU = RowRows<T>::R;
+    constexpr int S = kRowtStages;
+    constexpr int SE = kRowtStageBytes / (int)sizeof(T);   // elements of one stage
+    extern __shared__ __align__(128) unsigned char rt_smem[];
+    T* ring = reinterpret_cast<T*>(rt_smem);
+    float* x0 = reinterpret_cast<float*>(rt_smem + (size_t)S * kRowtStageBytes);
+    float* x1 = x0 + xcap;
+    float* x2 = x1 + xcap;
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ int abort_flag;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t b0 = blk_u[blockIdx.x], b1 = blk_u[blockIdx.x + 1];
+    const T* pool = reinterpret_cast<const T*>(B.pool);
+    pdl_trigger();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kRowtWarps);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == kRowtWarps) {
+        if (lane == 0) {
+            int g = 0, issued = 0;
+            bool ok = true;
+            for (int di = 0; di < n_desc && ok; ++di) {
+                const RowDesc D = descs[di];
+                const int64_t nu = (D.rows + RU - 1) / RU;
+                const int64_t lo = b0 > D.u0 ? b0 : D.u0;
+                const int64_t hi = b1 < D.u0 + nu ? b1 : D.u0 + nu;
+                if (hi <= lo) continue;
+                const int r_lo = (int)(lo - D.u0) * RU;
+                const int r_hi = min((int)(hi - D.u0) * RU, D.rows);
+                const int RS = max(1, SE / D.ld);
+                for (int r = r_lo; r < r_hi; r += RS, ++g) {
+                    const int slot = g % S;
+                    if (g >= S && !mbar_wait(&empty[slot], ((g / S) - 1) & 1, &abort_flag)) {
+                        abort_flag = 1;
+                        atomicOr(err, ERR_TIMEOUT);
+                        ok = false;
+                        break;
+                    }
+                    const int rows = min(RS, r_hi - r);
+                    const uint32_t bytes = (uint32_t)rows * (uint32_t)D.ld * (uint32_t)sizeof(T);
+                    mbar_arrive_expect_tx(&full[slot], bytes);
+                    bulk_g2s(ring + (size_t)slot * SE, pool + D.a_off + (int64_t)r * D.ld, bytes, &full[slot]);
+                    issued = g + 1;
+                }
+            }
+            for (int i = max(0, issued - S); i < issued; ++i)
+                if (!mbar_wait(&full[i % S], (i / S) & 1)) atomicOr(err, ERR_TIMEOUT);
+        }
+        return;
+    }
+    // after an abort every consumer warp still runs every segment's barriers
+    // (no warp may leave a barrier short); the stages are skipped
+    pdl_wait();   // x comes from the predecessor; the producer streams the constant rows meanwhile
+    int g = 0, pc = 0;
+    for (int di = 0; di < n_desc; ++di) {
+        const RowDesc D = descs[di];
+        const int64_t nu = (D.rows + RU - 1) / RU;
+        const int64_t lo = b0 > D.u0 ? b0 : D.u0;
+        const int64_t hi = b1 < D.u0 + nu ? b1 : D.u0 + nu;
+        if (hi <= lo) continue;
+        const int r_lo = (int)(lo - D.u0) * RU;
+        const int r_hi = min((int)(hi - D.u0) * RU, D.rows);
+        const int RS = max(1, SE / D.ld);
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kRowtWarps) : "memory");   // the previous x is no longer read
+        if (D.xidx_off >= 0) stage_planes(x0, x1, x2, D.cols, D.ld, B.x, B.bidx + D.xidx_off, threadIdx.x, 32 * kRowtWarps);
+        else stage_planes(x0, x1, x2, D.cols, D.ld, B.x + D.x_off, nullptr, threadIdx.x, 32 * kRowtWarps);
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kRowtWarps) : "memory");
+        for (int r = r_lo; r < r_hi; r += RS, ++g) {
+            const int slot = g % S;
+            if (*reinterpret_cast<volatile int*>(&abort_flag)) break;
+            if (!mbar_wait(&full[slot], (g / S) & 1, &abort_flag)) {
+                if (lane == 0) {
+                    abort_flag = 1;
+                    atomicOr(err, ERR_TIMEOUT);
+                }
+                break;
+            }
+            const int rows = min(RS, r_hi - r);
+            const T* st = ring + (size_t)slot * SE;
+            // rows in pairs sharing every x read; pair pc goes to warp pc mod kRowtWarps
+            const int np = (rows + 1) / 2;
+            for (int q = 0; q < np; ++q, ++pc) {
+                if (pc % kRowtWarps != warp) continue;
+                const int j0 = 2 * q;
+                const bool two = j0 + 1 < rows;
+                const T* a0 = st + (size_t)j0 * D.ld;
+                const T* a1 = two ? a0 + D.ld : a0;
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll 2
+                for (int c = lane * VN; c < D.ld; c += 32 * VN) {
+                    float v[VN], u[VN];
+                    load_vec_shared(a0 + c, v);
+                    load_vec_shared(a1 + c, u);
+#pragma unroll
+                    for (int q4 = 0; q4 < VN; q4 += 4) {
+                        const float4 p0 = *reinterpret_cast<const float4*>(x0 + c + q4);
+                        const float4 p1 = *reinterpret_cast<const float4*>(x1 + c + q4);
+                        const float4 p2 = *reinterpret_cast<const float4*>(x2 + c + q4);
+                        s0 = fmaf(v[q4], p0.x, fmaf(v[q4 + 1], p0.y, fmaf(v[q4 + 2], p0.z, fmaf(v[q4 + 3], p0.w, s0))));
+                        s1 = fmaf(v[q4], p1.x, fmaf(v[q4 + 1], p1.y, fmaf(v[q4 + 2], p1.z, fmaf(v[q4 + 3], p1.w, s1))));
+                        s2 = fmaf(v[q4], p2.x, fmaf(v[q4 + 1], p2.y, fmaf(v[q4 + 2], p2.z, fmaf(v[q4 + 3], p2.w, s2))));
+                        t0 = fmaf(u[q4], p0.x, fmaf(u[q4 + 1], p0.y, fmaf(u[q4 + 2], p0.z, fmaf(u[q4 + 3], p0.w, t0))));
+                        t1 = fmaf(u[q4], p1.x, fmaf(u[q4 + 1], p1.y, fmaf(u[q4 + 2], p1.z, fmaf(u[q4 + 3], p1.w, t1))));
+                        t2 = fmaf(u[q4], p2.x, fmaf(u[q4 + 1], p2.y, fmaf(u[q4 + 2], p2.z, fmaf(u[q4 + 3], p2.w, t2))));
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+                    t0 += __shfl_xor_sync(0xffffffffu, t0, off);
+                    t1 += __shfl_xor_sync(0xffffffffu, t1, off);
+                    t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+                }
+                if (lane == 0) {
+                    const int row = r + j0;
+                    const float4 ad = (D.add_off >= 0) ? B.add[D.add_off + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    B.out[D.out_off + row] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
+                    if (two) {
+                        const float4 ae = (D.add_off >= 0) ? B.add[D.add_off + row + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        B.out[D.out_off + row + 1] = make_float4(ae.x + t0, ae.y + t1, ae.z + t2, 0.f);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+    }
+}
+
 inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
 template <class T>
@@ -609,18 +1002,43 @@ void launch_coarse(pd_mesh* m, const T* pool, const float4* cin, float4* part, c
 }
 
 template <class T>
-void launch_ax(const AxDesc* descs, const AxBlock* blocks, int n_blocks, int k_max, const AxBases& B, cudaStream_t s) {
+int axt_smem_limit() {
+    static const int lim = allow_max_dynamic_smem(k_axpy_tma<T>);
+    return lim;
+}
+
+template <class T>
+void launch_ax(const AxDesc* descs, const AxBlock* blocks, int n_blocks, int k_max, const AxBases& B, cudaStream_t s,
+               int* tma_err = nullptr, int w_max = 0, bool pdl = false) {
     if (n_blocks <= 0) return;
-    k_axpy_form<T, false><<<n_blocks, 32 * kAxWarps, sizeof(float4) * std::max(k_max, 1), s>>>(descs, blocks, B,
-                                                                                             nullptr);
+    if (tma_err) {
+        // tiled matrices: the bulk-copy streaming kernel
+        const size_t ring = axt_ring_bytes<T>(w_max);
+        const size_t smem = ring + sizeof(float4) * std::max(k_max, 1);
+        if ((int)smem > axt_smem_limit<T>()) throw Fail{PD_ERR_UNSUPPORTED};
+        if (pdl)
+            launch_pdl(k_axpy_tma<T>, dim3(n_blocks), dim3(32 * (kAxtWarps + 1)), smem, s, descs, blocks, B, (int)ring,
+                       tma_err);
+        else
+            k_axpy_tma<T><<<n_blocks, 32 * (kAxtWarps + 1), smem, s>>>(descs, blocks, B, (int)ring, tma_err);
+    } else {
+        k_axpy_form<T, false><<<n_blocks, 32 * kAxWarps, sizeof(float4) * std::max(k_max, 1), s>>>(descs, blocks, B,
+                                                                                                 nullptr);
+    }
     PDG_CHECK_LAUNCH();
 }
 
 template <class T>
-void launch_rowdot(const RowPlan& P, const AxBases& B, cudaStream_t s) {
+void launch_rowdot(const RowPlan& P, const AxBases& B, cudaStream_t s, int* tma_err = nullptr) {
     if (P.n_blocks <= 0) return;
-    k_rowdot<T><<<P.n_blocks, 32 * kRowWarps, sizeof(float) * 3 * (size_t)P.xcap, s>>>(P.descs.p, P.n_desc,
-                                                                                         P.blk_u.p, B, P.xcap);
+    if (P.tma && tma_err) {
+        const size_t smem = (size_t)kRowtStages * kRowtStageBytes + sizeof(float) * 3 * (size_t)P.xcap;
+        k_rowdot_tma<T><<<P.n_blocks, 32 * (kRowtWarps + 1), smem, s>>>(P.descs.p, P.n_desc, P.blk_u.p, B, P.xcap,
+                                                                       tma_err);
+    } else {
+        k_rowdot<T><<<P.n_blocks, 32 * kRowWarps, sizeof(float) * 3 * (size_t)P.xcap, s>>>(P.descs.p, P.n_desc,
+                                                                                             P.blk_u.p, B, P.xcap);
+    }
     PDG_CHECK_LAUNCH();
 }
 
@@ -683,7 +1101,8 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
         } else {
             phase_begin(m, PH_INTERIOR, m->side[0]);
             launch_ax<T>(m->d_ax_desc_int.p, m->d_ax_blk_int.p, m->ax_blocks_int, m->ax_kmax_int,
-                         AxBases{pool, b, nullptr, nullptr, w.tc}, m->side[0]);
+                         AxBases{pool, b, nullptr, nullptr, w.tc}, m->side[0], m->ax_tiled ? m->d_err.p : nullptr,
+                         m->ax_wmax_int);
             phase_end(m, m->side[0]);
         }
         PDG_CUDA(cudaEventRecord(m->ev_join[0], m->side[0]));
@@ -691,7 +1110,8 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
     if (m->ax_blocks_cond > 0) {
         phase_begin(m, PH_CONDENSE, s);
         launch_ax<T>(m->d_ax_desc_cond.p, m->d_ax_blk_cond.p, m->ax_blocks_cond, m->ax_kmax_cond,
-                     AxBases{pool, b, nullptr, nullptr, w.tc}, s);
+                     AxBases{pool, b, nullptr, nullptr, w.tc}, s, m->ax_tiled ? m->d_err.p : nullptr, m->ax_wmax_cond,
+                     true);
         phase_end(m, s);
     }
     if (m->n_B > 0) {
@@ -709,12 +1129,12 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
                 PDG_CUDA(cudaEventRecord(m->ev_fork[1], s));
                 PDG_CUDA(cudaStreamWaitEvent(m->side[1], m->ev_fork[1], 0));
                 phase_begin(m, PH_INTERIOR2, m->side[1]);
-                launch_rowdot<T>(m->rows_int2, AxBases{pool, w.cB, nullptr, nullptr, w.tc2}, m->side[1]);
+                launch_rowdot<T>(m->rows_int2, AxBases{pool, w.cB, nullptr, nullptr, w.tc2}, m->side[1], m->d_err.p);
                 phase_end(m, m->side[1]);
                 PDG_CUDA(cudaEventRecord(m->ev_join[1], m->side[1]));
             }
             phase_begin(m, PH_CONDENSE2, s);
-            launch_rowdot<T>(m->rows_cond2, AxBases{pool, w.cB, nullptr, nullptr, w.tc2}, s);
+            launch_rowdot<T>(m->rows_cond2, AxBases{pool, w.cB, nullptr, nullptr, w.tc2}, s, m->d_err.p);
             phase_end(m, s);
             phase_begin(m, PH_GATHER2, s);
             k_gather<<<nblk(m->n_top, 256), 256, 0, s>>>(m->n_top, m->d_gat2_ptr.p, m->d_gat2.p, w.cB + T0, w.tc2,
@@ -735,7 +1155,7 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
             if (fork2) PDG_CUDA(cudaStreamWaitEvent(s, m->ev_join[1], 0));
             phase_begin(m, PH_BACKSUB2, s);
             launch_rowdot<T>(m->rows_back2, AxBases{pool, xout + m->n_int + T0, m->d_bidx2.p, w.tc2, xout + m->n_int},
-                             s);
+                             s, m->d_err.p);
             phase_end(m, s);
         }
     }
@@ -743,7 +1163,8 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
     if (m->ax_blocks_back > 0) {
         phase_begin(m, PH_BACKSUB, s);
         launch_ax<T>(m->d_ax_desc_back.p, m->d_ax_blk_back.p, m->ax_blocks_back, m->ax_kmax_back,
-                     AxBases{pool, xout + m->n_int, m->d_bidx.p, w.tc, xout}, s);
+                     AxBases{pool, xout + m->n_int, m->d_bidx.p, w.tc, xout}, s, m->ax_tiled ? m->d_err.p : nullptr,
+                     m->ax_wmax_back, true);
         phase_end(m, s);
     }
     const int S = (int)m->jacobi_omega.size();
@@ -788,6 +1209,12 @@ void launch_axpy_b(const AxDesc* descs, const AxBlock* blocks, const AxBases* ba
 }
 
 int ax_outputs_per_block(int prec) { return 32 * kAxM * (prec == PD_PREC_BF16 ? 8 : 4); }
+
+// raise the dynamic shared-memory limit of the bulk-copy kernel (outside any capture)
+void ax_prepare_tma(int prec) {
+    if (prec == PD_PREC_BF16) (void)axt_smem_limit<__nv_bfloat16>();
+    else (void)axt_smem_limit<float>();
+}
 
 // Returns false when the largest interface vector does not fit in shared memory.
 bool configure_coarse_b(int max_cols) {
@@ -861,6 +1288,12 @@ void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream
         set_error("row-form product: the x vector does not fit in shared memory");
         throw Fail{PD_ERR_UNSUPPORTED};
     }
+    // bulk-copy streaming when a whole row fits in one stage (16-byte aligned rows: ld % 8 == 0)
+    const int es = (prec == PD_PREC_BF16) ? 2 : 4;
+    const int optin_t = (prec == PD_PREC_BF16) ? allow_max_dynamic_smem(k_rowdot_tma<__nv_bfloat16>)
+                                               : allow_max_dynamic_smem(k_rowdot_tma<float>);
+    P.tma = (size_t)kRowtStages * kRowtStageBytes + smem <= (size_t)optin_t;
+    for (const auto& d : descs) P.tma = P.tma && d.ld * es <= kRowtStageBytes && d.ld % 8 == 0 && d.a_off % 8 == 0;
     upload(P.descs, descs, s);
     upload(P.blk_u, cut, s);
     PDG_CUDA(cudaStreamSynchronize(s));

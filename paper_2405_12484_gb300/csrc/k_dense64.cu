@@ -311,6 +311,21 @@ __global__ void k_cast_block(const double* __restrict__ src, int lds, int rows, 
     }
 }
 
+// the same cast into the tiled axpy layout (ax_tile_width), chunks of CW outputs
+__global__ void k_cast_tiled(const double* __restrict__ src, int lds, int rows, int cols, int transpose, int prec,
+                             float* __restrict__ d32, __nv_bfloat16* __restrict__ d16, int64_t off, int CW, int VN) {
+    const int64_t n = (int64_t)rows * cols;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        int r = (int)(l / cols), c = (int)(l % cols);
+        double v = transpose ? src[(int64_t)c * lds + r] : src[(int64_t)r * lds + c];
+        const int o0 = c / CW * CW;
+        const int64_t o = off + (int64_t)o0 * rows + (int64_t)r * ax_tile_width(cols, o0, CW, VN) + (c - o0);
+        if (prec == PD_PREC_BF16) d16[o] = __double2bfloat16(v);
+        else if (prec == PD_PREC_TF32) d32[o] = round_tf32((float)v);
+        else d32[o] = (float)v;
+    }
+}
+
 // dst[i][k] = S[r0 + i][cols ? c0 + cols[k] : c0 + k]
 __global__ void k_copy_block_idx(const double* __restrict__ S, int ldS, int r0, int nr, const int* __restrict__ cols,
                                  int c0, int nc, double* __restrict__ dst, int ldd) {
@@ -355,6 +370,14 @@ void launch_cast_block(const double* src, int lds, int rows, int cols, int trans
     if (rows <= 0 || cols <= 0) return;
     k_cast_block<<<grid_of((int64_t)rows * cols), 256, 0, s>>>(src, lds, rows, cols, transpose, prec, dst32, dst16,
                                                                 dst_off, ldd);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_cast_tiled(const double* src, int lds, int rows, int cols, int transpose, int prec, float* dst32,
+                       __nv_bfloat16* dst16, int64_t dst_off, int CW, int VN, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return;
+    k_cast_tiled<<<grid_of((int64_t)rows * cols), 256, 0, s>>>(src, lds, rows, cols, transpose, prec, dst32, dst16,
+                                                                dst_off, CW, VN);
     PDG_CHECK_LAUNCH();
 }
 

@@ -71,16 +71,18 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ Fin, 
 __global__ void __launch_bounds__(128) k_local(int n_t, const int4* __restrict__ tets,
                                                const float4* __restrict__ geo, const float4* __restrict__ x,
                                                float4* __restrict__ force) {
+    pdl_trigger();
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_t) return;
     const int4 tv = __ldg(&tets[e]);
     const float4 r1 = __ldg(&geo[e]);
     const float4 r2 = __ldg(&geo[n_t + e]);
     const float4 r3 = __ldg(&geo[2 * (int64_t)n_t + e]);
-    const float4 x0 = __ldg(&x[tv.x]);
-    const float4 x1 = __ldg(&x[tv.y]);
-    const float4 x2 = __ldg(&x[tv.z]);
-    const float4 x3 = __ldg(&x[tv.w]);
+    pdl_wait();   // x comes from the previous solve
+    const float4 x0 = x[tv.x];
+    const float4 x1 = x[tv.y];
+    const float4 x2 = x[tv.z];
+    const float4 x3 = x[tv.w];
     const float e1[3] = {x1.x - x0.x, x1.y - x0.y, x1.z - x0.z};
     const float e2[3] = {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z};
     const float e3[3] = {x3.x - x0.x, x3.y - x0.y, x3.z - x0.z};
@@ -122,7 +124,7 @@ void launch_project(const float* F, int n, float* R, float* V, float* sig, cudaS
 
 void launch_local(const pd_mesh* m, const float4* x, float4* force, cudaStream_t s) {
     if (m->n_t <= 0) return;
-    k_local<<<(m->n_t + 127) / 128, 128, 0, s>>>(m->n_t, m->d_tets.p, m->d_geo.p, x, force);
+    launch_pdl(k_local, dim3((m->n_t + 127) / 128), dim3(128), 0, s, m->n_t, m->d_tets.p, m->d_geo.p, x, force);
     PDG_CHECK_LAUNCH();
 }
 

@@ -34,10 +34,13 @@
 #include <algorithm>
 
 #include "pd_internal.h"
+#include "tma.cuh"
 
 namespace pdg {
 
 namespace {
+
+using namespace tma;
 
 constexpr int kColWarps = 16;                            // consumer warps
 constexpr int kEpiWarps = 4;                             // epilogue warps
@@ -49,7 +52,6 @@ constexpr int kMaxGroups = 16;                           // row groups per slab
 constexpr int kMaxPieceRows = 512;                       // x slice of a piece in shared memory
 constexpr int kMaxCtaPieces = 64;                        // piece records of one CTA in shared memory
 static_assert(sizeof(ColPieceRec) % 16 == 0, "piece records are copied in 16-byte words");
-constexpr unsigned long long kWaitNs = 1000000000ull;    // a wait gives up after 1 s
 
 template <class T>
 struct SVec;
@@ -61,65 +63,6 @@ template <>
 struct SVec<__nv_bfloat16> {
     static constexpr int N = 8;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long gtime_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait: false when it ran out (1 s) or, if `abort` is given, when the
-// CTA was marked aborted meanwhile.  Waits for copies still in flight pass no
-// abort flag: they must not end early.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int* abort = nullptr) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = gtime_ns();
-    for (unsigned k = 1;; ++k) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((k & 63u) == 0) {
-            if (abort && *reinterpret_cast<const volatile int*>(abort)) return false;
-            if (gtime_ns() - t0 > kWaitNs) return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
 
 __device__ __forceinline__ void epi_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");

@@ -64,27 +64,48 @@ __global__ void k_by0(int n_free, const float4* __restrict__ y, const float4* __
 }
 
 // b_v = by0_v + sum over incidences (t, c) of v, in increasing (4t + c) order.
+// b_i = by0_i + sum of the corner forces of vertex i.  Eight lanes per vertex
+// split its corners (lane l takes corners l, l + 8, ...), each with four
+// independent index loads and then four force loads in flight, and a
+// fixed-order shuffle tree adds the lanes (deterministic).
+constexpr int kAsmLanes = 8;
+
 __global__ void __launch_bounds__(256) k_assemble(int n_free, const int* __restrict__ inc_ptr,
                                                   const int* __restrict__ inc, const float4* __restrict__ force,
                                                   const float4* __restrict__ by0, float4* __restrict__ b) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_free) return;
-    float4 acc = by0[i];
-    int k0 = __ldg(&inc_ptr[i]), k1 = __ldg(&inc_ptr[i + 1]);
-    int k = k0;
-    for (; k + 4 <= k1; k += 4) {
-        int a0 = __ldg(&inc[k]), a1 = __ldg(&inc[k + 1]), a2 = __ldg(&inc[k + 2]), a3 = __ldg(&inc[k + 3]);
-        float4 f0 = force[a0], f1 = force[a1], f2 = force[a2], f3 = force[a3];
-        acc.x += f0.x; acc.y += f0.y; acc.z += f0.z;
-        acc.x += f1.x; acc.y += f1.y; acc.z += f1.z;
-        acc.x += f2.x; acc.y += f2.y; acc.z += f2.z;
-        acc.x += f3.x; acc.y += f3.y; acc.z += f3.z;
+    pdl_trigger();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / kAsmLanes, sub = t % kAsmLanes;
+    const bool live = i < n_free;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    const int k0 = live ? __ldg(&inc_ptr[i]) : 0, k1 = live ? __ldg(&inc_ptr[i + 1]) : 0;
+    pdl_wait();   // the corner forces come from the local step
+    if (live) {
+        for (int base = k0 + sub; base < k1; base += 4 * kAsmLanes) {
+            int a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = base + u * kAsmLanes < k1 ? __ldg(&inc[base + u * kAsmLanes]) : -1;
+            float4 f[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) f[u] = a[u] >= 0 ? force[a[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ax += f[u].x;
+                ay += f[u].y;
+                az += f[u].z;
+            }
+        }
     }
-    for (; k < k1; ++k) {
-        float4 f0 = force[__ldg(&inc[k])];
-        acc.x += f0.x; acc.y += f0.y; acc.z += f0.z;
+#pragma unroll
+    for (int off = 1; off < kAsmLanes; off <<= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, off, kAsmLanes);
+        ay += __shfl_xor_sync(0xffffffffu, ay, off, kAsmLanes);
+        az += __shfl_xor_sync(0xffffffffu, az, off, kAsmLanes);
     }
-    b[i] = acc;
+    if (live && sub == 0) {
+        const float4 y = by0[i];
+        b[i] = make_float4(y.x + ax, y.y + ay, y.z + az, 0.f);
+    }
 }
 
 __global__ void k_velocity(int n_v, float inv_h, const float4* __restrict__ x, const float4* __restrict__ xprev,
@@ -162,7 +183,8 @@ void launch_by0_from_y(const pd_mesh* m, const float4* y, float4* by0, cudaStrea
 
 void launch_assemble(const pd_mesh* m, const float4* by0, const float4* force, float4* b, cudaStream_t s) {
     if (m->n_free <= 0) return;
-    k_assemble<<<nblk(m->n_free, 256), 256, 0, s>>>(m->n_free, m->d_inc_ptr.p, m->d_inc.p, force, by0, b);
+    launch_pdl(k_assemble, dim3(nblk(m->n_free * kAsmLanes, 256)), dim3(256), 0, s, m->n_free, m->d_inc_ptr.p,
+               m->d_inc.p, force, by0, b);
     PDG_CHECK_LAUNCH();
 }
 

@@ -35,6 +35,9 @@ void launch_prefactor_add_block(double* S, int ldS, const double* Sd, int ldSd, 
                                 cudaStream_t s);
 void launch_cast_block(const double* src, int lds, int rows, int cols, int transpose, int prec, float* dst32,
                        __nv_bfloat16* dst16, int64_t dst_off, int ldd, cudaStream_t s);
+void launch_cast_tiled(const double* src, int lds, int rows, int cols, int transpose, int prec, float* dst32,
+                       __nv_bfloat16* dst16, int64_t dst_off, int OW, int VN, cudaStream_t s);
+void ax_prepare_tma(int prec);
 void launch_copy_block_idx(const double* S, int ldS, int r0, int nr, const int* cols, int c0, int nc, double* dst,
                            int ldd, cudaStream_t s);
 
@@ -592,9 +595,16 @@ pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tet
     }
 
     // ---- device uploads: topology, geometry, state (first CUDA call of the set-up)
-    PDG_CUDA(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    // Priorities: the frame is captured on a high-priority stream and the
+    // off-critical-path interior products on low-priority side streams, so
+    // that (with per-node priorities at instantiation) the blocks of the
+    // interface chain are scheduled ahead of the interior products they
+    // run beside.
+    int prio_low = 0, prio_high = 0;
+    PDG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+    PDG_CUDA(cudaStreamCreateWithPriority(&m->cap_stream, cudaStreamNonBlocking, prio_high));
     for (int k = 0; k < 2; ++k) {
-        PDG_CUDA(cudaStreamCreateWithFlags(&m->side[k], cudaStreamNonBlocking));
+        PDG_CUDA(cudaStreamCreateWithPriority(&m->side[k], cudaStreamNonBlocking, prio_low));
         PDG_CUDA(cudaEventCreateWithFlags(&m->ev_fork[k], cudaEventDisableTiming));
         PDG_CUDA(cudaEventCreateWithFlags(&m->ev_join[k], cudaEventDisableTiming));
     }
@@ -1069,6 +1079,20 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->d_mat32.alloc(pool);
         PDG_CUDA(cudaMemsetAsync(m->d_mat32.p, 0, sizeof(float) * pool, s));
     }
+    // the per-domain axpy-form matrices are stored as output-chunk tiles
+    // (streamed by bulk copies), except for the fused streaming solve, whose
+    // plan copies row-major blocks into its own panels
+    const bool tiled = !(o.flags & PD_SOLVE_STREAMING);
+    const int OWt = ax_outputs_per_block(m->prec), VNt = (m->prec == PD_PREC_BF16) ? 8 : 4;
+    m->ax_tiled = tiled;
+    if (tiled) ax_prepare_tma(m->prec);
+    auto cast_ax = [&](const double* src, int lds, int rows, int cols, int transpose, int64_t off, int ld) {
+        if (tiled)
+            launch_cast_tiled(src, lds, rows, cols, transpose, m->prec, m->d_mat32.p, m->d_mat16.p, off,
+                              ax_chunk_width(cols, OWt, VNt), VNt, s);
+        else
+            launch_cast_block(src, lds, rows, cols, transpose, m->prec, m->d_mat32.p, m->d_mat16.p, off, ld, s);
+    };
     for (int32_t d = 0; d < n_dom; ++d) {
         const int32_t ni = m->dom_n_int[d], nbd = (int32_t)m->dom_bnd[d].size();
         if (ni == 0) continue;
@@ -1083,11 +1107,11 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
                                   ldH[d], s);
             }
         } else {
-            launch_cast_block(Xd, NI, ni, ni, 0, m->prec, m->d_mat32.p, m->d_mat16.p, h_off[d], ldH[d], s);
+            cast_ax(Xd, NI, ni, ni, 0, h_off[d], ldH[d]);
         }
         if (nbd > 0) {
-            launch_cast_block(Pd, NBp, ni, nbd, 0, m->prec, m->d_mat32.p, m->d_mat16.p, p_off[d], ldP[d], s);
-            launch_cast_block(Pd, NBp, nbd, ni, 1, m->prec, m->d_mat32.p, m->d_mat16.p, t_off[d], ldT[d], s);
+            cast_ax(Pd, NBp, ni, nbd, 0, p_off[d], ldP[d]);
+            cast_ax(Pd, NBp, nbd, ni, 1, t_off[d], ldT[d]);
         }
     }
     if (n_B > 0 && !two)
@@ -1121,6 +1145,12 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         // (on the path to the interface solve) and the interior part
         // t_d = K_ii^-1 b_i (needed only by the back-substitution)
         const int OW = ax_outputs_per_block(m->prec);
+        // tiled descriptors: ld = the chunk width, one block per chunk
+        auto tile_desc = [&](AxDesc& a) {
+            if (!a.tiled) return OW;
+            a.ld = ax_chunk_width(a.n_out, OW, VN);
+            return (int)a.ld;
+        };
         std::vector<AxDesc> dc, di, db, dm1, dm2;
         std::vector<AxBlock> bc, bi, bb, bm1, bm2;
         for (int32_t d = 0; d < n_dom; ++d) {
@@ -1135,8 +1165,10 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             c.K = ni;
             c.ld = ldP[d];
             c.n_out = nbd;
+            c.tiled = tiled ? 1 : 0;
             if (nbd > 0) {
-                for (int32_t o0 = 0; o0 < c.n_out; o0 += OW) bc.push_back(AxBlock{(int32_t)dc.size(), o0});
+                const int cw = tile_desc(c);
+                for (int32_t o0 = 0; o0 < c.n_out; o0 += cw) bc.push_back(AxBlock{(int32_t)dc.size(), o0});
                 dc.push_back(c);
             }
             if (!modal) {
@@ -1145,7 +1177,8 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
                 t.out_off = tc_off[d];
                 t.ld = ldH[d];
                 t.n_out = ni;
-                for (int32_t o0 = 0; o0 < t.n_out; o0 += OW) bi.push_back(AxBlock{(int32_t)di.size(), o0});
+                const int cw = tile_desc(t);
+                for (int32_t o0 = 0; o0 < t.n_out; o0 += cw) bi.push_back(AxBlock{(int32_t)di.size(), o0});
                 di.push_back(t);
             } else if (r_dom[d] > 0) {
                 // p = Phi^T b_i (rows k of Phi), then t = (Phi Lambda^-1) p (rows j of its transpose)
@@ -1158,6 +1191,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
                 a1.K = ni;
                 a1.ld = NR;
                 a1.n_out = r_dom[d];
+                a1.tiled = 0;
                 for (int32_t o0 = 0; o0 < a1.n_out; o0 += OW) bm1.push_back(AxBlock{(int32_t)dm1.size(), o0});
                 dm1.push_back(a1);
                 AxDesc a2{};
@@ -1169,6 +1203,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
                 a2.K = r_dom[d];
                 a2.ld = ldH[d];
                 a2.n_out = ni;
+                a2.tiled = 0;
                 for (int32_t o0 = 0; o0 < a2.n_out; o0 += OW) bm2.push_back(AxBlock{(int32_t)dm2.size(), o0});
                 dm2.push_back(a2);
             }
@@ -1181,7 +1216,9 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             b.K = nbd;
             b.ld = ldT[d];
             b.n_out = ni;
-            for (int32_t o0 = 0; o0 < b.n_out; o0 += OW) bb.push_back(AxBlock{(int32_t)db.size(), o0});
+            b.tiled = tiled ? 1 : 0;
+            const int cwb = tile_desc(b);
+            for (int32_t o0 = 0; o0 < b.n_out; o0 += cwb) bb.push_back(AxBlock{(int32_t)db.size(), o0});
             db.push_back(b);
         }
         upload(m->d_ax_desc_cond, dc, s);
@@ -1210,6 +1247,10 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         for (const auto& a : dc) m->ax_kmax_cond = std::max(m->ax_kmax_cond, a.K);
         for (const auto& a : di) m->ax_kmax_int = std::max(m->ax_kmax_int, a.K);
         for (const auto& a : db) m->ax_kmax_back = std::max(m->ax_kmax_back, a.K);
+        m->ax_wmax_cond = m->ax_wmax_int = m->ax_wmax_back = 1;
+        for (const auto& a : dc) m->ax_wmax_cond = std::max(m->ax_wmax_cond, a.tiled ? a.ld : OW);
+        for (const auto& a : di) m->ax_wmax_int = std::max(m->ax_wmax_int, a.tiled ? a.ld : OW);
+        for (const auto& a : db) m->ax_wmax_back = std::max(m->ax_wmax_back, a.tiled ? a.ld : OW);
         (void)VN;
     }
     m->n_tc = tcr;
@@ -1663,7 +1704,7 @@ pd_status pd_step(pd_mesh* m, const float* pin_targets, const float* gravity, in
             m->ev_rec = nullptr;
             PDG_CUDA(cudaStreamEndCapture(m->cap_stream, &graph));
             cudaGraphExec_t exec = nullptr;
-            cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaError_t e = cudaGraphInstantiate(&exec, graph, m->node_priority ? cudaGraphInstantiateFlagUseNodePriority : 0);
             cudaGraphDestroy(graph);
             PDG_CUDA(e);
             it = m->graphs.emplace(key, pd_mesh::GraphEntry{exec, ts}).first;

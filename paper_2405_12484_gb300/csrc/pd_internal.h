@@ -48,6 +48,30 @@ inline int allow_max_dynamic_smem(K* kernel) {
     return lim;
 }
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with
+// launch_pdl may be scheduled while its stream predecessor is still running
+// (once every block of the predecessor has started or called pdl_trigger);
+// it must call pdl_wait() before it reads anything a predecessor wrote or
+// writes anything a predecessor reads.  Constant data (the prefactored
+// matrices, the topology) may be fetched before the wait.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    PDG_CUDA(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+}
+
 // Device error flag bits (d_err).
 enum : int { ERR_NONFINITE = 1, ERR_NOT_SPD = 2, ERR_TIMEOUT = 4 };
 
@@ -102,7 +126,26 @@ struct AxDesc {
     int32_t out_off;
     int32_t K, ld, n_out;  // rows, row stride, outputs
     int32_t slot;          // serving slot (batched launches)
+    int32_t tiled;         // 1: output-chunk tiles (see ax_tile_width); ld then holds the chunk width
+    int32_t pad_[3];
 };
+
+// Tiled layout of an axpy-form matrix (K rows x n_out outputs cut into
+// chunks of CW outputs, CW a multiple of VN, one chunk per block): the chunk
+// with first output o0 (a multiple of CW) is a contiguous K x w tile at
+// a_off + o0 K, row k at + k w, w = min(CW, n_out - o0 rounded up to VN).
+__host__ __device__ inline int ax_tile_width(int n_out, int o0, int CW, int VN) {
+    const int w = (n_out - o0 + VN - 1) / VN * VN;
+    return w < CW ? w : CW;
+}
+
+// Balanced chunk width: the fewest chunks of at most OW outputs, equal widths
+// (rounded up to VN).
+__host__ __device__ inline int ax_chunk_width(int n_out, int OW, int VN) {
+    const int c = (n_out + OW - 1) / OW;
+    const int w = (n_out + c - 1) / c;
+    return (w + VN - 1) / VN * VN;
+}
 struct AxBlock {
     int32_t desc, o0;      // descriptor and first output of one block
 };
@@ -125,6 +168,7 @@ struct RowPlan {
     DBuf<RowDesc> descs;
     DBuf<int64_t> blk_u;
     int n_desc = 0, n_blocks = 0, xcap = 8;
+    bool tma = false;              // rows streamed by bulk copies (k_rowdot_tma)
     std::vector<RowDesc> host;     // host copy (byte accounting)
 };
 
@@ -265,7 +309,9 @@ struct pd_mesh {
     // sizes
     int32_t n_v = 0, n_t = 0, n_dom = 0, n_pin = 0, n_free = 0, n_int = 0, n_B = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs (high priority)
+    bool node_priority = true;          // instantiate frames with the captured per-node priorities
+    bool ax_tiled = false;              // axpy-form matrices stored as tiles, streamed by bulk copies
     // side streams of the subspace solve: the interior parts of the two
     // condensations run beside the interface solve (fork/join by events)
     cudaStream_t side[2] = {nullptr, nullptr};
@@ -321,6 +367,7 @@ struct pd_mesh {
     pdg::DBuf<pdg::AxBlock> d_ax_blk_cond, d_ax_blk_int, d_ax_blk_back;
     int32_t ax_blocks_cond = 0, ax_blocks_int = 0, ax_blocks_back = 0;
     int32_t ax_kmax_cond = 1, ax_kmax_int = 1, ax_kmax_back = 1;   // largest K (shared-memory vector size)
+    int32_t ax_wmax_cond = 1, ax_wmax_int = 1, ax_wmax_back = 1;   // largest tile width (tiled layout)
     // second level (groups of domains): condensation onto the top-level interface
     bool two_level = false;
     int32_t cs_n = 0;                                       // rows of the dense coarse inverse in the pool

@@ -180,12 +180,14 @@ static void rebuild(pd_server* S) {
         basb[k] = AxBases{pool, m->d_x.p + m->n_int, m->d_bidx.p, m->d_tc.p, m->d_x.p};
         for (AxDesc a : m->h_ax_desc_cond) {
             a.slot = k;
-            for (int32_t o0 = 0; o0 < a.n_out; o0 += OW) blkc.push_back(AxBlock{(int32_t)axc.size(), o0});
+            const int32_t cw = a.tiled ? a.ld : OW;   // tiled: one block per chunk of ld outputs
+            for (int32_t o0 = 0; o0 < a.n_out; o0 += cw) blkc.push_back(AxBlock{(int32_t)axc.size(), o0});
             axc.push_back(a);
         }
         for (AxDesc a : m->h_ax_desc_back) {
             a.slot = k;
-            for (int32_t o0 = 0; o0 < a.n_out; o0 += OW) blkb.push_back(AxBlock{(int32_t)axb.size(), o0});
+            const int32_t cw = a.tiled ? a.ld : OW;
+            for (int32_t o0 = 0; o0 < a.n_out; o0 += cw) blkb.push_back(AxBlock{(int32_t)axb.size(), o0});
             axb.push_back(a);
         }
         if (m->n_B > 0) {
