@@ -1116,7 +1116,8 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
     }
     if (m->n_B > 0) {
         phase_begin(m, PH_GATHER, s);
-        k_gather<<<nblk(m->n_B, 256), 256, 0, s>>>(m->n_B, m->d_gat_ptr.p, m->d_gat.p, b + m->n_int, w.tc, w.cB);
+        launch_pdl(k_gather, dim3(nblk(m->n_B, 256)), dim3(256), 0, s, m->n_B, m->d_gat_ptr.p, m->d_gat.p,
+                   b + m->n_int, w.tc, w.cB);
         PDG_CHECK_LAUNCH();
         phase_end(m, s);
         const float4* cin = w.cB;
@@ -1137,8 +1138,8 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
             launch_rowdot<T>(m->rows_cond2, AxBases{pool, w.cB, nullptr, nullptr, w.tc2}, s, m->d_err.p);
             phase_end(m, s);
             phase_begin(m, PH_GATHER2, s);
-            k_gather<<<nblk(m->n_top, 256), 256, 0, s>>>(m->n_top, m->d_gat2_ptr.p, m->d_gat2.p, w.cB + T0, w.tc2,
-                                                         w.cT);
+            launch_pdl(k_gather, dim3(nblk(m->n_top, 256)), dim3(256), 0, s, m->n_top, m->d_gat2_ptr.p, m->d_gat2.p,
+                       w.cB + T0, w.tc2, w.cT);
             PDG_CHECK_LAUNCH();
             phase_end(m, s);
             cin = w.cT;
@@ -1148,7 +1149,7 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
         launch_coarse<T>(m, pool, cin, w.part, s);
         phase_end(m, s);
         phase_begin(m, PH_REDUCE, s);
-        k_reduce<<<nblk(m->cs_n, 256), 256, 0, s>>>(m->cs_n, m->coarse_nchunks, w.part, xcs);
+        launch_pdl(k_reduce, dim3(nblk(m->cs_n, 256)), dim3(256), 0, s, m->cs_n, m->coarse_nchunks, w.part, xcs);
         PDG_CHECK_LAUNCH();
         phase_end(m, s);
         if (m->two_level) {

@@ -64,31 +64,21 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ Fin, 
     }
 }
 
-// One thread per tet.  geo holds three float4 rows per tet in SoA blocks:
+// geo holds three float4 rows per tet in SoA blocks:
 // geo[t] = (g1, ws), geo[n_t + t] = (g2, wv), geo[2 n_t + t] = (g3, 0), with
 // g_k the rows of Dm^-1 and ws = V_e gamma_s, wv = V_e gamma_v.
 // Output: force[4 t + c] = (ws R + wv V) g_c, g_0 = -(g1 + g2 + g3).
-__global__ void __launch_bounds__(128) k_local(int n_t, const int4* __restrict__ tets,
-                                               const float4* __restrict__ geo, const float4* __restrict__ x,
-                                               float4* __restrict__ force) {
-    pdl_trigger();
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_t) return;
-    const int4 tv = __ldg(&tets[e]);
-    const float4 r1 = __ldg(&geo[e]);
-    const float4 r2 = __ldg(&geo[n_t + e]);
-    const float4 r3 = __ldg(&geo[2 * (int64_t)n_t + e]);
-    pdl_wait();   // x comes from the previous solve
-    const float4 x0 = x[tv.x];
-    const float4 x1 = x[tv.y];
-    const float4 x2 = x[tv.z];
-    const float4 x3 = x[tv.w];
-    const float e1[3] = {x1.x - x0.x, x1.y - x0.y, x1.z - x0.z};
-    const float e2[3] = {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z};
-    const float e3[3] = {x3.x - x0.x, x3.y - x0.y, x3.z - x0.z};
-    const float g1[3] = {r1.x, r1.y, r1.z};
-    const float g2[3] = {r2.x, r2.y, r2.z};
-    const float g3[3] = {r3.x, r3.y, r3.z};
+struct LocalIn {
+    float4 r1, r2, r3, x0, x1, x2, x3;
+};
+
+__device__ __forceinline__ void local_tet(const LocalIn& L, float4* __restrict__ out) {
+    const float e1[3] = {L.x1.x - L.x0.x, L.x1.y - L.x0.y, L.x1.z - L.x0.z};
+    const float e2[3] = {L.x2.x - L.x0.x, L.x2.y - L.x0.y, L.x2.z - L.x0.z};
+    const float e3[3] = {L.x3.x - L.x0.x, L.x3.y - L.x0.y, L.x3.z - L.x0.z};
+    const float g1[3] = {L.r1.x, L.r1.y, L.r1.z};
+    const float g2[3] = {L.r2.x, L.r2.y, L.r2.z};
+    const float g3[3] = {L.r3.x, L.r3.y, L.r3.z};
     float F[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -97,7 +87,7 @@ __global__ void __launch_bounds__(128) k_local(int n_t, const int4* __restrict__
     float U[3][3], W[3][3], s[3], d[3], P[3][3];
     svd3(F, U, s, W);
     volume_targets(s, d);
-    const float ws = r1.w, wv = r2.w;
+    const float ws = L.r1.w, wv = L.r2.w;
     const float c[3] = {ws + wv * d[0], ws + wv * d[1], ws + wv * d[2]};
     udwt(U, c, W, P);
     float f1[3], f2[3], f3[3];
@@ -107,11 +97,47 @@ __global__ void __launch_bounds__(128) k_local(int n_t, const int4* __restrict__
         f2[i] = P[i][0] * g2[0] + P[i][1] * g2[1] + P[i][2] * g2[2];
         f3[i] = P[i][0] * g3[0] + P[i][1] * g3[1] + P[i][2] * g3[2];
     }
-    float4* out = force + 4 * (int64_t)e;
     out[0] = make_float4(-(f1[0] + f2[0] + f3[0]), -(f1[1] + f2[1] + f3[1]), -(f1[2] + f2[2] + f3[2]), 0.f);
     out[1] = make_float4(f1[0], f1[1], f1[2], 0.f);
     out[2] = make_float4(f2[0], f2[1], f2[2], 0.f);
     out[3] = make_float4(f3[0], f3[1], f3[2], 0.f);
+}
+
+// kLocalTpt tets per thread (e, e + blockDim.x, ...) in the block's chunk: the
+// independent per-tet chains (SVD, volume solve) interleave in one thread.
+#ifndef PDG_LOCAL_TPT
+#define PDG_LOCAL_TPT 1
+#endif
+constexpr int kLocalTpt = PDG_LOCAL_TPT;
+
+__global__ void __launch_bounds__(128) k_local(int n_t, const int4* __restrict__ tets,
+                                               const float4* __restrict__ geo, const float4* __restrict__ x,
+                                               float4* __restrict__ force) {
+    pdl_trigger();
+    const int base = blockIdx.x * blockDim.x * kLocalTpt + threadIdx.x;
+    LocalIn L[kLocalTpt];
+    int4 tv[kLocalTpt];
+#pragma unroll
+    for (int u = 0; u < kLocalTpt; ++u) {
+        const int e = min(base + u * (int)blockDim.x, n_t - 1);
+        tv[u] = __ldg(&tets[e]);
+        L[u].r1 = __ldg(&geo[e]);
+        L[u].r2 = __ldg(&geo[n_t + e]);
+        L[u].r3 = __ldg(&geo[2 * (int64_t)n_t + e]);
+    }
+    pdl_wait();   // x comes from the previous solve
+#pragma unroll
+    for (int u = 0; u < kLocalTpt; ++u) {
+        L[u].x0 = x[tv[u].x];
+        L[u].x1 = x[tv[u].y];
+        L[u].x2 = x[tv[u].z];
+        L[u].x3 = x[tv[u].w];
+    }
+#pragma unroll
+    for (int u = 0; u < kLocalTpt; ++u) {
+        const int e = base + u * (int)blockDim.x;
+        if (e < n_t) local_tet(L[u], force + 4 * (int64_t)e);
+    }
 }
 
 }  // namespace
@@ -124,7 +150,8 @@ void launch_project(const float* F, int n, float* R, float* V, float* sig, cudaS
 
 void launch_local(const pd_mesh* m, const float4* x, float4* force, cudaStream_t s) {
     if (m->n_t <= 0) return;
-    launch_pdl(k_local, dim3((m->n_t + 127) / 128), dim3(128), 0, s, m->n_t, m->d_tets.p, m->d_geo.p, x, force);
+    launch_pdl(k_local, dim3((m->n_t + 128 * kLocalTpt - 1) / (128 * kLocalTpt)), dim3(128), 0, s, m->n_t, m->d_tets.p,
+               m->d_geo.p, x, force);
     PDG_CHECK_LAUNCH();
 }
 
