@@ -834,7 +834,7 @@ __global__ void k_cheb_jacobi(int n_free, const int* __restrict__ ptr, const int
 #define PDG_ROWT_STAGES 3
 #endif
 #ifndef PDG_ROWT_WARPS
-#define PDG_ROWT_WARPS 4
+#define PDG_ROWT_WARPS 8
 #endif
 constexpr int kRowtStageBytes = PDG_ROWT_STAGE_BYTES;
 constexpr int kRowtStages = PDG_ROWT_STAGES;

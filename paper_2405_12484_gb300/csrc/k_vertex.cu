@@ -64,11 +64,11 @@ __global__ void k_by0(int n_free, const float4* __restrict__ y, const float4* __
 }
 
 // b_v = by0_v + sum over incidences (t, c) of v, in increasing (4t + c) order.
-// b_i = by0_i + sum of the corner forces of vertex i.  Eight lanes per vertex
-// split its corners (lane l takes corners l, l + 8, ...), each with four
+// b_i = by0_i + sum of the corner forces of vertex i.  Four lanes per vertex
+// split its corners (lane l takes corners l, l + 4, ...), each with four
 // independent index loads and then four force loads in flight, and a
 // fixed-order shuffle tree adds the lanes (deterministic).
-constexpr int kAsmLanes = 8;
+constexpr int kAsmLanes = 4;
 
 __global__ void __launch_bounds__(256) k_assemble(int n_free, const int* __restrict__ inc_ptr,
                                                   const int* __restrict__ inc, const float4* __restrict__ force,
