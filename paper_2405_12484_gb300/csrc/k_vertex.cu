@@ -63,7 +63,6 @@ __global__ void k_by0(int n_free, const float4* __restrict__ y, const float4* __
     by0[i] = acc;
 }
 
-// b_v = by0_v + sum over incidences (t, c) of v, in increasing (4t + c) order.
 // b_i = by0_i + sum of the corner forces of vertex i.  Four lanes per vertex
 // split its corners (lane l takes corners l, l + 4, ...), each with four
 // independent index loads and then four force loads in flight, and a
