@@ -252,6 +252,18 @@ const char* pd_phase_name(int32_t k);
  */
 pd_status pd_test_offset_phase_counter(pd_mesh* mesh, int32_t phase, int32_t delta);
 
+/*
+ * Test hook for the bounded waits of the tile-streaming products (failure
+ * detection without a fault): the next tile stream to start (block 0, first
+ * stage) expects `bytes` more than its bulk copy delivers, so the consumers'
+ * wait for that stage runs out after 1 s; the launch drains its copies and
+ * ends, and the next pd_sync returns PD_ERR_TIMEOUT (the flags are cleared,
+ * the mesh stays usable; the state of that frame is not meaningful).
+ * bytes: a non-negative multiple of 16 (0 cancels).  Synchronous.
+ * Errors: INVALID_ARG (no tiled products: streaming solve, or bad bytes).
+ */
+pd_status pd_test_inflate_copy(pd_mesh* mesh, int32_t bytes);
+
 /* ---- Differentiation: equilibrium steps and the adjoint step (Sec. 6.1) ---- */
 
 typedef struct pd_adjoint pd_adjoint;   /* opaque workspace: CG vectors and the adjoint states */

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("pd_phase_times", C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     ("pd_phase_name", C.c_char_p, [C.c_int32]),
     ("pd_test_offset_phase_counter", C.c_int32, [C.c_void_p, C.c_int32, C.c_int32]),
+    ("pd_test_inflate_copy", C.c_int32, [C.c_void_p, C.c_int32]),
     ("pd_solve_noalloc", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pd_adjoint_create", C.c_int32, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     ("pd_adjoint_destroy", None, [C.c_void_p]),

@@ -21,6 +21,10 @@ namespace pdg {
 
 void launch_stream_solve(const StreamPlan& P, FusedArgs F, cudaStream_t s);
 
+// Test hook: bytes the next first stage of block 0 of a tile-streaming launch
+// expects beyond what its copy delivers (0 = none; consumed once).
+__device__ int g_test_copy_extra = 0;
+
 namespace {
 
 template <class T>
@@ -384,7 +388,10 @@ __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_tma(const AxDesc*
                 }
                 const int rows = min(R, D.K - i * R);
                 const uint32_t bytes = (uint32_t)(rows * w * (int)sizeof(T));
-                mbar_arrive_expect_tx(&full[slot], bytes);
+                uint32_t expect = bytes;
+                if (blockIdx.x == 0 && i == 0 && *reinterpret_cast<volatile int*>(&g_test_copy_extra) > 0)
+                    expect += (uint32_t)max(atomicExch(&g_test_copy_extra, 0), 0);
+                mbar_arrive_expect_tx(&full[slot], expect);
                 bulk_g2s(ring + (size_t)slot * R * w, tile + (int64_t)i * R * w, bytes, &full[slot]);
                 issued = i + 1;
             }
@@ -1210,6 +1217,11 @@ void launch_axpy_b(const AxDesc* descs, const AxBlock* blocks, const AxBases* ba
 }
 
 int ax_outputs_per_block(int prec) { return 32 * kAxM * (prec == PD_PREC_BF16 ? 8 : 4); }
+
+void test_set_copy_extra(int bytes, cudaStream_t s) {
+    PDG_CUDA(cudaMemcpyToSymbolAsync(g_test_copy_extra, &bytes, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    PDG_CUDA(cudaStreamSynchronize(s));
+}
 
 // raise the dynamic shared-memory limit of the bulk-copy kernel (outside any capture)
 void ax_prepare_tma(int prec) {

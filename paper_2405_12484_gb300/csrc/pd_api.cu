@@ -38,6 +38,7 @@ void launch_cast_block(const double* src, int lds, int rows, int cols, int trans
 void launch_cast_tiled(const double* src, int lds, int rows, int cols, int transpose, int prec, float* dst32,
                        __nv_bfloat16* dst16, int64_t dst_off, int OW, int VN, cudaStream_t s);
 void ax_prepare_tma(int prec);
+void test_set_copy_extra(int bytes, cudaStream_t s);
 void launch_copy_block_idx(const double* S, int ldS, int r0, int nr, const int* cols, int c0, int nc, double* dst,
                            int ldd, cudaStream_t s);
 
@@ -1869,6 +1870,15 @@ pd_status pd_test_offset_phase_counter(pd_mesh* m, int32_t phase, int32_t delta)
     PDG_CUDA(cudaMemcpy(&v, m->st_solve.phase_cnt.p + phase, sizeof(int32_t), cudaMemcpyDeviceToHost));
     v += delta;
     PDG_CUDA(cudaMemcpy(m->st_solve.phase_cnt.p + phase, &v, sizeof(int32_t), cudaMemcpyHostToDevice));
+    return PD_OK;
+    PD_API_END
+}
+
+pd_status pd_test_inflate_copy(pd_mesh* m, int32_t bytes) {
+    if (!m || !m->ax_tiled || bytes < 0 || bytes % 16 != 0)
+        return fail(PD_ERR_INVALID_ARG, "no tile-streaming products, or bytes not a non-negative multiple of 16");
+    PD_API_BEGIN
+    test_set_copy_extra(bytes, m->stream);
     return PD_OK;
     PD_API_END
 }

@@ -170,6 +170,10 @@ class Mesh:
         """Testing hook: makes the next streaming solve's wait on `phase` run out."""
         _check(lib().pd_test_offset_phase_counter(self._h, int(phase), int(delta)), "pd_test_offset_phase_counter")
 
+    def test_inflate_copy(self, nbytes):
+        """Test hook: make the next tile stream's bounded wait run out (see include/pd.h)."""
+        _check(lib().pd_test_inflate_copy(self._h, int(nbytes)), "pd_test_inflate_copy")
+
 
 class Adjoint:
     """Workspace for equilibrium steps and backward adjoint steps on one mesh."""

@@ -392,3 +392,35 @@ def test_streaming_wait_runs_out_and_reports_timeout():
     m.sync()
     assert torch.equal(out, ref)
     m.close()
+
+
+def test_bulk_copy_wait_runs_out_and_reports_timeout():
+    """Failure detection without a fault: one tile stage that expects 16 bytes
+    more than its bulk copy delivers makes the consumers' bounded wait in
+    k_axpy_tma run out; the launch drains its copies and ends, pd_sync reports
+    PD_ERR_TIMEOUT, and the mesh works again afterwards (bitwise as before)."""
+    from paper_2405_12484_gb300 import _lib
+    from paper_2405_12484_gb300.sim import Mesh
+    w = parity_slab()
+    m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density)
+    m.set_materials(w.gamma_s, w.gamma_v)
+    m.prefactor(w.dt)
+    x0 = torch.as_tensor(w.rest, dtype=torch.float32)
+    v0 = torch.zeros_like(x0)
+    pins = torch.as_tensor(w.pin_targets(0), dtype=torch.float32)
+    ref = torch.empty((w.n_v, 3), device="cuda")
+    m.set_state(x0, v0)
+    m.step(pins, w.gravity, 2, x_out=ref)
+    m.sync()
+    m.test_inflate_copy(16)
+    m.set_state(x0, v0)
+    m.step(pins, w.gravity, 1)
+    with pytest.raises(_lib.PDError) as e:
+        m.sync()
+    assert e.value.status == _lib.PD_ERR_TIMEOUT
+    out = torch.empty_like(ref)
+    m.set_state(x0, v0)
+    m.step(pins, w.gravity, 2, x_out=out)
+    m.sync()
+    assert torch.equal(out, ref)
+    m.close()
