@@ -419,8 +419,9 @@ def main():
                 phases[k] = {"ms": ms, "bytes": b, "GB/s": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / peak}
         m.enable_timing(0)
 
-    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    m.enable_timing(0)
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region;
+    # the same captured frame as the timed region (with the dominant kernel's events)
+    m.enable_timing(phase_bit(dominant))
     pins_h = torch.as_tensor(np.stack([w.pin_targets(n) for n in range(K)]), dtype=torch.float32).pin_memory()
     out_h = torch.empty((K, w.n_v, 3), dtype=torch.float32).pin_memory()
     pin_d = torch.empty((w.n_pinned if hasattr(w, "n_pinned") else int(w.pinned.sum()), 3), device="cuda")
