@@ -10,8 +10,10 @@
 //   backsub  : x_i = t_d + Psi_d x_B(d)                         (per domain)
 // Every product is a dense matrix times three right-hand sides (x, y, z
 // share the scalar matrix, K = K_s (x) I_3): HBM-bound streaming of the
-// matrices with 16-byte loads, FP32 accumulation, vectors staged in shared
-// memory, fixed-order warp reductions (deterministic), no atomics.
+// matrices (bulk asynchronous copies of whole tiles or rows into a
+// shared-memory ring, or 16-byte loads in the fallback kernels), FP32
+// accumulation, vectors staged in shared memory, fixed-order reductions
+// (deterministic), no atomics.
 #include <algorithm>
 
 #include "pd_internal.h"
@@ -192,7 +194,7 @@ constexpr int kMaxSubCols = 2048;   // largest per-domain internal / boundary co
 // Column-oriented per-domain products ("axpy form"): y = add + sum_k A[k, :] x_k
 // with A stored so that each output is a column (rows k of A are contiguous).
 // One block = one output chunk of one domain matrix: each lane owns VN
-// consecutive outputs, the 4 warps split k into equal ranges, x_k is a
+// consecutive outputs, the kAxWarps warps split k into equal ranges, x_k is a
 // shared-memory broadcast, and the warps' partial sums are combined in a
 // fixed order (deterministic).  No cross-lane reductions, fully coalesced
 // 16-byte row loads.
