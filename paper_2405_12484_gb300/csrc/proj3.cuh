@@ -159,8 +159,8 @@ static __device__ __forceinline__ bool solve_face(const float (&sh)[2], float st
     float t;
     if (v <= 0.0f) {
         // + branch: psi increasing on [tm, inf); bracket [a, b], Newton safeguarded by bisection.
-        // Four steps from the uniform-scaling guess converge in the common case; the
-        // bracketed loop continues only for the rare element that has not.
+        // Two fixed steps from the uniform-scaling guess (no divergence inside a warp), then
+        // the bracketed loop continues, to the tolerance, only for elements not yet converged.
         float a = tm, b = fmaxf(t_hi, tm);
         float prod = st;
 #pragma unroll
@@ -168,7 +168,7 @@ static __device__ __forceinline__ bool solve_face(const float (&sh)[2], float st
         t = (st > 0.f && prod > 0.f) ? st * expf((logp - logf(prod)) / (K + 1)) : 0.5f * (a + b);
         t = fminf(fmaxf(t, a), b);
 #pragma unroll 1
-        for (int it = 0; it < 4; ++it) {
+        for (int it = 0; it < 2; ++it) {
             face_eval<K>(sh, st, logp, t, v, dv, d);
             if (v <= 0.0f) a = t; else b = t;
             float tn = t - v / dv;
