@@ -18,6 +18,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -60,9 +61,9 @@ def parse():
 # traffic / algorithmic bytes of the kernel behind a phase, read from its ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum per launch), keyed by
 # (phase, precision, interface solve); a kernel changed since its capture has no entry.
-# ("dd_interior", fp32, two levels): the interior k_axpy_tma launch on the 153,600-tet shell
-# (profiles/k_axpy_tma_shell153k_fp32.md); the interior is one tile stream per domain, so the
-# ratio carries over to the full-size launch.
+# ("dd_interior", fp32, two levels): the ncu capture of the interior k_axpy_tma launch on the
+# 153,600-tet shell; the interior is one tile stream per domain, so the ratio carries over to the
+# full-size launch.
 TRAFFIC_RATIO = {("dd_interior", "fp32", "two"): 0.992}
 
 
@@ -123,7 +124,9 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.proc = None
         self.dev = device_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # the clock samples are kept as evidence in $PD_RECORD_DIR (a temporary directory if unset)
+        self.path = os.path.join(os.environ.get("PD_RECORD_DIR") or tempfile.gettempdir(),
+                                 f"clocks_rank{device_index}.csv")
 
     def start(self):
         try:

@@ -15,8 +15,10 @@ What it computes (Sec. 7, "Domain-decomposed projective dynamics"):
       b = (M/dt^2) y + sum_e V_e gs_e B_e^T (D^T : R_e)
                      + sum_e V_e gv_e B_e^T (D^T : V_e),
   solved with a direct Cholesky of the whole (not decomposed) matrix, since
-  the paper's exact subspace solve (Eq. cms_boundary, Eq. global_subspace)
-  reproduces the full solve (see the design doc for the identity).
+  the paper's subspace solve (Eq. cms_boundary, Eq. global_subspace) with
+  the full internal space reproduces the full solve: the Galerkin system is
+  block-diagonal, the interface values solve S x_b = b_b - sum_d K_bi K_ii^-1 b_i
+  exactly and the internal values follow as K_ii^-1 (b_i - K_ib x_b).
 
 Readings of the paper taken here:
 

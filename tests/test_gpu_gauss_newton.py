@@ -19,10 +19,13 @@ from oracle.gauss_newton import FLOOR, GaussNewtonOracle, fit_pose  # noqa: E402
 from oracle.pd_oracle import PDOracle  # noqa: E402
 from workloads.meshes import adjoint_slab, parity_slab, slab_workload  # noqa: E402
 
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+# measurement records go to $PD_RECORD_DIR when it is set (nothing is written otherwise)
+OUT = os.environ.get("PD_RECORD_DIR")
 
 
 def _record(name, payload):
+    if not OUT:
+        return
     try:
         os.makedirs(OUT, exist_ok=True)
         with open(os.path.join(OUT, f"gn_{name}.json"), "w") as f:

@@ -15,7 +15,8 @@ from gpu_helpers import f32, rel  # noqa: E402
 
 from workloads.meshes import sweater_shell  # noqa: E402
 
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+# measurement records go to $PD_RECORD_DIR when it is set (nothing is written otherwise)
+OUT = os.environ.get("PD_RECORD_DIR")
 
 
 @pytest.fixture(scope="module")
