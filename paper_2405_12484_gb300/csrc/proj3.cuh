@@ -25,6 +25,12 @@ namespace proj {
 
 constexpr float kClamp = 0.01f;
 
+// The Jacobi sweeps of the SVD stop after this many (of four) once the
+// off-diagonal of F^T F is below the rounding of its diagonal (0: always four)
+#ifndef PDG_SVD_EARLY_SWEEP
+#define PDG_SVD_EARLY_SWEEP 3
+#endif
+
 static __device__ __forceinline__ void jacobi_pair(float& app, float& aqq, float& apq, float& arp, float& arq,
                                             float (&v)[3][3], int p, int q) {
     if (fabsf(apq) < 1e-30f) return;
@@ -99,13 +105,20 @@ static __device__ __forceinline__ void svd3(const float (&F)[3][3], float (&U)[3
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) W[i][j] = (i == j) ? 1.f : 0.f;
-    // four cyclic sweeps reach FP32 rounding (quadratic convergence); a fixed
-    // count keeps the warp convergent
+    // four cyclic sweeps reach FP32 rounding (quadratic convergence); after
+    // the third the sweep loop ends once converged (nearly every element),
+    // which keeps most warps convergent
 #pragma unroll 1
     for (int sweep = 0; sweep < 4; ++sweep) {
         jacobi_pair(a00, a11, a01, a02, a12, W, 0, 1);   // pair (0,1), r = 2
         jacobi_pair(a00, a22, a02, a01, a12, W, 0, 2);   // pair (0,2), r = 1
         jacobi_pair(a11, a22, a12, a01, a02, W, 1, 2);   // pair (1,2), r = 0
+#if PDG_SVD_EARLY_SWEEP > 0
+        // converged to FP32: the off-diagonal is below rounding of the diagonal
+        if (sweep + 1 >= PDG_SVD_EARLY_SWEEP &&
+            a01 * a01 + a02 * a02 + a12 * a12 <= 1e-15f * (a00 * a00 + a11 * a11 + a22 * a22))
+            break;
+#endif
     }
     float l0 = a00, l1 = a11, l2 = a22;
     if (l0 < l1) { float t = l0; l0 = l1; l1 = t; swap_cols(W, 0, 1); }
