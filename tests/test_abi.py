@@ -75,3 +75,20 @@ def test_bad_inputs_are_rejected_before_any_cuda_call(lib):
     assert lib.pd_step(None, None, None, 1, None) == _lib.PD_ERR_INVALID_ARG
     assert lib.pd_prefactor(None, 0.01, None) == _lib.PD_ERR_INVALID_ARG
     assert lib.pd_sync(None) == _lib.PD_ERR_INVALID_ARG
+
+
+def test_fitting_entry_points_reject_bad_arguments_before_any_cuda_call(lib):
+    from paper_2405_12484_gb300 import _lib
+    E = _lib.PD_ERR_INVALID_ARG
+    # null mesh / workspace
+    assert lib.pd_pose_misfit(None, None, None, None, None) == E
+    assert lib.pd_gn_product(None, None, None, None, None, 2.0, None) == E
+    assert lib.pd_gn_direction(None, None, None, None, None, 1e-2, 2.0, 10, None, None) == E
+    opts = _lib.pd_fit_opts(1, 1, 0.01, 1.0, 1e-2, 1e-3, 12, 8, 30, 4, 20, 1.0 / 150, None)
+    rep = _lib.pd_fit_report()
+    assert lib.pd_fit_pose(None, None, C.byref(opts), None, None, None, None, None, None, None, C.byref(rep)) == E
+    assert lib.pd_fit_pose_reduced(None, None, C.byref(opts), None, 1, None, None, None, None, None, None, None,
+                                   C.byref(rep)) == E
+    assert lib.pd_harmonic_basis(None, 4, None, None, None) == E
+    assert lib.pd_test_inflate_copy(None, 16) == E
+    assert len(lib.pd_last_error()) > 0
