@@ -178,3 +178,23 @@ def test_planted_mistake_in_dg_dgamma_is_caught(pose, monkeypatch):
     pins = w.pin_targets(0)
     fd = (_x_of(w, gamma + h * v, pins) - _x_of(w, gamma - h * v, pins)) / (2 * h)
     assert rel(J @ v, fd[gn.o.free].ravel()) > 1e-2
+
+
+def test_pivoting_keeps_the_direction_a_descent_direction():
+    """With a tiny shift the clamped Gauss-Newton direction stops being a
+    descent direction on the softened pose; pivoting removes cached
+    parameters at the floor until it is one again (Sec. 6.3)."""
+    w = slab_workload(4, 4, 2, 0.01, 5, (2, 2), seed=3, n_iter=10, name="gn-pivot")
+    x0, v0, pins = w.rest, np.zeros_like(w.rest), w.pin_targets(0)
+    rng = np.random.default_rng(1)
+    gs_star = w.gamma_s.copy()
+    gs_star[rng.choice(w.n_t, 12, replace=False)] /= 50.0
+    target = _gn(w, gs_star, 10 * gs_star).equilibrium(x0, v0, pins)
+    gs, gv, losses, recs = fit_pose(w.rest, w.tets, w.pinned, w.density, w.dt, x0, v0, pins, target,
+                                    w.gamma_s, w.gamma_v, n_gd=1, n_gn=3, kappa_rel=1e-6)
+    assert recs[-1]["pivots"] > 0
+    assert all(losses[k + 1] < losses[k] for k in range(len(losses) - 1))
+    gamma = np.concatenate([gs, gv])
+    assert gamma.min() >= FLOOR
+    # after the pivots every direction taken is a descent direction
+    assert all(r["descent"] < 0 for r in recs)
