@@ -512,6 +512,14 @@ pd_status pd_submit(pd_server* server, const pd_request* request, pd_request_id*
  */
 pd_status pd_server_tick(pd_server* server, int32_t* n_active, float* frame_ms);
 
+/*
+ * pd_server_run -- pd_server_tick until no request is queued or resident,
+ * at most max_ticks (>= 1) ticks; *ticks (or NULL) receives the ticks run.
+ * Synchronous.  Errors: INVALID_ARG, and those of pd_server_tick (the loop
+ * stops at the first).
+ */
+pd_status pd_server_run(pd_server* server, int32_t max_ticks, int32_t* ticks);
+
 pd_status pd_poll(pd_server* server, pd_request_id id, int32_t* state, int32_t* frames_done);
 /* Final positions (n_v x 3, [host]) and per-frame GPU latencies (n_frames floats, [host]) of a finished request. */
 pd_status pd_fetch(pd_server* server, pd_request_id id, float* x_out, float* frame_ms);

@@ -119,6 +119,7 @@ SIGNATURES = [
     ("pd_server_destroy", None, [C.c_void_p]),
     ("pd_submit", C.c_int32, [C.c_void_p, C.POINTER(pd_request), C.POINTER(C.c_int64)]),
     ("pd_server_tick", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    ("pd_server_run", C.c_int32, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     ("pd_poll", C.c_int32, [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("pd_fetch", C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("pd_release", C.c_int32, [C.c_void_p, C.c_int64]),

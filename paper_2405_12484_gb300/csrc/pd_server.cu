@@ -433,6 +433,21 @@ pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
     return PD_OK;
 }
 
+pd_status pd_server_run(pd_server* S, int32_t max_ticks, int32_t* ticks) {
+    if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
+    if (max_ticks < 1) return sfail(PD_ERR_INVALID_ARG, "max_ticks must be >= 1");
+    int32_t t = 0;
+    for (; t < max_ticks && (!S->queue.empty() || !S->active.empty()); ++t) {
+        const pd_status st = pd_server_tick(S, nullptr, nullptr);
+        if (st != PD_OK) {
+            if (ticks) *ticks = t;
+            return st;
+        }
+    }
+    if (ticks) *ticks = t;
+    return PD_OK;
+}
+
 pd_status pd_poll(pd_server* S, pd_request_id id, int32_t* state, int32_t* frames_done) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
     auto it = S->reqs.find(id);

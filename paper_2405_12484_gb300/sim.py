@@ -388,6 +388,12 @@ class Server:
         _check(lib().pd_server_tick(self._h, C.byref(n), C.byref(ms)), "pd_server_tick")
         return n.value, ms.value
 
+    def run(self, max_ticks=100000):
+        """Tick until no request is queued or resident; returns the ticks run."""
+        t = C.c_int32()
+        _check(lib().pd_server_run(self._h, int(max_ticks), C.byref(t)), "pd_server_run")
+        return t.value
+
     def poll(self, rid):
         st, fd = C.c_int32(), C.c_int32()
         _check(lib().pd_poll(self._h, int(rid), C.byref(st), C.byref(fd)), "pd_poll")

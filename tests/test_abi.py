@@ -91,4 +91,5 @@ def test_fitting_entry_points_reject_bad_arguments_before_any_cuda_call(lib):
                                    C.byref(rep)) == E
     assert lib.pd_harmonic_basis(None, 4, None, None, None) == E
     assert lib.pd_test_inflate_copy(None, 16) == E
+    assert lib.pd_server_run(None, 10, None) == E
     assert len(lib.pd_last_error()) > 0
