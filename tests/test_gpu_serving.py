@@ -103,3 +103,20 @@ def test_admission_waits_for_the_hbm_budget():
     assert max_active < len(reqs)
     for k in range(len(reqs)):
         assert np.array_equal(alone[k], mix[k])
+
+
+def test_run_until_idle_matches_ticking():
+    """pd_server_run ticks until nothing is queued or resident; the results are
+    the ones the tick-by-tick loop gives (bitwise)."""
+    from paper_2405_12484_gb300.sim import Server
+    reqs = _requests()[:2]
+    frames = 4
+    ticked, _, _ = _run(reqs, frames, stagger=False)
+    S = Server(1 << 34, max_slots=16, n_iter=20)
+    ids = [S.submit(w, frames, drive) for w, drive in reqs]
+    ticks = S.run()
+    assert ticks >= frames
+    assert all(S.poll(i)[0] == 2 for i in ids)
+    for k, i in enumerate(ids):
+        assert np.array_equal(S.fetch(i)[0], ticked[k])
+    S.close()
