@@ -339,6 +339,29 @@ pd_status pd_residual(pd_mesh* mesh, const float* x, const float* x_prev, const 
 pd_status pd_pose_misfit(pd_mesh* mesh, const float* x, const float* target, float* dL_dx, double* loss);
 
 /*
+ * pd_pose_misfit_accumulate -- as pd_pose_misfit, but *loss += eps: the
+ * trajectory loss L = sum_n sum_free ||x_n - xhat_n||^2 of the adjoint
+ * gradient (Sec. 6.1, the pose-matching objective over a sequence of
+ * poses) summed on the device over the steps.  Asynchronous.  Errors: INVALID_ARG.
+ */
+pd_status pd_pose_misfit_accumulate(pd_mesh* mesh, const float* x, const float* target, float* dL_dx,
+                                    double* loss);
+
+/*
+ * pd_tied_gradient -- the gradient for one stiffness parameter per element
+ * with the volume weight tied to it (gamma_s = theta, gamma_v = ratio theta;
+ * Sec. 6's per-element gamma with a fixed volume-to-strain ratio):
+ * dL/dtheta = scale (dL/dgamma_s + ratio dL/dgamma_v), evaluated in FP64.
+ *   dL_dgamma_s, dL_dgamma_v [device] n_t floats (as pd_adjoint_step gives them).
+ *   scale     [device] one double (e.g. the incoming gradient of a composite
+ *             loss), or NULL for 1.
+ *   dL_dtheta [device] n_t floats out.
+ * Asynchronous on the mesh stream.  Errors: INVALID_ARG.
+ */
+pd_status pd_tied_gradient(pd_mesh* mesh, const float* dL_dgamma_s, const float* dL_dgamma_v, double ratio,
+                           const double* scale, float* dL_dtheta);
+
+/*
  * pd_gn_product -- P v, P = J^T G J with J = dx/dgamma = -H^-1 B
  * (Eq. pxpgamma; H = dg/dx, B = dg/dgamma) and G = g_scale I: the matrix of
  * Eq. gn, applied through the eliminated block system of Eq. agn:
@@ -504,7 +527,10 @@ pd_status pd_submit(pd_server* server, const pd_request* request, pd_request_id*
 /*
  * pd_server_tick -- retire requests that finished, admit queued requests
  * in arrival order while slots and the budget allow (mesh set-up and FP64
- * prefactorisation on the device), then advance every resident request by
+ * prefactorisation on the device; a request that does not fit the budget
+ * even with nothing resident is marked PD_REQ_FAILED and leaves the queue;
+ * one that must wait for resident requests to retire keeps its first
+ * memory estimate and is not rebuilt), then advance every resident request by
  * one frame in shared batched launches (one captured CUDA graph per set of
  * resident requests; the local steps, assemblies and subspace solves of all
  * requests run in the same kernels).  Synchronous; *frame_ms receives the
@@ -515,8 +541,9 @@ pd_status pd_server_tick(pd_server* server, int32_t* n_active, float* frame_ms);
 /*
  * pd_server_run -- pd_server_tick until no request is queued or resident,
  * at most max_ticks (>= 1) ticks; *ticks (or NULL) receives the ticks run.
- * Synchronous.  Errors: INVALID_ARG, and those of pd_server_tick (the loop
- * stops at the first).
+ * Synchronous.  Errors: INVALID_ARG; TIMEOUT when max_ticks ticks ran and
+ * requests are still queued or resident; and those of pd_server_tick (the
+ * loop stops at the first).
  */
 pd_status pd_server_run(pd_server* server, int32_t max_ticks, int32_t* ticks);
 
@@ -540,9 +567,13 @@ pd_status pd_server_stats(pd_server* server, int32_t* n_queued, int32_t* n_activ
  * Every temporary comes from one file-scope device array of 16 MiB
  * (16777216 bytes) that each GPU loading this library holds until the
  * process exits; a mesh whose temporaries exceed it is rejected with
- * PD_ERR_UNSUPPORTED (pd_last_error gives the bytes needed).  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress);
- * make it before any stream capture.  All calls share the one array, which
+ * PD_ERR_UNSUPPORTED (pd_last_error gives the bytes needed).  The array's
+ * device address is looked up (cudaGetSymbolAddress) once per device by
+ * pd_prefactor, which is also when the CUDA runtime, loading modules lazily,
+ * takes the 16 MiB from that device; after pd_prefactor, pd_solve_noalloc
+ * takes no device memory.  (Only a call on a device where no pd_prefactor
+ * ran makes the lookup itself; such a call must come before any stream
+ * capture.)  All calls share the one array, which
  * keeps the last call's contents (the solution buffer is cleared on entry):
  * calls that overlap on the GPU -- from two host threads, or on two meshes
  * with different streams -- race and must be serialised by the caller.

@@ -497,9 +497,21 @@ __global__ void __launch_bounds__(256) k_pdot_final(int nb, const double* __rest
     } else if (op == 2) {
         sc[G_BETA] = sc[G_RR] > 0.0 ? v / sc[G_RR] : 0.0;
         sc[G_RR] = v;
+    } else if (op == 4) {
+        sc[dst] += v;   // accumulated (a loss summed over time steps)
     } else {
         sc[G_KAPPA] = sc[G_RR] > 0.0 ? kr * v / sc[G_RR] : 0.0;
     }
+}
+
+// tied parameterisation gamma_s = theta, gamma_v = ratio theta:
+// dL/dtheta = scale (dL/dgamma_s + ratio dL/dgamma_v), in FP64, scale from the device (or 1)
+__global__ void k_tied_gradient(int n, const float* __restrict__ gs, const float* __restrict__ gv, double ratio,
+                                const double* __restrict__ scale, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double f = scale ? scale[0] : 1.0;
+    out[i] = (float)(((double)gs[i] + ratio * (double)gv[i]) * f);
 }
 
 // r = p = -g / |g| on the active parameters (0 elsewhere); d = 0
@@ -896,13 +908,20 @@ void launch_count_below(int n, const float* a, float fl, int* count, cudaStream_
     PDG_CHECK_LAUNCH();
 }
 
-// loss partial sums into partial[0..blocks), then sc[dst] = loss
+// loss partial sums into partial[0..blocks), then sc[dst] = loss (or += loss when accumulate)
 void launch_misfit(int n_free, const float4* x, const float4* xhat, float4* dldx, double* partial, double* sc, int dst,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool accumulate) {
     const int blocks = std::max(1, std::min(kPBlocks, nb(n_free, 256)));
     k_misfit<<<blocks, 256, 0, s>>>(n_free, x, xhat, dldx, partial);
     PDG_CHECK_LAUNCH();
-    k_pdot_final<<<1, 256, 0, s>>>(blocks, partial, 0, 0, dst, 0.0, sc);
+    k_pdot_final<<<1, 256, 0, s>>>(blocks, partial, 0, accumulate ? 4 : 0, dst, 0.0, sc);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_tied_gradient(int n, const float* gs, const float* gv, double ratio, const double* scale, float* out,
+                          cudaStream_t s) {
+    if (n <= 0) return;
+    k_tied_gradient<<<nb(n, 256), 256, 0, s>>>(n, gs, gv, ratio, scale, out);
     PDG_CHECK_LAUNCH();
 }
 

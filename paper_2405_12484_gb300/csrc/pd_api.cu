@@ -1601,6 +1601,12 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         PDG_CUDA(cudaMemset(m->d_err.p, 0, sizeof(int32_t)));
         return fail(PD_ERR_NOT_SPD, "a Cholesky pivot was not positive");
     }
+    // load the fixed scratch array of pd_solve_noalloc on this device now,
+    // while allocation is allowed (the runtime loads device modules lazily)
+    {
+        const pd_status ns = noalloc_prepare_device();
+        if (ns != PD_OK) return ns;
+    }
     m->dt = dt;
     m->prefactored = true;
     m->prefactor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

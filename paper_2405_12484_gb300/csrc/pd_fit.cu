@@ -43,7 +43,9 @@ void launch_pick_pivot(int n, const float* gamma, const float* raw, const uint8_
                        float fl, double* pval, int* pidx, int* out, cudaStream_t s);
 void launch_pcopy(int n, float sign, const float* a, const uint8_t* active, float* out, cudaStream_t s);
 void launch_misfit(int n_free, const float4* x, const float4* xhat, float4* dldx, double* partial, double* sc, int dst,
-                   cudaStream_t s);
+                   cudaStream_t s, bool accumulate = false);
+void launch_tied_gradient(int n, const float* gs, const float* gv, double ratio, const double* scale, float* out,
+                          cudaStream_t s);
 void launch_basis_t(int n_t, int r, const float* H, const float* w, double* out, cudaStream_t s);
 void launch_basis_apply(int n_t, int r, const float* H, const double* q, float* out, cudaStream_t s);
 void launch_basis_col(int n_t, int r, const float* H, int j, float* out, cudaStream_t s);
@@ -125,7 +127,8 @@ static bool check_mesh(pd_mesh* m, pd_adjoint* a) { return m && a && a->mesh == 
 
 extern "C" {
 
-pd_status pd_pose_misfit(pd_mesh* m, const float* x, const float* target, float* dL_dx, double* loss) {
+static pd_status pose_misfit(pd_mesh* m, const float* x, const float* target, float* dL_dx, double* loss,
+                             bool accumulate) {
     if (!m || !x || !target || !loss) return ffail(PD_ERR_INVALID_ARG, "null argument");
     try {
         cudaStream_t s = m->stream;
@@ -140,9 +143,29 @@ pd_status pd_pose_misfit(pd_mesh* m, const float* x, const float* target, float*
             gi.alloc(m->n_v);
             PDG_CUDA(cudaMemsetAsync(gi.p, 0, sizeof(float4) * m->n_v, s));
         }
-        launch_misfit(m->n_free, xi.p, ti.p, dL_dx ? gi.p : nullptr, part.p, loss, 0, s);
+        launch_misfit(m->n_free, xi.p, ti.p, dL_dx ? gi.p : nullptr, part.p, loss, 0, s, accumulate);
         if (dL_dx) launch_scatter_out(m, gi.p, dL_dx, 0, s);
         PDG_CUDA(cudaStreamSynchronize(s));   // the temporaries are freed on return
+    } catch (const Fail& f) {
+        return f.code;
+    }
+    return PD_OK;
+}
+
+pd_status pd_pose_misfit(pd_mesh* m, const float* x, const float* target, float* dL_dx, double* loss) {
+    return pose_misfit(m, x, target, dL_dx, loss, false);
+}
+
+pd_status pd_pose_misfit_accumulate(pd_mesh* m, const float* x, const float* target, float* dL_dx, double* loss) {
+    return pose_misfit(m, x, target, dL_dx, loss, true);
+}
+
+pd_status pd_tied_gradient(pd_mesh* m, const float* dL_dgamma_s, const float* dL_dgamma_v, double ratio,
+                           const double* scale, float* dL_dtheta) {
+    if (!m || !dL_dgamma_s || !dL_dgamma_v || !dL_dtheta) return ffail(PD_ERR_INVALID_ARG, "null argument");
+    if (!std::isfinite(ratio)) return ffail(PD_ERR_INVALID_ARG, "ratio must be finite");
+    try {
+        launch_tied_gradient(m->n_t, dL_dgamma_s, dL_dgamma_v, ratio, scale, dL_dtheta, m->stream);
     } catch (const Fail& f) {
         return f.code;
     }

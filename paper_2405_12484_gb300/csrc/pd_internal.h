@@ -504,6 +504,10 @@ void dense_gemm(bool ta, bool tb, int M, int N, int K, double alpha, const doubl
                 int64_t sC, int batch, bool lower_only, cudaStream_t s);
 void dense_set_identity(double* A, int n, int lda, int64_t strideA, int batch, cudaStream_t s);
 
+// Resolves the fixed scratch array of pd_solve_noalloc on the current device
+// (loads its module; called by pd_prefactor while allocation is allowed).
+pd_status noalloc_prepare_device();
+
 // timing helpers (no-ops unless the phase is in the mesh's timing mask)
 void phase_begin(pd_mesh* m, int phase, cudaStream_t s);
 void phase_end(pd_mesh* m, cudaStream_t s);

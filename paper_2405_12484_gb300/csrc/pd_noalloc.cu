@@ -12,8 +12,13 @@
 // (16 MiB).  Every GPU on which this library is loaded holds it until the
 // process exits.  Host code must not use the array's name as a device
 // address; its device address is obtained once per device with
-// cudaGetSymbolAddress, on the first call made on that device (so make that
-// first call before any stream capture begins).
+// cudaGetSymbolAddress.  That lookup loads this file's device module (the
+// CUDA runtime loads modules lazily), which is when the 16 MiB is actually
+// taken from the device; pd_prefactor therefore makes it, on the mesh's
+// device, while allocation is still allowed, and pd_solve_noalloc itself
+// only reads the cached address.  A call on a device where no pd_prefactor
+// has run yet makes the lookup itself (and so may take the 16 MiB then);
+// such a first call must come before any stream capture.
 #include <mutex>
 
 #include "pd_internal.h"
@@ -36,7 +41,46 @@ void* g_scratch_addr[kMaxDevices] = {nullptr};
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
+// Device address of the scratch array on the current device (looked up and
+// cached on first use).  Returns nullptr after recording the error.
+unsigned char* scratch_base(pd_status* code) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_error(std::string("pd_solve_noalloc: cudaGetDevice failed: ") + cudaGetErrorString(e));
+        *code = PD_ERR_CUDA;
+        return nullptr;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("pd_solve_noalloc: device ordinal out of range");
+        *code = PD_ERR_UNSUPPORTED;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            set_error(std::string("pd_solve_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+            *code = PD_ERR_CUDA;
+            return nullptr;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    return static_cast<unsigned char*>(g_scratch_addr[dev]);
+}
+
 }  // namespace
+
+// Called by pd_prefactor on the mesh's device: resolves (and so loads) the
+// scratch array there, so that later pd_solve_noalloc calls take no device
+// memory at all.
+pd_status noalloc_prepare_device() {
+    pd_status code = PD_OK;
+    return scratch_base(&code) ? PD_OK : code;
+}
+
 }  // namespace pdg
 
 using namespace pdg;
@@ -82,26 +126,9 @@ extern "C" pd_status pd_solve_noalloc(pd_mesh* m, const float* r, float* x) {
         return PD_ERR_UNSUPPORTED;
     }
     try {
-        int dev = 0;
-        PDG_CUDA(cudaGetDevice(&dev));
-        if (dev < 0 || dev >= kMaxDevices) {
-            set_error("pd_solve_noalloc: device ordinal out of range");
-            return PD_ERR_UNSUPPORTED;
-        }
-        unsigned char* base = nullptr;
-        {
-            std::lock_guard<std::mutex> lk(g_setup_mu);
-            if (!g_scratch_addr[dev]) {
-                void* p = nullptr;
-                cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-                if (e != cudaSuccess || !p) {
-                    set_error(std::string("pd_solve_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-                    return PD_ERR_CUDA;
-                }
-                g_scratch_addr[dev] = p;
-            }
-            base = static_cast<unsigned char*>(g_scratch_addr[dev]);
-        }
+        pd_status code = PD_OK;
+        unsigned char* base = scratch_base(&code);
+        if (!base) return code;
         float4* ri = reinterpret_cast<float4*>(base + off_r);
         float4* xi = reinterpret_cast<float4*>(base + off_x);
         float4* tc = reinterpret_cast<float4*>(base + off_tc);

@@ -48,6 +48,10 @@ struct Request {
     int32_t state = PD_REQ_QUEUED;
     pd_mesh* mesh = nullptr;
     int64_t steady_bytes = 0;
+    // device-memory estimate from the first build of the mesh (kept while the
+    // request waits, so that it is not rebuilt at every tick)
+    bool estimated = false;
+    int64_t est_steady = 0, est_transient = 0;
     DBuf<float4> pin_rest;
     DBuf<int32_t> frame;
     int32_t frames_done = 0;
@@ -264,8 +268,17 @@ static void rebuild(pd_server* S) {
     PDG_CUDA(e);
 }
 
+// Admits the request at the head of the queue if the budget allows.  Returns
+// true when the request leaves the queue (admitted, or failed: it can never
+// fit, or its mesh or factorisation failed), false when it must wait for
+// resident requests to retire.
 static bool admit(pd_server* S, Request& R) {
-    // build and factor on the device; false if it does not fit the budget now
+    // a request seen before waits on its cached estimate without being rebuilt
+    if (R.estimated && S->used + R.est_steady + R.est_transient > S->budget) {
+        if (!S->active.empty()) return false;
+        R.state = PD_REQ_FAILED;
+        return true;
+    }
     pd_mesh* m = nullptr;
     pd_status st = pd_create_mesh(R.rest.data(), R.n_v, R.tets.data(), R.n_t, nullptr, R.density,
                                   R.dom.empty() ? nullptr : R.dom.data(), R.n_dom,
@@ -274,11 +287,19 @@ static bool admit(pd_server* S, Request& R) {
         R.state = PD_REQ_FAILED;
         return true;
     }
+    R.mesh = m;   // owned by the request from here on (destroyed with it on any failure)
     int64_t steady = 0, transient = 0;
     estimate(m, steady, transient);
+    R.estimated = true;
+    R.est_steady = steady;
+    R.est_transient = transient;
     if (S->used + steady + transient > S->budget) {
         pd_destroy_mesh(m);
-        return false;
+        R.mesh = nullptr;
+        if (!S->active.empty()) return false;   // waits for resident requests to retire
+        // nothing is resident and it still does not fit: it never will
+        R.state = PD_REQ_FAILED;
+        return true;
     }
     st = pd_set_materials(m, R.gs.data(), R.gv.data());
     pd_solver_opts o{PD_PREC_FP32, 0, 0, PD_SOLVE_SINGLE_LEVEL};  // the batched coarse kernel is single-level
@@ -286,13 +307,14 @@ static bool admit(pd_server* S, Request& R) {
     if (st == PD_OK) st = pd_prefactor(m, R.dt, &o);
     if (st != PD_OK) {
         pd_destroy_mesh(m);
+        R.mesh = nullptr;
         R.state = PD_REQ_FAILED;
         return true;
     }
-    R.mesh = m;
     R.steady_bytes = steady;
     S->peak = std::max(S->peak, S->used + steady + transient);
     S->used += steady;
+    R.state = PD_REQ_ACTIVE;   // resident: retired (and its bytes returned) like any other from here on
     // pinned rest positions (increasing vertex id) and the frame counter
     std::vector<float4> pr;
     for (int32_t v = 0; v < R.n_v; ++v)
@@ -305,7 +327,6 @@ static bool admit(pd_server* S, Request& R) {
                                  S->stream));
     R.frame.alloc(1);
     PDG_CUDA(cudaMemsetAsync(R.frame.p, 0, sizeof(int32_t), S->stream));
-    R.state = PD_REQ_ACTIVE;
     return true;
 }
 
@@ -429,6 +450,10 @@ pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
         if (frame_ms) *frame_ms = ms;
     } catch (const Fail& f) {
         return f.code;
+    } catch (const std::bad_alloc&) {
+        return sfail(PD_ERR_NO_MEMORY, "pd_server_tick: host allocation failed");
+    } catch (...) {
+        return sfail(PD_ERR_CUDA, "pd_server_tick: unexpected host exception");
     }
     return PD_OK;
 }
@@ -445,6 +470,8 @@ pd_status pd_server_run(pd_server* S, int32_t max_ticks, int32_t* ticks) {
         }
     }
     if (ticks) *ticks = t;
+    if (!S->queue.empty() || !S->active.empty())
+        return sfail(PD_ERR_TIMEOUT, "pd_server_run: max_ticks ticks ran and requests are still queued or resident");
     return PD_OK;
 }
 

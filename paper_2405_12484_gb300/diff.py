@@ -36,8 +36,6 @@ class DiffSim:
         self.x0 = torch.as_tensor(np.asarray(rest if x0 is None else x0), dtype=torch.float32, device="cuda")
         self.v0 = torch.zeros((n_v, 3), device="cuda") if v0 is None else torch.as_tensor(v0, dtype=torch.float32,
                                                                                             device="cuda")
-        pinned = np.zeros(n_v, bool) if pinned is None else np.asarray(pinned, bool)
-        self.free = torch.as_tensor(~pinned, device="cuda")
         self._pins_dev = [None] * self.N
 
     def _pin(self, n):
@@ -58,17 +56,16 @@ class DiffSim:
         m.set_state(self.x0, self.v0)
         ckpts = {0: (self.x0.clone(), self.v0.clone())}
         stored = [] if self.store_all else None
-        loss = torch.zeros((), device="cuda", dtype=torch.float64)
+        loss = torch.zeros(1, device="cuda", dtype=torch.float64)
         x = torch.empty((m.n_v, 3), device="cuda")
         for n in range(self.N):
             a.equilibrium_step(self._pin(n), self.gravity, self.n_pd, self.n_newton, x_out=x)
-            d = (x - targets[n + 1])[self.free]
-            loss = loss + (d.double() ** 2).sum()
+            a.pose_misfit_accumulate(x, targets[n + 1], loss)
             if stored is not None:
                 stored.append(x.clone())
             if (n + 1) % self.C == 0 and n + 1 < self.N:
                 ckpts[n + 1] = tuple(t.clone() for t in m.get_state())
-        return loss, ckpts, stored
+        return loss.reshape(()), ckpts, stored
 
     def backward(self, ckpts, stored, targets):
         m, a = self.mesh, self.adj
@@ -76,6 +73,8 @@ class DiffSim:
         gv = torch.zeros(m.n_t, device="cuda")
         a.reset()
         x = torch.empty((m.n_v, 3), device="cuda")
+        dl = torch.empty((m.n_v, 3), device="cuda")
+        scratch = torch.zeros(1, device="cuda", dtype=torch.float64)
         for start in sorted(ckpts, reverse=True):
             end = min(start + self.C, self.N)
             if stored is not None:
@@ -88,8 +87,7 @@ class DiffSim:
                     xs.append(x.clone())
             for n in range(end - 1, start - 1, -1):
                 xn = xs[n - start]
-                dl = 2.0 * (xn - targets[n + 1])
-                dl[~self.free] = 0.0
+                a.pose_misfit_accumulate(xn, targets[n + 1], scratch, dl)   # dL/dx_n = 2 (x_n - xhat_n), 0 on pins
                 a.step(xn, dl, gs, gv)
         return gs, gv
 
@@ -108,8 +106,8 @@ class PoseLoss(torch.autograd.Function):
     def backward(ctx, grad_out):
         sim = ctx.sim
         gs, gv = sim.backward(ctx.ckpts, ctx.stored, ctx.targets)
-        g = (gs.double() + sim.ratio * gv.double()) * grad_out.to(device=gs.device, dtype=torch.float64)
-        return g.to(device=ctx.theta_device, dtype=torch.float32), None, None
+        g = sim.adj.tied_gradient(gs, gv, sim.ratio, scale=grad_out)
+        return g.to(device=ctx.theta_device), None, None
 
 
 def pose_loss(theta: torch.Tensor, sim: DiffSim, targets) -> torch.Tensor:

@@ -242,6 +242,24 @@ class Adjoint:
         _check(lib().pd_pose_misfit(m._h, _ptr(xt), _ptr(tt), _ptr(g), _ptr(loss)), "pd_pose_misfit")
         return loss, g
 
+    def pose_misfit_accumulate(self, x, target, loss, dl=None):
+        """loss (device float64, shape (1,)) += sum_free ||x - target||^2; dl (or None) <- 2 (x - target)."""
+        m = self.mesh
+        xt, tt = _dev_f32(x, (m.n_v, 3)), _dev_f32(target, (m.n_v, 3))
+        _check(lib().pd_pose_misfit_accumulate(m._h, _ptr(xt), _ptr(tt), _ptr(dl), _ptr(loss)),
+               "pd_pose_misfit_accumulate")
+        return loss
+
+    def tied_gradient(self, gs, gv, ratio, scale=None):
+        """dL/dtheta = scale (dL/dgamma_s + ratio dL/dgamma_v) for gamma_s = theta, gamma_v = ratio theta;
+        scale is a device float64 tensor of one element or None."""
+        m = self.mesh
+        out = torch.empty(m.n_t, device="cuda", dtype=torch.float32)
+        sc = None if scale is None else scale.to(device="cuda", dtype=torch.float64).reshape(1).contiguous()
+        _check(lib().pd_tied_gradient(m._h, _ptr(gs), _ptr(gv), float(ratio), _ptr(sc), _ptr(out)),
+               "pd_tied_gradient")
+        return out
+
     def gn_product(self, x, v, active=None, g_scale=2.0):
         m = self.mesh
         xt = _dev_f32(x, (m.n_v, 3))

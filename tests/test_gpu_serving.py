@@ -120,3 +120,37 @@ def test_run_until_idle_matches_ticking():
     for k, i in enumerate(ids):
         assert np.array_equal(S.fetch(i)[0], ticked[k])
     S.close()
+
+
+def test_request_larger_than_the_whole_budget_fails_and_leaves_the_queue():
+    """A request that would not fit the HBM budget even with nothing resident
+    is marked failed at once (it is not retried every tick), and the request
+    behind it is served."""
+    from paper_2405_12484_gb300.sim import Server
+    reqs = _requests()
+    small, big = reqs[0], reqs[1]
+    st = {}
+    _run([small], 2, stats=st)
+    S = Server(int(1.05 * st["peak"]), max_slots=16, n_iter=20)
+    i_big = S.submit(big[0], 2, big[1])
+    i_small = S.submit(small[0], 2, small[1])
+    ticks = S.run(max_ticks=50)
+    assert S.poll(i_big)[0] == 3
+    assert S.poll(i_small)[0] == 2
+    assert ticks <= 4
+    S.close()
+
+
+def test_run_reports_outstanding_work_after_max_ticks():
+    from paper_2405_12484_gb300 import _lib
+    from paper_2405_12484_gb300.sim import Server
+    w, drive = _requests()[0]
+    S = Server(1 << 34, max_slots=16, n_iter=20)
+    i = S.submit(w, 5, drive)
+    with pytest.raises(_lib.PDError) as e:
+        S.run(max_ticks=2)
+    assert e.value.status == _lib.PD_ERR_TIMEOUT
+    assert S.poll(i)[0] == 1
+    assert S.run() >= 1
+    assert S.poll(i)[0] == 2
+    S.close()
