@@ -3,18 +3,24 @@
 
 One step = one frame of the sweater-scale shell (325 x 100 x 2 hexes x 6 =
 390,000 tets, 98,475 vertices, 200 domains), 20 PD iterations, dt = 1/150 s,
-driven collar: inertia, then 20 x (local step, RHS assembly, subspace solve),
-then the velocity update, all in libpdgb300's kernels.
+driven collar: inertia, then 20 x (fused local step and RHS assembly,
+subspace solve), then the velocity update, all in libpdgb300's kernels.
 
-Prints one JSON line.  `value` is PD iterations per second (whole job);
-`ms_per_step` is ms per frame.  `--impl reference` times the FP64 CPU
-oracle on the same workload instead (the reference arm of this method).
+Prints one JSON line.  `value` is PD iterations per second (whole job) of
+the FP32 solve; `ms_per_step` is ms per frame.  The same line carries the
+mixed-precision leg (BF16 matrices on the tensor cores in the correction
+form), the frame-0 error of both against the FP64 oracle (computed on the
+host cores meanwhile), the per-phase bytes and rates, the end-to-end rate
+with host copies, the serving stream and the CPU baseline.  `--impl
+reference` times the FP64 CPU oracle on the same workload instead (the
+reference arm of this method).
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -50,11 +56,14 @@ def parse():
     p.add_argument("--iters", type=int, default=20, help="PD iterations per frame")
     p.add_argument("--small", action="store_true", help="small shell (profiling captures)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--phase-report", action="store_true", help="also time every phase after the timed region")
-    p.add_argument("--serving", action="store_true",
-                   help="also run the serving stream (64 Poisson requests, 5K-200K tets, 60 frames each)")
+    p.add_argument("--no-serving", action="store_true",
+                   help="skip the serving stream (64 Poisson requests, 5K-200K tets, 60 frames each)")
     p.add_argument("--serving-requests", type=int, default=64)
     p.add_argument("--serving-budget-gib", type=float, default=16.0)
+    p.add_argument("--no-mixed", action="store_true",
+                   help="skip the mixed-precision leg (BF16 matrices on the tensor cores, correction form)")
+    p.add_argument("--no-oracle-check", action="store_true",
+                   help="skip the frame-0 error of each precision against the FP64 oracle")
     return p.parse_args()
 
 
@@ -177,11 +186,25 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline_sample(n_iter_sample: int, small: bool):
-    """Time the FP64 oracle on host cores (single thread, fresh process)."""
-    code = f"""
+def host_info():
+    """Host cores and CPU model (the CPU baseline's hardware)."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    if low.startswith("model name"):
+                        break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model, "machine": platform.machine()}
+
+
+_ORACLE_JOB = """
 import os, sys, time, json
-sys.path.insert(0, {ROOT!r})
+sys.path.insert(0, {root!r})
 import numpy as np
 from bench import workload
 from oracle.pd_oracle import PDOracle
@@ -191,30 +214,76 @@ x = w.rest.copy(); v = np.zeros_like(x)
 y = o.inertial_target(x, v, w.gravity)
 xp = w.pin_targets(0)
 x = y.copy(); x[o.pin_ids] = xp
-t = time.perf_counter()
-for _ in range({n_iter_sample}):
-    R, V = o.local(x)
-    b = o.rhs(y, R, V)
-    x[o.free] = o.global_solve(b, xp)
-dt = time.perf_counter() - t
-print(json.dumps({{"seconds": dt, "iters": {n_iter_sample}}}))
+mode = {mode!r}
+if mode == "frame":
+    # frame 0 from rest with the benchmark's iterations: the FP64 reference of the accuracy check
+    xo, _ = o.step(w.rest, np.zeros_like(w.rest), w.pin_targets(0), w.gravity, {iters})
+    np.save({out!r}, xo)
+    print(json.dumps({{"done": True}}))
+else:
+    t = time.perf_counter()
+    for _ in range({n}):
+        R, V = o.local(x)
+        b = o.rhs(y, R, V)
+        x[o.free] = o.global_solve(b, xp)
+    dt = time.perf_counter() - t
+    print(json.dumps({{"seconds": dt, "iters": {n}}}))
 """
-    env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
-    env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        return None, r.stderr[-500:]
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d, None
+
+
+class OracleJobs:
+    """The FP64 oracle on the host cores, in child processes started before the
+    first CUDA call and run one after the other in a background thread: the
+    timed CPU baseline (3 PD iterations of frame 0, on one thread and on all
+    cores) and the FP64 frame 0 that each precision's first frame is checked
+    against."""
+
+    def __init__(self, small: bool, iters: int, check: bool):
+        import threading
+        self.small, self.iters, self.check = small, iters, check
+        self.results = {}
+        self.out = os.path.join(tempfile.mkdtemp(prefix="pd_oracle_"), "frame0.npy")
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def _one(self, mode, threads, n=3):
+        code = _ORACLE_JOB.format(root=ROOT, small=self.small, mode=mode, iters=self.iters, out=self.out, n=n)
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = str(threads)
+        env["CUDA_VISIBLE_DEVICES"] = ""
+        try:
+            r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+        except subprocess.TimeoutExpired:
+            return None, "timeout"
+        if r.returncode != 0:
+            return None, r.stderr[-400:]
+        return json.loads(r.stdout.strip().splitlines()[-1]), None
+
+    def _run(self):
+        self.results["one_thread"] = self._one("sample", 1)
+        self.results["all_cores"] = self._one("sample", os.cpu_count() or 1)
+        if self.check:
+            self.results["frame"] = self._one("frame", os.cpu_count() or 1)
+
+    def join(self, timeout=600):
+        self.thread.join(timeout)
+        return self.results
+
+    def frame0(self):
+        import numpy as np
+        d = self.results.get("frame", (None, "not run"))[0]
+        return np.load(self.out) if d and os.path.exists(self.out) else None
 
 
 def run_serving(args):
-    """Serving stream: Poisson arrivals of garment requests of mixed sizes, continuous batching.
-
-    Returns a dict with p50/p99 frame latency, aggregate tets*iters/s and the
-    same requests run one at a time on the plain FP32 stepper."""
+    """Serving stream: Poisson arrivals of garment requests of mixed sizes,
+    continuous batching (admission in the background while resident requests
+    advance).  Returns the per-request frame latency (wall time between a
+    request's frames, every stall included) p50/p99, the GPU time of the
+    batched frames, aggregate tets*iters/s over the wall time, and the same
+    requests run one at a time on the single-mesh stepper (mesh set-up and
+    prefactorisation included, as the server's wall time includes them)."""
     import numpy as np
     import torch
 
@@ -231,7 +300,7 @@ def run_serving(args):
     S = Server(budget, max_slots=64, n_iter=20)
     t0 = time.perf_counter()
     subs, pending = [], list(works)        # subs: (request id, n_tets, arrival)
-    frame_ms, active_hist = [], []
+    gpu_ms, active_hist = [], []
 
     def unfinished():
         return any(S.poll(i)[0] in (0, 1) for i, _, _ in subs)
@@ -243,18 +312,25 @@ def run_serving(args):
             subs.append((S.submit(w, frames, d), w.n_t, a))
         n, ms = S.tick()
         if n > 0:
-            frame_ms.append(ms)
+            gpu_ms.append(ms)
             active_hist.append(n)
-        elif pending:
+        elif pending and not subs:
             time.sleep(min(0.002, max(0.0, pending[0][0] - (time.perf_counter() - t0))))
     wall = time.perf_counter() - t0
+    lat = []
+    failed = 0
+    for i, _, _ in subs:
+        if S.poll(i)[0] == 2:
+            lat.extend(S.fetch(i)[1].tolist())
+        else:
+            failed += 1
     tet_iters = sum(nt for _, nt, _ in subs) * frames * 20
-    lat = sorted(frame_ms)
+    stats = S.stats()
     S.close()
-    # one at a time, plain single-mesh stepper
+    # one at a time, plain single-mesh stepper (set-up and prefactorisation included)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    gpu_ms = 0.0
+    seq_gpu_ms = 0.0
     for _, w, d in works:
         m = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density)
         m.set_materials(w.gamma_s, w.gamma_v)
@@ -267,28 +343,41 @@ def run_serving(args):
             m.step(pins[n], w.gravity, 20)
         e1.record()
         e1.synchronize()
-        gpu_ms += e0.elapsed_time(e1)
+        seq_gpu_ms += e0.elapsed_time(e1)
         m.close()
     wall_seq = time.perf_counter() - t1
-    return {"requests": len(works), "frames_per_request": frames, "pd_iters_per_frame": 20,
-            "hbm_budget_gib": args.serving_budget_gib,
-            "frame_ms_p50": lat[len(lat) // 2], "frame_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+    return {"requests": len(works), "failed": failed, "frames_per_request": frames, "pd_iters_per_frame": 20,
+            "hbm_budget_gib": args.serving_budget_gib, "peak_budgeted_gib": stats["peak_bytes"] / (1 << 30),
+            "frame_latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": max(lat),
+                                 "what": "per request, wall time between its frames (stalls included)"},
+            "batched_frame_gpu_ms": {"p50": pct(gpu_ms, 0.5), "p99": pct(gpu_ms, 0.99)},
             "mean_resident": float(np.mean(active_hist)), "max_resident": int(max(active_hist)),
             "wall_s": wall, "tet_iters_per_s_wall": tet_iters / wall,
-            "tet_iters_per_s_gpu": tet_iters / (sum(frame_ms) / 1e3),
-            "one_at_a_time": {"wall_s": wall_seq, "gpu_frame_s": gpu_ms / 1e3,
-                              "tet_iters_per_s_gpu": tet_iters / (gpu_ms / 1e3),
+            "tet_iters_per_s_gpu": tet_iters / (sum(gpu_ms) / 1e3),
+            "one_at_a_time": {"wall_s": wall_seq, "gpu_frame_s": seq_gpu_ms / 1e3,
+                              "tet_iters_per_s_gpu": tet_iters / (seq_gpu_ms / 1e3),
                               "tet_iters_per_s_wall": tet_iters / wall_seq}}
 
 
+def workload_config(w, args, world):
+    """The `config` of both arms: the workload, not the implementation."""
+    return {"workload": (f"{w.name}: 390,000-tet thick cylindrical shell, 98,475 vertices, 200 domains"
+                         if not args.small else f"{w.name} (small profiling case)"),
+            "pd_iters_per_frame": args.iters, "dt": w.dt,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "per-iteration working set > 129 MB L2 (the solve's matrices alone > 0.3 GB): no flush needed"}
+
+
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle, each step one PD iteration of frame 0."""
+    """Reference arm: the FP64 CPU oracle.  A frame of the workload (20 PD
+    iterations, ~75 s on one host core) is too long for a timed step, so a
+    step is one PD iteration of frame 0 (the bounded sample): value = PD
+    iterations/s, ms_per_step = ms per such step."""
     if rank != 0:
         return
     import numpy as np
 
     from oracle.pd_oracle import PDOracle
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     w = workload(args.small)
     o = PDOracle(w.rest, w.tets, w.pinned, w.gamma_s, w.gamma_v, w.density, w.dt)
     x = w.rest.copy()
@@ -310,18 +399,95 @@ def run_reference(args, rank, world):
         one()
     sec = time.perf_counter() - t
     value = args.steps / sec
+    hi = host_info()
+    sample = f"each step: 1 PD iteration of frame 0 of the same workload (FP64, 1 thread); {args.steps} steps"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps * args.iters,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name + " (390,000 tets, 98,475 vertices)", "pd_iters_per_frame": args.iters,
-                   "dt": w.dt, "solver": "FP64 oracle, banded Cholesky of the full matrix"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} PD iterations of frame 0 (each step = 1 iteration)"},
+        "config": workload_config(w, args, world),
+        "step": "one PD iteration (a frame is pd_iters_per_frame of them)",
+        "solver": "FP64 oracle: banded Cholesky of the full matrix",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "nproc": hi["nproc"], "cpu": hi["cpu"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
     print(json.dumps(line))
+
+
+def time_leg(m, w, info, pins, n_iter, K, W, stream, local, world, phase_report=True):
+    """Warm-up with every phase timed (the phase with the largest time per
+    frame is the dominant kernel), then K frames timed with CUDA events on the
+    mesh's stream (only the dominant kernel carries events), clocks sampled
+    meanwhile; then the per-phase report.  Returns a dict."""
+    import torch
+    from paper_2405_12484_gb300.sim import phase_bit
+    m.enable_timing(-1)
+    for n in range(W):
+        m.step(pins[n], w.gravity, n_iter)
+    m.sync()
+    warm = m.phase_times()
+    per_iter = {k: v for k, v in warm.items() if k not in ("inertia", "velocity") and v > 0}
+    t_max = max(per_iter.values())
+    # near-ties (kernels that run side by side): the one streaming the most bytes
+    dominant = max((k for k, v in per_iter.items() if v >= 0.9 * t_max), key=lambda k: info["phase_bytes"][k])
+    m.enable_timing(phase_bit(dominant))
+    for n in range(2):
+        m.step(pins[n], w.gravity, n_iter)
+    m.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev[0].record(stream)
+    for k in range(K):
+        m.step(pins[W + k], w.gravity, n_iter)
+        ev[k + 1].record(stream)
+    ev[K].synchronize()
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    barrier(world)
+    m.sync()
+    frame_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+    total_ms = ev[0].elapsed_time(ev[K])
+    phase = m.phase_times()
+    out = {"dominant": dominant, "dom_ms": phase.get(dominant, 0.0), "frame_ms": frame_ms, "total_ms": total_ms,
+           "clocks": clock_info}
+    if phase_report:
+        peak, _ = measured_peaks()
+        m.enable_timing(-1)
+        for n in range(3):
+            m.step(pins[n], w.gravity, n_iter)
+        pt = m.phase_times()
+        out["phases"] = {}
+        for k, ms in pt.items():
+            if ms > 0:
+                by = info["phase_bytes"].get(k, 0)
+                out["phases"][k] = {"ms": ms, "bytes": by, "GB/s": by / (ms * 1e-3) / 1e9,
+                                    "frac": by / (ms * 1e-3) / 1e9 / peak}
+        m.enable_timing(phase_bit(dominant))
+    return out
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))]
+
+
+def frame0_error(m, w, x0ref, n_iter):
+    """Relative error (and displacement-relative error) of the first frame from rest against the FP64 oracle."""
+    import numpy as np
+    import torch
+    m.set_state(torch.as_tensor(w.rest, dtype=torch.float32), torch.zeros((w.n_v, 3)))
+    x = torch.empty((w.n_v, 3), device="cuda")
+    m.step(torch.as_tensor(w.pin_targets(0), dtype=torch.float32), w.gravity, n_iter, x_out=x)
+    m.sync()
+    xg = x.cpu().numpy().astype(np.float64)
+    return {"e_frame0": float(np.linalg.norm(xg - x0ref) / np.linalg.norm(x0ref)),
+            "e_frame0_disp": float(np.linalg.norm(xg - x0ref) / np.linalg.norm(x0ref - w.rest))}
 
 
 def main():
@@ -330,6 +496,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    # the oracle's host-side jobs start before the first CUDA call (child processes)
+    jobs = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        jobs = OracleJobs(args.small, args.iters, check=not args.no_oracle_check)
     import numpy as np
     import torch
 
@@ -356,46 +526,15 @@ def main():
     pins = torch.as_tensor(np.stack([w.pin_targets(n) for n in range(W + K)]), dtype=torch.float32,
                            device="cuda").contiguous()
     x_out = torch.empty((w.n_v, 3), device="cuda", dtype=torch.float32)
-    # warm-up with every phase timed; the phase with the largest time per frame is
-    # the dominant kernel, the only one timed (on its own stream) in the timed region
-    m.enable_timing(-1)
-    for n in range(W):
-        m.step(pins[n], w.gravity, n_iter)
-    m.sync()
-    warm = m.phase_times()
-    per_iter = {k: v for k, v in warm.items() if k not in ("inertia", "velocity") and v > 0}
-    t_max = max(per_iter.values())
-    # near-ties (kernels that run side by side): the one streaming the most bytes
-    dominant = max((k for k, v in per_iter.items() if v >= 0.9 * t_max), key=lambda k: info["phase_bytes"][k])
-    m.enable_timing(phase_bit(dominant))
-    for n in range(2):
-        m.step(pins[n], w.gravity, n_iter)
-    m.sync()
 
     # ---- timed region: K frames, inputs resident in HBM
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
-    clocks = ClockSampler(local)
-    barrier(world)
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    ev[0].record(stream)
-    for k in range(K):
-        m.step(pins[W + k], w.gravity, n_iter)
-        ev[k + 1].record(stream)
-    ev[K].synchronize()
-    torch.cuda.synchronize()
-    clock_info = clocks.stop()
-    barrier(world)
-    m.sync()
-    frame_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
-    total_ms = ev[0].elapsed_time(ev[K])
-    phase = m.phase_times()   # the dominant kernel, timed on its own stream inside the captured frames
-    value, total_ms = whole_job_rate(K * n_iter, total_ms, world)
+    leg = time_leg(m, w, info, pins, n_iter, K, W, stream, local, world)
+    value, total_ms = whole_job_rate(K * n_iter, leg["total_ms"], world)
     ms_frame = total_ms / K
+    dominant = leg["dominant"]
 
     peak, peak_kind = measured_peaks()
-    dom_ms = phase.get(dominant, 0.0)
+    dom_ms = leg["dom_ms"]
     dom_bytes = info["phase_bytes"][dominant]
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
     # DRAM traffic per launch from an ncu capture of the same kernel (summarised under
@@ -409,25 +548,11 @@ def main():
         roofline["note"] = ("runs on a low-priority side stream beside the interface chain (off the critical "
                             "path): its live duration includes the time it yields the GPU to that chain")
 
-    # ---- per-phase report (events around every kernel of a captured frame), after the timed region
-    phases = {}
-    if args.phase_report:
-        m.enable_timing(-1)
-        for n in range(3):
-            m.step(pins[n], w.gravity, n_iter)
-        pt = m.phase_times()
-        for k, ms in pt.items():
-            if ms > 0:
-                b = info["phase_bytes"].get(k, 0)
-                phases[k] = {"ms": ms, "bytes": b, "GB/s": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / peak}
-        m.enable_timing(0)
-
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region;
     # the same captured frame as the timed region (with the dominant kernel's events)
-    m.enable_timing(phase_bit(dominant))
     pins_h = torch.as_tensor(np.stack([w.pin_targets(n) for n in range(K)]), dtype=torch.float32).pin_memory()
     out_h = torch.empty((K, w.n_v, 3), dtype=torch.float32).pin_memory()
-    pin_d = torch.empty((w.n_pinned if hasattr(w, "n_pinned") else int(w.pinned.sum()), 3), device="cuda")
+    pin_d = torch.empty((int(w.pinned.sum()), 3), device="cuda")
     for n in range(2):
         m.step(pins[n], w.gravity, n_iter, x_out=x_out)
     m.sync()
@@ -444,48 +569,82 @@ def main():
     e2e_value, e2e_ms = whole_job_rate(K * n_iter, e0.elapsed_time(e1), world)
     m.sync()
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_s = 3 if not args.small else 5
-        d, err = cpu_baseline_sample(n_s, args.small)
-        if d is not None:
-            cpu = {"value": d["iters"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{d['iters']} PD iterations of frame 0 of the same workload, FP64, 1 thread"}
+    # ---- mixed precision: BF16 matrices on the tensor cores, the correction form (the residual
+    # b - K x formed per tet inside the fused local step), same frames, same timing
+    mixed = None
+    mm = None
+    plain = (args.precision == "fp32" and not args.correction and not args.modal and not args.streaming
+             and not args.single_level and args.refine == 0)
+    if rank == 0 and plain and not args.no_mixed:
+        mm = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density, stream=stream)
+        mm.set_materials(w.gamma_s, w.gamma_v)
+        mm.prefactor(w.dt, precision="bf16", correction=True, use_graphs=True)
+        info_m = mm.info()
+        lm = time_leg(mm, w, info_m, pins, n_iter, K, W, stream, local, 1)
+        mixed = {"precision": "bf16", "form": "correction (residual per PD iteration, FP32 vectors)",
+                 "ms_per_frame": lm["total_ms"] / K, "pd_iters_per_s": K * n_iter / (lm["total_ms"] / 1e3),
+                 "frame_ms": {"p50": pct(lm["frame_ms"], 0.5), "p99": pct(lm["frame_ms"], 0.99)},
+                 "dominant": lm["dominant"], "phases": lm.get("phases", {}), "clocks": lm["clocks"],
+                 "tensor_core_kernels": ["k_axpy_mma (interior, boundary-mode and back-substitution products)"]}
+
+    # ---- accuracy of each precision's first frame against the FP64 oracle (host-side job)
+    accuracy = None
+    if jobs is not None and not args.no_oracle_check:
+        jobs.join(timeout=900)
+        ref = jobs.frame0()
+        if ref is not None:
+            accuracy = {"fp32" if args.precision == "fp32" else args.precision: frame0_error(m, w, ref, n_iter)}
+            if mm is not None:
+                accuracy["bf16_correction"] = frame0_error(mm, w, ref, n_iter)
         else:
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {err}"}
+            accuracy = {"error": str(jobs.results.get("frame", (None, "not run"))[1])}
+    if mm is not None:
+        mm.close()
+
+    cpu = None
+    if jobs is not None:
+        res = jobs.join(timeout=900)
+        hi = host_info()
+        one, err1 = res.get("one_thread", (None, "not run"))
+        alln, errn = res.get("all_cores", (None, "not run"))
+        if alln is not None:
+            cpu = {"value": alln["iters"] / alln["seconds"], "unit": UNIT, "cores": hi["nproc"], "kind": "oracle",
+                   "sample": f"{alln['iters']} PD iterations of frame 0 of the same workload, FP64, "
+                             f"BLAS threads = {hi['nproc']}",
+                   "one_thread": (one["iters"] / one["seconds"]) if one else None,
+                   "nproc": hi["nproc"], "cpu": hi["cpu"]}
+        else:
+            cpu = {"value": None, "unit": UNIT, "cores": hi["nproc"], "kind": "oracle",
+                   "sample": f"failed: {errn or err1}"}
 
     launches = K * (info["launches_per_frame"] + n_iter * info["launches_per_iter"])
     if rank == 0:
-        frame_sorted = sorted(frame_ms)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_frame, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
-            "config": {"workload": f"{w.name}: 390,000-tet thick cylindrical shell, 98,475 vertices, 200 domains"
-                       if not args.small else f"{w.name} (small profiling case)",
-                       "pd_iters_per_frame": n_iter, "dt": w.dt, "precision": args.precision,
-                       "refine_steps": args.refine, "correction_form": args.correction,
-                       "solver": ("modal, %d modes, %d Chebyshev-Jacobi sweeps" % (args.modes, args.sweeps)
+            "config": workload_config(w, args, world),
+            "solver": {"precision": args.precision, "refine_steps": args.refine, "correction_form": args.correction,
+                       "method": ("modal, %d modes, %d Chebyshev-Jacobi sweeps" % (args.modes, args.sweeps)
                                   if args.modal else "exact subspace solve"),
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "per-iteration working set > 129 MB L2 (the solve's matrices alone > 0.3 GB): "
-                             "no flush needed",
                        "n_interface": info["n_interface"], "two_level": bool(info["two_level"]),
                        "n_groups": info["n_groups"], "n_top_interface": info["n_top_interface"],
                        "prefactor_s": prefactor_s},
-            "frame_ms": {"p50": frame_sorted[len(frame_sorted) // 2],
-                         "p99": frame_sorted[min(len(frame_sorted) - 1, int(0.99 * len(frame_sorted)))],
-                         "min": frame_sorted[0], "max": frame_sorted[-1]},
+            "frame_ms": {"p50": pct(leg["frame_ms"], 0.5), "p99": pct(leg["frame_ms"], 0.99),
+                         "min": min(leg["frame_ms"]), "max": max(leg["frame_ms"])},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pin_d.numel() * 4),
                     "d2h_bytes_per_step": int(w.n_v * 3 * 4), "ms_per_step": e2e_ms / K},
             "gpu_launches": launches,
-            "clocks": clock_info,
+            "clocks": leg["clocks"],
+            "phases": leg.get("phases", {}),
         }
-        if phases:
-            line["phases"] = phases
-        if args.serving:
+        if mixed is not None:
+            line["mixed_precision"] = mixed
+        if accuracy is not None:
+            line["accuracy_vs_fp64"] = accuracy
+        if not args.no_serving and world == 1:
             line["serving"] = run_serving(args)
         print(json.dumps(line))
     m.close()

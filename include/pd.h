@@ -283,8 +283,10 @@ pd_status pd_adjoint_reset(pd_adjoint* adj);
 /*
  * pd_equilibrium_step -- one time step solved to equilibrium (Eq. g):
  * n_pd_iter PD iterations as pd_step, then n_newton (0..50) Newton steps
- * H dx = -g(x), g = (M/dt^2)(x - y) + grad E(x).  Same arguments as pd_step;
- * the mesh state (x, v) advances.  Asynchronous.
+ * H dx = -g(x), g = (M/dt^2)(x - y) + grad E(x), with g evaluated in FP64
+ * at the workspace's FP64 state (see pd_adjoint_get_state64) and dx by FP32
+ * PCG.  Same arguments as pd_step; the mesh state (x, v) advances.
+ * Asynchronous.
  */
 pd_status pd_equilibrium_step(pd_mesh* mesh, pd_adjoint* adj, const float* pin_targets, const float* gravity,
                               int32_t n_pd_iter, int32_t n_newton, float* x_out);
@@ -307,6 +309,35 @@ pd_status pd_equilibrium_step(pd_mesh* mesh, pd_adjoint* adj, const float* pin_t
  */
 pd_status pd_adjoint_step(pd_mesh* mesh, pd_adjoint* adj, const float* x_n, const float* dL_dx,
                           float* dL_dgamma_s, float* dL_dgamma_v);
+
+/*
+ * pd_adjoint_step64 -- pd_adjoint_step at an FP64 state x_n ([device]
+ * n_v x 3 double, caller's vertex order), as pd_adjoint_get_state64 gives
+ * it after the equilibrium step n.  Both entry points form every per-tet
+ * term in FP64 (F, its SVD, R(F), V(F), the stress derivative and
+ * V_e <F - P(F), Lambda_e>) and refine the FP32 PCG solution of the adjoint
+ * state once with an FP64 residual rhs - H(x_n) lambda_n: at strains of
+ * 1e-3 the FP32 rounding of F - R(F) alone would cost 1e-4 relative in the
+ * gradient.  pd_adjoint_step rounds nothing further but starts from its
+ * FP32 x_n.  Asynchronous.  Errors: INVALID_ARG, NOT_PREFACTORED, CUDA.
+ */
+pd_status pd_adjoint_step64(pd_mesh* mesh, pd_adjoint* adj, const double* x_n, const float* dL_dx,
+                            float* dL_dgamma_s, float* dL_dgamma_v);
+
+/*
+ * FP64 state of the equilibrium steps.  pd_equilibrium_step keeps the
+ * mesh's positions and velocities in FP64 inside the workspace: its Newton
+ * steps evaluate the residual g of Eq. g in FP64 at that state and add FP32
+ * PCG corrections to it (iterative refinement), so the equilibrium is met
+ * to FP64 accuracy; the mesh's FP32 state is its rounding.  The FP64 state
+ * follows the FP32 one whenever that changed by other means (pd_set_state,
+ * pd_step).  get: [device] n_v x 3 double out (either may be NULL);
+ * set: [device] n_v x 3 double in, also sets the mesh's FP32 state (a
+ * checkpoint restored this way continues bitwise as the original run).
+ * Asynchronous.  Errors: INVALID_ARG, CUDA.
+ */
+pd_status pd_adjoint_get_state64(pd_adjoint* adj, double* x, double* v);
+pd_status pd_adjoint_set_state64(pd_adjoint* adj, const double* x, const double* v);
 
 /* Diagnostics: H(x) v with v = 0 on pinned vertices (rows of pinned vertices
  * of Hv are 0), and the equilibrium residual g(x) of Eq. g for the step that
@@ -512,47 +543,58 @@ typedef struct pd_request {
 } pd_request;
 
 /*
- * pd_server_create -- a serving loop on one stream.  hbm_budget_bytes caps
- * the device memory of resident requests (their steady footprint plus the
- * transient FP64 prefactorisation of the one being admitted); max_slots caps
- * how many are resident; n_iter is the PD iteration count of every frame.
+ * pd_server_create -- a serving loop on one stream, with continuous batching.
+ * hbm_budget_bytes caps the device memory of resident requests (their steady
+ * footprint plus the transient FP64 prefactorisation of the one being
+ * admitted); max_slots caps how many are resident; n_iter is the PD
+ * iteration count of every frame.  An admission thread of the server builds
+ * and prefactors queued requests on its own low-priority stream while the
+ * resident ones keep advancing, and frees the meshes of retired requests.
  */
 pd_status pd_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t n_iter, void* cuda_stream,
                            pd_server** out);
+/* Stops the admission thread and releases every request and resource. */
 void pd_server_destroy(pd_server* server);
 
-/* Queue a request (host copy of its arrays); returns its id.  Admission happens in pd_server_tick. */
+/* Queue a request (host copy of its arrays); returns its id.  Admission runs in the background. */
 pd_status pd_submit(pd_server* server, const pd_request* request, pd_request_id* id);
 
 /*
- * pd_server_tick -- retire requests that finished, admit queued requests
- * in arrival order while slots and the budget allow (mesh set-up and FP64
- * prefactorisation on the device; a request that does not fit the budget
- * even with nothing resident is marked PD_REQ_FAILED and leaves the queue;
- * one that must wait for resident requests to retire keeps its first
- * memory estimate and is not rebuilt), then advance every resident request by
- * one frame in shared batched launches (one captured CUDA graph per set of
- * resident requests; the local steps, assemblies and subspace solves of all
- * requests run in the same kernels).  Synchronous; *frame_ms receives the
- * GPU time of that batched frame (every resident request's frame latency).
+ * pd_server_tick -- retire requests that finished (their meshes are freed by
+ * the admission thread), let the requests it has prepared join the batch,
+ * then advance every resident request by one frame in shared batched launches
+ * (one captured CUDA graph per set of resident requests; the local steps,
+ * assemblies and subspace solves of all requests run in the same kernels).
+ * Admission (in arrival order, while slots and the budget allow) happens
+ * meanwhile on the admission thread: a request that does not fit the budget
+ * even with nothing resident is marked PD_REQ_FAILED and leaves the queue; one
+ * that must wait for resident requests to retire keeps its first memory
+ * estimate and is not rebuilt.  When nothing is resident but requests are
+ * being prepared, the tick waits up to 5 ms for the first of them.
+ * Synchronous; *frame_ms receives the GPU time of the batched frame.
+ * Errors: TIMEOUT (a bounded wait of the batched products ran out), CUDA,
+ * NO_MEMORY, UNSUPPORTED.
  */
 pd_status pd_server_tick(pd_server* server, int32_t* n_active, float* frame_ms);
 
 /*
- * pd_server_run -- pd_server_tick until no request is queued or resident,
- * at most max_ticks (>= 1) ticks; *ticks (or NULL) receives the ticks run.
- * Synchronous.  Errors: INVALID_ARG; TIMEOUT when max_ticks ticks ran and
- * requests are still queued or resident; and those of pd_server_tick (the
- * loop stops at the first).
+ * pd_server_run -- pd_server_tick until no request is queued, being
+ * prepared or resident, at most max_ticks (>= 1) ticks; *ticks (or NULL)
+ * receives the ticks run.  Synchronous.  Errors: INVALID_ARG; TIMEOUT when
+ * max_ticks ticks ran and requests are still outstanding; and those of
+ * pd_server_tick (the loop stops at the first).
  */
 pd_status pd_server_run(pd_server* server, int32_t max_ticks, int32_t* ticks);
 
 pd_status pd_poll(pd_server* server, pd_request_id id, int32_t* state, int32_t* frames_done);
-/* Final positions (n_v x 3, [host]) and per-frame GPU latencies (n_frames floats, [host]) of a finished request. */
+/* Final positions (n_v x 3, [host]) and per-frame latencies (n_frames floats, [host], ms) of a finished
+ * request: the wall time from the end of its admission (first frame) or of its previous frame to the end of
+ * the frame, so it includes every wait of the request (admissions of others, graph rebuilds, the tick cadence). */
 pd_status pd_fetch(pd_server* server, pd_request_id id, float* x_out, float* frame_ms);
 pd_status pd_release(pd_server* server, pd_request_id id);
-/* Queue length, resident requests, their estimated device bytes, and the largest admission-time
- * estimate (resident + new request + its prefactorisation workspace) seen so far. */
+/* Requests waiting for admission (not yet prepared), resident requests (prepared or running), their
+ * estimated device bytes, and the largest admission-time estimate (resident + new request + its
+ * prefactorisation workspace) seen so far. */
 pd_status pd_server_stats(pd_server* server, int32_t* n_queued, int32_t* n_active, int64_t* used_bytes,
                           int64_t* peak_bytes);
 

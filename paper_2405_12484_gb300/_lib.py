@@ -101,6 +101,9 @@ SIGNATURES = [
     ("pd_equilibrium_step", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                         C.c_void_p]),
     ("pd_adjoint_step", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_adjoint_step64", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_adjoint_get_state64", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pd_adjoint_set_state64", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pd_hessian_vec", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pd_residual", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pd_pose_misfit", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

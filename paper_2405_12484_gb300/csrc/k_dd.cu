@@ -15,6 +15,7 @@
 // accumulation, vectors staged in shared memory, fixed-order reductions
 // (deterministic), no atomics.
 #include <algorithm>
+#include <type_traits>
 
 #include "pd_internal.h"
 #include "tma.cuh"
@@ -346,9 +347,11 @@ inline size_t axt_ring_bytes(int wmax) {
     return (std::max(ring, red) + 15) / 16 * 16;
 }
 
-template <class T>
+template <class T, bool BATCHED>
 __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_tma(const AxDesc* __restrict__ descs,
-                                                                   const AxBlock* __restrict__ blocks, AxBases B,
+                                                                   const AxBlock* __restrict__ blocks,
+                                                                   AxBases single,
+                                                                   const AxBases* __restrict__ multi,
                                                                    int ring_bytes, int* __restrict__ err) {
     using namespace tma;
     constexpr int VN = VecN<T>::N;
@@ -361,6 +364,7 @@ __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_tma(const AxDesc*
     __shared__ int abort_flag;
     const AxBlock bk = blocks[blockIdx.x];
     const AxDesc D = descs[bk.desc];
+    const AxBases B = BATCHED ? multi[D.slot] : single;   // serving: the request's own arrays
     const int w = ax_tile_width(D.n_out, bk.o0, D.ld, VN);
     const T* tile = reinterpret_cast<const T*>(B.pool) + D.a_off + (int64_t)bk.o0 * D.K;
     const int n_st = (D.K + R - 1) / R;
@@ -467,6 +471,183 @@ __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_tma(const AxDesc*
             }
             const float4 b = add ? add[oi] : make_float4(0.f, 0.f, 0.f, 0.f);
             out[oi] = make_float4(b.x + r0, b.y + r1, b.z + r2, 0.f);
+        }
+    }
+}
+
+// BF16 tiles on the tensor cores.  A BF16 axpy-form tile is stored with its
+// rows padded to a multiple of 16 and cut into 16 x 8 (rows k x outputs n)
+// blocks in row-block-major order, each block in the register order of the
+// B operand of mma.m16n8k16 (lane 4 n + q holds rows 2q, 2q+1, 2q+8, 2q+9 of
+// column n), so a bulk-copied stage is consumed with one 8-byte shared load
+// per lane and block, free of bank conflicts.  The A operand is the
+// right-hand sides: rows 0..2 hold x, y, z rounded to BF16 and rows 8..10
+// their BF16 remainders (x - bf16(x)), so the FP32 accumulators of the
+// product carry x to about 16 bits while the matrix is BF16.  Output n of
+// right-hand side c is D[c][n] + D[c + 8][n].  The consumer warps own
+// disjoint output columns (no cross-warp reduction); the copy ring, the
+// producer lane and the bounded waits are those of k_axpy_tma.
+__host__ __device__ inline int64_t mma_frag_index(int r, int c_in_tile, int w) {
+    const int kb = r >> 4, kk = r & 15, nb = c_in_tile >> 3, n = c_in_tile & 7;
+    const int q = (kk & 7) >> 1, j = (kk & 1) + ((kk >> 3) << 1);
+    return ((int64_t)kb * (w >> 3) + nb) * 128 + (4 * n + q) * 4 + j;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint4& a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+constexpr int kAxmNb = 8;   // n8 blocks per consumer warp (tile width <= 8 * 8 * kAxtWarps = 256)
+static_assert(kAxmNb * 8 * kAxtWarps >= 256, "one consumer warp per output column group");
+
+inline size_t axm_ring_bytes(int wmax) {
+    return ((size_t)kAxtStages * kAxtRows * wmax * sizeof(__nv_bfloat16) + 15) / 16 * 16;
+}
+
+__global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_mma(const AxDesc* __restrict__ descs,
+                                                                   const AxBlock* __restrict__ blocks, AxBases B,
+                                                                   int ring_bytes, int* __restrict__ err) {
+    using namespace tma;
+    constexpr int S = kAxtStages, R = kAxtRows;
+    static_assert(R % 16 == 0, "stages hold whole 16-row blocks");
+    extern __shared__ __align__(128) unsigned char axm_smem[];
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ int abort_flag;
+    const AxBlock bk = blocks[blockIdx.x];
+    const AxDesc D = descs[bk.desc];
+    const int w = ax_tile_width(D.n_out, bk.o0, D.ld, 8);
+    const int Kp = (D.K + 15) & ~15;
+    __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(axm_smem);
+    uint4* frag = reinterpret_cast<uint4*>(axm_smem + ring_bytes);                  // Kp / 16 x 32 lanes
+    float4* xs = reinterpret_cast<float4*>(axm_smem + ring_bytes + (size_t)Kp * 32);  // K entries
+    const __nv_bfloat16* tile = reinterpret_cast<const __nv_bfloat16*>(B.pool) + D.a_off + (int64_t)bk.o0 * Kp;
+    const int n_st = (Kp + R - 1) / R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    pdl_trigger();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kAxtWarps);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == kAxtWarps) {
+        // producer: whole 16-row blocks per stage, one bulk copy each
+        if (lane == 0) {
+            int issued = 0;
+            for (int i = 0; i < n_st; ++i) {
+                const int slot = i % S;
+                if (i >= S && !mbar_wait(&empty[slot], ((i / S) - 1) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    atomicOr(err, ERR_TIMEOUT);
+                    break;
+                }
+                const int rows = min(R, Kp - i * R);
+                const uint32_t bytes = (uint32_t)(rows * w * (int)sizeof(__nv_bfloat16));
+                uint32_t expect = bytes;
+                if (blockIdx.x == 0 && i == 0 && *reinterpret_cast<volatile int*>(&g_test_copy_extra) > 0)
+                    expect += (uint32_t)max(atomicExch(&g_test_copy_extra, 0), 0);
+                mbar_arrive_expect_tx(&full[slot], expect);
+                bulk_g2s(ring + (size_t)slot * R * w, tile + (int64_t)i * R * w, bytes, &full[slot]);
+                issued = i + 1;
+            }
+            for (int i = max(0, issued - S); i < issued; ++i)
+                if (!mbar_wait(&full[i % S], (i / S) & 1)) atomicOr(err, ERR_TIMEOUT);
+        }
+        return;
+    }
+    // consumers: stage x, then the A operands of every 16-row block (hi rows 0..2, remainders 8..10)
+    pdl_wait();
+    stage_f4(xs, D.K, B.x + D.x_off, D.bidx_off >= 0 ? B.bidx + D.bidx_off : nullptr, threadIdx.x, 32 * kAxtWarps);
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kAxtWarps) : "memory");
+    for (int f = threadIdx.x; f < (Kp >> 4) * 32; f += 32 * kAxtWarps) {
+        const int kb = f >> 5, l = f & 31, g = l >> 2, q = l & 3;
+        uint32_t hv[4] = {0u, 0u, 0u, 0u}, lv[4] = {0u, 0u, 0u, 0u};   // (a0, a2) hi, (a1, a3) lo
+        if (g < 3) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {       // h = 0: rows 2q, 2q+1; h = 1: rows 2q+8, 2q+9
+                __nv_bfloat16 hi[2], lo[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int k = kb * 16 + 2 * q + 8 * h + e;
+                    float v = 0.f;
+                    if (k < D.K) {
+                        const float4 xv = xs[k];
+                        v = g == 0 ? xv.x : (g == 1 ? xv.y : xv.z);
+                    }
+                    hi[e] = __float2bfloat16_rn(v);
+                    lo[e] = __float2bfloat16_rn(v - __bfloat162float(hi[e]));
+                }
+                hv[h] = pack_bf16(hi[0], hi[1]);
+                lv[h] = pack_bf16(lo[0], lo[1]);
+            }
+        }
+        frag[f] = make_uint4(hv[0], lv[0], hv[1], lv[1]);
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kAxtWarps) : "memory");
+    const int nb8 = w >> 3;
+    float acc[kAxmNb][4];
+#pragma unroll
+    for (int j = 0; j < kAxmNb; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int i = 0; i < n_st; ++i) {
+        const int slot = i % S;
+        if (!mbar_wait(&full[slot], (i / S) & 1, &abort_flag)) {
+            if (lane == 0) {
+                abort_flag = 1;
+                atomicOr(err, ERR_TIMEOUT);
+            }
+            break;
+        }
+        const int kbs = min(R, Kp - i * R) >> 4;
+        const uint2* st = reinterpret_cast<const uint2*>(ring + (size_t)slot * R * w);
+        for (int kk = 0; kk < kbs; ++kk) {
+            const uint4 a = frag[(i * (R >> 4) + kk) * 32 + lane];
+            const uint2* blk = st + (size_t)kk * nb8 * 32;
+#pragma unroll
+            for (int j = 0; j < kAxmNb; ++j) {
+                const int nb = warp + kAxtWarps * j;
+                if (nb < nb8) {
+                    const uint2 bv = blk[nb * 32 + lane];
+                    mma_bf16_16816(acc[j], a, bv.x, bv.y);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+    }
+    // epilogue: lanes 0..3 gather x, y, z of outputs 2q, 2q+1 from lanes q, q+4, q+8
+    const int q = lane & 3;
+    float4* out = B.out + D.out_off;
+    const float4* add = (D.add_off >= 0) ? B.add + D.add_off : nullptr;
+#pragma unroll
+    for (int j = 0; j < kAxmNb; ++j) {
+        const int nb = warp + kAxtWarps * j;
+        if (nb >= nb8) break;   // uniform across the warp
+        const float v0 = acc[j][0] + acc[j][2], v1 = acc[j][1] + acc[j][3];
+        const float y0 = __shfl_sync(0xffffffffu, v0, q + 4), y1 = __shfl_sync(0xffffffffu, v1, q + 4);
+        const float z0 = __shfl_sync(0xffffffffu, v0, q + 8), z1 = __shfl_sync(0xffffffffu, v1, q + 8);
+        if (lane < 4) {
+            const int o = bk.o0 + nb * 8 + 2 * q;
+            if (o < D.n_out) {
+                const float4 b = add ? add[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+                out[o] = make_float4(b.x + v0, b.y + y0, b.z + z0, 0.f);
+            }
+            if (o + 1 < D.n_out) {
+                const float4 b = add ? add[o + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                out[o + 1] = make_float4(b.x + v1, b.y + y1, b.z + z1, 0.f);
+            }
         }
     }
 }
@@ -1012,7 +1193,13 @@ void launch_coarse(pd_mesh* m, const T* pool, const float4* cin, float4* part, c
 
 template <class T>
 int axt_smem_limit() {
-    static const int lim = allow_max_dynamic_smem(k_axpy_tma<T>);
+    static const int lim = std::min(allow_max_dynamic_smem(k_axpy_tma<T, false>),
+                                    allow_max_dynamic_smem(k_axpy_tma<T, true>));
+    return lim;
+}
+
+int axm_smem_limit() {
+    static const int lim = allow_max_dynamic_smem(k_axpy_mma);
     return lim;
 }
 
@@ -1020,16 +1207,28 @@ template <class T>
 void launch_ax(const AxDesc* descs, const AxBlock* blocks, int n_blocks, int k_max, const AxBases& B, cudaStream_t s,
                int* tma_err = nullptr, int w_max = 0, bool pdl = false) {
     if (n_blocks <= 0) return;
-    if (tma_err) {
+    if (tma_err && std::is_same<T, __nv_bfloat16>::value) {
+        // BF16 tiles in the tensor-core fragment layout
+        const int kp = (std::max(k_max, 1) + 15) & ~15;
+        const size_t ring = axm_ring_bytes(w_max);
+        const size_t smem = ring + (size_t)kp * 32 + sizeof(float4) * std::max(k_max, 1);
+        if ((int)smem > axm_smem_limit()) throw Fail{PD_ERR_UNSUPPORTED};
+        if (pdl)
+            launch_pdl(k_axpy_mma, dim3(n_blocks), dim3(32 * (kAxtWarps + 1)), smem, s, descs, blocks, B, (int)ring,
+                       tma_err);
+        else
+            k_axpy_mma<<<n_blocks, 32 * (kAxtWarps + 1), smem, s>>>(descs, blocks, B, (int)ring, tma_err);
+    } else if (tma_err) {
         // tiled matrices: the bulk-copy streaming kernel
         const size_t ring = axt_ring_bytes<T>(w_max);
         const size_t smem = ring + sizeof(float4) * std::max(k_max, 1);
         if ((int)smem > axt_smem_limit<T>()) throw Fail{PD_ERR_UNSUPPORTED};
         if (pdl)
-            launch_pdl(k_axpy_tma<T>, dim3(n_blocks), dim3(32 * (kAxtWarps + 1)), smem, s, descs, blocks, B, (int)ring,
-                       tma_err);
+            launch_pdl(k_axpy_tma<T, false>, dim3(n_blocks), dim3(32 * (kAxtWarps + 1)), smem, s, descs, blocks, B,
+                       (const AxBases*)nullptr, (int)ring, tma_err);
         else
-            k_axpy_tma<T><<<n_blocks, 32 * (kAxtWarps + 1), smem, s>>>(descs, blocks, B, (int)ring, tma_err);
+            k_axpy_tma<T, false><<<n_blocks, 32 * (kAxtWarps + 1), smem, s>>>(descs, blocks, B, nullptr, (int)ring,
+                                                                              tma_err);
     } else {
         k_axpy_form<T, false><<<n_blocks, 32 * kAxWarps, sizeof(float4) * std::max(k_max, 1), s>>>(descs, blocks, B,
                                                                                                  nullptr);
@@ -1210,11 +1409,16 @@ void launch_dd_solve_scratch(pd_mesh* m, const float4* b, float4* xout, float4* 
     else dd_solve_impl<float>(m, m->d_mat32.p, b, xout, w, s);
 }
 
+// Serving batches: every resident request's tiled products in one launch of
+// the bulk-copy kernel (each block reads its request's arrays from `bases`).
 void launch_axpy_b(const AxDesc* descs, const AxBlock* blocks, const AxBases* bases, int n_blocks, int k_max,
-                   cudaStream_t s) {
+                   int w_max, int* err, cudaStream_t s) {
     if (n_blocks <= 0) return;
-    k_axpy_form<float, true><<<n_blocks, 32 * kAxWarps, sizeof(float4) * std::max(k_max, 1), s>>>(descs, blocks,
-                                                                                                AxBases{}, bases);
+    const size_t ring = axt_ring_bytes<float>(w_max);
+    const size_t smem = ring + sizeof(float4) * std::max(k_max, 1);
+    if ((int)smem > axt_smem_limit<float>()) throw Fail{PD_ERR_UNSUPPORTED};
+    k_axpy_tma<float, true><<<n_blocks, 32 * (kAxtWarps + 1), smem, s>>>(descs, blocks, AxBases{}, bases, (int)ring,
+                                                                          err);
     PDG_CHECK_LAUNCH();
 }
 
@@ -1227,7 +1431,7 @@ void test_set_copy_extra(int bytes, cudaStream_t s) {
 
 // raise the dynamic shared-memory limit of the bulk-copy kernel (outside any capture)
 void ax_prepare_tma(int prec) {
-    if (prec == PD_PREC_BF16) (void)axt_smem_limit<__nv_bfloat16>();
+    if (prec == PD_PREC_BF16) (void)axm_smem_limit();
     else (void)axt_smem_limit<float>();
 }
 

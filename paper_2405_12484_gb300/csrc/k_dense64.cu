@@ -326,6 +326,25 @@ __global__ void k_cast_tiled(const double* __restrict__ src, int lds, int rows, 
     }
 }
 
+// BF16 tile in the tensor-core fragment order (rows padded to 16; see k_axpy_mma):
+// element (r, c) of chunk o0 = c - c % CW lands in its 16 x 8 block at the
+// lane and register the mma B operand reads it from.
+__global__ void k_cast_frag16(const double* __restrict__ src, int lds, int rows, int cols, int transpose,
+                              __nv_bfloat16* __restrict__ d16, int64_t off, int CW) {
+    const int64_t n = (int64_t)rows * cols;
+    const int kp = (rows + 15) & ~15;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(l / cols), c = (int)(l % cols);
+        const double v = transpose ? src[(int64_t)c * lds + r] : src[(int64_t)r * lds + c];
+        const int o0 = c / CW * CW;
+        const int w = ax_tile_width(cols, o0, CW, 8);
+        const int kb = r >> 4, kk = r & 15, cc = c - o0, nb = cc >> 3, nn = cc & 7;
+        const int q = (kk & 7) >> 1, j = (kk & 1) + ((kk >> 3) << 1);
+        d16[off + (int64_t)o0 * kp + ((int64_t)kb * (w >> 3) + nb) * 128 + (4 * nn + q) * 4 + j] =
+            __double2bfloat16(v);
+    }
+}
+
 // dst[i][k] = S[r0 + i][cols ? c0 + cols[k] : c0 + k]
 __global__ void k_copy_block_idx(const double* __restrict__ S, int ldS, int r0, int nr, const int* __restrict__ cols,
                                  int c0, int nc, double* __restrict__ dst, int ldd) {
@@ -370,6 +389,13 @@ void launch_cast_block(const double* src, int lds, int rows, int cols, int trans
     if (rows <= 0 || cols <= 0) return;
     k_cast_block<<<grid_of((int64_t)rows * cols), 256, 0, s>>>(src, lds, rows, cols, transpose, prec, dst32, dst16,
                                                                 dst_off, ldd);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_cast_frag16(const double* src, int lds, int rows, int cols, int transpose, __nv_bfloat16* dst16,
+                        int64_t dst_off, int CW, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return;
+    k_cast_frag16<<<grid_of((int64_t)rows * cols), 256, 0, s>>>(src, lds, rows, cols, transpose, dst16, dst_off, CW);
     PDG_CHECK_LAUNCH();
 }
 

@@ -19,7 +19,7 @@ __global__ void k_inertia(int n_v, int n_free, float h, float gx, float gy, floa
                           float4* __restrict__ xprev, const float4* __restrict__ v, const float4* __restrict__ tgt,
                           const float* __restrict__ mh2, const int* __restrict__ kfp_ptr,
                           const int* __restrict__ kfp_col, const float* __restrict__ kfp_val,
-                          float4* __restrict__ by0) {
+                          float4* __restrict__ by0, float4* __restrict__ yout) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_v) return;
     float4 xp = x[i];
@@ -29,6 +29,7 @@ __global__ void k_inertia(int n_v, int n_free, float h, float gx, float gy, floa
         float h2 = h * h;
         float4 y = f4(xp.x + h * vv.x + h2 * gx, xp.y + h * vv.y + h2 * gy, xp.z + h * vv.z + h2 * gz);
         x[i] = y;
+        if (yout) yout[i] = y;
         float m = mh2[i];
         float4 acc = f4(m * y.x, m * y.y, m * y.z);
         for (int k = kfp_ptr[i]; k < kfp_ptr[i + 1]; ++k) {
@@ -61,50 +62,6 @@ __global__ void k_by0(int n_free, const float4* __restrict__ y, const float4* __
         acc.z -= kv * p.z;
     }
     by0[i] = acc;
-}
-
-// b_i = by0_i + sum of the corner forces of vertex i.  Four lanes per vertex
-// split its corners (lane l takes corners l, l + 4, ...), each with four
-// independent index loads and then four force loads in flight, and a
-// fixed-order shuffle tree adds the lanes (deterministic).
-constexpr int kAsmLanes = 4;
-
-__global__ void __launch_bounds__(256) k_assemble(int n_free, const int* __restrict__ inc_ptr,
-                                                  const int* __restrict__ inc, const float4* __restrict__ force,
-                                                  const float4* __restrict__ by0, float4* __restrict__ b) {
-    pdl_trigger();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / kAsmLanes, sub = t % kAsmLanes;
-    const bool live = i < n_free;
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    const int k0 = live ? __ldg(&inc_ptr[i]) : 0, k1 = live ? __ldg(&inc_ptr[i + 1]) : 0;
-    pdl_wait();   // the corner forces come from the local step
-    if (live) {
-        for (int base = k0 + sub; base < k1; base += 4 * kAsmLanes) {
-            int a[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) a[u] = base + u * kAsmLanes < k1 ? __ldg(&inc[base + u * kAsmLanes]) : -1;
-            float4 f[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) f[u] = a[u] >= 0 ? force[a[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                ax += f[u].x;
-                ay += f[u].y;
-                az += f[u].z;
-            }
-        }
-    }
-#pragma unroll
-    for (int off = 1; off < kAsmLanes; off <<= 1) {
-        ax += __shfl_xor_sync(0xffffffffu, ax, off, kAsmLanes);
-        ay += __shfl_xor_sync(0xffffffffu, ay, off, kAsmLanes);
-        az += __shfl_xor_sync(0xffffffffu, az, off, kAsmLanes);
-    }
-    if (live && sub == 0) {
-        const float4 y = by0[i];
-        b[i] = make_float4(y.x + ax, y.y + ay, y.z + az, 0.f);
-    }
 }
 
 __global__ void k_velocity(int n_v, float inv_h, const float4* __restrict__ x, const float4* __restrict__ xprev,
@@ -168,7 +125,7 @@ inline int nblk(int n, int b) { return (n + b - 1) / b; }
 void launch_inertia(const pd_mesh* m, float h, float gx, float gy, float gz, cudaStream_t s) {
     k_inertia<<<nblk(m->n_v, 256), 256, 0, s>>>(m->n_v, m->n_free, h, gx, gy, gz, m->d_x.p, m->d_xprev.p, m->d_v.p,
                                                 m->d_pin_tgt.p, m->d_mh2.p, m->d_kfp_ptr.p, m->d_kfp_col.p,
-                                                m->d_kfp_val.p, m->d_by0.p);
+                                                m->d_kfp_val.p, m->d_by0.p, m->correction ? m->d_y.p : nullptr);
     PDG_CHECK_LAUNCH();
 }
 
@@ -177,13 +134,6 @@ void launch_by0_from_y(const pd_mesh* m, const float4* y, float4* by0, cudaStrea
     // pinned positions come from the pin-target buffer (filled by the caller)
     k_by0<<<nblk(m->n_free, 256), 256, 0, s>>>(m->n_free, y, m->d_pin_tgt.p, m->d_mh2.p, m->d_kfp_ptr.p,
                                                m->d_kfp_col.p, m->d_kfp_val.p, by0);
-    PDG_CHECK_LAUNCH();
-}
-
-void launch_assemble(const pd_mesh* m, const float4* by0, const float4* force, float4* b, cudaStream_t s) {
-    if (m->n_free <= 0) return;
-    launch_pdl(k_assemble, dim3(nblk(m->n_free * kAsmLanes, 256)), dim3(256), 0, s, m->n_free, m->d_inc_ptr.p,
-               m->d_inc.p, force, by0, b);
     PDG_CHECK_LAUNCH();
 }
 

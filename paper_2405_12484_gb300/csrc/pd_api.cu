@@ -35,6 +35,8 @@ void launch_prefactor_add_block(double* S, int ldS, const double* Sd, int ldSd, 
                                 cudaStream_t s);
 void launch_cast_block(const double* src, int lds, int rows, int cols, int transpose, int prec, float* dst32,
                        __nv_bfloat16* dst16, int64_t dst_off, int ldd, cudaStream_t s);
+void launch_cast_frag16(const double* src, int lds, int rows, int cols, int transpose, __nv_bfloat16* dst16,
+                        int64_t dst_off, int CW, cudaStream_t s);
 void launch_cast_tiled(const double* src, int lds, int rows, int cols, int transpose, int prec, float* dst32,
                        __nv_bfloat16* dst16, int64_t dst_off, int OW, int VN, cudaStream_t s);
 void ax_prepare_tma(int prec);
@@ -623,6 +625,7 @@ pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tet
     upload(m->d_geo, hg, s);
     upload(m->d_inc_ptr, inc_ptr, s);
     upload(m->d_inc, inc, s);
+    build_local_plan(m, inc_ptr, inc, s);
     upload(m->d_old_of_new, m->old_of_new, s);
     std::vector<float4> hx(n_v);
     for (int32_t i = 0; i < n_v; ++i) {
@@ -638,6 +641,7 @@ pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tet
     m->d_force.alloc(4 * (size_t)n_t);
     m->d_by0.alloc(std::max(m->n_free, 1));
     m->d_b.alloc(std::max(m->n_free, 1));
+    m->d_y.alloc(std::max(m->n_free, 1));
     m->d_pin_tgt.alloc(std::max(n_pin, 1));
     m->d_r.alloc(std::max(m->n_free, 1));
     m->d_dx.alloc(n_v);
@@ -685,6 +689,7 @@ pd_status pd_set_materials(pd_mesh* m, const float* gamma_s, const float* gamma_
     PDG_CUDA(cudaStreamSynchronize(m->stream));
     m->materials_set = true;
     m->prefactored = false;
+    ++m->mat_gen;
     return PD_OK;
     PD_API_END
 }
@@ -695,6 +700,8 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     if (!m->materials_set) return fail(PD_ERR_BAD_MATERIAL, "materials not set");
     pd_solver_opts o{PD_PREC_FP32, 0, 1, 0};
     if (opts) o = *opts;
+    if ((o.flags & PD_SOLVE_CORRECTION) && o.refine_steps > 0)
+        return fail(PD_ERR_INVALID_ARG, "the correction form refines every PD iteration itself: refine_steps must be 0");
     if (o.precision < PD_PREC_FP32 || o.precision > PD_PREC_TF32 || o.refine_steps < 0 || o.refine_steps > 2 ||
         (o.flags & ~(PD_SOLVE_CORRECTION | PD_SOLVE_SINGLE_LEVEL | PD_SOLVE_STREAMING | PD_SOLVE_MODAL)) != 0)
         return fail(PD_ERR_INVALID_ARG, "bad solver options");
@@ -1023,6 +1030,9 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     // to 8 entries so every row starts on a 16-byte boundary
     std::vector<int64_t> h_off(n_dom), p_off(n_dom), t_off(n_dom), m1_off(n_dom), m2_off(n_dom);
     std::vector<int32_t> ldH(n_dom), ldP(n_dom), ldT(n_dom), tc_off(n_dom), pm_off(n_dom);
+    // BF16 tiles for the tensor cores hold their rows padded to a multiple of 16
+    const bool frag16 = !(o.flags & PD_SOLVE_STREAMING) && m->prec == PD_PREC_BF16;
+    auto krows = [&](int32_t k) { return frag16 ? (int64_t)round_up(k, 16) : (int64_t)k; };
     int64_t pool = 0;
     int32_t tcr = 0, pmr = 0;
     for (int32_t d = 0; d < n_dom; ++d) {
@@ -1040,12 +1050,12 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             pm_off[d] = pmr;
             pmr += r_dom[d];
         } else {
-            pool += (int64_t)ni * ldH[d];
+            pool += krows(ni) * ldH[d];
         }
         p_off[d] = pool;
-        pool += (int64_t)ni * ldP[d];
+        pool += krows(ni) * ldP[d];
         t_off[d] = pool;
-        pool += (int64_t)nbd * ldT[d];
+        pool += krows(nbd) * ldT[d];
         tc_off[d] = tcr;
         tcr += ni + nbd;
     }
@@ -1088,7 +1098,10 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     m->ax_tiled = tiled;
     if (tiled) ax_prepare_tma(m->prec);
     auto cast_ax = [&](const double* src, int lds, int rows, int cols, int transpose, int64_t off, int ld) {
-        if (tiled)
+        if (frag16)
+            launch_cast_frag16(src, lds, rows, cols, transpose, m->d_mat16.p, off, ax_chunk_width(cols, OWt, VNt),
+                               s);
+        else if (tiled)
             launch_cast_tiled(src, lds, rows, cols, transpose, m->prec, m->d_mat32.p, m->d_mat16.p, off,
                               ax_chunk_width(cols, OWt, VNt), VNt, s);
         else
@@ -1549,8 +1562,15 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         for (const auto& d : m->rows_back2.host) mat_b2 += (int64_t)d.rows * d.ld * es;
         for (int k = 0; k < 24; ++k) m->phase_bytes[k] = 0;
         m->phase_bytes[PH_INERTIA] = nv * 48 + nf * (16 + 4 + 16 + 4) + nkfp * 8 + (int64_t)m->n_pin * 16;
-        m->phase_bytes[PH_LOCAL] = nt * (16 + 48 + 64) + nv * 16;
-        m->phase_bytes[PH_ASSEMBLE] = nf * (4 + 16 + 16) + ninc * (4 + 16);
+        // fused local step + assembly: tets and rest operators, x once, by0 (or y and m/dt^2) and b per
+        // free vertex, the block plan (16 B per block-vertex entry, 2 B per corner), partial sums of the
+        // shared vertices written and read, their counters
+        m->phase_bytes[PH_LOCAL] = nt * (16 + 48) + nv * 16 + nf * (m->correction ? 16 + 4 + 16 : 16 + 16) +
+                                   (int64_t)m->la_entries * 12 + (int64_t)m->la_corners * 2 +
+                                   (int64_t)m->la_slots * 32 + (int64_t)m->la_shared * 8 +
+                                   (int64_t)(m->la_blocks + 1) * 4;
+        m->phase_bytes[PH_ASSEMBLE] = 0;
+        (void)ninc;
         m->phase_bytes[PH_CONDENSE] = mat_c + (int64_t)n_int * 16 + nbd_tot * 16;
         m->phase_bytes[PH_INTERIOR] = mat_i + (int64_t)n_int * 32;
         if (modal) {
@@ -1591,7 +1611,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             dd += (m->rows_cond2.n_blocks > 0 ? 1 : 0) + (m->rows_int2.n_blocks > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) +
                   (m->rows_back2.n_blocks > 0 ? 1 : 0);
         if (m->use_stream) dd = 1;   // the fused solve
-        m->launches_per_iter = 2 + dd + (m->correction ? 2 : 0) + m->refine * (2 + dd);
+        m->launches_per_iter = 1 + (m->la_shared > 0 ? 1 : 0) + dd + (m->correction ? 1 : 0) + m->refine * (2 + dd);
     }
 
     PDG_CUDA(cudaStreamSynchronize(s));
@@ -1619,6 +1639,7 @@ pd_status pd_set_state(pd_mesh* m, const float* x, const float* v) {
     PD_API_BEGIN
     if (x) launch_gather_in(m, x, m->d_x.p, m->stream);
     if (v) launch_gather_in(m, v, m->d_v.p, m->stream);
+    ++m->state_gen;
     return PD_OK;
     PD_API_END
 }
@@ -1640,17 +1661,13 @@ static void run_frame(pd_mesh* m, int n_iter, const float g[3], cudaStream_t s) 
     launch_inertia(m, h, g[0], g[1], g[2], s);
     phase_end(m, s);
     for (int it = 0; it < n_iter; ++it) {
+        // fused local step and assembly: the RHS b, or in the correction form
+        // the residual b - K x itself (formed per tet without cancellation)
         phase_begin(m, PH_LOCAL, s);
-        launch_local(m, m->d_x.p, m->d_force.p, s);
-        phase_end(m, s);
-        phase_begin(m, PH_ASSEMBLE, s);
-        launch_assemble(m, m->d_by0.p, m->d_force.p, m->d_b.p, s);
+        launch_local_assemble(m, m->d_x.p, m->d_by0.p, m->d_y.p, m->d_b.p, m->correction, s);
         phase_end(m, s);
         if (m->correction) {
-            phase_begin(m, PH_RESIDUAL, s);
-            launch_residual(m, m->d_b.p, m->d_x.p, m->d_r.p, s);
-            phase_end(m, s);
-            launch_dd_solve(m, m->d_r.p, m->d_dx.p, s, false);
+            launch_dd_solve(m, m->d_b.p, m->d_dx.p, s, false);
             launch_axpy_free(m, m->d_dx.p, m->d_x.p, s);
         } else {
             launch_dd_solve(m, m->d_b.p, m->d_x.p, s, false);
@@ -1682,6 +1699,7 @@ pd_status pd_step(pd_mesh* m, const float* pin_targets, const float* gravity, in
         g[2] = gravity[2];
     }
     cudaStream_t s = m->stream;
+    ++m->state_gen;
     if (pin_targets) launch_pin_copy(m, pin_targets, s);
     else launch_pin_hold(m, s);
     if (m->use_graphs) {
@@ -1827,8 +1845,7 @@ pd_status pd_local_rhs(pd_mesh* m, const float* x, const float* y, float* b) {
         PDG_CUDA(cudaMemcpyAsync(m->d_pin_tgt.p, xi.p + m->n_free, sizeof(float4) * m->n_pin,
                                  cudaMemcpyDeviceToDevice, s));
     launch_by0_from_y(m, yi.p, by0.p, s);
-    launch_local(m, xi.p, frc.p, s);
-    launch_assemble(m, by0.p, frc.p, bb.p, s);
+    launch_local_assemble(m, xi.p, by0.p, nullptr, bb.p, false, s);
     launch_scatter_out(m, bb.p, b, 1, s);
     PDG_CUDA(cudaStreamSynchronize(s));
     return PD_OK;

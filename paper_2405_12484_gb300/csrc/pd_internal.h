@@ -266,6 +266,27 @@ struct StreamPlan {
     std::vector<ColDesc> host;
 };
 
+// Tets per block of the fused local step and RHS assembly.
+#ifndef PDG_LA_TETS
+#define PDG_LA_TETS 128
+#endif
+
+// Arguments of the fused local step and assembly (see k_local.cu).
+struct LocalAsmArgs {
+    int n_t;
+    const int4* tets;
+    const float4* geo;
+    const float4* x;
+    const float4* by0;     // RHS form: (m/dt^2) y - K_fp x_p
+    const float4* y;       // residual form: the inertial target
+    const float* mh2;
+    float4* b;             // RHS or residual (free vertices)
+    const int *vptr, *vert, *slot, *cptr;
+    const uint16_t* corner;
+    const int *sh_ptr, *sh_vert;
+    float4* part;
+};
+
 // One resident request of the serving loop, as the batched kernels see it.
 struct BatchSlot {
     const int4* tets;
@@ -349,6 +370,15 @@ struct pd_mesh {
     pdg::DBuf<float4> d_pin_tgt;    // n_pin
     pdg::DBuf<float> d_mh2;         // n_free: m / dt^2
     pdg::DBuf<int32_t> d_inc_ptr, d_inc;   // free-vertex -> (tet*4+corner) CSR
+    pdg::DBuf<float4> d_y;                 // inertial target of the free vertices (residual form)
+    // fused local step + assembly: per block the free vertices it touches
+    // (vptr over blocks; vertex, slot or -1, corner CSR of block-local corner
+    // ids), the shared vertices (sh_vert) with their slots (sh_ptr) and the
+    // partial sums of the slots
+    pdg::DBuf<int32_t> d_la_vptr, d_la_vert, d_la_slot, d_la_cptr, d_la_sh_ptr, d_la_sh_vert;
+    pdg::DBuf<uint16_t> d_la_corner;
+    pdg::DBuf<float4> d_la_part;
+    int32_t la_blocks = 0, la_entries = 0, la_corners = 0, la_slots = 0, la_shared = 0;
     pdg::DBuf<int32_t> d_kfp_ptr, d_kfp_col;
     pdg::DBuf<float> d_kfp_val;
     pdg::DBuf<int32_t> d_old_of_new;       // n_v
@@ -414,6 +444,10 @@ struct pd_mesh {
     pdg::DBuf<double> d_K_val;
     pdg::DBuf<float4> d_r, d_dx;             // refinement residual / correction (n_free)
 
+    // generations of the FP32 state (pd_set_state, pd_step) and of the
+    // materials (pd_set_materials): the adjoint workspace's FP64 state and
+    // FP64 per-tet weights follow them
+    uint64_t state_gen = 0, mat_gen = 0;
     // state flags
     bool materials_set = false;
     bool prefactored = false;
@@ -468,6 +502,15 @@ struct pd_adjoint {
     pdg::DBuf<double> gn_sc, gn_partial;
     pdg::DBuf<int32_t> gn_ipartial;
     bool gn_ready = false;
+    // FP64 state of the equilibrium steps (3 doubles per vertex, library
+    // order): x, v, the state the step started from, the state given to the
+    // adjoint step; FP64 per-tet operators (12 doubles per tet), M/dt^2,
+    // corner terms; the adjoint refinement vectors
+    pdg::DBuf<double> x64, v64, xprev64, vprev64, xa64, geo64, mh2_64, force64;
+    pdg::DBuf<float4> rhs2, dlam;
+    uint64_t gen64 = ~uint64_t(0);       // mesh state generation x64/v64 belong to
+    uint64_t mat_gen64 = ~uint64_t(0);   // material generation of geo64
+    double dt64 = 0.0;                   // dt of mh2_64
 };
 
 namespace pdg {
@@ -482,8 +525,11 @@ void jacobi_eig(std::vector<double>& A, int q, std::vector<double>& w, std::vect
 
 // ---------------------------------------------------------------- kernels (launchers)
 void launch_project(const float* F, int n, float* R, float* V, float* sig, cudaStream_t s);
-void launch_local(const pd_mesh* m, const float4* x, float4* force, cudaStream_t s);
-void launch_assemble(const pd_mesh* m, const float4* by0, const float4* force, float4* b, cudaStream_t s);
+void build_local_plan(pd_mesh* m, const std::vector<int32_t>& inc_ptr, const std::vector<int32_t>& inc,
+                      cudaStream_t s);
+// fused local step + assembly: b = by0 + sum (RHS form) or b = (M/dt^2)(y - x) + sum (residual form)
+void launch_local_assemble(const pd_mesh* m, const float4* x, const float4* by0, const float4* y, float4* b,
+                           bool residual, cudaStream_t s);
 void launch_inertia(const pd_mesh* m, float h, float gx, float gy, float gz, cudaStream_t s);
 void launch_velocity(const pd_mesh* m, float inv_h, cudaStream_t s);
 void launch_pin_copy(const pd_mesh* m, const float* user_targets, cudaStream_t s);

@@ -1,14 +1,23 @@
-// Serving loop of the C ABI: requests (one garment mesh each) are admitted
-// while the HBM budget allows, stay resident on the device, and advance one
+// Serving loop of the C ABI: continuous batching of garment simulations on
+// one GPU.  Requests (one mesh each) are admitted by a worker thread while
+// the HBM budget and the slots allow: it builds the mesh and runs the FP64
+// prefactorisation on its own low-priority stream, so the requests already
+// resident keep advancing meanwhile.  Every resident request advances one
 // frame per pd_server_tick in shared batched launches (one CUDA graph per
-// set of resident requests).  Requests that arrive while others run are
-// admitted at the next tick as memory and slots free up.
+// set of resident requests); a newly prepared request joins at the next
+// tick.  Retired meshes are freed by the worker too, so the tick thread
+// never waits on a device-wide free.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <deque>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "pd_internal.h"
@@ -23,7 +32,7 @@ void launch_b_gather(const BatchSlot* slots, const int* off, int n_slots, int bl
 void launch_b_reduce(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_b_velocity(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_axpy_b(const AxDesc* descs, const AxBlock* blocks, const AxBases* bases, int n_blocks, int k_max,
-                   cudaStream_t s);
+                   int w_max, int* err, cudaStream_t s);
 int ax_outputs_per_block(int prec);
 bool configure_coarse_b(int max_cols);
 void launch_coarse_b(const CoarseDescB* cd, int n_desc, int64_t U, int max_cols, int blocks, cudaStream_t s);
@@ -55,11 +64,16 @@ struct Request {
     DBuf<float4> pin_rest;
     DBuf<int32_t> frame;
     int32_t frames_done = 0;
+    // per-frame latency seen by the request: wall time from its admission (or
+    // its previous frame) to the completion of the frame, stalls included
+    std::chrono::steady_clock::time_point t_last;
     std::vector<float> frame_ms, x_final;
     ~Request() {
         if (mesh) pd_destroy_mesh(mesh);
     }
 };
+
+using Clock = std::chrono::steady_clock;
 
 enum { PH_DRIVE = 0, PH_INER, PH_LOC, PH_ASM, PH_GAT, PH_RED, PH_VEL, PH_NB };
 
@@ -68,32 +82,49 @@ enum { PH_DRIVE = 0, PH_INER, PH_LOC, PH_ASM, PH_GAT, PH_RED, PH_VEL, PH_NB };
 struct pd_server {
     int64_t budget = 0;
     int32_t max_slots = 0, n_iter = 20;
+    int device = 0;
     cudaStream_t stream = nullptr, cap = nullptr;
+    cudaStream_t adm = nullptr;            // admission stream (lowest priority)
     pd_request_id next_id = 1;
+    // shared with the admission worker (under mu)
+    std::mutex mu;
+    std::condition_variable cv;            // work for the worker
+    std::condition_variable cv_ready;      // a request became ready (or failed)
     std::map<pd_request_id, std::unique_ptr<Request>> reqs;
-    std::deque<pd_request_id> queue;
+    std::deque<pd_request_id> queue;       // waiting for admission, in arrival order
+    std::deque<pd_request_id> ready;       // prepared by the worker, joining at the next tick
+    std::vector<std::pair<pd_mesh*, int64_t>> retired;   // meshes the worker frees, with their budgeted bytes
+    int32_t n_active = 0;                  // resident requests (read by the worker)
+    bool preparing = false;                // the worker holds the queue head
+    bool stop = false;
+    int64_t used = 0, reserved = 0, peak = 0;
+    uint64_t freed_gen = 0;                // bumps whenever memory or a slot is returned
+    std::thread worker;
+    // tick thread only
     std::vector<pd_request_id> active;
-    int64_t used = 0, peak = 0;
     bool dirty = true;
     cudaGraphExec_t graph = nullptr;
     int sms = 0;
-    // batch descriptors
+    // batch descriptors (capacity grows, never shrinks: no free on the tick thread)
     DBuf<BatchSlot> d_slots;
     DBuf<int32_t> d_off[PH_NB];
     int blocks[PH_NB] = {0};
     DBuf<AxDesc> d_axc, d_axb;
     DBuf<AxBlock> d_blkc, d_blkb;
     DBuf<AxBases> d_basc, d_basb;
-    int blocks_c = 0, blocks_b = 0, kmax_c = 1, kmax_b = 1;
+    int blocks_c = 0, blocks_b = 0, kmax_c = 1, kmax_b = 1, wmax_c = 1, wmax_b = 1;
     DBuf<CoarseDescB> d_cd;
     int n_cd = 0, max_cols = 0, coarse_blocks = 0;
     int64_t units = 0;
+    DBuf<float> d_out;                     // final positions of a retiring request
+    DBuf<int32_t> d_err;                   // bounded-wait flag of the batched products
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     ~pd_server() {
         if (graph) cudaGraphExecDestroy(graph);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         if (cap) cudaStreamDestroy(cap);
+        if (adm) cudaStreamDestroy(adm);
     }
 };
 
@@ -116,6 +147,15 @@ static void estimate(pd_mesh* m, int64_t& steady, int64_t& transient) {
     transient = nd * (2 * NI * NI + 2 * NI * NB + NB * NB) * 8 + 2 * nBp * nBp * 8 + nBp * 64 * 8 * 2;
 }
 
+// Copies a host vector into a device buffer whose capacity only grows (a
+// reallocation, the only free here, happens when a larger resident set first
+// appears).
+template <class T>
+static void put(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
+    if (h.size() > d.n) d.alloc(std::max(h.size(), 2 * d.n));
+    if (!h.empty()) PDG_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
 static void rebuild(pd_server* S) {
     const int n = (int)S->active.size();
     if (S->graph) {
@@ -132,7 +172,6 @@ static void rebuild(pd_server* S) {
     std::vector<AxBases> basc(n), basb(n);
     std::vector<CoarseDescB> cd;
     int64_t units = 0;
-    const int OW = ax_outputs_per_block(PD_PREC_FP32);
     int max_cols = 0;
     for (int k = 0; k < n; ++k) {
         Request& R = *S->reqs[S->active[k]];
@@ -182,16 +221,15 @@ static void rebuild(pd_server* S) {
         const float* pool = m->d_mat32.p;
         basc[k] = AxBases{pool, m->d_b.p, nullptr, nullptr, m->d_tc.p};
         basb[k] = AxBases{pool, m->d_x.p + m->n_int, m->d_bidx.p, m->d_tc.p, m->d_x.p};
+        // the meshes' products are tiled (bulk-copy layout): one block per output chunk of ld outputs
         for (AxDesc a : m->h_ax_desc_cond) {
             a.slot = k;
-            const int32_t cw = a.tiled ? a.ld : OW;   // tiled: one block per chunk of ld outputs
-            for (int32_t o0 = 0; o0 < a.n_out; o0 += cw) blkc.push_back(AxBlock{(int32_t)axc.size(), o0});
+            for (int32_t o0 = 0; o0 < a.n_out; o0 += a.ld) blkc.push_back(AxBlock{(int32_t)axc.size(), o0});
             axc.push_back(a);
         }
         for (AxDesc a : m->h_ax_desc_back) {
             a.slot = k;
-            const int32_t cw = a.tiled ? a.ld : OW;
-            for (int32_t o0 = 0; o0 < a.n_out; o0 += cw) blkb.push_back(AxBlock{(int32_t)axb.size(), o0});
+            for (int32_t o0 = 0; o0 < a.n_out; o0 += a.ld) blkb.push_back(AxBlock{(int32_t)axb.size(), o0});
             axb.push_back(a);
         }
         if (m->n_B > 0) {
@@ -208,28 +246,29 @@ static void rebuild(pd_server* S) {
             max_cols = std::max(max_cols, m->ld_S);
         }
     }
-    auto up = [&](auto& dbuf, const auto& h) {
-        dbuf.alloc(h.size());
-        if (!h.empty())
-            PDG_CUDA(cudaMemcpyAsync(dbuf.p, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice, S->stream));
-    };
-    up(S->d_slots, slots);
+    put(S->d_slots, slots, S->stream);
     for (int p = 0; p < PH_NB; ++p) {
-        up(S->d_off[p], off[p]);
+        put(S->d_off[p], off[p], S->stream);
         S->blocks[p] = off[p][n];
     }
-    up(S->d_axc, axc);
-    up(S->d_axb, axb);
-    up(S->d_blkc, blkc);
-    up(S->d_blkb, blkb);
-    up(S->d_basc, basc);
-    up(S->d_basb, basb);
+    put(S->d_axc, axc, S->stream);
+    put(S->d_axb, axb, S->stream);
+    put(S->d_blkc, blkc, S->stream);
+    put(S->d_blkb, blkb, S->stream);
+    put(S->d_basc, basc, S->stream);
+    put(S->d_basb, basb, S->stream);
     S->blocks_c = (int)blkc.size();
     S->blocks_b = (int)blkb.size();
-    S->kmax_c = S->kmax_b = 1;
-    for (const auto& a : axc) S->kmax_c = std::max(S->kmax_c, a.K);
-    for (const auto& a : axb) S->kmax_b = std::max(S->kmax_b, a.K);
-    up(S->d_cd, cd);
+    S->kmax_c = S->kmax_b = S->wmax_c = S->wmax_b = 1;
+    for (const auto& a : axc) {
+        S->kmax_c = std::max(S->kmax_c, a.K);
+        S->wmax_c = std::max(S->wmax_c, a.ld);
+    }
+    for (const auto& a : axb) {
+        S->kmax_b = std::max(S->kmax_b, a.K);
+        S->wmax_b = std::max(S->wmax_b, a.ld);
+    }
+    put(S->d_cd, cd, S->stream);
     S->n_cd = (int)cd.size();
     S->units = units;
     S->max_cols = max_cols;
@@ -250,11 +289,11 @@ static void rebuild(pd_server* S) {
         for (int it = 0; it < S->n_iter; ++it) {
             launch_b_local(sl, S->d_off[PH_LOC].p, n, S->blocks[PH_LOC], c);
             launch_b_assemble(sl, S->d_off[PH_ASM].p, n, S->blocks[PH_ASM], c);
-            launch_axpy_b(S->d_axc.p, S->d_blkc.p, S->d_basc.p, S->blocks_c, S->kmax_c, c);
+            launch_axpy_b(S->d_axc.p, S->d_blkc.p, S->d_basc.p, S->blocks_c, S->kmax_c, S->wmax_c, S->d_err.p, c);
             launch_b_gather(sl, S->d_off[PH_GAT].p, n, S->blocks[PH_GAT], c);
             launch_coarse_b(S->d_cd.p, S->n_cd, S->units, S->max_cols, S->coarse_blocks, c);
             launch_b_reduce(sl, S->d_off[PH_RED].p, n, S->blocks[PH_RED], c);
-            launch_axpy_b(S->d_axb.p, S->d_blkb.p, S->d_basb.p, S->blocks_b, S->kmax_b, c);
+            launch_axpy_b(S->d_axb.p, S->d_blkb.p, S->d_basb.p, S->blocks_b, S->kmax_b, S->wmax_b, S->d_err.p, c);
         }
         launch_b_velocity(sl, S->d_off[PH_VEL].p, n, S->blocks[PH_VEL], c);
     } catch (...) {
@@ -268,66 +307,130 @@ static void rebuild(pd_server* S) {
     PDG_CUDA(e);
 }
 
-// Admits the request at the head of the queue if the budget allows.  Returns
-// true when the request leaves the queue (admitted, or failed: it can never
-// fit, or its mesh or factorisation failed), false when it must wait for
-// resident requests to retire.
-static bool admit(pd_server* S, Request& R) {
+// ---------------------------------------------------------------- admission worker
+// Builds and prefactors the request at the head of the queue when the budget
+// and the slots allow, on the admission stream.  Under lk except while it
+// works on the device.  Returns after one admission attempt.
+static void prepare_head(pd_server* S, std::unique_lock<std::mutex>& lk) {
+    const pd_request_id id = S->queue.front();
+    Request& R = *S->reqs[id];
+    auto leave_queue = [&](int32_t state) {
+        R.state = state;
+        S->queue.pop_front();
+        S->cv_ready.notify_all();
+    };
+    auto nothing_resident = [&]() { return S->n_active == 0 && S->ready.empty() && S->retired.empty(); };
     // a request seen before waits on its cached estimate without being rebuilt
-    if (R.estimated && S->used + R.est_steady + R.est_transient > S->budget) {
-        if (!S->active.empty()) return false;
-        R.state = PD_REQ_FAILED;
-        return true;
+    if (R.estimated && S->used + S->reserved + R.est_steady + R.est_transient > S->budget) {
+        if (nothing_resident()) leave_queue(PD_REQ_FAILED);   // it can never fit
+        return;
     }
+    S->preparing = true;
+    lk.unlock();
     pd_mesh* m = nullptr;
     pd_status st = pd_create_mesh(R.rest.data(), R.n_v, R.tets.data(), R.n_t, nullptr, R.density,
                                   R.dom.empty() ? nullptr : R.dom.data(), R.n_dom,
-                                  R.pinned.empty() ? nullptr : R.pinned.data(), S->stream, &m);
-    if (st != PD_OK) {
-        R.state = PD_REQ_FAILED;
-        return true;
-    }
-    R.mesh = m;   // owned by the request from here on (destroyed with it on any failure)
+                                  R.pinned.empty() ? nullptr : R.pinned.data(), S->adm, &m);
     int64_t steady = 0, transient = 0;
-    estimate(m, steady, transient);
+    if (st == PD_OK) estimate(m, steady, transient);
+    lk.lock();
+    S->preparing = false;
+    if (st != PD_OK) {
+        leave_queue(PD_REQ_FAILED);
+        return;
+    }
     R.estimated = true;
     R.est_steady = steady;
     R.est_transient = transient;
-    if (S->used + steady + transient > S->budget) {
+    if (S->used + S->reserved + steady + transient > S->budget) {
+        const bool never = nothing_resident();
+        lk.unlock();
         pd_destroy_mesh(m);
-        R.mesh = nullptr;
-        if (!S->active.empty()) return false;   // waits for resident requests to retire
-        // nothing is resident and it still does not fit: it never will
-        R.state = PD_REQ_FAILED;
-        return true;
+        lk.lock();
+        if (never) leave_queue(PD_REQ_FAILED);
+        return;
     }
+    S->reserved += steady + transient;
+    S->peak = std::max(S->peak, S->used + S->reserved);
+    S->preparing = true;
+    lk.unlock();
     st = pd_set_materials(m, R.gs.data(), R.gv.data());
     pd_solver_opts o{PD_PREC_FP32, 0, 0, PD_SOLVE_SINGLE_LEVEL};  // the batched coarse kernel is single-level
     m->batched_only = true;   // the serving loop runs its own batched kernels: no streaming copies
     if (st == PD_OK) st = pd_prefactor(m, R.dt, &o);
-    if (st != PD_OK) {
-        pd_destroy_mesh(m);
-        R.mesh = nullptr;
-        R.state = PD_REQ_FAILED;
-        return true;
+    if (st == PD_OK) {
+        try {
+            // pinned rest positions (increasing vertex id) and the frame counter
+            std::vector<float4> pr;
+            for (int32_t v = 0; v < R.n_v; ++v)
+                if (!R.pinned.empty() && R.pinned[v])
+                    pr.push_back(make_float4((float)R.rest[3 * (size_t)v], (float)R.rest[3 * (size_t)v + 1],
+                                             (float)R.rest[3 * (size_t)v + 2], 0.f));
+            R.pin_rest.alloc(std::max<size_t>(pr.size(), 1));
+            if (!pr.empty())
+                PDG_CUDA(cudaMemcpyAsync(R.pin_rest.p, pr.data(), pr.size() * sizeof(float4),
+                                         cudaMemcpyHostToDevice, S->adm));
+            R.frame.alloc(1);
+            PDG_CUDA(cudaMemsetAsync(R.frame.p, 0, sizeof(int32_t), S->adm));
+            PDG_CUDA(cudaStreamSynchronize(S->adm));
+        } catch (const Fail& f) {
+            st = f.code;
+        } catch (const std::bad_alloc&) {
+            st = PD_ERR_NO_MEMORY;
+        }
     }
-    R.steady_bytes = steady;
-    S->peak = std::max(S->peak, S->used + steady + transient);
+    if (st != PD_OK) {
+        R.pin_rest.free();
+        R.frame.free();
+        pd_destroy_mesh(m);
+        lk.lock();
+        S->preparing = false;
+        S->reserved -= steady + transient;
+        leave_queue(PD_REQ_FAILED);
+        return;
+    }
+    lk.lock();
+    S->preparing = false;
+    S->reserved -= steady + transient;
     S->used += steady;
-    R.state = PD_REQ_ACTIVE;   // resident: retired (and its bytes returned) like any other from here on
-    // pinned rest positions (increasing vertex id) and the frame counter
-    std::vector<float4> pr;
-    for (int32_t v = 0; v < R.n_v; ++v)
-        if (!R.pinned.empty() && R.pinned[v])
-            pr.push_back(make_float4((float)R.rest[3 * (size_t)v], (float)R.rest[3 * (size_t)v + 1],
-                                     (float)R.rest[3 * (size_t)v + 2], 0.f));
-    R.pin_rest.alloc(std::max<size_t>(pr.size(), 1));
-    if (!pr.empty())
-        PDG_CUDA(cudaMemcpyAsync(R.pin_rest.p, pr.data(), pr.size() * sizeof(float4), cudaMemcpyHostToDevice,
-                                 S->stream));
-    R.frame.alloc(1);
-    PDG_CUDA(cudaMemsetAsync(R.frame.p, 0, sizeof(int32_t), S->stream));
-    return true;
+    R.mesh = m;
+    R.steady_bytes = steady;
+    R.t_last = Clock::now();
+    S->queue.pop_front();
+    S->ready.push_back(id);
+    S->cv_ready.notify_all();
+}
+
+static void worker_main(pd_server* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    uint64_t seen_gen = ~uint64_t(0);
+    for (;;) {
+        // free the meshes the tick thread retired
+        while (!S->retired.empty()) {
+            std::vector<std::pair<pd_mesh*, int64_t>> dead;
+            dead.swap(S->retired);
+            lk.unlock();
+            for (auto& d : dead) pd_destroy_mesh(d.first);
+            lk.lock();
+            for (auto& d : dead) S->used -= d.second;   // returned to the budget once actually freed
+            ++S->freed_gen;
+        }
+        if (S->stop) break;
+        const bool slot_free = S->n_active + (int32_t)S->ready.size() < S->max_slots;
+        if (!S->queue.empty() && slot_free) {
+            const pd_request_id head = S->queue.front();
+            const Request& R = *S->reqs[head];
+            // a request waiting on the budget is retried only after memory was returned
+            if (!(R.estimated && seen_gen == S->freed_gen &&
+                  S->used + S->reserved + R.est_steady + R.est_transient > S->budget)) {
+                seen_gen = S->freed_gen;
+                prepare_head(S, lk);
+                continue;
+            }
+        }
+        S->cv.wait(lk);
+    }
 }
 
 extern "C" {
@@ -344,15 +447,23 @@ pd_status pd_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t 
         S->max_slots = max_slots;
         S->n_iter = n_iter;
         S->stream = static_cast<cudaStream_t>(stream);
+        PDG_CUDA(cudaGetDevice(&S->device));
         PDG_CUDA(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
+        int prio_low = 0, prio_high = 0;
+        PDG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+        PDG_CUDA(cudaStreamCreateWithPriority(&S->adm, cudaStreamNonBlocking, prio_low));
         PDG_CUDA(cudaEventCreate(&S->e0));
         PDG_CUDA(cudaEventCreate(&S->e1));
-        int dev = 0;
-        PDG_CUDA(cudaGetDevice(&dev));
-        PDG_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, dev));
+        PDG_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device));
+        S->d_err.alloc(1);
+        PDG_CUDA(cudaMemset(S->d_err.p, 0, sizeof(int32_t)));
+        S->worker = std::thread(worker_main, S);
     } catch (const Fail& f) {
         delete S;
         return f.code;
+    } catch (const std::system_error&) {
+        delete S;
+        return sfail(PD_ERR_NO_MEMORY, "could not start the admission thread");
     }
     *out = S;
     return PD_OK;
@@ -360,7 +471,15 @@ pd_status pd_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t 
 
 void pd_server_destroy(pd_server* S) {
     if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->worker.joinable()) S->worker.join();
     cudaStreamSynchronize(S->stream);
+    for (auto& d : S->retired) pd_destroy_mesh(d.first);
+    S->retired.clear();
     delete S;
 }
 
@@ -370,7 +489,6 @@ pd_status pd_submit(pd_server* S, const pd_request* q, pd_request_id* id) {
         return sfail(PD_ERR_INVALID_ARG, "bad request");
     try {
         auto R = std::make_unique<Request>();
-        R->id = S->next_id++;
         R->n_v = q->n_v;
         R->n_t = q->n_t;
         R->n_dom = q->n_domains;
@@ -387,9 +505,14 @@ pd_status pd_submit(pd_server* S, const pd_request* q, pd_request_id* id) {
         R->amp = q->drive_amp;
         R->freq = q->drive_freq;
         R->axis = q->drive_axis;
-        *id = R->id;
-        S->queue.push_back(R->id);
-        S->reqs[R->id] = std::move(R);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            R->id = S->next_id++;
+            *id = R->id;
+            S->queue.push_back(R->id);
+            S->reqs[R->id] = std::move(R);
+        }
+        S->cv.notify_all();
     } catch (const std::bad_alloc&) {
         return sfail(PD_ERR_NO_MEMORY, "host allocation failed");
     }
@@ -399,39 +522,54 @@ pd_status pd_submit(pd_server* S, const pd_request* q, pd_request_id* id) {
 pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
     try {
-        // retire finished requests
+        // retire finished requests: read back their positions, hand their meshes to the worker
+        std::vector<std::pair<pd_mesh*, int64_t>> dead;
         for (size_t k = 0; k < S->active.size();) {
-            Request& R = *S->reqs[S->active[k]];
-            if (R.frames_done >= R.n_frames) {
-                R.x_final.resize(3 * (size_t)R.n_v);
-                DBuf<float> tmp;
-                tmp.alloc(3 * (size_t)R.n_v);
-                launch_scatter_out(R.mesh, R.mesh->d_x.p, tmp.p, 0, S->stream);
-                PDG_CUDA(cudaMemcpyAsync(R.x_final.data(), tmp.p, sizeof(float) * 3 * R.n_v, cudaMemcpyDeviceToHost,
+            Request* R;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                R = S->reqs[S->active[k]].get();
+            }
+            if (R->frames_done >= R->n_frames) {
+                const size_t n3 = 3 * (size_t)R->n_v;
+                R->x_final.resize(n3);
+                if (n3 > S->d_out.n) S->d_out.alloc(std::max(n3, 2 * S->d_out.n));
+                launch_scatter_out(R->mesh, R->mesh->d_x.p, S->d_out.p, 0, S->stream);
+                PDG_CUDA(cudaMemcpyAsync(R->x_final.data(), S->d_out.p, sizeof(float) * n3, cudaMemcpyDeviceToHost,
                                          S->stream));
                 PDG_CUDA(cudaStreamSynchronize(S->stream));
-                pd_destroy_mesh(R.mesh);
-                R.mesh = nullptr;
-                R.pin_rest.free();
-                R.frame.free();
-                S->used -= R.steady_bytes;
-                R.state = PD_REQ_DONE;
+                std::lock_guard<std::mutex> lk(S->mu);
+                dead.emplace_back(R->mesh, R->steady_bytes);
+                R->mesh = nullptr;
+                R->state = PD_REQ_DONE;
                 S->active.erase(S->active.begin() + k);
+                S->n_active = (int32_t)S->active.size();
                 S->dirty = true;
             } else {
                 ++k;
             }
         }
-        // admit in arrival order while slots and memory allow
-        while (!S->queue.empty() && (int)S->active.size() < S->max_slots) {
-            Request& R = *S->reqs[S->queue.front()];
-            if (!admit(S, R)) break;
-            S->queue.pop_front();
-            if (R.state == PD_REQ_ACTIVE) {
-                S->active.push_back(R.id);
+        bool wait_for_ready = false;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            for (auto& d : dead) S->retired.push_back(d);
+            // nothing to run yet but requests on their way: wait (bounded) for the first to be ready
+            wait_for_ready = S->active.empty() && S->ready.empty() && (!S->queue.empty() || S->preparing);
+            if (wait_for_ready) {
+                S->cv.notify_all();
+                S->cv_ready.wait_for(lk, std::chrono::milliseconds(5));
+            }
+            // requests prepared by the worker join the batch
+            while (!S->ready.empty()) {
+                const pd_request_id id = S->ready.front();
+                S->ready.pop_front();
+                S->reqs[id]->state = PD_REQ_ACTIVE;
+                S->active.push_back(id);
                 S->dirty = true;
             }
+            S->n_active = (int32_t)S->active.size();
         }
+        S->cv.notify_all();   // slots or memory may have been returned
         if (S->dirty) rebuild(S);
         if (n_active) *n_active = (int32_t)S->active.size();
         float ms = 0.f;
@@ -441,13 +579,22 @@ pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
             PDG_CUDA(cudaEventRecord(S->e1, S->stream));
             PDG_CUDA(cudaEventSynchronize(S->e1));
             PDG_CUDA(cudaEventElapsedTime(&ms, S->e0, S->e1));
+            const auto now = Clock::now();
+            std::lock_guard<std::mutex> lk(S->mu);
             for (auto id : S->active) {
                 Request& R = *S->reqs[id];
                 R.frames_done++;
-                R.frame_ms.push_back(ms);
+                R.frame_ms.push_back(std::chrono::duration<float, std::milli>(now - R.t_last).count());
+                R.t_last = now;
             }
         }
         if (frame_ms) *frame_ms = ms;
+        int32_t herr = 0;
+        PDG_CUDA(cudaMemcpy(&herr, S->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (herr) {
+            PDG_CUDA(cudaMemset(S->d_err.p, 0, sizeof(int32_t)));
+            return sfail(PD_ERR_TIMEOUT, "pd_server_tick: a bounded wait of the batched products ran out");
+        }
     } catch (const Fail& f) {
         return f.code;
     } catch (const std::bad_alloc&) {
@@ -458,11 +605,16 @@ pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
     return PD_OK;
 }
 
+static bool outstanding(pd_server* S) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    return !S->queue.empty() || !S->ready.empty() || S->preparing || !S->active.empty();
+}
+
 pd_status pd_server_run(pd_server* S, int32_t max_ticks, int32_t* ticks) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
     if (max_ticks < 1) return sfail(PD_ERR_INVALID_ARG, "max_ticks must be >= 1");
     int32_t t = 0;
-    for (; t < max_ticks && (!S->queue.empty() || !S->active.empty()); ++t) {
+    for (; t < max_ticks && outstanding(S); ++t) {
         const pd_status st = pd_server_tick(S, nullptr, nullptr);
         if (st != PD_OK) {
             if (ticks) *ticks = t;
@@ -470,13 +622,14 @@ pd_status pd_server_run(pd_server* S, int32_t max_ticks, int32_t* ticks) {
         }
     }
     if (ticks) *ticks = t;
-    if (!S->queue.empty() || !S->active.empty())
+    if (outstanding(S))
         return sfail(PD_ERR_TIMEOUT, "pd_server_run: max_ticks ticks ran and requests are still queued or resident");
     return PD_OK;
 }
 
 pd_status pd_poll(pd_server* S, pd_request_id id, int32_t* state, int32_t* frames_done) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->reqs.find(id);
     if (it == S->reqs.end()) return sfail(PD_ERR_INVALID_ARG, "unknown request id");
     if (state) *state = it->second->state;
@@ -486,6 +639,7 @@ pd_status pd_poll(pd_server* S, pd_request_id id, int32_t* state, int32_t* frame
 
 pd_status pd_fetch(pd_server* S, pd_request_id id, float* x_out, float* frame_ms) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->reqs.find(id);
     if (it == S->reqs.end()) return sfail(PD_ERR_INVALID_ARG, "unknown request id");
     Request& R = *it->second;
@@ -497,19 +651,25 @@ pd_status pd_fetch(pd_server* S, pd_request_id id, float* x_out, float* frame_ms
 
 pd_status pd_release(pd_server* S, pd_request_id id) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
-    auto it = S->reqs.find(id);
-    if (it == S->reqs.end()) return sfail(PD_ERR_INVALID_ARG, "unknown request id");
-    if (it->second->state == PD_REQ_ACTIVE || it->second->state == PD_REQ_QUEUED)
-        return sfail(PD_ERR_INVALID_ARG, "request still queued or active");
-    S->reqs.erase(it);
+    std::unique_ptr<Request> gone;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(id);
+        if (it == S->reqs.end()) return sfail(PD_ERR_INVALID_ARG, "unknown request id");
+        if (it->second->state == PD_REQ_ACTIVE || it->second->state == PD_REQ_QUEUED)
+            return sfail(PD_ERR_INVALID_ARG, "request still queued or active");
+        gone = std::move(it->second);
+        S->reqs.erase(it);
+    }
     return PD_OK;
 }
 
 pd_status pd_server_stats(pd_server* S, int32_t* n_queued, int32_t* n_active, int64_t* used_bytes,
                           int64_t* peak_bytes) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
     if (n_queued) *n_queued = (int32_t)S->queue.size();
-    if (n_active) *n_active = (int32_t)S->active.size();
+    if (n_active) *n_active = (int32_t)(S->active.size() + S->ready.size());
     if (used_bytes) *used_bytes = S->used;
     if (peak_bytes) *peak_bytes = S->peak;
     return PD_OK;

@@ -3,8 +3,8 @@ every per-element stiffness parameter (the quantity the paper's adjoint
 Gauss-Newton material fitting consumes, Sec. 6.1).
 
 The forward pass runs N time steps solved to equilibrium (PD iterations
-followed by Newton steps, `pd_equilibrium_step`), keeping only the state
-(x, v) every `checkpoint_every` steps.  The backward pass walks the
+followed by Newton steps with an FP64 residual, `pd_equilibrium_step`),
+keeping only the FP64 state (x, v) every `checkpoint_every` steps.  The backward pass walks the
 segments from the last one, recomputes each segment's positions from its
 checkpoint, and runs the adjoint recurrence backwards through them
 (`pd_adjoint_step`).  Parameterisation: gamma_s = theta, gamma_v =
@@ -53,8 +53,8 @@ class DiffSim:
         """Returns (loss tensor, checkpoints, stored positions or None)."""
         self.set_theta(theta)
         m, a = self.mesh, self.adj
-        m.set_state(self.x0, self.v0)
-        ckpts = {0: (self.x0.clone(), self.v0.clone())}
+        a.set_state64(self.x0.double(), self.v0.double())
+        ckpts = {0: a.get_state64()}
         stored = [] if self.store_all else None
         loss = torch.zeros(1, device="cuda", dtype=torch.float64)
         x = torch.empty((m.n_v, 3), device="cuda")
@@ -62,9 +62,9 @@ class DiffSim:
             a.equilibrium_step(self._pin(n), self.gravity, self.n_pd, self.n_newton, x_out=x)
             a.pose_misfit_accumulate(x, targets[n + 1], loss)
             if stored is not None:
-                stored.append(x.clone())
+                stored.append((x.clone(), a.get_state64()[0]))
             if (n + 1) % self.C == 0 and n + 1 < self.N:
-                ckpts[n + 1] = tuple(t.clone() for t in m.get_state())
+                ckpts[n + 1] = a.get_state64()      # FP64 checkpoints: the recomputation is bitwise the original
         return loss.reshape(()), ckpts, stored
 
     def backward(self, ckpts, stored, targets):
@@ -80,15 +80,15 @@ class DiffSim:
             if stored is not None:
                 xs = stored[start:end]
             else:
-                m.set_state(*ckpts[start])
+                a.set_state64(*ckpts[start])
                 xs = []
                 for n in range(start, end):
                     a.equilibrium_step(self._pin(n), self.gravity, self.n_pd, self.n_newton, x_out=x)
-                    xs.append(x.clone())
+                    xs.append((x.clone(), a.get_state64()[0]))
             for n in range(end - 1, start - 1, -1):
-                xn = xs[n - start]
+                xn, xn64 = xs[n - start]
                 a.pose_misfit_accumulate(xn, targets[n + 1], scratch, dl)   # dL/dx_n = 2 (x_n - xhat_n), 0 on pins
-                a.step(xn, dl, gs, gv)
+                a.step64(xn64, dl, gs, gv)
         return gs, gv
 
 

@@ -216,6 +216,30 @@ class Adjoint:
                "pd_adjoint_step")
         m._keep["adj"] = (xt, gt)
 
+    def step64(self, x_n, dL_dx, dL_dgs, dL_dgv):
+        """pd_adjoint_step64: one backward step at an FP64 state x_n (n_v, 3) float64 on the device."""
+        m = self.mesh
+        xt = x_n.to(device="cuda", dtype=torch.float64).contiguous()
+        gt = _dev_f32(dL_dx, (m.n_v, 3))
+        _check(lib().pd_adjoint_step64(m._h, self._h, _ptr(xt), _ptr(gt), _ptr(dL_dgs), _ptr(dL_dgv)),
+               "pd_adjoint_step64")
+        m._keep["adj"] = (xt, gt)
+
+    def get_state64(self):
+        """(x, v) of the FP64 equilibrium state, (n_v, 3) float64 device tensors."""
+        m = self.mesh
+        x = torch.empty((m.n_v, 3), device="cuda", dtype=torch.float64)
+        v = torch.empty((m.n_v, 3), device="cuda", dtype=torch.float64)
+        _check(lib().pd_adjoint_get_state64(self._h, _ptr(x), _ptr(v)), "pd_adjoint_get_state64")
+        return x, v
+
+    def set_state64(self, x, v):
+        m = self.mesh
+        xt = x.to(device="cuda", dtype=torch.float64).contiguous()
+        vt = v.to(device="cuda", dtype=torch.float64).contiguous()
+        _check(lib().pd_adjoint_set_state64(self._h, _ptr(xt), _ptr(vt)), "pd_adjoint_set_state64")
+        m._keep["state64"] = (xt, vt)
+
     def hessian_vec(self, x, v):
         m = self.mesh
         out = torch.empty((m.n_v, 3), device="cuda", dtype=torch.float32)

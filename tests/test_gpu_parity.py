@@ -86,6 +86,68 @@ def test_projection_matches_oracle():
     assert np.abs(np.linalg.det(V.astype(np.float64)) - 1).max() < 1e-4
 
 
+# the oracle's adversarial singular values (ties, inverted, huge stretch, clamp active)
+ADVERSARIAL = [
+    (1, 1, 1), (2, 2, 1), (100, 1, 1), (3, 1, 0.2), (1.1, 0.9, -0.3), (0.5, 0.5, 0.5),
+    (5, 5, 5), (1.5, 1.5, 1.5), (1.0001, 1.0, 0.9999), (2, 1e-3, 1e-3), (1, 1, 0.0),
+    (1, 1, -1), (0.02, 0.02, 0.02), (50, 50, 1e-4), (1.9, 1.8, 1.7), (3, 3, 0.5),
+    (10, 0.5, 0.5), (0.3, 0.2, -0.1), (2.5, 0.4, 0.05), (8, 8, 8), (1.2, 1.2, -2.0),
+]
+
+
+def test_projection_adversarial_and_wide_range():
+    """The local-step projections on the hard branches of the volume target:
+    the oracle's 21 adversarial singular-value triples (each under 50 random
+    rotation pairs), 10^4 triples log-uniform in [1e-3, 100] with 20 %
+    inverted, and near-ties (relative gaps 1e-6 .. 1e-2).  Compared where the
+    answer is unique: the signed singular values, the sorted volume targets
+    and the optimal cost ||F - V||^2 (always), R where the polar factor is
+    well conditioned; V must satisfy det V = 1 and targets >= 0.01."""
+    from paper_2405_12484_gb300.sim import project
+    rng = np.random.default_rng(31)
+    sig = [np.repeat(np.array(ADVERSARIAL, float), 50, axis=0)]
+    wide = np.sort(np.exp(rng.uniform(np.log(1e-3), np.log(100.0), (10000, 3))), axis=1)[:, ::-1].copy()
+    wide[rng.uniform(size=10000) < 0.2, 2] *= -1
+    sig.append(wide)
+    base = np.exp(rng.uniform(np.log(0.05), np.log(20.0), (2000, 1)))
+    gaps = 10.0 ** rng.uniform(-6, -2, (2000, 2))
+    ties = np.concatenate([base, base * (1 - gaps[:, :1]), base * (1 - gaps[:, :1]) * (1 - gaps[:, 1:])], axis=1)
+    ties[rng.uniform(size=2000) < 0.2, 2] *= -1
+    sig.append(ties)
+    s = np.concatenate(sig)
+    n = s.shape[0]
+    U, W = _rot(n, rng), _rot(n, rng)
+    F32 = ((U * s[:, None, :]) @ np.swapaxes(W, 1, 2)).astype(np.float32)
+    F = F32.astype(np.float64)
+    R, V, sg = project(torch.as_tensor(F32))
+    R, V, sg = (t.cpu().numpy().astype(np.float64) for t in (R, V, sg))
+    Ro, Vo, Uo, so, Wo, do = project_both(F)
+    assert np.all(np.isfinite(R)) and np.all(np.isfinite(V))
+    smax = np.abs(so).max(axis=1)
+    e_sig = float((np.abs(sg - so).max(axis=1) / smax).max())
+    # targets of the GPU's V (its singular values), sorted, against the oracle's
+    dv = np.sort(np.linalg.svd(V, compute_uv=False), axis=1)
+    dor = np.sort(np.abs(do), axis=1)
+    e_d = float((np.abs(dv - dor) / np.maximum(1.0, dor.max(axis=1, keepdims=True))).max())
+    cost_g = np.sum((F - V) ** 2, axis=(1, 2))
+    cost_o = np.sum((F - Vo) ** 2, axis=(1, 2))
+    excess = (cost_g - cost_o) / np.maximum(cost_o, 1e-6 * smax ** 2)
+    # R is unique where sigma_2 + sigma_3 > 0; FP32 error grows with kappa = sigma_1 / (sigma_2 + sigma_3)
+    kappa = smax / np.maximum(so[:, 1] + so[:, 2], 1e-30)
+    okR = kappa < 1e3
+    e_R = float((np.abs(R - Ro).max(axis=(1, 2))[okR] / (2e-5 + 2e-6 * kappa[okR])).max())
+    detV = np.linalg.det(V)
+    _record("projection_adversarial", {"n": int(n), "max_rel_err_sigma": e_sig, "max_rel_err_targets": e_d,
+                                       "max_rel_cost_excess": float(excess.max()),
+                                       "max_R_err_over_bound": e_R, "max_det_V_err": float(np.abs(detV - 1).max())})
+    assert e_sig < 2e-5
+    assert e_d < 5e-4
+    assert excess.max() < 3e-4      # FP32 rounding of V's entries, relative to a small optimal cost
+    assert e_R < 1.0
+    assert np.abs(detV - 1).max() < 1e-3
+    assert dv.min() >= 0.01 * (1 - 1e-3)
+
+
 def _deformed(w, rng, amp=0.02):
     X = w.rest
     x = X.copy()
@@ -116,6 +178,46 @@ def test_local_step_and_rhs_match_oracle():
     e_elastic = rel(b_gpu[o.free] - inertia[o.free], b_or[o.free] - inertia[o.free])
     _record("local_rhs", {"rel_err_b": e_total, "rel_err_elastic_part": e_elastic})
     assert np.all(b_gpu[o.pin_ids] == 0.0)
+    assert e_total < 1e-6
+    assert e_elastic < 2e-5
+
+
+def test_local_step_inverted_and_stretched_tets():
+    """Local step and RHS on the parity slab with a 50x stretched band
+    (x < 0.03 stretched 50x along x) and an inverted patch (z mirrored and
+    halved about the mid-plane for 0.09 < x < 0.13, 0.05 < y < 0.11), so that
+    the volume targets take the clamped and inverted branches."""
+    w = parity_slab()
+    m, o = make_pair(w)
+    rng = np.random.default_rng(14)
+    X = w.rest
+    x = X.copy()
+    band = X[:, 0] < 0.03
+    x[band, 0] = 50.0 * X[band, 0]
+    x[~band, 0] += 49.0 * 0.03
+    patch = (X[:, 0] > 0.09) & (X[:, 0] < 0.13) & (X[:, 1] > 0.05) & (X[:, 1] < 0.11)
+    zc = 0.5 * X[:, 2].max()
+    x[patch, 2] = zc - 0.5 * (X[patch, 2] - zc)
+    x += 1e-4 * rng.standard_normal(x.shape)
+    x[o.pin_ids] = X[o.pin_ids]
+    y = x + 1e-3 * rng.standard_normal(x.shape)
+    x32, y32 = x.astype(np.float32), y.astype(np.float32)
+    xd, yd = x32.astype(np.float64), y32.astype(np.float64)
+    F = deformation_gradient(xd, o.tets, o.g)
+    dets = np.linalg.det(F)
+    n_inv, n_str = int((dets < 0).sum()), int((np.linalg.svd(F, compute_uv=False)[:, 0] > 20).sum())
+    b_gpu = m.local_rhs(torch.as_tensor(x32), torch.as_tensor(y32)).cpu().numpy()
+    R, V = o.local(xd)
+    b_or = o.rhs(yd, R, V)
+    b_or[o.free] -= o.K_fp @ xd[o.pin_ids]
+    b_or[o.pin_ids] = 0.0
+    inertia = (o.mass / o.dt ** 2)[:, None] * yd
+    inertia[o.pin_ids] = 0.0
+    e_total = rel(b_gpu, b_or)
+    e_elastic = rel(b_gpu[o.free] - inertia[o.free], b_or[o.free] - inertia[o.free])
+    _record("local_rhs_inverted_stretched", {"rel_err_b": e_total, "rel_err_elastic_part": e_elastic,
+                                             "inverted_tets": n_inv, "stretched_tets": n_str})
+    assert n_inv > 100 and n_str > 100
     assert e_total < 1e-6
     assert e_elastic < 2e-5
 
@@ -164,8 +266,11 @@ def test_one_step_error_slab(slab_traj):
         disp = np.linalg.norm(xs[n] - w.rest)
         errs[n] = (rel(xg, xs[n]), float(np.linalg.norm(xg - xs[n]) / disp))
     _record("one_step_slab", {str(k): {"e_n": a, "e_disp": b} for k, (a, b) in errs.items()})
-    for n, (e, _) in errs.items():
+    for n, (e, ed) in errs.items():
         assert e < 1e-5, (n, e)
+        # relative to the displacement: FP32 positions carry eps32 |x| of rounding, which is
+        # 3e-5 of the 0.4 mm sag after the first step, so the bound is looser while the sag is small
+        assert ed < (5e-4 if n < 10 else 1e-5), (n, ed)
 
 
 def test_trajectory_slab(slab_traj):
@@ -179,7 +284,7 @@ def test_trajectory_slab(slab_traj):
             m.sync()
             e.append(rel(out.cpu().numpy(), xs[n + 1]))
     _record("trajectory_slab", {"e_n_every_10": e})
-    assert max(e) < 1e-3
+    assert max(e) < 2e-5
 
 
 def test_frames_are_bitwise_deterministic():
@@ -281,21 +386,32 @@ def test_status_codes_on_device():
     m.sync()   # the flag was cleared and the mesh is usable again
 
 
-def test_shell_full_size_one_frame():
-    """The 390K-tet shell in the benchmark's launch configuration (graphs, FP32),
-    2 PD iterations against the oracle."""
+@pytest.fixture(scope="module")
+def shell_frame():
+    """The oracle's first frame of the 390K-tet shell with the benchmark's 20 PD iterations."""
+    from oracle.pd_oracle import PDOracle
     w = sweater_shell()
-    m, o = make_pair(w)
+    o = PDOracle(w.rest, w.tets, w.pinned, f32(w.gamma_s), f32(w.gamma_v), w.density, w.dt)
+    xo, _ = o.step(w.rest, np.zeros_like(w.rest), w.pin_targets(0), w.gravity, 20)
+    return w, xo
+
+
+def test_shell_full_size_one_frame(shell_frame):
+    """The 390K-tet shell in the benchmark's launch configuration (graphs, FP32,
+    20 PD iterations) against the oracle's frame."""
+    w, xo = shell_frame
+    m, _ = make_pair(w, factor_oracle=False)
     info = m.info()
     assert info["n_tets"] == 390000 and info["n_domains"] == 200
     x = torch.empty((w.n_v, 3), device="cuda")
-    m.step(torch.as_tensor(w.pin_targets(0), dtype=torch.float32), w.gravity, 2, x_out=x)
+    m.step(torch.as_tensor(w.pin_targets(0), dtype=torch.float32), w.gravity, 20, x_out=x)
     m.sync()
-    xo, _ = o.step(w.rest, np.zeros_like(w.rest), w.pin_targets(0), w.gravity, 2)
     e = rel(x.cpu().numpy(), xo)
     disp = float(np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo - w.rest))
-    _record("shell_full_size", {"e_n": e, "e_disp": disp, "info": info})
+    _record("shell_full_size", {"e_n": e, "e_disp": disp, "pd_iters": 20, "info": info})
+    m.close()
     assert e < 1e-5
+    assert disp < 1e-3
 
 
 @pytest.mark.parametrize("prec,refine,correction,tol", [("bf16", 0, True, 1e-5), ("tf32", 0, True, 1e-5),
@@ -350,21 +466,21 @@ def test_streaming_solve_slab(slab_traj, prec, refine, tol):
     assert max(errs.values()) < tol, errs
 
 
-def test_shell_full_size_mixed_precision():
-    """The 390K-tet shell, BF16 matrices in the correction form, 2 PD iterations
-    against the oracle (the FP32 run of the same frame is in the test above)."""
-    w = sweater_shell()
-    m, o = make_pair(w, precision="bf16")
+def test_shell_full_size_mixed_precision(shell_frame):
+    """The 390K-tet shell, BF16 matrices in the correction form, 20 PD
+    iterations against the oracle's frame (the FP32 run is the test above)."""
+    w, xo = shell_frame
+    m, _ = make_pair(w, precision="bf16", factor_oracle=False)
     m.prefactor(w.dt, precision="bf16", correction=True)
     x = torch.empty((w.n_v, 3), device="cuda")
-    m.step(torch.as_tensor(w.pin_targets(0), dtype=torch.float32), w.gravity, 2, x_out=x)
+    m.step(torch.as_tensor(w.pin_targets(0), dtype=torch.float32), w.gravity, 20, x_out=x)
     m.sync()
-    xo, _ = o.step(w.rest, np.zeros_like(w.rest), w.pin_targets(0), w.gravity, 2)
     e = rel(x.cpu().numpy(), xo)
-    _record("shell_full_size_bf16_correction", {"e_n": e,
-                                                "e_disp": float(np.linalg.norm(x.cpu().numpy() - xo)
-                                                                / np.linalg.norm(xo - w.rest))})
+    disp = float(np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo - w.rest))
+    _record("shell_full_size_bf16_correction", {"e_n": e, "e_disp": disp, "pd_iters": 20})
+    m.close()
     assert e < 1e-5
+    assert disp < 1e-3
 
 
 def test_streaming_wait_runs_out_and_reports_timeout():

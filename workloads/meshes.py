@@ -272,3 +272,22 @@ def request_workload(gen: str, n_tets: float, seed: int, n_iter: int = 20) -> Wo
     dz = min(dz, n_z)
     dth = min(dth, n_theta)
     return sweater_shell(seed=seed, n_theta=n_theta, n_z=n_z, n_r=2, dom_theta=dth, dom_z=dz, n_iter=n_iter)
+
+
+def target_trajectory(rest: np.ndarray, n_steps: int, seed: int) -> list:
+    """Seeded target poses xhat_0 .. xhat_{n_steps} for a pose-matching loss.
+
+    The rest shape plus a smooth seeded displacement that grows linearly
+    with the step index: a sag along the length (y), a bulge across the
+    width (x) and a sideways sway, with amplitudes drawn from `seed`
+    (centimetre scale on a 0.5 m slab).  Plain geometry: no mechanics.
+    """
+    rng = np.random.default_rng(seed)
+    a, b, c = rng.uniform(0.5, 1.5, size=3)
+    lo, hi = rest.min(axis=0), rest.max(axis=0)
+    span = np.where(hi - lo > 0, hi - lo, 1.0)
+    u = (rest - lo) / span
+    disp = np.zeros_like(rest)
+    disp[:, 2] = -0.02 * a * (1.0 - u[:, 1]) ** 2 + 0.004 * b * np.sin(np.pi * u[:, 0])
+    disp[:, 0] = 0.005 * c * (1.0 - u[:, 1]) ** 2
+    return [rest + (n / max(n_steps, 1)) * disp for n in range(n_steps + 1)]
