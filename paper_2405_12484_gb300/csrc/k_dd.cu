@@ -1424,6 +1424,15 @@ void launch_axpy_b(const AxDesc* descs, const AxBlock* blocks, const AxBases* ba
 
 int ax_outputs_per_block(int prec) { return 32 * kAxM * (prec == PD_PREC_BF16 ? 8 : 4); }
 
+// Outputs of one tile of the tiled (bulk-copy) layout, one CTA each: 128 in
+// FP32; the BF16 tiles of the tensor cores keep 128 outputs too, so that a
+// launch has as many CTAs streaming (each with half the bytes), not half as
+// many.
+#ifndef PDG_AXM_CW
+#define PDG_AXM_CW 128
+#endif
+int ax_tile_outputs(int prec) { return prec == PD_PREC_BF16 ? PDG_AXM_CW : 32 * 4; }
+
 void test_set_copy_extra(int bytes, cudaStream_t s) {
     PDG_CUDA(cudaMemcpyToSymbolAsync(g_test_copy_extra, &bytes, sizeof(int), 0, cudaMemcpyHostToDevice, s));
     PDG_CUDA(cudaStreamSynchronize(s));

@@ -25,6 +25,7 @@ int dd_max_sub_cols();
 int dd_coarse_chunk();
 int dd_configure_coarse(int ld_S);
 int ax_outputs_per_block(int prec);
+int ax_tile_outputs(int prec);
 void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s);
 bool build_stream_plan(StreamPlan& P, const std::vector<ColDesc>& blocks, int prec, const void* src,
                        cudaStream_t s);
@@ -1094,7 +1095,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     // (streamed by bulk copies), except for the fused streaming solve, whose
     // plan copies row-major blocks into its own panels
     const bool tiled = !(o.flags & PD_SOLVE_STREAMING);
-    const int OWt = ax_outputs_per_block(m->prec), VNt = (m->prec == PD_PREC_BF16) ? 8 : 4;
+    const int OWt = ax_tile_outputs(m->prec), VNt = (m->prec == PD_PREC_BF16) ? 8 : 4;
     m->ax_tiled = tiled;
     if (tiled) ax_prepare_tma(m->prec);
     auto cast_ax = [&](const double* src, int lds, int rows, int cols, int transpose, int64_t off, int ld) {
@@ -1162,7 +1163,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         // tiled descriptors: ld = the chunk width, one block per chunk
         auto tile_desc = [&](AxDesc& a) {
             if (!a.tiled) return OW;
-            a.ld = ax_chunk_width(a.n_out, OW, VN);
+            a.ld = ax_chunk_width(a.n_out, OWt, VN);
             return (int)a.ld;
         };
         std::vector<AxDesc> dc, di, db, dm1, dm2;

@@ -85,6 +85,7 @@ struct pd_server {
     int device = 0;
     cudaStream_t stream = nullptr, cap = nullptr;
     cudaStream_t adm = nullptr;            // admission stream (lowest priority)
+    std::vector<cudaStream_t> adm_streams; // one per admission thread (lowest priority)
     pd_request_id next_id = 1;
     // shared with the admission worker (under mu)
     std::mutex mu;
@@ -94,12 +95,13 @@ struct pd_server {
     std::deque<pd_request_id> queue;       // waiting for admission, in arrival order
     std::deque<pd_request_id> ready;       // prepared by the worker, joining at the next tick
     std::vector<std::pair<pd_mesh*, int64_t>> retired;   // meshes the worker frees, with their budgeted bytes
-    int32_t n_active = 0;                  // resident requests (read by the worker)
-    bool preparing = false;                // the worker holds the queue head
+    int32_t n_active = 0;                  // resident requests (read by the workers)
+    int32_t n_preparing = 0;               // requests taken from the queue by a worker
     bool stop = false;
     int64_t used = 0, reserved = 0, peak = 0;
     uint64_t freed_gen = 0;                // bumps whenever memory or a slot is returned
-    std::thread worker;
+    std::vector<std::thread> workers;      // admission threads (mesh set-up is host work: several in parallel)
+    std::mutex prefactor_mu;               // one FP64 prefactorisation on the GPU at a time beside the frames
     // tick thread only
     std::vector<pd_request_id> active;
     bool dirty = true;
@@ -125,6 +127,8 @@ struct pd_server {
         if (e1) cudaEventDestroy(e1);
         if (cap) cudaStreamDestroy(cap);
         if (adm) cudaStreamDestroy(adm);
+        for (auto st : adm_streams)
+            if (st) cudaStreamDestroy(st);
     }
 };
 
@@ -307,57 +311,71 @@ static void rebuild(pd_server* S) {
     PDG_CUDA(e);
 }
 
-// ---------------------------------------------------------------- admission worker
-// Builds and prefactors the request at the head of the queue when the budget
-// and the slots allow, on the admission stream.  Under lk except while it
-// works on the device.  Returns after one admission attempt.
-static void prepare_head(pd_server* S, std::unique_lock<std::mutex>& lk) {
+// ---------------------------------------------------------------- admission workers
+constexpr int kAdmissionWorkers = 4;
+
+// Takes the request at the head of the queue and builds and prefactors it on
+// the admission stream when the budget and the slots allow.  Under lk except
+// while it works on the host or the device.  A request that must wait for
+// memory goes back to the head of the queue.
+static void prepare_head(pd_server* S, std::unique_lock<std::mutex>& lk, cudaStream_t adm) {
     const pd_request_id id = S->queue.front();
     Request& R = *S->reqs[id];
-    auto leave_queue = [&](int32_t state) {
-        R.state = state;
-        S->queue.pop_front();
+    auto nothing_resident = [&]() {
+        return S->n_active == 0 && S->ready.empty() && S->retired.empty() && S->n_preparing == 0;
+    };
+    auto fail_it = [&]() {
+        R.state = PD_REQ_FAILED;
         S->cv_ready.notify_all();
     };
-    auto nothing_resident = [&]() { return S->n_active == 0 && S->ready.empty() && S->retired.empty(); };
     // a request seen before waits on its cached estimate without being rebuilt
     if (R.estimated && S->used + S->reserved + R.est_steady + R.est_transient > S->budget) {
-        if (nothing_resident()) leave_queue(PD_REQ_FAILED);   // it can never fit
+        if (nothing_resident()) {
+            S->queue.pop_front();
+            fail_it();   // it can never fit
+        }
         return;
     }
-    S->preparing = true;
+    S->queue.pop_front();
+    ++S->n_preparing;
     lk.unlock();
     pd_mesh* m = nullptr;
     pd_status st = pd_create_mesh(R.rest.data(), R.n_v, R.tets.data(), R.n_t, nullptr, R.density,
                                   R.dom.empty() ? nullptr : R.dom.data(), R.n_dom,
-                                  R.pinned.empty() ? nullptr : R.pinned.data(), S->adm, &m);
+                                  R.pinned.empty() ? nullptr : R.pinned.data(), adm, &m);
     int64_t steady = 0, transient = 0;
     if (st == PD_OK) estimate(m, steady, transient);
     lk.lock();
-    S->preparing = false;
     if (st != PD_OK) {
-        leave_queue(PD_REQ_FAILED);
+        --S->n_preparing;
+        fail_it();
         return;
     }
     R.estimated = true;
     R.est_steady = steady;
     R.est_transient = transient;
     if (S->used + S->reserved + steady + transient > S->budget) {
+        --S->n_preparing;
         const bool never = nothing_resident();
         lk.unlock();
         pd_destroy_mesh(m);
         lk.lock();
-        if (never) leave_queue(PD_REQ_FAILED);
+        if (never) fail_it();
+        else S->queue.push_front(id);   // waits at the head for memory
+        S->cv.notify_all();
         return;
     }
     S->reserved += steady + transient;
     S->peak = std::max(S->peak, S->used + S->reserved);
-    S->preparing = true;
     lk.unlock();
     st = pd_set_materials(m, R.gs.data(), R.gv.data());
     pd_solver_opts o{PD_PREC_FP32, 0, 0, PD_SOLVE_SINGLE_LEVEL};  // the batched coarse kernel is single-level
     m->batched_only = true;   // the serving loop runs its own batched kernels: no streaming copies
-    if (st == PD_OK) st = pd_prefactor(m, R.dt, &o);
+    if (st == PD_OK) {
+        // the FP64 factorisation shares the GPU with the resident requests' frames: one at a time
+        std::lock_guard<std::mutex> pk(S->prefactor_mu);
+        st = pd_prefactor(m, R.dt, &o);
+    }
     if (st == PD_OK) {
         try {
             // pinned rest positions (increasing vertex id) and the frame counter
@@ -369,10 +387,10 @@ static void prepare_head(pd_server* S, std::unique_lock<std::mutex>& lk) {
             R.pin_rest.alloc(std::max<size_t>(pr.size(), 1));
             if (!pr.empty())
                 PDG_CUDA(cudaMemcpyAsync(R.pin_rest.p, pr.data(), pr.size() * sizeof(float4),
-                                         cudaMemcpyHostToDevice, S->adm));
+                                         cudaMemcpyHostToDevice, adm));
             R.frame.alloc(1);
-            PDG_CUDA(cudaMemsetAsync(R.frame.p, 0, sizeof(int32_t), S->adm));
-            PDG_CUDA(cudaStreamSynchronize(S->adm));
+            PDG_CUDA(cudaMemsetAsync(R.frame.p, 0, sizeof(int32_t), adm));
+            PDG_CUDA(cudaStreamSynchronize(adm));
         } catch (const Fail& f) {
             st = f.code;
         } catch (const std::bad_alloc&) {
@@ -384,30 +402,32 @@ static void prepare_head(pd_server* S, std::unique_lock<std::mutex>& lk) {
         R.frame.free();
         pd_destroy_mesh(m);
         lk.lock();
-        S->preparing = false;
+        --S->n_preparing;
         S->reserved -= steady + transient;
-        leave_queue(PD_REQ_FAILED);
+        fail_it();
+        S->cv.notify_all();
         return;
     }
     lk.lock();
-    S->preparing = false;
+    --S->n_preparing;
     S->reserved -= steady + transient;
     S->used += steady;
     R.mesh = m;
     R.steady_bytes = steady;
     R.t_last = Clock::now();
-    S->queue.pop_front();
     S->ready.push_back(id);
     S->cv_ready.notify_all();
+    S->cv.notify_all();
 }
 
-static void worker_main(pd_server* S) {
+static void worker_main(pd_server* S, int index) {
     cudaSetDevice(S->device);
+    cudaStream_t adm = S->adm_streams[index];
     std::unique_lock<std::mutex> lk(S->mu);
     uint64_t seen_gen = ~uint64_t(0);
     for (;;) {
-        // free the meshes the tick thread retired
-        while (!S->retired.empty()) {
+        // free the meshes the tick thread retired (worker 0)
+        while (index == 0 && !S->retired.empty()) {
             std::vector<std::pair<pd_mesh*, int64_t>> dead;
             dead.swap(S->retired);
             lk.unlock();
@@ -415,17 +435,17 @@ static void worker_main(pd_server* S) {
             lk.lock();
             for (auto& d : dead) S->used -= d.second;   // returned to the budget once actually freed
             ++S->freed_gen;
+            S->cv.notify_all();
         }
         if (S->stop) break;
-        const bool slot_free = S->n_active + (int32_t)S->ready.size() < S->max_slots;
+        const bool slot_free = S->n_active + (int32_t)S->ready.size() + S->n_preparing < S->max_slots;
         if (!S->queue.empty() && slot_free) {
-            const pd_request_id head = S->queue.front();
-            const Request& R = *S->reqs[head];
+            const Request& R = *S->reqs[S->queue.front()];
             // a request waiting on the budget is retried only after memory was returned
             if (!(R.estimated && seen_gen == S->freed_gen &&
                   S->used + S->reserved + R.est_steady + R.est_transient > S->budget)) {
                 seen_gen = S->freed_gen;
-                prepare_head(S, lk);
+                prepare_head(S, lk, adm);
                 continue;
             }
         }
@@ -452,12 +472,14 @@ pd_status pd_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t 
         int prio_low = 0, prio_high = 0;
         PDG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
         PDG_CUDA(cudaStreamCreateWithPriority(&S->adm, cudaStreamNonBlocking, prio_low));
+        S->adm_streams.assign(kAdmissionWorkers, nullptr);
+        for (auto& st : S->adm_streams) PDG_CUDA(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_low));
         PDG_CUDA(cudaEventCreate(&S->e0));
         PDG_CUDA(cudaEventCreate(&S->e1));
         PDG_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device));
         S->d_err.alloc(1);
         PDG_CUDA(cudaMemset(S->d_err.p, 0, sizeof(int32_t)));
-        S->worker = std::thread(worker_main, S);
+        for (int k = 0; k < kAdmissionWorkers; ++k) S->workers.emplace_back(worker_main, S, k);
     } catch (const Fail& f) {
         delete S;
         return f.code;
@@ -476,10 +498,12 @@ void pd_server_destroy(pd_server* S) {
         S->stop = true;
     }
     S->cv.notify_all();
-    if (S->worker.joinable()) S->worker.join();
+    for (auto& t : S->workers)
+        if (t.joinable()) t.join();
     cudaStreamSynchronize(S->stream);
     for (auto& d : S->retired) pd_destroy_mesh(d.first);
     S->retired.clear();
+    S->reqs.clear();   // resident and prepared meshes, while their streams still exist
     delete S;
 }
 
@@ -554,7 +578,7 @@ pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
             std::unique_lock<std::mutex> lk(S->mu);
             for (auto& d : dead) S->retired.push_back(d);
             // nothing to run yet but requests on their way: wait (bounded) for the first to be ready
-            wait_for_ready = S->active.empty() && S->ready.empty() && (!S->queue.empty() || S->preparing);
+            wait_for_ready = S->active.empty() && S->ready.empty() && (!S->queue.empty() || S->n_preparing > 0);
             if (wait_for_ready) {
                 S->cv.notify_all();
                 S->cv_ready.wait_for(lk, std::chrono::milliseconds(5));
@@ -607,7 +631,7 @@ pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
 
 static bool outstanding(pd_server* S) {
     std::lock_guard<std::mutex> lk(S->mu);
-    return !S->queue.empty() || !S->ready.empty() || S->preparing || !S->active.empty();
+    return !S->queue.empty() || !S->ready.empty() || S->n_preparing > 0 || !S->active.empty();
 }
 
 pd_status pd_server_run(pd_server* S, int32_t max_ticks, int32_t* ticks) {
@@ -668,7 +692,7 @@ pd_status pd_server_stats(pd_server* S, int32_t* n_queued, int32_t* n_active, in
                           int64_t* peak_bytes) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
     std::lock_guard<std::mutex> lk(S->mu);
-    if (n_queued) *n_queued = (int32_t)S->queue.size();
+    if (n_queued) *n_queued = (int32_t)S->queue.size() + S->n_preparing;
     if (n_active) *n_active = (int32_t)(S->active.size() + S->ready.size());
     if (used_bytes) *used_bytes = S->used;
     if (peak_bytes) *peak_bytes = S->peak;

@@ -146,7 +146,8 @@ static __device__ __forceinline__ void svd3(const float (&F)[3][3], float (&U)[3
     // eigenvectors mixed and B keeps a trailing 2x2 block.  One-sided Jacobi on
     // that block's two columns (their Gram matrix is free of sigma_1) makes them
     // orthogonal, a Givens rotation re-triangularises, and the pair is re-sorted.
-    if (B[1][2] != 0.f) {
+    // (skipped when the off-diagonal is negligible: its effect on s is second order)
+    if (fabsf(B[1][2]) > 1e-5f * (fabsf(B[1][1]) + fabsf(B[2][2]))) {
         const float al = B[1][1] * B[1][1], be = B[1][2] * B[1][2] + B[2][2] * B[2][2], ga = B[1][1] * B[1][2];
         const float zeta = (be - al) / (2.f * ga);
         const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
