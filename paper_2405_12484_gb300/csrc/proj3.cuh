@@ -297,9 +297,10 @@ static __device__ __forceinline__ bool solve_face(const float (&sh)[2], float st
         }
     };
     if (v <= 0.0f) {
-        // + branch: bracket [a, b], Newton safeguarded by bisection.  Two fixed steps from the
-        // uniform-scaling guess (no divergence inside a warp), then the bracketed loop continues,
-        // to the tolerance, only for elements not yet converged.
+        // + branch: bracket [a, b], Newton safeguarded by bisection.  One fixed step from the
+        // uniform-scaling guess (no divergence inside a warp; near rest that guess is within
+        // O(strain^2) of the root), then the bracketed loop continues, to the tolerance, only
+        // for elements not yet converged.
         float a = tm, b = fmaxf(t_hi, tm);
         float prod = st;
 #pragma unroll
@@ -307,7 +308,7 @@ static __device__ __forceinline__ bool solve_face(const float (&sh)[2], float st
         float t = (st > 0.f && prod > 0.f) ? st * expf((logp - logf(prod)) / (K + 1)) : 0.5f * (a + b);
         t = fminf(fmaxf(t, a), b);
 #pragma unroll 1
-        for (int it = 0; it < 2; ++it) {
+        for (int it = 0; it < 1; ++it) {
             face_eval<K>(sh, st, logp, t, v, dv, dd);
             if (v <= 0.0f) a = t; else b = t;
             float tn = t - v / dv;
