@@ -38,7 +38,7 @@ UNIT = "PD iters/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["fp32", "bf16", "tf32"], default="fp32")
@@ -126,7 +126,7 @@ def max_over_ranks(x: float, world: int) -> float:
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -142,10 +142,17 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.dev)], stdout=self.f,
+                                          "-lms", "100", "-i", str(self.dev)], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def mark(self, begin: bool):
+        """Host wall time of the timed region's start and end: samples outside it are not counted."""
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -156,24 +163,32 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+        t0, t1 = getattr(self, "t0", None), getattr(self, "t1", None)
+        inside = [r for r in rows if t0 is not None and t1 is not None and t0 - 0.05 <= r[0] <= t1 + 0.05]
+        use = inside or rows
+        sm = [r[1] for r in use]
+        smax = [r[2] for r in use]
+        reasons = set()
+        for r in use:
+            for n, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "in_timed_window": bool(inside)}
 
 
 def measured_peaks():
@@ -300,7 +315,7 @@ def run_serving(args):
     S = Server(budget, max_slots=64, n_iter=20)
     t0 = time.perf_counter()
     subs, pending = [], list(works)        # subs: (request id, n_tets, arrival)
-    gpu_ms, active_hist = [], []
+    gpu_ms, active_hist, tick_ms = [], [], []
 
     def unfinished():
         return any(S.poll(i)[0] in (0, 1) for i, _, _ in subs)
@@ -310,10 +325,12 @@ def run_serving(args):
         while pending and pending[0][0] <= now:
             a, w, d = pending.pop(0)
             subs.append((S.submit(w, frames, d), w.n_t, a))
+        t_tick = time.perf_counter()
         n, ms = S.tick()
         if n > 0:
             gpu_ms.append(ms)
             active_hist.append(n)
+            tick_ms.append((time.perf_counter() - t_tick) * 1e3)
         elif pending and not subs:
             time.sleep(min(0.002, max(0.0, pending[0][0] - (time.perf_counter() - t0))))
     wall = time.perf_counter() - t0
@@ -354,7 +371,9 @@ def run_serving(args):
                                  "what": "per request, wall time between its consecutive frames (stalls included)"},
             "first_frame_latency_ms": {"p50": pct(first, 0.5), "p99": pct(first, 0.99), "max": max(first),
                                        "what": "per request, from the end of its admission to its first frame"},
-            "batched_frame_gpu_ms": {"p50": pct(gpu_ms, 0.5), "p99": pct(gpu_ms, 0.99)},
+            "batched_frame_gpu_ms": {"p50": pct(gpu_ms, 0.5), "p99": pct(gpu_ms, 0.99), "max": max(gpu_ms)},
+            "tick_wall_ms": {"p50": pct(tick_ms, 0.5), "p99": pct(tick_ms, 0.99), "max": max(tick_ms),
+                             "what": "host wall time of pd_server_tick calls that ran a frame"},
             "mean_resident": float(np.mean(active_hist)), "max_resident": int(max(active_hist)),
             "wall_s": wall, "tet_iters_per_s_wall": tet_iters / wall,
             "tet_iters_per_s_gpu": tet_iters / (sum(gpu_ms) / 1e3),
@@ -436,7 +455,10 @@ def time_leg(m, w, info, pins, n_iter, K, W, stream, local, world, phase_report=
     t_max = max(per_iter.values())
     # near-ties (kernels that run side by side): the one streaming the most bytes
     dominant = max((k for k, v in per_iter.items() if v >= 0.9 * t_max), key=lambda k: info["phase_bytes"][k])
-    m.enable_timing(phase_bit(dominant))
+    # events around the dominant kernel in one PD iteration of every frame (an event pair
+    # in every iteration would add its own cost to the frame time)
+    sample_it = n_iter // 2
+    m.enable_timing(phase_bit(dominant), iteration=sample_it)
     for n in range(2):
         m.step(pins[n], w.gravity, n_iter)
     m.sync()
@@ -446,11 +468,13 @@ def time_leg(m, w, info, pins, n_iter, K, W, stream, local, world, phase_report=
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    clocks.mark(True)
     ev[0].record(stream)
     for k in range(K):
         m.step(pins[W + k], w.gravity, n_iter)
         ev[k + 1].record(stream)
     ev[K].synchronize()
+    clocks.mark(False)
     torch.cuda.synchronize()
     clock_info = clocks.stop()
     barrier(world)
@@ -459,7 +483,7 @@ def time_leg(m, w, info, pins, n_iter, K, W, stream, local, world, phase_report=
     total_ms = ev[0].elapsed_time(ev[K])
     phase = m.phase_times()
     out = {"dominant": dominant, "dom_ms": phase.get(dominant, 0.0), "frame_ms": frame_ms, "total_ms": total_ms,
-           "clocks": clock_info}
+           "clocks": clock_info, "dom_sampled_iteration": sample_it}
     if phase_report:
         peak, _ = measured_peaks()
         m.enable_timing(-1)
@@ -472,7 +496,7 @@ def time_leg(m, w, info, pins, n_iter, K, W, stream, local, world, phase_report=
                 by = info["phase_bytes"].get(k, 0)
                 out["phases"][k] = {"ms": ms, "bytes": by, "GB/s": by / (ms * 1e-3) / 1e9,
                                     "frac": by / (ms * 1e-3) / 1e9 / peak}
-        m.enable_timing(phase_bit(dominant))
+        m.enable_timing(phase_bit(dominant), iteration=sample_it)
     return out
 
 
@@ -547,7 +571,9 @@ def main():
     traffic = ratio * dom_bytes if (ratio is not None and not args.small) else None
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                "traffic": traffic, "algorithmic_bytes": dom_bytes, "avg_launch_ms": dom_ms}
+                "traffic": traffic, "algorithmic_bytes": dom_bytes, "avg_launch_ms": dom_ms,
+                "launches_timed": K, "timed": f"CUDA events on the mesh stream, one launch per timed frame "
+                                             f"(PD iteration {leg['dom_sampled_iteration']})"}
     if dominant in ("dd_interior", "dd_interior2"):
         roofline["note"] = ("runs on a low-priority side stream beside the interface chain (off the critical "
                             "path): its live duration includes the time it yields the GPU to that chain")
@@ -555,7 +581,7 @@ def main():
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region;
     # the same captured frame as the timed region (with the dominant kernel's events)
     pins_h = torch.as_tensor(np.stack([w.pin_targets(n) for n in range(K)]), dtype=torch.float32).pin_memory()
-    out_h = torch.empty((K, w.n_v, 3), dtype=torch.float32).pin_memory()
+    out_h = torch.empty((4, w.n_v, 3), dtype=torch.float32).pin_memory()   # every frame read back, ring of 4
     pin_d = torch.empty((int(w.pinned.sum()), 3), device="cuda")
     for n in range(2):
         m.step(pins[n], w.gravity, n_iter, x_out=x_out)
@@ -567,7 +593,7 @@ def main():
     for k in range(K):
         pin_d.copy_(pins_h[k], non_blocking=True)
         m.step(pin_d, w.gravity, n_iter, x_out=x_out)
-        out_h[k].copy_(x_out, non_blocking=True)
+        out_h[k % 4].copy_(x_out, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
     e2e_value, e2e_ms = whole_job_rate(K * n_iter, e0.elapsed_time(e1), world)
@@ -589,7 +615,8 @@ def main():
                  "ms_per_frame": lm["total_ms"] / K, "pd_iters_per_s": K * n_iter / (lm["total_ms"] / 1e3),
                  "frame_ms": {"p50": pct(lm["frame_ms"], 0.5), "p99": pct(lm["frame_ms"], 0.99)},
                  "dominant": lm["dominant"], "phases": lm.get("phases", {}), "clocks": lm["clocks"],
-                 "tensor_core_kernels": ["k_axpy_mma (interior, boundary-mode and back-substitution products)"]}
+                 "tensor_core_kernels": ["k_axpy_mma (interior, boundary-mode and back-substitution products)",
+                                         "k_rowdot_mma (second-level and coarse row-form products)"]}
 
     # ---- accuracy of each precision's first frame against the FP64 oracle (host-side job)
     accuracy = None

@@ -238,6 +238,16 @@ pd_status pd_solve(pd_mesh* mesh, const float* r, float* x);
  * pd_phase_name(k).  Returns the number of phases in *n_phases.
  */
 pd_status pd_enable_timing(pd_mesh* mesh, int32_t enable);
+/*
+ * pd_set_timing_iteration -- restrict the events of the kernel classes that
+ * run inside the PD iteration loop (local step, solve phases, residual) to
+ * iteration `iteration` of every frame (0-based; -1, the default: every
+ * iteration).  One event pair per frame instead of one per iteration keeps
+ * the timing's own cost out of the frame time; pd_phase_times then averages
+ * the sampled launches.  Kernels outside the loop (inertia, velocity) are
+ * timed in every frame.  Errors: INVALID_ARG (iteration < -1).
+ */
+pd_status pd_set_timing_iteration(pd_mesh* mesh, int32_t iteration);
 pd_status pd_phase_times(pd_mesh* mesh, float* out, int32_t n_out, int32_t* n_phases);
 const char* pd_phase_name(int32_t k);
 
@@ -543,13 +553,17 @@ typedef struct pd_request {
 } pd_request;
 
 /*
- * pd_server_create -- a serving loop on one stream, with continuous batching.
+ * pd_server_create -- a serving loop with continuous batching.
  * hbm_budget_bytes caps the device memory of resident requests (their steady
  * footprint plus the transient FP64 prefactorisation of the one being
  * admitted); max_slots caps how many are resident; n_iter is the PD
- * iteration count of every frame.  An admission thread of the server builds
- * and prefactors queued requests on its own low-priority stream while the
- * resident ones keep advancing, and frees the meshes of retired requests.
+ * iteration count of every frame.  Admission threads of the server build
+ * and prefactor queued requests, each on its own stream of the device's
+ * lowest priority, while the resident ones keep advancing; the first of them
+ * also frees the meshes of retired requests.  The frames run on a stream of
+ * the server's own at the device's highest priority (ahead of admission work
+ * whenever an SM frees up); every pd_server_tick is ordered after the work
+ * queued on cuda_stream (NULL: the legacy default stream) before the call.
  */
 pd_status pd_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t n_iter, void* cuda_stream,
                            pd_server** out);

@@ -90,6 +90,7 @@ SIGNATURES = [
     ("pd_local_rhs", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pd_solve", C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pd_enable_timing", C.c_int32, [C.c_void_p, C.c_int32]),
+    ("pd_set_timing_iteration", C.c_int32, [C.c_void_p, C.c_int32]),
     ("pd_phase_times", C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     ("pd_phase_name", C.c_char_p, [C.c_int32]),
     ("pd_test_offset_phase_counter", C.c_int32, [C.c_void_p, C.c_int32, C.c_int32]),

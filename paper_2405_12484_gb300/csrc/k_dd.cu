@@ -1176,6 +1176,202 @@ __global__ void __launch_bounds__(32 * (kRowtWarps + 1)) k_rowdot_tma(const RowD
     }
 }
 
+// Row-form BF16 products on the tensor cores: out[r] = add[r] + A[r, :] . x
+// with A stored as 16 x 16 blocks in the register order of the A operand of
+// mma.m16n8k16 (rows and columns padded to 16; a 16-row block-row is one
+// contiguous range), so one 16-byte shared load per lane feeds one mma.
+// The B operand is x: columns 0..2 hold x, y, z rounded to BF16, columns
+// 3..5 their BF16 remainders.  A CTA streams whole 16-row block-rows of its
+// unit range in stages of up to kRowtStageBytes with bulk copies; the 16-col
+// blocks of a stage go to the consumer warps in turn, each warp accumulating
+// its own 16 x 8 tile, and the warps' tiles are added in warp order
+// (deterministic) before the 16 outputs of the block-row are written.
+__host__ __device__ inline int64_t rowfrag_index(int r, int c, int Kp) {
+    const int rb = r >> 4, kb = c >> 4, rr = r & 15, kk = c & 15;
+    const int g = rr & 7, rhi = rr >> 3, q = (kk & 7) >> 1, j = kk & 1, khi = kk >> 3;
+    return ((int64_t)rb * (Kp >> 4) + kb) * 256 + (4 * g + q) * 8 + (rhi + 2 * khi) * 2 + j;
+}
+
+__device__ __forceinline__ void mma_bf16_rowform(float (&d)[4], const uint4& a, const uint2& b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+}
+
+#ifndef PDG_ROWM_STAGE_BYTES
+#define PDG_ROWM_STAGE_BYTES 16384
+#endif
+#ifndef PDG_ROWM_STAGES
+#define PDG_ROWM_STAGES 3
+#endif
+constexpr int kRowmStageBytes = PDG_ROWM_STAGE_BYTES;   // a multiple of 512 (whole 16 x 16 blocks)
+constexpr int kRowmStages = PDG_ROWM_STAGES;
+
+// ring, B fragments (16 B per padded column), the warps' tiles
+inline size_t rowm_smem_bytes(int xcap) {
+    const int kp = (std::max(xcap, 1) + 15) & ~15;
+    return (size_t)kRowmStages * kRowmStageBytes + sizeof(uint2) * 2 * (size_t)kp + sizeof(float) * 4 * 32 * kRowtWarps;
+}
+
+__global__ void __launch_bounds__(32 * (kRowtWarps + 1)) k_rowdot_mma(const RowDesc* __restrict__ descs, int n_desc,
+                                                                      const int64_t* __restrict__ blk_u, AxBases B,
+                                                                      int xcap, int* __restrict__ err) {
+    using namespace tma;
+    constexpr int S = kRowmStages;
+    constexpr int SB = kRowmStageBytes / 512;   // 16 x 16 blocks of one stage
+    extern __shared__ __align__(128) unsigned char rm_smem[];
+    const int kcap = (xcap + 15) & ~15;
+    __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(rm_smem);
+    uint2* bfr = reinterpret_cast<uint2*>(rm_smem + (size_t)S * kRowmStageBytes);   // kcap / 16 blocks x 32 lanes
+    float* red = reinterpret_cast<float*>(bfr + 2 * kcap);                           // kRowtWarps x 32 lanes x 4
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ int abort_flag;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t b0 = blk_u[blockIdx.x], b1 = blk_u[blockIdx.x + 1];
+    const __nv_bfloat16* pool = reinterpret_cast<const __nv_bfloat16*>(B.pool);
+    pdl_trigger();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kRowtWarps);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == kRowtWarps) {
+        // producer: every block-row of the range, in stages of up to SB blocks
+        if (lane == 0) {
+            int g = 0, issued = 0;
+            bool ok = true;
+            for (int di = 0; di < n_desc && ok; ++di) {
+                const RowDesc D = descs[di];
+                const int64_t nu = (D.rows + 15) / 16;
+                const int64_t lo = b0 > D.u0 ? b0 : D.u0;
+                const int64_t hi = b1 < D.u0 + nu ? b1 : D.u0 + nu;
+                const int nkb = D.ld >> 4;
+                for (int64_t u = lo; u < hi && ok; ++u) {
+                    const __nv_bfloat16* row = pool + D.a_off + (u - D.u0) * 16 * (int64_t)D.ld;
+                    for (int kb0 = 0; kb0 < nkb; kb0 += SB, ++g) {
+                        const int slot = g % S;
+                        if (g >= S && !mbar_wait(&empty[slot], ((g / S) - 1) & 1, &abort_flag)) {
+                            abort_flag = 1;
+                            atomicOr(err, ERR_TIMEOUT);
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t bytes = (uint32_t)min(SB, nkb - kb0) * 512u;
+                        mbar_arrive_expect_tx(&full[slot], bytes);
+                        bulk_g2s(ring + (size_t)slot * (SB * 256), row + (int64_t)kb0 * 256, bytes, &full[slot]);
+                        issued = g + 1;
+                    }
+                }
+            }
+            for (int i = max(0, issued - S); i < issued; ++i)
+                if (!mbar_wait(&full[i % S], (i / S) & 1)) atomicOr(err, ERR_TIMEOUT);
+        }
+        return;
+    }
+    pdl_wait();   // x comes from the predecessor; the producer streams the constant rows meanwhile
+    int g = 0;
+    for (int di = 0; di < n_desc; ++di) {
+        const RowDesc D = descs[di];
+        const int64_t nu = (D.rows + 15) / 16;
+        const int64_t lo = b0 > D.u0 ? b0 : D.u0;
+        const int64_t hi = b1 < D.u0 + nu ? b1 : D.u0 + nu;
+        if (hi <= lo) continue;
+        const int nkb = D.ld >> 4;
+        // the B operands of this block's x, one thread per column k: B[k][n] for
+        // n = 0..2 is x, y, z rounded to BF16, n = 3..5 their BF16 remainders,
+        // n = 6, 7 and the padded columns are zero.  In the mma B layout, k lies
+        // in block k / 16 at lane 4 n + ((k mod 8) / 2), register (k mod 16) / 8,
+        // half k mod 2.
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kRowtWarps) : "memory");   // the previous B is no longer read
+        {
+            __nv_bfloat16* bh = reinterpret_cast<__nv_bfloat16*>(bfr);
+            for (int k = threadIdx.x; k < nkb * 16; k += 32 * kRowtWarps) {
+                float v[3] = {0.f, 0.f, 0.f};
+                if (k < D.cols) {
+                    const float4 xv = D.xidx_off >= 0 ? B.x[B.bidx[D.xidx_off + k]] : B.x[D.x_off + k];
+                    v[0] = xv.x;
+                    v[1] = xv.y;
+                    v[2] = xv.z;
+                }
+                const int kb = k >> 4, kk = k & 15, q = (kk & 7) >> 1, h = kk >> 3, e = kk & 1;
+                __nv_bfloat16* col = bh + (size_t)kb * 32 * 4 + q * 4 + h * 2 + e;   // lane 4 n + q: + 16 n halves
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const __nv_bfloat16 vh = __float2bfloat16_rn(v[c]);
+                    col[16 * c] = vh;
+                    col[16 * (c + 3)] = __float2bfloat16_rn(v[c] - __bfloat162float(vh));
+                }
+                col[16 * 6] = __float2bfloat16_rn(0.f);
+                col[16 * 7] = __float2bfloat16_rn(0.f);
+            }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kRowtWarps) : "memory");
+        for (int64_t u = lo; u < hi; ++u) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int kb0 = 0; kb0 < nkb; kb0 += SB, ++g) {
+                const int slot = g % S;
+                if (*reinterpret_cast<volatile int*>(&abort_flag)) break;
+                if (!mbar_wait(&full[slot], (g / S) & 1, &abort_flag)) {
+                    if (lane == 0) {
+                        abort_flag = 1;
+                        atomicOr(err, ERR_TIMEOUT);
+                    }
+                    break;
+                }
+                const int nb = min(SB, nkb - kb0);
+                const uint4* st = reinterpret_cast<const uint4*>(ring + (size_t)slot * (SB * 256));
+                for (int kb = warp; kb < nb; kb += kRowtWarps)
+                    mma_bf16_rowform(acc, st[kb * 32 + lane], bfr[(kb0 + kb) * 32 + lane]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            }
+            // the warps' 16 x 8 tiles, added in warp order
+#pragma unroll
+            for (int i = 0; i < 4; ++i) red[(warp * 32 + lane) * 4 + i] = acc[i];
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * kRowtWarps) : "memory");
+            if (warp == 0) {
+                float d[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int w = 0; w < kRowtWarps; ++w)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) d[i] += red[(w * 32 + lane) * 4 + i];
+                // lane 4 r + q holds columns 2q, 2q + 1 of rows r (d0, d1) and r + 8 (d2, d3):
+                // x = col 0 + col 3, y = col 1 + col 4, z = col 2 + col 5
+                const int base = lane & ~3;
+                float o1[4], o2[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    o1[i] = __shfl_sync(0xffffffffu, d[i], base + 1);
+                    o2[i] = __shfl_sync(0xffffffffu, d[i], base + 2);
+                }
+                if ((lane & 3) == 0) {
+                    const int r0 = (int)(u - D.u0) * 16 + (lane >> 2);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int r = r0 + 8 * h;
+                        if (r < D.rows) {
+                            const float x = d[2 * h] + o1[2 * h + 1];
+                            const float y = d[2 * h + 1] + o2[2 * h];
+                            const float z = o1[2 * h] + o2[2 * h + 1];
+                            const float4 ad = (D.add_off >= 0) ? B.add[D.add_off + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            B.out[D.out_off + r] = make_float4(ad.x + x, ad.y + y, ad.z + z, 0.f);
+                        }
+                    }
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * kRowtWarps) : "memory");   // red is free again
+        }
+    }
+}
+
 inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
 template <class T>
@@ -1239,7 +1435,10 @@ void launch_ax(const AxDesc* descs, const AxBlock* blocks, int n_blocks, int k_m
 template <class T>
 void launch_rowdot(const RowPlan& P, const AxBases& B, cudaStream_t s, int* tma_err = nullptr) {
     if (P.n_blocks <= 0) return;
-    if (P.tma && tma_err) {
+    if (P.mma && tma_err) {
+        k_rowdot_mma<<<P.n_blocks, 32 * (kRowtWarps + 1), rowm_smem_bytes(P.xcap), s>>>(P.descs.p, P.n_desc, P.blk_u.p,
+                                                                                     B, P.xcap, tma_err);
+    } else if (P.tma && tma_err) {
         const size_t smem = (size_t)kRowtStages * kRowtStageBytes + sizeof(float) * 3 * (size_t)P.xcap;
         k_rowdot_tma<T><<<P.n_blocks, 32 * (kRowtWarps + 1), smem, s>>>(P.descs.p, P.n_desc, P.blk_u.p, B, P.xcap,
                                                                        tma_err);
@@ -1353,13 +1552,21 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
             cin = w.cT;
             xcs = xout + m->n_int + T0;
         }
-        phase_begin(m, PH_COARSE, s);
-        launch_coarse<T>(m, pool, cin, w.part, s);
-        phase_end(m, s);
-        phase_begin(m, PH_REDUCE, s);
-        launch_pdl(k_reduce, dim3(nblk(m->cs_n, 256)), dim3(256), 0, s, m->cs_n, m->coarse_nchunks, w.part, xcs);
-        PDG_CHECK_LAUNCH();
-        phase_end(m, s);
+        if (m->rows_coarse.n_blocks > 0) {
+            // BF16 on the tensor cores: whole block-rows, written straight to x
+            phase_begin(m, PH_COARSE, s);
+            launch_rowdot<T>(m->rows_coarse, AxBases{pool, cin, nullptr, nullptr, xcs}, s, m->d_err.p);
+            phase_end(m, s);
+        } else {
+            phase_begin(m, PH_COARSE, s);
+            launch_coarse<T>(m, pool, cin, w.part, s);
+            phase_end(m, s);
+            phase_begin(m, PH_REDUCE, s);
+            launch_pdl(k_reduce, dim3(nblk(m->cs_n, 256)), dim3(256), 0, s, m->cs_n, m->coarse_nchunks, w.part,
+                       xcs);
+            PDG_CHECK_LAUNCH();
+            phase_end(m, s);
+        }
         if (m->two_level) {
             if (fork2) PDG_CUDA(cudaStreamWaitEvent(s, m->ev_join[1], 0));
             phase_begin(m, PH_BACKSUB2, s);
@@ -1478,8 +1685,15 @@ int rowdot_rows_per_unit(int prec) { return prec == PD_PREC_BF16 ? RowRows<__nv_
 // Unit numbering and block cuts of a row-form launch: block b gets the units
 // whose cumulative cost (matrix columns streamed plus a fixed per-unit cost)
 // starts in [W b / C, W (b+1) / C), C = one block per SM.
-void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s) {
-    const int RU = rowdot_rows_per_unit(prec);
+bool rowdot_row_fits_stage(int ld, int elem_bytes) { return (int64_t)ld * elem_bytes <= kRowtStageBytes; }
+
+bool rowdot_mma_fits(int xcap) {
+    static const int optin_m = allow_max_dynamic_smem(k_rowdot_mma);
+    return rowm_smem_bytes(xcap) <= (size_t)optin_m;
+}
+
+void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s, bool mma) {
+    const int RU = mma ? 16 : rowdot_rows_per_unit(prec);
     int64_t u = 0;
     int xcap = 8;
     double W = 0.0;
@@ -1497,7 +1711,15 @@ void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream
     int dev = 0, sms = 0;
     PDG_CUDA(cudaGetDevice(&dev));
     PDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int C = std::max(1, sms) * kRowBps;
+    int bps = kRowBps;
+    if (mma && rowdot_mma_fits(xcap)) {
+        // as many blocks as are resident at once (its shared memory grows with x)
+        int occ = 0;
+        PDG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rowdot_mma, 32 * (kRowtWarps + 1),
+                                                               rowm_smem_bytes(xcap)));
+        bps = std::max(1, std::min(bps, occ));
+    }
+    const int C = std::max(1, sms) * bps;
     std::vector<int64_t> cut(C + 1, u);
     cut[0] = 0;
     double acc = 0.0;
@@ -1512,7 +1734,7 @@ void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream
     }
     const size_t smem = sizeof(float) * 3 * (size_t)xcap;
     const int optin = std::min(allow_max_dynamic_smem(k_rowdot<float>), allow_max_dynamic_smem(k_rowdot<__nv_bfloat16>));
-    if (smem > (size_t)optin) {
+    if (!mma && smem > (size_t)optin) {
         set_error("row-form product: the x vector does not fit in shared memory");
         throw Fail{PD_ERR_UNSUPPORTED};
     }
@@ -1522,6 +1744,20 @@ void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream
                                                : allow_max_dynamic_smem(k_rowdot_tma<float>);
     P.tma = (size_t)kRowtStages * kRowtStageBytes + smem <= (size_t)optin_t;
     for (const auto& d : descs) P.tma = P.tma && d.ld * es <= kRowtStageBytes && d.ld % 8 == 0 && d.a_off % 8 == 0;
+    P.mma = false;
+    if (mma) {
+        // BF16 fragment layout: whole 16-row block-rows, columns padded to 16
+        if (!rowdot_mma_fits(xcap)) {
+            set_error("row-form tensor-core product: the x vector does not fit in shared memory");
+            throw Fail{PD_ERR_UNSUPPORTED};
+        }
+        for (const auto& d : descs)
+            if (d.ld % 16 != 0 || d.a_off % 8 != 0) {
+                set_error("row-form tensor-core product: block not in the fragment layout");
+                throw Fail{PD_ERR_UNSUPPORTED};
+            }
+        P.mma = true;
+    }
     upload(P.descs, descs, s);
     upload(P.blk_u, cut, s);
     PDG_CUDA(cudaStreamSynchronize(s));

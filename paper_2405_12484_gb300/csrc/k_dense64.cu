@@ -345,6 +345,22 @@ __global__ void k_cast_frag16(const double* __restrict__ src, int lds, int rows,
     }
 }
 
+// BF16 row-form block in the tensor-core fragment order (rows and columns
+// padded to 16, see k_rowdot_mma): element (r, c) lands in 16 x 16 block
+// (r / 16, c / 16) at the lane and register of the mma A operand.
+__global__ void k_cast_rowfrag16(const double* __restrict__ src, int lds, int rows, int cols, int transpose,
+                                 __nv_bfloat16* __restrict__ d16, int64_t off, int Kp) {
+    const int64_t n = (int64_t)rows * cols;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(l / cols), c = (int)(l % cols);
+        const double v = transpose ? src[(int64_t)c * lds + r] : src[(int64_t)r * lds + c];
+        const int rb = r >> 4, kb = c >> 4, rr = r & 15, kk = c & 15;
+        const int g = rr & 7, rhi = rr >> 3, q = (kk & 7) >> 1, j = kk & 1, khi = kk >> 3;
+        d16[off + ((int64_t)rb * (Kp >> 4) + kb) * 256 + (4 * g + q) * 8 + (rhi + 2 * khi) * 2 + j] =
+            __double2bfloat16(v);
+    }
+}
+
 // dst[i][k] = S[r0 + i][cols ? c0 + cols[k] : c0 + k]
 __global__ void k_copy_block_idx(const double* __restrict__ S, int ldS, int r0, int nr, const int* __restrict__ cols,
                                  int c0, int nc, double* __restrict__ dst, int ldd) {
@@ -389,6 +405,14 @@ void launch_cast_block(const double* src, int lds, int rows, int cols, int trans
     if (rows <= 0 || cols <= 0) return;
     k_cast_block<<<grid_of((int64_t)rows * cols), 256, 0, s>>>(src, lds, rows, cols, transpose, prec, dst32, dst16,
                                                                 dst_off, ldd);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_cast_rowfrag16(const double* src, int lds, int rows, int cols, int transpose, __nv_bfloat16* dst16,
+                           int64_t dst_off, int Kp, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return;
+    k_cast_rowfrag16<<<grid_of((int64_t)rows * cols), 256, 0, s>>>(src, lds, rows, cols, transpose, dst16, dst_off,
+                                                                    Kp);
     PDG_CHECK_LAUNCH();
 }
 

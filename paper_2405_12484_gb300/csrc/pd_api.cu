@@ -26,7 +26,11 @@ int dd_coarse_chunk();
 int dd_configure_coarse(int ld_S);
 int ax_outputs_per_block(int prec);
 int ax_tile_outputs(int prec);
-void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s);
+void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s, bool mma = false);
+bool rowdot_mma_fits(int xcap);
+bool rowdot_row_fits_stage(int ld, int elem_bytes);
+void launch_cast_rowfrag16(const double* src, int lds, int rows, int cols, int transpose, __nv_bfloat16* dst16,
+                           int64_t dst_off, int Kp, cudaStream_t s);
 bool build_stream_plan(StreamPlan& P, const std::vector<ColDesc>& blocks, int prec, const void* src,
                        cudaStream_t s);
 void reset_stream_plan(StreamPlan& P, cudaStream_t s);
@@ -121,6 +125,7 @@ void jacobi_eig(std::vector<double>& A, int q, std::vector<double>& w, std::vect
 
 void phase_begin(pd_mesh* m, int phase, cudaStream_t s) {
     if (!m->timing_armed || !m->ev_rec || !(m->timing_mask & (1 << phase))) return;
+    if (m->timing_iter >= 0 && m->cur_iter >= 0 && m->cur_iter != m->timing_iter) return;
     pd_mesh::TimingSet& T = *m->ev_rec;
     size_t k = (size_t)T.used;
     if (2 * k + 1 >= T.ev.size()) {
@@ -1065,22 +1070,28 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     std::vector<int64_t> h2_off(G), t2_off(G);
     std::vector<int32_t> ldH2(G), ldT2(G), tc2_off(G);
     int32_t tc2r = 0;
+    // (BF16 on the tensor cores: rows and columns padded to 16, 16 x 16 blocks
+    // in the mma operand order, the Psi2^T rows starting a block-row of their own)
+    std::vector<int32_t> psi2_row(G);   // first row of Psi2^T in the stacked block
     for (int g = 0; g < G; ++g) {
         const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
-        ldH2[g] = (int32_t)round_up(std::max(n2, 1), 8);
-        ldT2[g] = (int32_t)round_up(std::max(nb, 1), 8);
+        ldH2[g] = (int32_t)round_up(std::max(n2, 1), frag16 ? 16 : 8);
+        ldT2[g] = (int32_t)round_up(std::max(nb, 1), frag16 ? 16 : 8);
+        psi2_row[g] = (int32_t)krows(n2);
         h2_off[g] = pool;
-        pool += (int64_t)(n2 + nb) * ldH2[g];
+        pool += (krows(n2) + krows(nb)) * ldH2[g];
         t2_off[g] = pool;
-        pool += (int64_t)n2 * ldT2[g];
+        pool += krows(n2) * ldT2[g];
         pool = round_up(pool, 8);
         tc2_off[g] = tc2r;
         tc2r += n2 + nb;
     }
     m->cs_n = two ? nT : n_B;
+    // the coarse block too, where its x fits in shared memory beside the stages
+    const bool coarse_frag = frag16 && rowdot_mma_fits((int)round_up(std::max(m->cs_n, 1), 16));
     m->off_S = pool;
-    m->ld_S = (int32_t)round_up(std::max(m->cs_n, 1), 8);
-    pool += (int64_t)m->cs_n * m->ld_S;
+    m->ld_S = (int32_t)round_up(std::max(m->cs_n, 1), coarse_frag ? 16 : 8);
+    pool += (coarse_frag ? krows(m->cs_n) : (int64_t)m->cs_n) * m->ld_S;
     pool = std::max<int64_t>(pool, 8);
     m->d_mat32.free();
     m->d_mat16.free();
@@ -1129,23 +1140,26 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             cast_ax(Pd, NBp, nbd, ni, 1, t_off[d], ldT[d]);
         }
     }
-    if (n_B > 0 && !two)
-        launch_cast_block(dXS.p, nBp, n_B, n_B, 0, m->prec, m->d_mat32.p, m->d_mat16.p, m->off_S, m->ld_S, s);
+    // row-form blocks: row-major, or the BF16 fragment layout of the tensor cores
+    auto cast_row = [&](const double* src, int lds, int rows, int cols, int transpose, int64_t off, int ld,
+                        bool frag) {
+        if (frag) launch_cast_rowfrag16(src, lds, rows, cols, transpose, m->d_mat16.p, off, ld, s);
+        else launch_cast_block(src, lds, rows, cols, transpose, m->prec, m->d_mat32.p, m->d_mat16.p, off, ld, s);
+    };
+    if (n_B > 0 && !two) cast_row(dXS.p, nBp, n_B, n_B, 0, m->off_S, m->ld_S, coarse_frag);
     if (two) {
         const int64_t s2ii = (int64_t)NI2 * NI2, s2it = (int64_t)NI2 * NB2;
         for (int g = 0; g < G; ++g) {
             const int32_t n2 = m->grp_n2[g], nb = (int32_t)b2[g].size();
             if (n2 == 0) continue;
-            launch_cast_block(dX2ii.p + g * s2ii, NI2, n2, n2, 0, m->prec, m->d_mat32.p, m->d_mat16.p, h2_off[g],
-                              ldH2[g], s);
+            cast_row(dX2ii.p + g * s2ii, NI2, n2, n2, 0, h2_off[g], ldH2[g], frag16);
             if (nb > 0) {
-                launch_cast_block(dPsi2.p + g * s2it, NB2, nb, n2, 1, m->prec, m->d_mat32.p, m->d_mat16.p,
-                                  h2_off[g] + (int64_t)n2 * ldH2[g], ldH2[g], s);
-                launch_cast_block(dPsi2.p + g * s2it, NB2, n2, nb, 0, m->prec, m->d_mat32.p, m->d_mat16.p, t2_off[g],
-                                  ldT2[g], s);
+                cast_row(dPsi2.p + g * s2it, NB2, nb, n2, 1, h2_off[g] + (int64_t)psi2_row[g] * ldH2[g], ldH2[g],
+                         frag16);
+                cast_row(dPsi2.p + g * s2it, NB2, n2, nb, 0, t2_off[g], ldT2[g], frag16);
             }
         }
-        launch_cast_block(dX2.p, nTp, nT, nT, 0, m->prec, m->d_mat32.p, m->d_mat16.p, m->off_S, m->ld_S, s);
+        cast_row(dX2.p, nTp, nT, nT, 0, m->off_S, m->ld_S, coarse_frag);
     }
 
     // ---- descriptors of the per-domain products: one block per output chunk
@@ -1347,7 +1361,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             di.push_back(t);
             if (nb == 0) continue;
             RowDesc c = t;
-            c.a_off = h2_off[g] + (int64_t)n2 * ldH2[g];
+            c.a_off = h2_off[g] + (int64_t)psi2_row[g] * ldH2[g];
             c.rows = nb;
             c.out_off = tc2_off[g] + n2;
             dc.push_back(c);
@@ -1362,9 +1376,9 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             b.out_off = i2_off[g];
             db.push_back(b);
         }
-        build_row_plan(m->rows_cond2, dc, m->prec, s);
-        build_row_plan(m->rows_int2, di, m->prec, s);
-        build_row_plan(m->rows_back2, db, m->prec, s);
+        build_row_plan(m->rows_cond2, dc, m->prec, s, frag16);
+        build_row_plan(m->rows_int2, di, m->prec, s, frag16);
+        build_row_plan(m->rows_back2, db, m->prec, s, frag16);
         upload(m->d_bidx2, b2all, s);
         // top-level gather lists (groups in increasing order)
         std::vector<int32_t> gp(nT + 1, 0), gl;
@@ -1407,6 +1421,26 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     m->coarse_nchunks = (int32_t)((m->ld_S + m->coarse_chunk - 1) / m->coarse_chunk);
     m->d_part.alloc((size_t)std::max(m->cs_n, 1) * m->coarse_nchunks);
     m->coarse_blocks = (m->cs_n > 0) ? dd_configure_coarse(m->ld_S) : 0;
+    // The coarse product as a row-form product of whole rows (no split into
+    // column chunks, no partial sums to reduce): BF16 on the tensor cores, FP32
+    // where a row fits one bulk-copy stage; otherwise the balanced split kernel.
+    m->rows_coarse.n_blocks = 0;
+    m->rows_coarse.host.clear();
+    const bool coarse_rows =
+        coarse_frag || (m->prec == PD_PREC_FP32 && !(o.flags & PD_SOLVE_STREAMING) && rowdot_row_fits_stage(m->ld_S, 4));
+    if (coarse_rows && m->cs_n > 0) {
+        RowDesc c{};
+        c.a_off = m->off_S;
+        c.rows = m->cs_n;
+        c.cols = m->cs_n;
+        c.ld = m->ld_S;
+        c.x_off = 0;
+        c.xidx_off = -1;
+        c.add_off = -1;
+        c.out_off = 0;
+        build_row_plan(m->rows_coarse, std::vector<RowDesc>{c}, m->prec, s, coarse_frag);
+        if (!m->rows_coarse.mma && !m->rows_coarse.tma) m->rows_coarse.n_blocks = 0;   // rows too long
+    }
 
     // ---- fused streaming solve (column form), phase by phase:
     //   0: c_d = Psi_d^T b_i over the rows of Psi_d, t_d = K_ii^-1 b_i over the rows of K_ii^-1
@@ -1557,10 +1591,14 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         const int64_t nkfp = (int64_t)m->Kfp_col.size(), nk = (int64_t)m->K_col.size();
         const int64_t ngat = nbd_tot;
         const int64_t colsS = (int64_t)round_up(std::max(m->cs_n, 1), VN);
-        int64_t mat_c2 = 0, mat_i2 = 0, mat_b2 = 0;
-        for (const auto& d : m->rows_cond2.host) mat_c2 += (int64_t)d.rows * d.ld * es;
-        for (const auto& d : m->rows_int2.host) mat_i2 += (int64_t)d.rows * d.ld * es;
-        for (const auto& d : m->rows_back2.host) mat_b2 += (int64_t)d.rows * d.ld * es;
+        // (tensor-core layout: whole 16-row block-rows are streamed)
+        auto plan_bytes = [&](const RowPlan& P) {
+            int64_t b = 0;
+            for (const auto& d : P.host) b += (int64_t)(P.mma ? round_up(d.rows, 16) : d.rows) * d.ld * es;
+            return b;
+        };
+        const int64_t mat_c2 = plan_bytes(m->rows_cond2), mat_i2 = plan_bytes(m->rows_int2),
+                      mat_b2 = plan_bytes(m->rows_back2);
         for (int k = 0; k < 24; ++k) m->phase_bytes[k] = 0;
         m->phase_bytes[PH_INERTIA] = nv * 48 + nf * (16 + 4 + 16 + 4) + nkfp * 8 + (int64_t)m->n_pin * 16;
         // fused local step + assembly: tets and rest operators, x once, by0 (or y and m/dt^2) and b per
@@ -1586,8 +1624,13 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
 
         m->phase_bytes[PH_GATHER] = (int64_t)n_B * (4 + 16 + 16) + ngat * (4 + 16);
         const int64_t ncs = m->cs_n;
-        m->phase_bytes[PH_COARSE] = ncs * colsS * es + ncs * 16 + (int64_t)m->coarse_nchunks * ncs * 16;
-        m->phase_bytes[PH_REDUCE] = (int64_t)m->coarse_nchunks * ncs * 16 + ncs * 16;
+        if (m->rows_coarse.n_blocks > 0) {
+            m->phase_bytes[PH_COARSE] = plan_bytes(m->rows_coarse) + ncs * 16 + ncs * 16;
+            m->phase_bytes[PH_REDUCE] = 0;
+        } else {
+            m->phase_bytes[PH_COARSE] = ncs * colsS * es + ncs * 16 + (int64_t)m->coarse_nchunks * ncs * 16;
+            m->phase_bytes[PH_REDUCE] = (int64_t)m->coarse_nchunks * ncs * 16 + ncs * 16;
+        }
         if (two) {
             m->phase_bytes[PH_CONDENSE2] = mat_c2 + (int64_t)(n_B - nT) * 16 + (int64_t)b2all.size() * 16;
             m->phase_bytes[PH_INTERIOR2] = mat_i2 + (int64_t)(n_B - nT) * 32;
@@ -1606,7 +1649,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             m->phase_bytes[PH_SOLVE] = sb;
         }
         int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (m->ax_blocks_int > 0 ? 1 : 0) +
-                 (n_B > 0 ? 3 : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
+                 (n_B > 0 ? (m->rows_coarse.n_blocks > 0 ? 2 : 3) : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
         if (modal) dd += (m->ax_blocks_m1 > 0 ? 2 : 0) + (int)m->jacobi_omega.size();
         if (two)
             dd += (m->rows_cond2.n_blocks > 0 ? 1 : 0) + (m->rows_int2.n_blocks > 0 ? 1 : 0) + (nT > 0 ? 1 : 0) +
@@ -1662,6 +1705,7 @@ static void run_frame(pd_mesh* m, int n_iter, const float g[3], cudaStream_t s) 
     launch_inertia(m, h, g[0], g[1], g[2], s);
     phase_end(m, s);
     for (int it = 0; it < n_iter; ++it) {
+        m->cur_iter = it;
         // fused local step and assembly: the RHS b, or in the correction form
         // the residual b - K x itself (formed per tet without cancellation)
         phase_begin(m, PH_LOCAL, s);
@@ -1681,6 +1725,7 @@ static void run_frame(pd_mesh* m, int n_iter, const float g[3], cudaStream_t s) 
             launch_axpy_free(m, m->d_dx.p, m->d_x.p, s);
         }
     }
+    m->cur_iter = -1;
     phase_begin(m, PH_VELOCITY, s);
     launch_velocity(m, 1.0f / h, s);
     phase_end(m, s);
@@ -1709,6 +1754,7 @@ pd_status pd_step(pd_mesh* m, const float* pin_targets, const float* gravity, in
         std::memcpy(&key[1], g, sizeof(g));
         key[4] = (uint32_t)m->refine;
         key[5] = (uint32_t)m->timing_mask;
+        key.push_back((uint32_t)(m->timing_iter + 1));
         auto it = m->graphs.find(key);
         if (it == m->graphs.end()) {
             cudaGraph_t graph = nullptr;
@@ -1808,6 +1854,7 @@ pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
     bytes += m->d_gat_ptr.bytes() + m->d_gat.bytes() + m->d_cB.bytes() + m->d_part.bytes();
     bytes += m->d_K_ptr.bytes() + m->d_K_col.bytes() + m->d_K_val.bytes() + m->d_r.bytes() + m->d_dx.bytes();
     bytes += m->rows_cond2.descs.bytes() + m->rows_cond2.blk_u.bytes() + m->rows_back2.descs.bytes();
+    bytes += m->rows_coarse.descs.bytes() + m->rows_coarse.blk_u.bytes();
     bytes += m->rows_back2.blk_u.bytes() + m->d_bidx2.bytes() + m->d_gat2_ptr.bytes() + m->d_gat2.bytes();
     bytes += m->d_tc2.bytes() + m->d_cT.bytes();
     bytes += m->st_solve.pan32.bytes() + m->st_solve.pan16.bytes() + m->st_solve.recs.bytes() +
@@ -1882,6 +1929,13 @@ pd_status pd_solve(pd_mesh* m, const float* r, float* x) {
 pd_status pd_enable_timing(pd_mesh* m, int32_t mask) {
     if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
     m->timing_mask = mask < 0 ? ((1 << PH_COUNT) - 1) : (mask & ((1 << PH_COUNT) - 1));
+    return PD_OK;
+}
+
+pd_status pd_set_timing_iteration(pd_mesh* m, int32_t iteration) {
+    if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
+    if (iteration < -1) return fail(PD_ERR_INVALID_ARG, "iteration must be >= -1");
+    m->timing_iter = iteration;
     return PD_OK;
 }
 

@@ -169,6 +169,7 @@ struct RowPlan {
     DBuf<int64_t> blk_u;
     int n_desc = 0, n_blocks = 0, xcap = 8;
     bool tma = false;              // rows streamed by bulk copies (k_rowdot_tma)
+    bool mma = false;              // BF16 fragment layout on the tensor cores (k_rowdot_mma)
     std::vector<RowDesc> host;     // host copy (byte accounting)
 };
 
@@ -403,6 +404,7 @@ struct pd_mesh {
     int32_t cs_n = 0;                                       // rows of the dense coarse inverse in the pool
     pdg::RowPlan rows_cond2, rows_back2;   // row-form launches of the second level
     pdg::RowPlan rows_int2;                // second-level interior part S_II^-1 c_I
+    pdg::RowPlan rows_coarse;              // BF16 tensor cores: the coarse product as a row-form product
     // the fused streaming solve (one cooperative launch per solve); used when it
     // could be planned (every panel row fits one pipeline stage)
     bool use_stream = false;
@@ -477,6 +479,8 @@ struct pd_mesh {
     std::map<std::vector<uint32_t>, GraphEntry> graphs;
 
     int32_t timing_mask = 0;
+    int32_t timing_iter = -1;   // >= 0: loop phases timed in this iteration only
+    int32_t cur_iter = -1;      // the iteration being recorded (-1 outside the loop)
     TimingSet* ev_rec = nullptr;                  // set being recorded into (during capture / plain launches)
     std::shared_ptr<TimingSet> ev_plain;          // set of the plain launches
     std::shared_ptr<TimingSet> ev_last;           // set of the last frame launched (read by pd_phase_times)

@@ -83,7 +83,10 @@ struct pd_server {
     int64_t budget = 0;
     int32_t max_slots = 0, n_iter = 20;
     int device = 0;
-    cudaStream_t stream = nullptr, cap = nullptr;
+    cudaStream_t user = nullptr;           // the caller's stream: each tick is ordered after its prior work
+    cudaStream_t stream = nullptr, cap = nullptr;   // the frames' own stream (highest priority)
+    cudaEvent_t e_user = nullptr;
+    int32_t* h_err = nullptr;              // pinned copy of d_err
     cudaStream_t adm = nullptr;            // admission stream (lowest priority)
     std::vector<cudaStream_t> adm_streams; // one per admission thread (lowest priority)
     pd_request_id next_id = 1;
@@ -125,7 +128,10 @@ struct pd_server {
         if (graph) cudaGraphExecDestroy(graph);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
+        if (e_user) cudaEventDestroy(e_user);
+        if (h_err) cudaFreeHost(h_err);
         if (cap) cudaStreamDestroy(cap);
+        if (stream) cudaStreamDestroy(stream);
         if (adm) cudaStreamDestroy(adm);
         for (auto st : adm_streams)
             if (st) cudaStreamDestroy(st);
@@ -466,11 +472,16 @@ pd_status pd_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t 
         S->budget = hbm_budget_bytes;
         S->max_slots = max_slots;
         S->n_iter = n_iter;
-        S->stream = static_cast<cudaStream_t>(stream);
+        S->user = static_cast<cudaStream_t>(stream);
         PDG_CUDA(cudaGetDevice(&S->device));
         PDG_CUDA(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
         int prio_low = 0, prio_high = 0;
         PDG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+        // the frames ahead of the admission work (FP64 prefactorisations) whenever an SM frees up
+        PDG_CUDA(cudaStreamCreateWithPriority(&S->stream, cudaStreamNonBlocking, prio_high));
+        PDG_CUDA(cudaEventCreateWithFlags(&S->e_user, cudaEventDisableTiming));
+        PDG_CUDA(cudaMallocHost((void**)&S->h_err, sizeof(int32_t)));
+        *S->h_err = 0;
         PDG_CUDA(cudaStreamCreateWithPriority(&S->adm, cudaStreamNonBlocking, prio_low));
         S->adm_streams.assign(kAdmissionWorkers, nullptr);
         for (auto& st : S->adm_streams) PDG_CUDA(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_low));
@@ -478,7 +489,8 @@ pd_status pd_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t 
         PDG_CUDA(cudaEventCreate(&S->e1));
         PDG_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device));
         S->d_err.alloc(1);
-        PDG_CUDA(cudaMemset(S->d_err.p, 0, sizeof(int32_t)));
+        PDG_CUDA(cudaMemsetAsync(S->d_err.p, 0, sizeof(int32_t), S->stream));
+        PDG_CUDA(cudaStreamSynchronize(S->stream));
         for (int k = 0; k < kAdmissionWorkers; ++k) S->workers.emplace_back(worker_main, S, k);
     } catch (const Fail& f) {
         delete S;
@@ -546,6 +558,9 @@ pd_status pd_submit(pd_server* S, const pd_request* q, pd_request_id* id) {
 pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
     try {
+        // this tick after the caller's prior work
+        PDG_CUDA(cudaEventRecord(S->e_user, S->user));
+        PDG_CUDA(cudaStreamWaitEvent(S->stream, S->e_user, 0));
         // retire finished requests: read back their positions, hand their meshes to the worker
         std::vector<std::pair<pd_mesh*, int64_t>> dead;
         for (size_t k = 0; k < S->active.size();) {
@@ -601,7 +616,8 @@ pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
             PDG_CUDA(cudaEventRecord(S->e0, S->stream));
             PDG_CUDA(cudaGraphLaunch(S->graph, S->stream));
             PDG_CUDA(cudaEventRecord(S->e1, S->stream));
-            PDG_CUDA(cudaEventSynchronize(S->e1));
+            PDG_CUDA(cudaMemcpyAsync(S->h_err, S->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, S->stream));
+            PDG_CUDA(cudaStreamSynchronize(S->stream));
             PDG_CUDA(cudaEventElapsedTime(&ms, S->e0, S->e1));
             const auto now = Clock::now();
             std::lock_guard<std::mutex> lk(S->mu);
@@ -613,10 +629,10 @@ pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
             }
         }
         if (frame_ms) *frame_ms = ms;
-        int32_t herr = 0;
-        PDG_CUDA(cudaMemcpy(&herr, S->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
-        if (herr) {
-            PDG_CUDA(cudaMemset(S->d_err.p, 0, sizeof(int32_t)));
+        if (*S->h_err) {
+            *S->h_err = 0;
+            PDG_CUDA(cudaMemsetAsync(S->d_err.p, 0, sizeof(int32_t), S->stream));
+            PDG_CUDA(cudaStreamSynchronize(S->stream));
             return sfail(PD_ERR_TIMEOUT, "pd_server_tick: a bounded wait of the batched products ran out");
         }
     } catch (const Fail& f) {

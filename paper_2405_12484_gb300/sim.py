@@ -157,8 +157,11 @@ class Mesh:
         _check(lib().pd_solve_noalloc(self._h, _ptr(r), _ptr(x)), "pd_solve_noalloc")
         return x
 
-    def enable_timing(self, mask=-1):
+    def enable_timing(self, mask=-1, iteration=-1):
+        """Phase events for the kernel classes in `mask` (-1: all); the loop
+        phases only in PD iteration `iteration` of each frame (-1: every one)."""
         _check(lib().pd_enable_timing(self._h, int(mask)), "pd_enable_timing")
+        _check(lib().pd_set_timing_iteration(self._h, int(iteration)), "pd_set_timing_iteration")
 
     def phase_times(self) -> dict:
         out = (C.c_float * 24)()
