@@ -506,17 +506,24 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint4& a, ui
 }
 
 constexpr int kAxmNb = 8;   // n8 blocks per consumer warp (tile width <= 8 * 8 * kAxtWarps = 256)
+// stages of 64 BF16 rows: the bytes of the FP32 kernel's 32-row stages (measured: 64-row
+// stages 1.88 ms per frame against 1.93 ms with 32; the FP32 kernel is fastest at 32)
+#ifndef PDG_AXM_ROWS
+#define PDG_AXM_ROWS 64
+#endif
+constexpr int kAxmRows = PDG_AXM_ROWS;
+constexpr int kAxmStages = kAxtStages;
 static_assert(kAxmNb * 8 * kAxtWarps >= 256, "one consumer warp per output column group");
 
 inline size_t axm_ring_bytes(int wmax) {
-    return ((size_t)kAxtStages * kAxtRows * wmax * sizeof(__nv_bfloat16) + 15) / 16 * 16;
+    return ((size_t)kAxmStages * kAxmRows * wmax * sizeof(__nv_bfloat16) + 15) / 16 * 16;
 }
 
 __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_mma(const AxDesc* __restrict__ descs,
                                                                    const AxBlock* __restrict__ blocks, AxBases B,
                                                                    int ring_bytes, int* __restrict__ err) {
     using namespace tma;
-    constexpr int S = kAxtStages, R = kAxtRows;
+    constexpr int S = kAxmStages, R = kAxmRows;
     static_assert(R % 16 == 0, "stages hold whole 16-row blocks");
     extern __shared__ __align__(128) unsigned char axm_smem[];
     __shared__ __align__(8) uint64_t full[S], empty[S];

@@ -347,6 +347,7 @@ pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tet
     m->n_t = n_t;
     m->n_dom = n_domains;
     m->stream = static_cast<cudaStream_t>(cuda_stream);
+    pdg::AllocStreamScope alloc_scope(m->stream);
 
     // ---- validate tets, rest operators (Dm^-1, V_e); fix orientation
     std::vector<int32_t> T(tets, tets + 4 * (size_t)n_t);
@@ -664,6 +665,7 @@ pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tet
 pd_status pd_set_materials(pd_mesh* m, const float* gamma_s, const float* gamma_v) {
     if (!m || !gamma_s || !gamma_v) return fail(PD_ERR_INVALID_ARG, "null argument");
     PD_API_BEGIN
+    pdg::AllocStreamScope alloc_scope(m->stream);
     const int32_t n_t = m->n_t;
     std::vector<float> gs(n_t), gv(n_t);
     auto fetch = [&](const float* src, std::vector<float>& dst) {
@@ -716,6 +718,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
          o.jacobi_sweeps > 1000 || !(o.jacobi_rho < 1.0) || !std::isfinite(o.jacobi_rho)))
         return fail(PD_ERR_INVALID_ARG, "bad modal-solve options");
     PD_API_BEGIN
+    pdg::AllocStreamScope alloc_scope(m->stream);
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = m->stream;
     m->prefactored = false;
@@ -1658,11 +1661,13 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->launches_per_iter = 1 + (m->la_shared > 0 ? 1 : 0) + dd + (m->correction ? 1 : 0) + m->refine * (2 + dd);
     }
 
-    PDG_CUDA(cudaStreamSynchronize(s));
+    // (the flag is read on the mesh's stream, never through the legacy default stream)
     int32_t herr = 0;
-    PDG_CUDA(cudaMemcpy(&herr, m->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    PDG_CUDA(cudaMemcpyAsync(&herr, m->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PDG_CUDA(cudaStreamSynchronize(s));
     if (herr & ERR_NOT_SPD) {
-        PDG_CUDA(cudaMemset(m->d_err.p, 0, sizeof(int32_t)));
+        PDG_CUDA(cudaMemsetAsync(m->d_err.p, 0, sizeof(int32_t), s));
+        PDG_CUDA(cudaStreamSynchronize(s));
         return fail(PD_ERR_NOT_SPD, "a Cholesky pivot was not positive");
     }
     // load the fixed scratch array of pd_solve_noalloc on this device now,
@@ -1681,6 +1686,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
 pd_status pd_set_state(pd_mesh* m, const float* x, const float* v) {
     if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
     PD_API_BEGIN
+    pdg::AllocStreamScope alloc_scope(m->stream);
     if (x) launch_gather_in(m, x, m->d_x.p, m->stream);
     if (v) launch_gather_in(m, v, m->d_v.p, m->stream);
     ++m->state_gen;
@@ -1691,6 +1697,7 @@ pd_status pd_set_state(pd_mesh* m, const float* x, const float* v) {
 pd_status pd_get_state(pd_mesh* m, float* x, float* v) {
     if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
     PD_API_BEGIN
+    pdg::AllocStreamScope alloc_scope(m->stream);
     if (x) launch_scatter_out(m, m->d_x.p, x, 0, m->stream);
     if (v) launch_scatter_out(m, m->d_v.p, v, 0, m->stream);
     return PD_OK;
@@ -1738,6 +1745,7 @@ pd_status pd_step(pd_mesh* m, const float* pin_targets, const float* gravity, in
     if (!m->prefactored) return fail(PD_ERR_NOT_PREFACTORED, "pd_prefactor has not run since the last change");
     if (n_iter < 1 || n_iter > 1000) return fail(PD_ERR_INVALID_ARG, "n_iter out of range");
     PD_API_BEGIN
+    pdg::AllocStreamScope alloc_scope(m->stream);
     float g[3] = {0.f, 0.f, -9.81f};
     if (gravity) {
         g[0] = gravity[0];
@@ -1808,11 +1816,13 @@ pd_status pd_step(pd_mesh* m, const float* pin_targets, const float* gravity, in
 pd_status pd_sync(pd_mesh* m) {
     if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
     PD_API_BEGIN
-    PDG_CUDA(cudaStreamSynchronize(m->stream));
+    pdg::AllocStreamScope alloc_scope(m->stream);
     int32_t herr = 0;
-    PDG_CUDA(cudaMemcpy(&herr, m->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    PDG_CUDA(cudaMemcpyAsync(&herr, m->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, m->stream));
+    PDG_CUDA(cudaStreamSynchronize(m->stream));
     if (herr) {
-        PDG_CUDA(cudaMemset(m->d_err.p, 0, sizeof(int32_t)));
+        PDG_CUDA(cudaMemsetAsync(m->d_err.p, 0, sizeof(int32_t), m->stream));
+        PDG_CUDA(cudaStreamSynchronize(m->stream));
         if (herr & ERR_TIMEOUT) {   // the root cause: the solve's values are not meaningful
             reset_stream_plan(m->st_solve, m->stream);
             PDG_CUDA(cudaStreamSynchronize(m->stream));
@@ -1879,6 +1889,7 @@ pd_status pd_local_rhs(pd_mesh* m, const float* x, const float* y, float* b) {
     if (!m || !x || !y || !b) return fail(PD_ERR_INVALID_ARG, "null argument");
     if (!m->prefactored) return fail(PD_ERR_NOT_PREFACTORED, "pd_prefactor has not run");
     PD_API_BEGIN
+    pdg::AllocStreamScope alloc_scope(m->stream);
     cudaStream_t s = m->stream;
     DBuf<float4> xi, yi, by0, bb, frc;
     xi.alloc(m->n_v);
@@ -1904,6 +1915,7 @@ pd_status pd_solve(pd_mesh* m, const float* r, float* x) {
     if (!m || !r || !x) return fail(PD_ERR_INVALID_ARG, "null argument");
     if (!m->prefactored) return fail(PD_ERR_NOT_PREFACTORED, "pd_prefactor has not run");
     PD_API_BEGIN
+    pdg::AllocStreamScope alloc_scope(m->stream);
     cudaStream_t s = m->stream;
     DBuf<float4> ri, xi;
     ri.alloc(m->n_v);
@@ -1943,6 +1955,7 @@ pd_status pd_test_offset_phase_counter(pd_mesh* m, int32_t phase, int32_t delta)
     if (!m || !m->use_stream || phase < 0 || phase >= m->st_solve.n_phases)
         return fail(PD_ERR_INVALID_ARG, "no streaming plan or phase out of range");
     PD_API_BEGIN
+    pdg::AllocStreamScope alloc_scope(m->stream);
     PDG_CUDA(cudaStreamSynchronize(m->stream));
     int32_t v = 0;
     PDG_CUDA(cudaMemcpy(&v, m->st_solve.phase_cnt.p + phase, sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -1956,6 +1969,7 @@ pd_status pd_test_inflate_copy(pd_mesh* m, int32_t bytes) {
     if (!m || !m->ax_tiled || bytes < 0 || bytes % 16 != 0)
         return fail(PD_ERR_INVALID_ARG, "no tile-streaming products, or bytes not a non-negative multiple of 16");
     PD_API_BEGIN
+    pdg::AllocStreamScope alloc_scope(m->stream);
     test_set_copy_extra(bytes, m->stream);
     return PD_OK;
     PD_API_END
@@ -1964,6 +1978,7 @@ pd_status pd_test_inflate_copy(pd_mesh* m, int32_t bytes) {
 pd_status pd_phase_times(pd_mesh* m, float* out, int32_t n_out, int32_t* n_phases) {
     if (!m) return fail(PD_ERR_INVALID_ARG, "mesh is NULL");
     PD_API_BEGIN
+    pdg::AllocStreamScope alloc_scope(m->stream);
     if (n_phases) *n_phases = PH_COUNT;
     std::vector<double> sum(PH_COUNT, 0.0);
     std::vector<int> cnt(PH_COUNT, 0);

@@ -76,22 +76,61 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 enum : int { ERR_NONFINITE = 1, ERR_NOT_SPD = 2, ERR_TIMEOUT = 4 };
 
 // ---------------------------------------------------------------- device buffer
+// Allocation stream of the calling thread (set by AllocStreamScope): buffers
+// allocated while one is set are stream-ordered (cudaMallocAsync on it) and
+// freed on it (cudaFreeAsync, after the work queued there), so neither the
+// allocation nor the free waits for the whole device.  cudaFree does: while
+// one thread's prefactorisation freed a temporary, another thread's frames
+// stalled until every queued kernel of that prefactorisation had finished.
+// Without a scope (or while the stream is being captured) plain
+// cudaMalloc / cudaFree.  Every use of a stream-ordered buffer is ordered
+// after its allocation on that stream (the same stream, or a graph or a
+// joined fork launched there), and its last use precedes the free there.
+inline cudaStream_t& alloc_stream() {
+    static thread_local cudaStream_t s = nullptr;
+    return s;
+}
+struct AllocStreamScope {
+    cudaStream_t prev;
+    explicit AllocStreamScope(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
+    ~AllocStreamScope() { alloc_stream() = prev; }
+    AllocStreamScope(const AllocStreamScope&) = delete;
+    AllocStreamScope& operator=(const AllocStreamScope&) = delete;
+};
+
 template <class T>
 struct DBuf {
     T* p = nullptr;
     size_t n = 0;
+    cudaStream_t owner = nullptr;   // stream-ordered: allocated and freed on this stream
+    bool ordered = false;
     void alloc(size_t count) {
         free();
         if (count == 0) count = 1;
         void* q = nullptr;
-        PDG_CUDA(cudaMalloc(&q, count * sizeof(T)));
+        cudaStream_t s = alloc_stream();
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (s) PDG_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (s && cs == cudaStreamCaptureStatusNone) {
+            PDG_CUDA(cudaMallocAsync(&q, count * sizeof(T), s));
+            owner = s;
+            ordered = true;
+        } else {
+            PDG_CUDA(cudaMalloc(&q, count * sizeof(T)));
+            owner = nullptr;
+            ordered = false;
+        }
         p = static_cast<T*>(q);
         n = count;
     }
     void free() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (ordered) cudaFreeAsync(p, owner);
+            else cudaFree(p);
+        }
         p = nullptr;
         n = 0;
+        ordered = false;
     }
     size_t bytes() const { return n * sizeof(T); }
     ~DBuf() { free(); }

@@ -79,12 +79,23 @@ enum { PH_DRIVE = 0, PH_INER, PH_LOC, PH_ASM, PH_GAT, PH_RED, PH_VEL, PH_NB };
 
 }  // namespace
 
+// A stream destroyed with its owner.  Declared first in pd_server, so that it
+// outlives every member buffer freed on it (members are destroyed in reverse
+// order, after the destructor's body).
+struct OwnedStream {
+    cudaStream_t s = nullptr;
+    ~OwnedStream() {
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
 struct pd_server {
+    OwnedStream frame_stream;              // the frames' stream (highest priority)
     int64_t budget = 0;
     int32_t max_slots = 0, n_iter = 20;
     int device = 0;
     cudaStream_t user = nullptr;           // the caller's stream: each tick is ordered after its prior work
-    cudaStream_t stream = nullptr, cap = nullptr;   // the frames' own stream (highest priority)
+    cudaStream_t stream = nullptr, cap = nullptr;   // stream = frame_stream.s
     cudaEvent_t e_user = nullptr;
     int32_t* h_err = nullptr;              // pinned copy of d_err
     cudaStream_t adm = nullptr;            // admission stream (lowest priority)
@@ -131,7 +142,6 @@ struct pd_server {
         if (e_user) cudaEventDestroy(e_user);
         if (h_err) cudaFreeHost(h_err);
         if (cap) cudaStreamDestroy(cap);
-        if (stream) cudaStreamDestroy(stream);
         if (adm) cudaStreamDestroy(adm);
         for (auto st : adm_streams)
             if (st) cudaStreamDestroy(st);
@@ -325,6 +335,7 @@ constexpr int kAdmissionWorkers = 4;
 // while it works on the host or the device.  A request that must wait for
 // memory goes back to the head of the queue.
 static void prepare_head(pd_server* S, std::unique_lock<std::mutex>& lk, cudaStream_t adm) {
+    AllocStreamScope alloc_scope(adm);   // the request's own buffers: allocated and freed on its admission stream
     const pd_request_id id = S->queue.front();
     Request& R = *S->reqs[id];
     auto nothing_resident = [&]() {
@@ -478,10 +489,12 @@ pd_status pd_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t 
         int prio_low = 0, prio_high = 0;
         PDG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
         // the frames ahead of the admission work (FP64 prefactorisations) whenever an SM frees up
-        PDG_CUDA(cudaStreamCreateWithPriority(&S->stream, cudaStreamNonBlocking, prio_high));
+        PDG_CUDA(cudaStreamCreateWithPriority(&S->frame_stream.s, cudaStreamNonBlocking, prio_high));
+        S->stream = S->frame_stream.s;
         PDG_CUDA(cudaEventCreateWithFlags(&S->e_user, cudaEventDisableTiming));
         PDG_CUDA(cudaMallocHost((void**)&S->h_err, sizeof(int32_t)));
         *S->h_err = 0;
+        AllocStreamScope alloc_scope(S->stream);
         PDG_CUDA(cudaStreamCreateWithPriority(&S->adm, cudaStreamNonBlocking, prio_low));
         S->adm_streams.assign(kAdmissionWorkers, nullptr);
         for (auto& st : S->adm_streams) PDG_CUDA(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_low));
@@ -558,6 +571,7 @@ pd_status pd_submit(pd_server* S, const pd_request* q, pd_request_id* id) {
 pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
     try {
+        AllocStreamScope alloc_scope(S->stream);   // the batch descriptors: allocated and freed on the frame stream
         // this tick after the caller's prior work
         PDG_CUDA(cudaEventRecord(S->e_user, S->user));
         PDG_CUDA(cudaStreamWaitEvent(S->stream, S->e_user, 0));
