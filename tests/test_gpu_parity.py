@@ -543,3 +543,31 @@ def test_bulk_copy_wait_runs_out_and_reports_timeout():
     m.sync()
     assert torch.equal(out, ref)
     m.close()
+
+
+def test_phase_timing_sampled_iteration_leaves_results_unchanged():
+    """Phase events (every iteration, or one sampled PD iteration per frame)
+    time the kernels without changing a bit of the frame's result; a negative
+    iteration other than -1 is rejected."""
+    from paper_2405_12484_gb300._lib import PDError
+    from paper_2405_12484_gb300.sim import phase_bit
+    w = parity_slab()
+    m, _ = make_pair(w, factor_oracle=False)
+    x0 = torch.as_tensor(w.rest, dtype=torch.float32)
+    v0 = torch.zeros((w.n_v, 3))
+    outs = {}
+    for mode, (mask, it) in {"off": (0, -1), "all": (-1, -1), "sampled": (phase_bit("local"), 3)}.items():
+        m.enable_timing(mask, iteration=it)
+        m.set_state(x0, v0)
+        x = torch.empty((w.n_v, 3), device="cuda")
+        for n in range(3):
+            m.step(torch.as_tensor(w.pin_targets(n), dtype=torch.float32, device="cuda"), w.gravity, 10, x_out=x)
+        m.sync()
+        outs[mode] = (x.cpu(), m.phase_times())
+    assert torch.equal(outs["off"][0], outs["all"][0])
+    assert torch.equal(outs["off"][0], outs["sampled"][0])
+    assert outs["all"][1]["local"] > 0 and outs["all"][1]["dd_condense"] > 0
+    assert outs["sampled"][1]["local"] > 0 and outs["sampled"][1]["dd_condense"] == 0
+    with pytest.raises(PDError):
+        m.enable_timing(-1, iteration=-2)
+    m.close()
