@@ -562,8 +562,10 @@ typedef struct pd_request {
  * lowest priority, while the resident ones keep advancing; the first of them
  * also frees the meshes of retired requests.  The frames run on a stream of
  * the server's own at the device's highest priority (ahead of admission work
- * whenever an SM frees up); every pd_server_tick is ordered after the work
- * queued on cuda_stream (NULL: the legacy default stream) before the call.
+ * whenever an SM frees up).  Requests and results are host arrays, so the
+ * frames need no ordering with the caller's work; if cuda_stream is not
+ * NULL, every pd_server_tick is still ordered after the work queued on it
+ * before the call (NULL, the legacy default stream, is not waited on).
  */
 pd_status pd_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t n_iter, void* cuda_stream,
                            pd_server** out);

@@ -572,9 +572,14 @@ pd_status pd_server_tick(pd_server* S, int32_t* n_active, float* frame_ms) {
     if (!S) return sfail(PD_ERR_INVALID_ARG, "server is NULL");
     try {
         AllocStreamScope alloc_scope(S->stream);   // the batch descriptors: allocated and freed on the frame stream
-        // this tick after the caller's prior work
-        PDG_CUDA(cudaEventRecord(S->e_user, S->user));
-        PDG_CUDA(cudaStreamWaitEvent(S->stream, S->e_user, 0));
+        // this tick after the caller's prior work on its own stream.  Not on the legacy
+        // default stream: an event recorded there waited 12-50 ms for the driver while an
+        // admission thread was inside a prefactorisation (requests and results are host
+        // arrays, so the frames need no ordering with it).
+        if (S->user) {
+            PDG_CUDA(cudaEventRecord(S->e_user, S->user));
+            PDG_CUDA(cudaStreamWaitEvent(S->stream, S->e_user, 0));
+        }
         // retire finished requests: read back their positions, hand their meshes to the worker
         std::vector<std::pair<pd_mesh*, int64_t>> dead;
         for (size_t k = 0; k < S->active.size();) {
