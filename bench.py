@@ -601,22 +601,27 @@ def main():
 
     # ---- mixed precision: BF16 matrices on the tensor cores, the correction form (the residual
     # b - K x formed per tet inside the fused local step), same frames, same timing
-    mixed = None
-    mm = None
+    mixed, mixed_tf32 = None, None
+    mm, mt = None, None
     plain = (args.precision == "fp32" and not args.correction and not args.modal and not args.streaming
              and not args.single_level and args.refine == 0)
+
+    def mixed_leg(prec, kernels):
+        mx = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density, stream=stream)
+        mx.set_materials(w.gamma_s, w.gamma_v)
+        mx.prefactor(w.dt, precision=prec, correction=True, use_graphs=True)
+        lm = time_leg(mx, w, mx.info(), pins, n_iter, K, W, stream, local, 1)
+        return mx, {"precision": prec, "form": "correction (residual per PD iteration, FP32 vectors)",
+                    "ms_per_frame": lm["total_ms"] / K, "pd_iters_per_s": K * n_iter / (lm["total_ms"] / 1e3),
+                    "frame_ms": {"p50": pct(lm["frame_ms"], 0.5), "p99": pct(lm["frame_ms"], 0.99)},
+                    "dominant": lm["dominant"], "phases": lm.get("phases", {}), "clocks": lm["clocks"],
+                    "tensor_core_kernels": kernels}
+
     if rank == 0 and plain and not args.no_mixed:
-        mm = Mesh(w.rest, w.tets, w.pinned, w.tet_domain, w.n_domains, w.density, stream=stream)
-        mm.set_materials(w.gamma_s, w.gamma_v)
-        mm.prefactor(w.dt, precision="bf16", correction=True, use_graphs=True)
-        info_m = mm.info()
-        lm = time_leg(mm, w, info_m, pins, n_iter, K, W, stream, local, 1)
-        mixed = {"precision": "bf16", "form": "correction (residual per PD iteration, FP32 vectors)",
-                 "ms_per_frame": lm["total_ms"] / K, "pd_iters_per_s": K * n_iter / (lm["total_ms"] / 1e3),
-                 "frame_ms": {"p50": pct(lm["frame_ms"], 0.5), "p99": pct(lm["frame_ms"], 0.99)},
-                 "dominant": lm["dominant"], "phases": lm.get("phases", {}), "clocks": lm["clocks"],
-                 "tensor_core_kernels": ["k_axpy_mma (interior, boundary-mode and back-substitution products)",
-                                         "k_rowdot_mma (second-level and coarse row-form products)"]}
+        mm, mixed = mixed_leg("bf16", ["k_axpy_mma<false> (interior, boundary-mode and back-substitution products)",
+                                       "k_rowdot_mma (second-level and coarse row-form products)"])
+        mt, mixed_tf32 = mixed_leg("tf32", ["k_axpy_mma<true> (interior, boundary-mode and back-substitution "
+                                            "products; the row-form products stay FP32-sized on the CUDA cores)"])
 
     # ---- accuracy of each precision's first frame against the FP64 oracle (host-side job)
     accuracy = None
@@ -627,10 +632,13 @@ def main():
             accuracy = {"fp32" if args.precision == "fp32" else args.precision: frame0_error(m, w, ref, n_iter)}
             if mm is not None:
                 accuracy["bf16_correction"] = frame0_error(mm, w, ref, n_iter)
+            if mt is not None:
+                accuracy["tf32_correction"] = frame0_error(mt, w, ref, n_iter)
         else:
             accuracy = {"error": str(jobs.results.get("frame", (None, "not run"))[1])}
-    if mm is not None:
-        mm.close()
+    for mx in (mm, mt):
+        if mx is not None:
+            mx.close()
 
     cpu = None
     if jobs is not None:
@@ -673,6 +681,7 @@ def main():
         }
         if mixed is not None:
             line["mixed_precision"] = mixed
+            line["mixed_precision_tf32"] = mixed_tf32
         if accuracy is not None:
             line["accuracy_vs_fp64"] = accuracy
         if not args.no_serving and world == 1:

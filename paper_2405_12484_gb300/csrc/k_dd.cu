@@ -515,27 +515,57 @@ constexpr int kAxmRows = PDG_AXM_ROWS;
 constexpr int kAxmStages = kAxtStages;
 static_assert(kAxmNb * 8 * kAxtWarps >= 256, "one consumer warp per output column group");
 
-inline size_t axm_ring_bytes(int wmax) {
-    return ((size_t)kAxmStages * kAxmRows * wmax * sizeof(__nv_bfloat16) + 15) / 16 * 16;
+// TF32 tiles: stages of 32 FP32-sized rows (the FP32 kernel's stage), 8-row k-blocks
+constexpr int kAxfRows = kAxtRows;
+// lanes whose A operand is not zero: groups 0..2 (x, y, z in rows g and g + 8)
+constexpr int kAxmFragLanes = 12;
+
+inline size_t axm_ring_bytes(int wmax, bool tf32 = false) {
+    const size_t b = tf32 ? (size_t)kAxmStages * kAxfRows * wmax * sizeof(float)
+                          : (size_t)kAxmStages * kAxmRows * wmax * sizeof(__nv_bfloat16);
+    return (b + 15) / 16 * 16;
 }
 
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void mma_tf32_1688(float (&d)[4], const uint4& a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+// TF32 = true: the same product from FP32-sized TF32 tiles with mma.m16n8k8
+// (8-row k-blocks; B fragment b0 = row q, b1 = row q + 4 of output g; the A
+// operand holds x, y, z rounded to TF32 in rows 0-2 and their TF32
+// remainders in rows 8-10, so x again carries about twice the storage
+// precision).
+template <bool TF32>
 __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_mma(const AxDesc* __restrict__ descs,
                                                                    const AxBlock* __restrict__ blocks, AxBases B,
                                                                    int ring_bytes, int* __restrict__ err) {
     using namespace tma;
-    constexpr int S = kAxmStages, R = kAxmRows;
-    static_assert(R % 16 == 0, "stages hold whole 16-row blocks");
+    using E = typename std::conditional<TF32, float, __nv_bfloat16>::type;
+    constexpr int KB = TF32 ? 8 : 16;   // matrix rows per mma k-block
+    constexpr int S = kAxmStages, R = TF32 ? kAxfRows : kAxmRows;
+    static_assert(R % KB == 0, "stages hold whole k-blocks");
     extern __shared__ __align__(128) unsigned char axm_smem[];
     __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ int abort_flag;
     const AxBlock bk = blocks[blockIdx.x];
     const AxDesc D = descs[bk.desc];
     const int w = ax_tile_width(D.n_out, bk.o0, D.ld, 8);
-    const int Kp = (D.K + 15) & ~15;
-    __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(axm_smem);
-    uint4* frag = reinterpret_cast<uint4*>(axm_smem + ring_bytes);                  // Kp / 16 x 32 lanes
-    float4* xs = reinterpret_cast<float4*>(axm_smem + ring_bytes + (size_t)Kp * 32);  // K entries
-    const __nv_bfloat16* tile = reinterpret_cast<const __nv_bfloat16*>(B.pool) + D.a_off + (int64_t)bk.o0 * Kp;
+    const int Kp = (D.K + KB - 1) / KB * KB;
+    E* ring = reinterpret_cast<E*>(axm_smem);
+    // A operands of lanes 0..11 only (rows 0-2 and 8-10: the lanes of groups 3..7 hold zeros)
+    uint4* frag = reinterpret_cast<uint4*>(axm_smem + ring_bytes);   // Kp / KB x 12 lanes
+    float4* xs = reinterpret_cast<float4*>(axm_smem + ring_bytes + (size_t)(Kp / KB) * kAxmFragLanes * sizeof(uint4));
+    const E* tile = reinterpret_cast<const E*>(B.pool) + D.a_off + (int64_t)bk.o0 * Kp;
     const int n_st = (Kp + R - 1) / R;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     pdl_trigger();
@@ -562,7 +592,7 @@ __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_mma(const AxDesc*
                     break;
                 }
                 const int rows = min(R, Kp - i * R);
-                const uint32_t bytes = (uint32_t)(rows * w * (int)sizeof(__nv_bfloat16));
+                const uint32_t bytes = (uint32_t)(rows * w * (int)sizeof(E));
                 uint32_t expect = bytes;
                 if (blockIdx.x == 0 && i == 0 && *reinterpret_cast<volatile int*>(&g_test_copy_extra) > 0)
                     expect += (uint32_t)max(atomicExch(&g_test_copy_extra, 0), 0);
@@ -575,14 +605,36 @@ __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_mma(const AxDesc*
         }
         return;
     }
-    // consumers: stage x, then the A operands of every 16-row block (hi rows 0..2, remainders 8..10)
+    // consumers: stage x, then the A operands of every k-block (hi rows 0..2, remainders 8..10)
     pdl_wait();
     stage_f4(xs, D.K, B.x + D.x_off, D.bidx_off >= 0 ? B.bidx + D.bidx_off : nullptr, threadIdx.x, 32 * kAxtWarps);
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kAxtWarps) : "memory");
-    for (int f = threadIdx.x; f < (Kp >> 4) * 32; f += 32 * kAxtWarps) {
-        const int kb = f >> 5, l = f & 31, g = l >> 2, q = l & 3;
+    if (TF32) {
+        // a0 = (row g, k q), a1 = (row g + 8, k q), a2 = (row g, k q + 4), a3 = (row g + 8, k q + 4)
+        for (int f = threadIdx.x; f < (Kp / KB) * kAxmFragLanes; f += 32 * kAxtWarps) {
+            const int kb = f / kAxmFragLanes, l = f % kAxmFragLanes, g = l >> 2, q = l & 3;
+            uint32_t a[4] = {0u, 0u, 0u, 0u};
+            {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = kb * 8 + q + 4 * h;
+                    float v = 0.f;
+                    if (k < D.K) {
+                        const float4 xv = xs[k];
+                        v = g == 0 ? xv.x : (g == 1 ? xv.y : xv.z);
+                    }
+                    const uint32_t hi = to_tf32(v);
+                    a[2 * h] = hi;
+                    a[2 * h + 1] = to_tf32(v - __uint_as_float(hi));
+                }
+            }
+            frag[f] = make_uint4(a[0], a[1], a[2], a[3]);
+        }
+    } else
+    for (int f = threadIdx.x; f < (Kp >> 4) * kAxmFragLanes; f += 32 * kAxtWarps) {
+        const int kb = f / kAxmFragLanes, l = f % kAxmFragLanes, g = l >> 2, q = l & 3;
         uint32_t hv[4] = {0u, 0u, 0u, 0u}, lv[4] = {0u, 0u, 0u, 0u};   // (a0, a2) hi, (a1, a3) lo
-        if (g < 3) {
+        {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {       // h = 0: rows 2q, 2q+1; h = 1: rows 2q+8, 2q+9
                 __nv_bfloat16 hi[2], lo[2];
@@ -617,17 +669,19 @@ __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_mma(const AxDesc*
             }
             break;
         }
-        const int kbs = min(R, Kp - i * R) >> 4;
+        const int kbs = min(R, Kp - i * R) / KB;
         const uint2* st = reinterpret_cast<const uint2*>(ring + (size_t)slot * R * w);
         for (int kk = 0; kk < kbs; ++kk) {
-            const uint4 a = frag[(i * (R >> 4) + kk) * 32 + lane];
-            const uint2* blk = st + (size_t)kk * nb8 * 32;
+            const uint4 a = lane < kAxmFragLanes ? frag[(i * (R / KB) + kk) * kAxmFragLanes + lane]
+                                                 : make_uint4(0u, 0u, 0u, 0u);
+            const uint2* blk = st + (size_t)kk * nb8 * 32;   // a k-block x 8-output block: 32 lanes x 8 bytes
 #pragma unroll
             for (int j = 0; j < kAxmNb; ++j) {
                 const int nb = warp + kAxtWarps * j;
                 if (nb < nb8) {
                     const uint2 bv = blk[nb * 32 + lane];
-                    mma_bf16_16816(acc[j], a, bv.x, bv.y);
+                    if (TF32) mma_tf32_1688(acc[j], a, bv.x, bv.y);
+                    else mma_bf16_16816(acc[j], a, bv.x, bv.y);
                 }
             }
         }
@@ -1402,25 +1456,29 @@ int axt_smem_limit() {
 }
 
 int axm_smem_limit() {
-    static const int lim = allow_max_dynamic_smem(k_axpy_mma);
+    static const int lim = std::min(allow_max_dynamic_smem(k_axpy_mma<false>), allow_max_dynamic_smem(k_axpy_mma<true>));
     return lim;
 }
 
 template <class T>
 void launch_ax(const AxDesc* descs, const AxBlock* blocks, int n_blocks, int k_max, const AxBases& B, cudaStream_t s,
-               int* tma_err = nullptr, int w_max = 0, bool pdl = false) {
+               int* tma_err = nullptr, int w_max = 0, bool pdl = false, bool tf32 = false) {
     if (n_blocks <= 0) return;
-    if (tma_err && std::is_same<T, __nv_bfloat16>::value) {
-        // BF16 tiles in the tensor-core fragment layout
-        const int kp = (std::max(k_max, 1) + 15) & ~15;
-        const size_t ring = axm_ring_bytes(w_max);
-        const size_t smem = ring + (size_t)kp * 32 + sizeof(float4) * std::max(k_max, 1);
+    const bool bf16 = std::is_same<T, __nv_bfloat16>::value;
+    if (tma_err && (bf16 || tf32)) {
+        // BF16 or TF32 tiles in the tensor-core fragment layout (k-blocks of 16 or 8 rows;
+        // the A operands take 16 bytes per k-block for each of lanes 0..11)
+        const int kb = bf16 ? 16 : 8;
+        const int kp = (std::max(k_max, 1) + kb - 1) / kb * kb;
+        const size_t ring = axm_ring_bytes(w_max, !bf16);
+        const size_t smem = ring + (size_t)(kp / kb) * kAxmFragLanes * sizeof(uint4) + sizeof(float4) * std::max(k_max, 1);
         if ((int)smem > axm_smem_limit()) throw Fail{PD_ERR_UNSUPPORTED};
+        auto kern = bf16 ? k_axpy_mma<false> : k_axpy_mma<true>;
         if (pdl)
-            launch_pdl(k_axpy_mma, dim3(n_blocks), dim3(32 * (kAxtWarps + 1)), smem, s, descs, blocks, B, (int)ring,
+            launch_pdl(kern, dim3(n_blocks), dim3(32 * (kAxtWarps + 1)), smem, s, descs, blocks, B, (int)ring,
                        tma_err);
         else
-            k_axpy_mma<<<n_blocks, 32 * (kAxtWarps + 1), smem, s>>>(descs, blocks, B, (int)ring, tma_err);
+            kern<<<n_blocks, 32 * (kAxtWarps + 1), smem, s>>>(descs, blocks, B, (int)ring, tma_err);
     } else if (tma_err) {
         // tiled matrices: the bulk-copy streaming kernel
         const size_t ring = axt_ring_bytes<T>(w_max);
@@ -1516,7 +1574,7 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
             phase_begin(m, PH_INTERIOR, m->side[0]);
             launch_ax<T>(m->d_ax_desc_int.p, m->d_ax_blk_int.p, m->ax_blocks_int, m->ax_kmax_int,
                          AxBases{pool, b, nullptr, nullptr, w.tc}, m->side[0], m->ax_tiled ? m->d_err.p : nullptr,
-                         m->ax_wmax_int);
+                         m->ax_wmax_int, false, m->ax_tf32);
             phase_end(m, m->side[0]);
         }
         PDG_CUDA(cudaEventRecord(m->ev_join[0], m->side[0]));
@@ -1525,7 +1583,7 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
         phase_begin(m, PH_CONDENSE, s);
         launch_ax<T>(m->d_ax_desc_cond.p, m->d_ax_blk_cond.p, m->ax_blocks_cond, m->ax_kmax_cond,
                      AxBases{pool, b, nullptr, nullptr, w.tc}, s, m->ax_tiled ? m->d_err.p : nullptr, m->ax_wmax_cond,
-                     true);
+                     true, m->ax_tf32);
         phase_end(m, s);
     }
     if (m->n_B > 0) {
@@ -1587,7 +1645,7 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
         phase_begin(m, PH_BACKSUB, s);
         launch_ax<T>(m->d_ax_desc_back.p, m->d_ax_blk_back.p, m->ax_blocks_back, m->ax_kmax_back,
                      AxBases{pool, xout + m->n_int, m->d_bidx.p, w.tc, xout}, s, m->ax_tiled ? m->d_err.p : nullptr,
-                     m->ax_wmax_back, true);
+                     m->ax_wmax_back, true, m->ax_tf32);
         phase_end(m, s);
     }
     const int S = (int)m->jacobi_omega.size();

@@ -345,6 +345,24 @@ __global__ void k_cast_frag16(const double* __restrict__ src, int lds, int rows,
     }
 }
 
+// TF32 tile (rows padded to 8) in the register order of the B operand of
+// mma.m16n8k8 (tf32): 8 x 8 blocks, lane 4 n + (k mod 4) holding rows k mod 4
+// and k mod 4 + 4 of output n; values rounded to TF32.
+__global__ void k_cast_frag32(const double* __restrict__ src, int lds, int rows, int cols, int transpose,
+                              float* __restrict__ d32, int64_t off, int CW) {
+    const int64_t n = (int64_t)rows * cols;
+    const int kp = (rows + 7) & ~7;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(l / cols), c = (int)(l % cols);
+        const double v = transpose ? src[(int64_t)c * lds + r] : src[(int64_t)r * lds + c];
+        const int o0 = c / CW * CW;
+        const int w = ax_tile_width(cols, o0, CW, 8);
+        const int kb = r >> 3, kk = r & 7, cc = c - o0, nb = cc >> 3, nn = cc & 7;
+        d32[off + (int64_t)o0 * kp + ((int64_t)kb * (w >> 3) + nb) * 64 + (4 * nn + (kk & 3)) * 2 + (kk >> 2)] =
+            round_tf32((float)v);
+    }
+}
+
 // BF16 row-form block in the tensor-core fragment order (rows and columns
 // padded to 16, see k_rowdot_mma): element (r, c) lands in 16 x 16 block
 // (r / 16, c / 16) at the lane and register of the mma A operand.
@@ -405,6 +423,13 @@ void launch_cast_block(const double* src, int lds, int rows, int cols, int trans
     if (rows <= 0 || cols <= 0) return;
     k_cast_block<<<grid_of((int64_t)rows * cols), 256, 0, s>>>(src, lds, rows, cols, transpose, prec, dst32, dst16,
                                                                 dst_off, ldd);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_cast_frag32(const double* src, int lds, int rows, int cols, int transpose, float* dst32,
+                        int64_t dst_off, int CW, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return;
+    k_cast_frag32<<<grid_of((int64_t)rows * cols), 256, 0, s>>>(src, lds, rows, cols, transpose, dst32, dst_off, CW);
     PDG_CHECK_LAUNCH();
 }
 

@@ -29,6 +29,8 @@ int ax_tile_outputs(int prec);
 void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s, bool mma = false);
 bool rowdot_mma_fits(int xcap);
 bool rowdot_row_fits_stage(int ld, int elem_bytes);
+void launch_cast_frag32(const double* src, int lds, int rows, int cols, int transpose, float* dst32,
+                        int64_t dst_off, int CW, cudaStream_t s);
 void launch_cast_rowfrag16(const double* src, int lds, int rows, int cols, int transpose, __nv_bfloat16* dst16,
                            int64_t dst_off, int Kp, cudaStream_t s);
 bool build_stream_plan(StreamPlan& P, const std::vector<ColDesc>& blocks, int prec, const void* src,
@@ -1042,6 +1044,9 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     // BF16 tiles for the tensor cores hold their rows padded to a multiple of 16
     const bool frag16 = !(o.flags & PD_SOLVE_STREAMING) && m->prec == PD_PREC_BF16;
     auto krows = [&](int32_t k) { return frag16 ? (int64_t)round_up(k, 16) : (int64_t)k; };
+    // TF32 tiles for the tensor cores: rows padded to a multiple of 8 (the row-form blocks stay row-major)
+    const bool fragT = !(o.flags & PD_SOLVE_STREAMING) && m->prec == PD_PREC_TF32;
+    auto kax = [&](int32_t k) { return fragT ? (int64_t)round_up(k, 8) : krows(k); };
     int64_t pool = 0;
     int32_t tcr = 0, pmr = 0;
     for (int32_t d = 0; d < n_dom; ++d) {
@@ -1059,12 +1064,12 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
             pm_off[d] = pmr;
             pmr += r_dom[d];
         } else {
-            pool += krows(ni) * ldH[d];
+            pool += kax(ni) * ldH[d];
         }
         p_off[d] = pool;
-        pool += krows(ni) * ldP[d];
+        pool += kax(ni) * ldP[d];
         t_off[d] = pool;
-        pool += krows(nbd) * ldT[d];
+        pool += kax(nbd) * ldT[d];
         tc_off[d] = tcr;
         tcr += ni + nbd;
     }
@@ -1109,13 +1114,16 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     // (streamed by bulk copies), except for the fused streaming solve, whose
     // plan copies row-major blocks into its own panels
     const bool tiled = !(o.flags & PD_SOLVE_STREAMING);
-    const int OWt = ax_tile_outputs(m->prec), VNt = (m->prec == PD_PREC_BF16) ? 8 : 4;
+    const int OWt = ax_tile_outputs(m->prec), VNt = (m->prec == PD_PREC_BF16 || fragT) ? 8 : 4;
     m->ax_tiled = tiled;
+    m->ax_tf32 = fragT;
     if (tiled) ax_prepare_tma(m->prec);
     auto cast_ax = [&](const double* src, int lds, int rows, int cols, int transpose, int64_t off, int ld) {
         if (frag16)
             launch_cast_frag16(src, lds, rows, cols, transpose, m->d_mat16.p, off, ax_chunk_width(cols, OWt, VNt),
                                s);
+        else if (fragT)
+            launch_cast_frag32(src, lds, rows, cols, transpose, m->d_mat32.p, off, ax_chunk_width(cols, OWt, VNt), s);
         else if (tiled)
             launch_cast_tiled(src, lds, rows, cols, transpose, m->prec, m->d_mat32.p, m->d_mat16.p, off,
                               ax_chunk_width(cols, OWt, VNt), VNt, s);
@@ -1166,7 +1174,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     }
 
     // ---- descriptors of the per-domain products: one block per output chunk
-    const int VN = (m->prec == PD_PREC_BF16) ? 8 : 4;
+    const int VN = (m->prec == PD_PREC_BF16 || m->ax_tf32) ? 8 : 4;
     std::vector<int32_t> bidx_off(n_dom + 1, 0), bidx;
     for (int32_t d = 0; d < n_dom; ++d) bidx_off[d + 1] = bidx_off[d] + (int32_t)m->dom_bnd[d].size();
     bidx.reserve(bidx_off.back());
@@ -1426,11 +1434,12 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     m->coarse_blocks = (m->cs_n > 0) ? dd_configure_coarse(m->ld_S) : 0;
     // The coarse product as a row-form product of whole rows (no split into
     // column chunks, no partial sums to reduce): BF16 on the tensor cores, FP32
-    // where a row fits one bulk-copy stage; otherwise the balanced split kernel.
+    // and TF32 where a row fits one bulk-copy stage; otherwise the balanced split kernel.
     m->rows_coarse.n_blocks = 0;
     m->rows_coarse.host.clear();
     const bool coarse_rows =
-        coarse_frag || (m->prec == PD_PREC_FP32 && !(o.flags & PD_SOLVE_STREAMING) && rowdot_row_fits_stage(m->ld_S, 4));
+        coarse_frag || ((m->prec == PD_PREC_FP32 || m->prec == PD_PREC_TF32) && !(o.flags & PD_SOLVE_STREAMING) &&
+                        rowdot_row_fits_stage(m->ld_S, 4));
     if (coarse_rows && m->cs_n > 0) {
         RowDesc c{};
         c.a_off = m->off_S;

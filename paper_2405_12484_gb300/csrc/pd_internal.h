@@ -373,6 +373,7 @@ struct pd_mesh {
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs (high priority)
     bool node_priority = true;          // instantiate frames with the captured per-node priorities
     bool ax_tiled = false;              // axpy-form matrices stored as tiles, streamed by bulk copies
+    bool ax_tf32 = false;               // TF32 tiles in the tensor-core fragment layout (k_axpy_mma<true>)
     // side streams of the subspace solve: the interior parts of the two
     // condensations run beside the interface solve (fork/join by events)
     cudaStream_t side[2] = {nullptr, nullptr};
