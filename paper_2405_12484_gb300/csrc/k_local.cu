@@ -139,11 +139,12 @@ __device__ __forceinline__ float4 assembly_base(const LocalAsmArgs& A, int v) {
     return A.by0[v];
 }
 
+// One block of the fused kernel: tets [blk kLaTets, (blk + 1) kLaTets) of the mesh in A.
 template <bool RESID>
-__global__ void __launch_bounds__(kLaTets, PDG_LA_MINB) k_local_assemble(LocalAsmArgs A) {
+__device__ __forceinline__ void local_assemble_block(const LocalAsmArgs& A, int blk) {
     __shared__ float fx[4 * kLaTets], fy[4 * kLaTets], fz[4 * kLaTets];
     pdl_trigger();
-    const int e = blockIdx.x * kLaTets + threadIdx.x;
+    const int e = blk * kLaTets + threadIdx.x;
     const bool live = e < A.n_t;
     const int ec = live ? e : A.n_t - 1;
     LocalIn L;
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(kLaTets, PDG_LA_MINB) k_local_assemble(LocalAs
     L.r1 = __ldg(&A.geo[ec]);
     L.r2 = __ldg(&A.geo[A.n_t + ec]);
     L.r3 = __ldg(&A.geo[2 * (int64_t)A.n_t + ec]);
-    const int j0 = __ldg(&A.vptr[blockIdx.x]), j1 = __ldg(&A.vptr[blockIdx.x + 1]);
+    const int j0 = __ldg(&A.vptr[blk]), j1 = __ldg(&A.vptr[blk + 1]);
     pdl_wait();   // x comes from the previous solve
     L.x0 = A.x[tv.x];
     L.x1 = A.x[tv.y];
@@ -188,11 +189,16 @@ __global__ void __launch_bounds__(kLaTets, PDG_LA_MINB) k_local_assemble(LocalAs
     }
 }
 
+template <bool RESID>
+__global__ void __launch_bounds__(kLaTets, PDG_LA_MINB) k_local_assemble(LocalAsmArgs A) {
+    local_assemble_block<RESID>(A, blockIdx.x);
+}
+
 // shared vertices: b_v = base + the blocks' partial sums in block order
 template <bool RESID>
-__global__ void __launch_bounds__(256) k_assemble_shared(LocalAsmArgs A, int n_shared) {
+__device__ __forceinline__ void assemble_shared_block(const LocalAsmArgs& A, int n_shared, int blk) {
     pdl_trigger();
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blk * 256 + threadIdx.x;
     const bool live = j < n_shared;
     const int v = live ? __ldg(&A.sh_vert[j]) : 0;
     const int s0 = live ? __ldg(&A.sh_ptr[j]) : 0, s1 = live ? __ldg(&A.sh_ptr[j + 1]) : 0;
@@ -206,6 +212,46 @@ __global__ void __launch_bounds__(256) k_assemble_shared(LocalAsmArgs A, int n_s
         acc.z += p.z;
     }
     A.b[v] = make_float4(acc.x, acc.y, acc.z, 0.f);
+}
+
+template <bool RESID>
+__global__ void __launch_bounds__(256) k_assemble_shared(LocalAsmArgs A, int n_shared) {
+    assemble_shared_block<RESID>(A, n_shared, blockIdx.x);
+}
+
+// Serving: the same two kernels over every resident request of a batch (RHS
+// form); a block finds its request from the per-kernel block offsets, so each
+// request's values come from exactly the arithmetic and order above.
+__device__ __forceinline__ LocalAsmArgs batch_args(const BatchSlot& S) {
+    LocalAsmArgs A{};
+    A.n_t = S.n_t;
+    A.tets = S.tets;
+    A.geo = S.geo;
+    A.x = S.x;
+    A.by0 = S.by0;
+    A.b = S.b;
+    A.vptr = S.la_vptr;
+    A.vert = S.la_vert;
+    A.slot = S.la_slot;
+    A.cptr = S.la_cptr;
+    A.corner = S.la_corner;
+    A.sh_ptr = S.la_sh_ptr;
+    A.sh_vert = S.la_sh_vert;
+    A.part = S.la_part;
+    return A;
+}
+
+__global__ void __launch_bounds__(kLaTets, PDG_LA_MINB) k_b_local_assemble(const BatchSlot* __restrict__ slots,
+                                                                         const int* __restrict__ off, int n_slots) {
+    const int s = batch_find_slot(off, n_slots, blockIdx.x);
+    local_assemble_block<false>(batch_args(slots[s]), blockIdx.x - off[s]);
+}
+
+__global__ void __launch_bounds__(256) k_b_assemble_shared(const BatchSlot* __restrict__ slots,
+                                                         const int* __restrict__ off, int n_slots) {
+    const int s = batch_find_slot(off, n_slots, blockIdx.x);
+    const BatchSlot& S = slots[s];
+    assemble_shared_block<false>(batch_args(S), S.la_shared, blockIdx.x - off[s]);
 }
 
 }  // namespace
@@ -317,6 +363,18 @@ void launch_local_assemble(const pd_mesh* m, const float4* x, const float4* by0,
         launch_pdl(k_local_assemble<false>, dim3(m->la_blocks), dim3(kLaTets), 0, s, A);
         if (nsb > 0) launch_pdl(k_assemble_shared<false>, dim3(nsb), dim3(256), 0, s, A, m->la_shared);
     }
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_b_local_assemble(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s) {
+    if (blocks <= 0) return;
+    k_b_local_assemble<<<blocks, kLaTets, 0, s>>>(slots, off, n_slots);
+    PDG_CHECK_LAUNCH();
+}
+
+void launch_b_assemble_shared(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s) {
+    if (blocks <= 0) return;
+    k_b_assemble_shared<<<blocks, 256, 0, s>>>(slots, off, n_slots);
     PDG_CHECK_LAUNCH();
 }
 

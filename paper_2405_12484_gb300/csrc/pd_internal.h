@@ -331,20 +331,37 @@ struct LocalAsmArgs {
 struct BatchSlot {
     const int4* tets;
     const float4* geo;
-    float4 *x, *xprev, *v, *force, *by0, *b, *pin_tgt;
+    float4 *x, *xprev, *v, *by0, *b, *pin_tgt;
     const float4* pin_rest;
     const float* mh2;
-    const int *inc_ptr, *inc, *kfp_ptr, *kfp_col;
+    const int *kfp_ptr, *kfp_col;
     const float* kfp_val;
     float4 *tc, *cB, *part;
     const int *gat_ptr, *gat;
     int* err;
     int* frame;          // frames completed (device counter)
+    // plan of the fused local step + assembly (see LocalAsmArgs)
+    const int *la_vptr, *la_vert, *la_slot, *la_cptr, *la_sh_ptr, *la_sh_vert;
+    const uint16_t* la_corner;
+    float4* la_part;
+    int la_shared;
     int n_t, n_v, n_free, n_pin, n_int, n_B, nch;
     float h, gx, gy, gz;
     float drive_amp, drive_w;
     int drive_axis;
 };
+
+// The slot of a block of a batched launch: the last s with off[s] <= b
+// (off[0] = 0, off increasing).
+__device__ __forceinline__ int batch_find_slot(const int* __restrict__ off, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 // The interface matrix S^-1 of one slot in the batched coarse kernel.
 struct CoarseDescB {

@@ -26,8 +26,8 @@ namespace pdg {
 
 void launch_b_drive(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_b_inertia(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
-void launch_b_local(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
-void launch_b_assemble(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
+void launch_b_local_assemble(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
+void launch_b_assemble_shared(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_b_gather(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_b_reduce(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_b_velocity(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
@@ -202,14 +202,11 @@ static void rebuild(pd_server* S) {
         b.x = m->d_x.p;
         b.xprev = m->d_xprev.p;
         b.v = m->d_v.p;
-        b.force = m->d_force.p;
         b.by0 = m->d_by0.p;
         b.b = m->d_b.p;
         b.pin_tgt = m->d_pin_tgt.p;
         b.pin_rest = R.pin_rest.p;
         b.mh2 = m->d_mh2.p;
-        b.inc_ptr = m->d_inc_ptr.p;
-        b.inc = m->d_inc.p;
         b.kfp_ptr = m->d_kfp_ptr.p;
         b.kfp_col = m->d_kfp_col.p;
         b.kfp_val = m->d_kfp_val.p;
@@ -220,6 +217,15 @@ static void rebuild(pd_server* S) {
         b.gat = m->d_gat.p;
         b.err = m->d_err.p;
         b.frame = R.frame.p;
+        b.la_vptr = m->d_la_vptr.p;
+        b.la_vert = m->d_la_vert.p;
+        b.la_slot = m->d_la_slot.p;
+        b.la_cptr = m->d_la_cptr.p;
+        b.la_corner = m->d_la_corner.p;
+        b.la_sh_ptr = m->d_la_sh_ptr.p;
+        b.la_sh_vert = m->d_la_sh_vert.p;
+        b.la_part = m->d_la_part.p;
+        b.la_shared = m->la_shared;
         b.n_t = m->n_t;
         b.n_v = m->n_v;
         b.n_free = m->n_free;
@@ -234,8 +240,9 @@ static void rebuild(pd_server* S) {
         b.drive_amp = R.amp;
         b.drive_w = 2.0f * 3.14159265358979f * R.freq;
         b.drive_axis = R.axis;
-        const int cnt[PH_NB] = {(m->n_pin + 255) / 256, (m->n_v + 255) / 256, (m->n_t + 127) / 128,
-                                (m->n_free + 255) / 256, (m->n_B + 255) / 256, (m->n_B + 255) / 256,
+        // (the fused local step: one block per plan block; the finish of the shared vertices)
+        const int cnt[PH_NB] = {(m->n_pin + 255) / 256, (m->n_v + 255) / 256, m->la_blocks,
+                                (m->la_shared + 255) / 256, (m->n_B + 255) / 256, (m->n_B + 255) / 256,
                                 (m->n_v + 255) / 256};
         for (int p = 0; p < PH_NB; ++p) off[p][k + 1] = off[p][k] + cnt[p];
         const float* pool = m->d_mat32.p;
@@ -307,8 +314,8 @@ static void rebuild(pd_server* S) {
         launch_b_drive(sl, S->d_off[PH_DRIVE].p, n, S->blocks[PH_DRIVE], c);
         launch_b_inertia(sl, S->d_off[PH_INER].p, n, S->blocks[PH_INER], c);
         for (int it = 0; it < S->n_iter; ++it) {
-            launch_b_local(sl, S->d_off[PH_LOC].p, n, S->blocks[PH_LOC], c);
-            launch_b_assemble(sl, S->d_off[PH_ASM].p, n, S->blocks[PH_ASM], c);
+            launch_b_local_assemble(sl, S->d_off[PH_LOC].p, n, S->blocks[PH_LOC], c);
+            launch_b_assemble_shared(sl, S->d_off[PH_ASM].p, n, S->blocks[PH_ASM], c);
             launch_axpy_b(S->d_axc.p, S->d_blkc.p, S->d_basc.p, S->blocks_c, S->kmax_c, S->wmax_c, S->d_err.p, c);
             launch_b_gather(sl, S->d_off[PH_GAT].p, n, S->blocks[PH_GAT], c);
             launch_coarse_b(S->d_cd.p, S->n_cd, S->units, S->max_cols, S->coarse_blocks, c);
