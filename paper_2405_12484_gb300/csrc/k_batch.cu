@@ -68,6 +68,20 @@ __global__ void k_b_gather(const BatchSlot* __restrict__ slots, const int* __res
     S.cB[j] = acc;
 }
 
+// two-level requests: c_T = c_B[T0:] + the gathered second-level terms (as k_gather)
+__global__ void k_b_gather2(const BatchSlot* __restrict__ slots, const int* __restrict__ off, int n_slots) {
+    const int s = batch_find_slot(off, n_slots, blockIdx.x);
+    const BatchSlot& S = slots[s];
+    const int j = (blockIdx.x - off[s]) * blockDim.x + threadIdx.x;
+    if (j >= S.n_top) return;
+    float4 acc = S.cB[S.n_B - S.n_top + j];
+    for (int k = S.gat2_ptr[j]; k < S.gat2_ptr[j + 1]; ++k) {
+        const float4 c = S.tc2[S.gat2[k]];
+        acc.x += c.x; acc.y += c.y; acc.z += c.z;
+    }
+    S.cT[j] = acc;
+}
+
 __global__ void k_b_reduce(const BatchSlot* __restrict__ slots, const int* __restrict__ off, int n_slots) {
     const int s = batch_find_slot(off, n_slots, blockIdx.x);
     const BatchSlot& S = slots[s];
@@ -115,6 +129,11 @@ void launch_b_inertia(const BatchSlot* slots, const int* off, int n_slots, int b
 void launch_b_gather(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s) {
     if (blocks <= 0) return;
     k_b_gather<<<blocks, 256, 0, s>>>(slots, off, n_slots);
+    PDG_CHECK_LAUNCH();
+}
+void launch_b_gather2(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s) {
+    if (blocks <= 0) return;
+    k_b_gather2<<<blocks, 256, 0, s>>>(slots, off, n_slots);
     PDG_CHECK_LAUNCH();
 }
 void launch_b_reduce(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s) {

@@ -1091,10 +1091,13 @@ constexpr int kRowtStageBytes = PDG_ROWT_STAGE_BYTES;
 constexpr int kRowtStages = PDG_ROWT_STAGES;
 constexpr int kRowtWarps = PDG_ROWT_WARPS;
 
-template <class T>
+// BATCHED (serving): descriptor D works on the arrays of request D.slot,
+// multi[D.slot]; otherwise on B.
+template <class T, bool BATCHED>
 __global__ void __launch_bounds__(32 * (kRowtWarps + 1)) k_rowdot_tma(const RowDesc* __restrict__ descs, int n_desc,
                                                                       const int64_t* __restrict__ blk_u, AxBases B,
-                                                                      int xcap, int* __restrict__ err) {
+                                                                      const AxBases* __restrict__ multi, int xcap,
+                                                                      int* __restrict__ err) {
     using namespace tma;
     constexpr int VN = VecN<T>::N;
     constexpr int RU = RowRows<T>::R;
@@ -1147,7 +1150,8 @@ __global__ void __launch_bounds__(32 * (kRowtWarps + 1)) k_rowdot_tma(const RowD
                     const int rows = min(RS, r_hi - r);
                     const uint32_t bytes = (uint32_t)rows * (uint32_t)D.ld * (uint32_t)sizeof(T);
                     mbar_arrive_expect_tx(&full[slot], bytes);
-                    bulk_g2s(ring + (size_t)slot * SE, pool + D.a_off + (int64_t)r * D.ld, bytes, &full[slot]);
+                    const T* pl = BATCHED ? reinterpret_cast<const T*>(multi[D.slot].pool) : pool;
+                    bulk_g2s(ring + (size_t)slot * SE, pl + D.a_off + (int64_t)r * D.ld, bytes, &full[slot]);
                     issued = g + 1;
                 }
             }
@@ -1170,8 +1174,9 @@ __global__ void __launch_bounds__(32 * (kRowtWarps + 1)) k_rowdot_tma(const RowD
         const int r_hi = min((int)(hi - D.u0) * RU, D.rows);
         const int RS = max(1, SE / D.ld);
         asm volatile("bar.sync 1, %0;" ::"n"(32 * kRowtWarps) : "memory");   // the previous x is no longer read
-        if (D.xidx_off >= 0) stage_planes(x0, x1, x2, D.cols, D.ld, B.x, B.bidx + D.xidx_off, threadIdx.x, 32 * kRowtWarps);
-        else stage_planes(x0, x1, x2, D.cols, D.ld, B.x + D.x_off, nullptr, threadIdx.x, 32 * kRowtWarps);
+        const AxBases Bd = BATCHED ? multi[D.slot] : B;
+        if (D.xidx_off >= 0) stage_planes(x0, x1, x2, D.cols, D.ld, Bd.x, Bd.bidx + D.xidx_off, threadIdx.x, 32 * kRowtWarps);
+        else stage_planes(x0, x1, x2, D.cols, D.ld, Bd.x + D.x_off, nullptr, threadIdx.x, 32 * kRowtWarps);
         asm volatile("bar.sync 1, %0;" ::"n"(32 * kRowtWarps) : "memory");
         for (int r = r_lo; r < r_hi; r += RS, ++g) {
             const int slot = g % S;
@@ -1223,11 +1228,11 @@ __global__ void __launch_bounds__(32 * (kRowtWarps + 1)) k_rowdot_tma(const RowD
                 }
                 if (lane == 0) {
                     const int row = r + j0;
-                    const float4 ad = (D.add_off >= 0) ? B.add[D.add_off + row] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    B.out[D.out_off + row] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
+                    const float4 ad = (D.add_off >= 0) ? Bd.add[D.add_off + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    Bd.out[D.out_off + row] = make_float4(ad.x + s0, ad.y + s1, ad.z + s2, 0.f);
                     if (two) {
-                        const float4 ae = (D.add_off >= 0) ? B.add[D.add_off + row + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        B.out[D.out_off + row + 1] = make_float4(ae.x + t0, ae.y + t1, ae.z + t2, 0.f);
+                        const float4 ae = (D.add_off >= 0) ? Bd.add[D.add_off + row + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        Bd.out[D.out_off + row + 1] = make_float4(ae.x + t0, ae.y + t1, ae.z + t2, 0.f);
                     }
                 }
             }
@@ -1505,8 +1510,8 @@ void launch_rowdot(const RowPlan& P, const AxBases& B, cudaStream_t s, int* tma_
                                                                                      B, P.xcap, tma_err);
     } else if (P.tma && tma_err) {
         const size_t smem = (size_t)kRowtStages * kRowtStageBytes + sizeof(float) * 3 * (size_t)P.xcap;
-        k_rowdot_tma<T><<<P.n_blocks, 32 * (kRowtWarps + 1), smem, s>>>(P.descs.p, P.n_desc, P.blk_u.p, B, P.xcap,
-                                                                       tma_err);
+        k_rowdot_tma<T, false><<<P.n_blocks, 32 * (kRowtWarps + 1), smem, s>>>(P.descs.p, P.n_desc, P.blk_u.p, B,
+                                                                              nullptr, P.xcap, tma_err);
     } else {
         k_rowdot<T><<<P.n_blocks, 32 * kRowWarps, sizeof(float) * 3 * (size_t)P.xcap, s>>>(P.descs.p, P.n_desc,
                                                                                              P.blk_u.p, B, P.xcap);
@@ -1805,8 +1810,9 @@ void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream
     }
     // bulk-copy streaming when a whole row fits in one stage (16-byte aligned rows: ld % 8 == 0)
     const int es = (prec == PD_PREC_BF16) ? 2 : 4;
-    const int optin_t = (prec == PD_PREC_BF16) ? allow_max_dynamic_smem(k_rowdot_tma<__nv_bfloat16>)
-                                               : allow_max_dynamic_smem(k_rowdot_tma<float>);
+    const int optin_t = (prec == PD_PREC_BF16) ? allow_max_dynamic_smem(k_rowdot_tma<__nv_bfloat16, false>)
+                                               : std::min(allow_max_dynamic_smem(k_rowdot_tma<float, false>),
+                                                          allow_max_dynamic_smem(k_rowdot_tma<float, true>));
     P.tma = (size_t)kRowtStages * kRowtStageBytes + smem <= (size_t)optin_t;
     for (const auto& d : descs) P.tma = P.tma && d.ld * es <= kRowtStageBytes && d.ld % 8 == 0 && d.a_off % 8 == 0;
     P.mma = false;
@@ -1828,6 +1834,18 @@ void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream
     PDG_CUDA(cudaStreamSynchronize(s));
     P.host = std::move(descs);
     P.n_blocks = C;
+}
+
+// Serving: one row-form launch over the descriptors of several requests (each
+// descriptor's slot selects its request's arrays); FP32 rows streamed by bulk
+// copies, so every row must fit one stage (checked when the plan is built).
+void launch_rowdot_b(const RowPlan& P, const AxBases* multi, int* err, cudaStream_t s) {
+    if (P.n_blocks <= 0) return;
+    if (!P.tma) throw Fail{PD_ERR_UNSUPPORTED};
+    const size_t smem = (size_t)kRowtStages * kRowtStageBytes + sizeof(float) * 3 * (size_t)P.xcap;
+    k_rowdot_tma<float, true><<<P.n_blocks, 32 * (kRowtWarps + 1), smem, s>>>(P.descs.p, P.n_desc, P.blk_u.p,
+                                                                             AxBases{}, multi, P.xcap, err);
+    PDG_CHECK_LAUNCH();
 }
 
 void launch_dd_solve(pd_mesh* m, const float4* b, float4* xout, cudaStream_t s, bool /*timed*/) {

@@ -200,7 +200,7 @@ struct RowDesc {
     int32_t xidx_off;      // >= 0: x_k = x[bidx[xidx_off + k]]
     int32_t add_off;       // >= 0: add offset
     int32_t out_off;
-    int32_t pad;
+    int32_t slot;          // serving batches: the request whose arrays the descriptor uses
 };
 // One row-form launch: its descriptors and the unit range of every block.
 struct RowPlan {
@@ -338,6 +338,10 @@ struct BatchSlot {
     const float* kfp_val;
     float4 *tc, *cB, *part;
     const int *gat_ptr, *gat;
+    // second level (two-level interface solve): c_T = c_B[T0:] - gathered t2 entries
+    const int *gat2_ptr, *gat2;
+    float4 *tc2, *cT;
+    int n_top, two_level;
     int* err;
     int* frame;          // frames completed (device counter)
     // plan of the fused local step + assembly (see LocalAsmArgs)

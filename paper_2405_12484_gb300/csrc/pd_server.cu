@@ -30,6 +30,9 @@ void launch_b_local_assemble(const BatchSlot* slots, const int* off, int n_slots
 void launch_b_assemble_shared(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_b_gather(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_b_reduce(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
+void launch_b_gather2(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
+void launch_rowdot_b(const RowPlan& P, const AxBases* multi, int* err, cudaStream_t s);
+void build_row_plan(RowPlan& P, std::vector<RowDesc> descs, int prec, cudaStream_t s, bool mma);
 void launch_b_velocity(const BatchSlot* slots, const int* off, int n_slots, int blocks, cudaStream_t s);
 void launch_axpy_b(const AxDesc* descs, const AxBlock* blocks, const AxBases* bases, int n_blocks, int k_max,
                    int w_max, int* err, cudaStream_t s);
@@ -75,7 +78,7 @@ struct Request {
 
 using Clock = std::chrono::steady_clock;
 
-enum { PH_DRIVE = 0, PH_INER, PH_LOC, PH_ASM, PH_GAT, PH_RED, PH_VEL, PH_NB };
+enum { PH_DRIVE = 0, PH_INER, PH_LOC, PH_ASM, PH_GAT, PH_RED, PH_VEL, PH_GAT2, PH_NB };
 
 }  // namespace
 
@@ -128,6 +131,9 @@ struct pd_server {
     DBuf<AxDesc> d_axc, d_axb;
     DBuf<AxBlock> d_blkc, d_blkb;
     DBuf<AxBases> d_basc, d_basb;
+    // two-level requests: the second level's row-form products over every such request
+    RowPlan rows_r2, rows_co, rows_b2;      // S_II^-1 and Psi2^T rows; S2^-1 rows; Psi2 rows
+    DBuf<AxBases> d_basr2, d_basco, d_basb2;
     int blocks_c = 0, blocks_b = 0, kmax_c = 1, kmax_b = 1, wmax_c = 1, wmax_b = 1;
     DBuf<CoarseDescB> d_cd;
     int n_cd = 0, max_cols = 0, coarse_blocks = 0;
@@ -191,6 +197,8 @@ static void rebuild(pd_server* S) {
     std::vector<AxBlock> blkc, blkb;
     std::vector<AxBases> basc(n), basb(n);
     std::vector<CoarseDescB> cd;
+    std::vector<RowDesc> r2, co, b2;
+    std::vector<AxBases> basr2(n), basco(n), basb2(n);
     int64_t units = 0;
     int max_cols = 0;
     for (int k = 0; k < n; ++k) {
@@ -226,6 +234,12 @@ static void rebuild(pd_server* S) {
         b.la_sh_vert = m->d_la_sh_vert.p;
         b.la_part = m->d_la_part.p;
         b.la_shared = m->la_shared;
+        b.two_level = m->two_level ? 1 : 0;
+        b.n_top = m->two_level ? m->n_top : 0;
+        b.gat2_ptr = m->d_gat2_ptr.p;
+        b.gat2 = m->d_gat2.p;
+        b.tc2 = m->d_tc2.p;
+        b.cT = m->d_cT.p;
         b.n_t = m->n_t;
         b.n_v = m->n_v;
         b.n_free = m->n_free;
@@ -241,9 +255,11 @@ static void rebuild(pd_server* S) {
         b.drive_w = 2.0f * 3.14159265358979f * R.freq;
         b.drive_axis = R.axis;
         // (the fused local step: one block per plan block; the finish of the shared vertices)
+        // (two levels: no partial sums to reduce, the second-level gather instead)
         const int cnt[PH_NB] = {(m->n_pin + 255) / 256, (m->n_v + 255) / 256, m->la_blocks,
-                                (m->la_shared + 255) / 256, (m->n_B + 255) / 256, (m->n_B + 255) / 256,
-                                (m->n_v + 255) / 256};
+                                (m->la_shared + 255) / 256, (m->n_B + 255) / 256,
+                                m->two_level ? 0 : (m->n_B + 255) / 256, (m->n_v + 255) / 256,
+                                m->two_level ? (m->n_top + 255) / 256 : 0};
         for (int p = 0; p < PH_NB; ++p) off[p][k + 1] = off[p][k] + cnt[p];
         const float* pool = m->d_mat32.p;
         basc[k] = AxBases{pool, m->d_b.p, nullptr, nullptr, m->d_tc.p};
@@ -259,7 +275,26 @@ static void rebuild(pd_server* S) {
             for (int32_t o0 = 0; o0 < a.n_out; o0 += a.ld) blkb.push_back(AxBlock{(int32_t)axb.size(), o0});
             axb.push_back(a);
         }
-        if (m->n_B > 0) {
+        if (m->two_level) {
+            // the single-mesh frame's second-level row plans, on this request's arrays
+            const int T0 = m->n_B - m->n_top;
+            basr2[k] = AxBases{pool, m->d_cB.p, nullptr, nullptr, m->d_tc2.p};
+            basco[k] = AxBases{pool, m->d_cT.p, nullptr, nullptr, m->d_x.p + m->n_int + T0};
+            basb2[k] = AxBases{pool, m->d_x.p + m->n_int + T0, m->d_bidx2.p, m->d_tc2.p, m->d_x.p + m->n_int};
+            for (const RowPlan* P : {&m->rows_int2, &m->rows_cond2})
+                for (RowDesc d : P->host) {
+                    d.slot = k;
+                    r2.push_back(d);
+                }
+            for (RowDesc d : m->rows_coarse.host) {
+                d.slot = k;
+                co.push_back(d);
+            }
+            for (RowDesc d : m->rows_back2.host) {
+                d.slot = k;
+                b2.push_back(d);
+            }
+        } else if (m->n_B > 0) {
             CoarseDescB c{};
             c.S = pool + m->off_S;
             c.cB = m->d_cB.p;
@@ -297,6 +332,12 @@ static void rebuild(pd_server* S) {
     }
     put(S->d_cd, cd, S->stream);
     S->n_cd = (int)cd.size();
+    put(S->d_basr2, basr2, S->stream);
+    put(S->d_basco, basco, S->stream);
+    put(S->d_basb2, basb2, S->stream);
+    build_row_plan(S->rows_r2, r2, PD_PREC_FP32, S->stream, false);
+    build_row_plan(S->rows_co, co, PD_PREC_FP32, S->stream, false);
+    build_row_plan(S->rows_b2, b2, PD_PREC_FP32, S->stream, false);
     S->units = units;
     S->max_cols = max_cols;
     S->coarse_blocks = 0;
@@ -318,8 +359,12 @@ static void rebuild(pd_server* S) {
             launch_b_assemble_shared(sl, S->d_off[PH_ASM].p, n, S->blocks[PH_ASM], c);
             launch_axpy_b(S->d_axc.p, S->d_blkc.p, S->d_basc.p, S->blocks_c, S->kmax_c, S->wmax_c, S->d_err.p, c);
             launch_b_gather(sl, S->d_off[PH_GAT].p, n, S->blocks[PH_GAT], c);
-            launch_coarse_b(S->d_cd.p, S->n_cd, S->units, S->max_cols, S->coarse_blocks, c);
+            launch_rowdot_b(S->rows_r2, S->d_basr2.p, S->d_err.p, c);
+            launch_b_gather2(sl, S->d_off[PH_GAT2].p, n, S->blocks[PH_GAT2], c);
+            if (S->n_cd > 0) launch_coarse_b(S->d_cd.p, S->n_cd, S->units, S->max_cols, S->coarse_blocks, c);
+            launch_rowdot_b(S->rows_co, S->d_basco.p, S->d_err.p, c);
             launch_b_reduce(sl, S->d_off[PH_RED].p, n, S->blocks[PH_RED], c);
+            launch_rowdot_b(S->rows_b2, S->d_basb2.p, S->d_err.p, c);
             launch_axpy_b(S->d_axb.p, S->d_blkb.p, S->d_basb.p, S->blocks_b, S->kmax_b, S->wmax_b, S->d_err.p, c);
         }
         launch_b_velocity(sl, S->d_off[PH_VEL].p, n, S->blocks[PH_VEL], c);
@@ -393,12 +438,21 @@ static void prepare_head(pd_server* S, std::unique_lock<std::mutex>& lk, cudaStr
     S->peak = std::max(S->peak, S->used + S->reserved);
     lk.unlock();
     st = pd_set_materials(m, R.gs.data(), R.gv.data());
-    pd_solver_opts o{PD_PREC_FP32, 0, 0, PD_SOLVE_SINGLE_LEVEL};  // the batched coarse kernel is single-level
+    // FP32; two interface levels where the prefactorisation chooses them and the batched
+    // row-form kernels can stream their rows (every row within one stage), else one level
+    pd_solver_opts o{PD_PREC_FP32, 0, 0, 0};
     m->batched_only = true;   // the serving loop runs its own batched kernels: no streaming copies
     if (st == PD_OK) {
         // the FP64 factorisation shares the GPU with the resident requests' frames: one at a time
         std::lock_guard<std::mutex> pk(S->prefactor_mu);
         st = pd_prefactor(m, R.dt, &o);
+        auto streamable = [](const RowPlan& P) { return P.n_blocks == 0 || P.tma; };
+        if (st == PD_OK && m->two_level &&
+            !(m->rows_coarse.n_blocks > 0 && streamable(m->rows_coarse) && streamable(m->rows_int2) &&
+              streamable(m->rows_cond2) && streamable(m->rows_back2))) {
+            o.flags = PD_SOLVE_SINGLE_LEVEL;
+            st = pd_prefactor(m, R.dt, &o);
+        }
     }
     if (st == PD_OK) {
         try {

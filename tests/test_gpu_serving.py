@@ -209,3 +209,30 @@ def test_frame_latencies_include_the_stalls():
         assert lat.shape == (6,)
         assert np.all(lat >= min(gpu) * 0.99)
     S.close()
+
+
+def test_two_level_requests_in_the_batch():
+    """A request large enough for the two-level interface solve is served with
+    the second level's batched row-form products: the same result alone and
+    beside a one-level request (bitwise), and the single-mesh stepper's
+    result within the FP32 tolerance."""
+    from paper_2405_12484_gb300.sim import Mesh
+    big = sweater_shell(seed=25, n_theta=200, n_z=60, n_r=2, dom_theta=20, dom_z=6)
+    small = slab_workload(8, 8, 2, 0.01, 6, (2, 2), seed=26, n_iter=20, name="r-slab8b")
+    frames = 3
+    m = Mesh(big.rest, big.tets, big.pinned, big.tet_domain, big.n_domains, big.density)
+    m.set_materials(big.gamma_s, big.gamma_v)
+    m.prefactor(big.dt)
+    info = m.info()
+    assert info["two_level"] == 1 and info["n_top_interface"] * 4 <= 24576, info
+    x = torch.empty((big.n_v, 3), device="cuda")
+    for n in range(frames):
+        m.step(torch.as_tensor(big.pin_targets(n), dtype=torch.float32), big.gravity, 20, x_out=x)
+    m.sync()
+    ref = x.cpu().numpy().astype(np.float64)
+    m.close()
+    alone, _, _ = _run([(big, (0.2, 1.0, 0))], frames, wait_admitted=True)
+    mix, _, _ = _run([(small, None), (big, (0.2, 1.0, 0))], frames, wait_admitted=True)
+    assert np.array_equal(alone[0], mix[1])
+    e = np.linalg.norm(alone[0] - ref) / np.linalg.norm(ref)
+    assert e < 1e-5, e
