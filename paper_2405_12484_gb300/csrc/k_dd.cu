@@ -717,12 +717,26 @@ __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_mma(const AxDesc*
 __global__ void k_gather(int n_B, const int* __restrict__ ptr, const int* __restrict__ rows,
                          const float4* __restrict__ bB, const float4* __restrict__ tc, float4* __restrict__ cB) {
     pdl_trigger();
-    pdl_wait();
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_B) return;
+    // the index lists are constant: read them (the first four entries) before
+    // the wait for the predecessor, so only the sums' own loads follow it
+    constexpr int kPre = 4;
+    const int k0 = ptr[j], k1 = ptr[j + 1];
+    int r[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) r[q] = (k0 + q < k1) ? rows[k0 + q] : -1;
+    pdl_wait();
     float4 acc = bB[j];
-    for (int k = ptr[j]; k < ptr[j + 1]; ++k) {
-        float4 c = tc[rows[k]];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+        if (r[q] >= 0) {
+            const float4 c = tc[r[q]];
+            acc.x += c.x; acc.y += c.y; acc.z += c.z;
+        }
+    }
+    for (int k = k0 + kPre; k < k1; ++k) {
+        const float4 c = tc[rows[k]];
         acc.x += c.x; acc.y += c.y; acc.z += c.z;
     }
     cB[j] = acc;
