@@ -100,6 +100,53 @@ __device__ __forceinline__ void stage_f4(float4* __restrict__ xs, int n, const f
     }
 }
 
+// stage_f4 in two parts around the wait for the predecessor: the indices of
+// the first kStageU entries per thread (constant) before it, the values after.
+struct StageIdx {
+    int id[kStageU];
+};
+
+__device__ __forceinline__ void stage_f4_indices(StageIdx& S, int n, const int* __restrict__ idx, int tid,
+                                                 int nthreads) {
+#pragma unroll
+    for (int u = 0; u < kStageU; ++u) {
+        const int k = tid + u * nthreads;
+        S.id[u] = k < n ? (idx ? idx[k] : k) : -1;
+    }
+}
+
+__device__ __forceinline__ void stage_f4_values(float4* __restrict__ xs, int n, const float4* __restrict__ x,
+                                                const int* __restrict__ idx, const StageIdx& S, int tid,
+                                                int nthreads) {
+    float4 v[kStageU];
+#pragma unroll
+    for (int u = 0; u < kStageU; ++u) v[u] = S.id[u] >= 0 ? x[S.id[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < kStageU; ++u) {
+        const int k = tid + u * nthreads;
+        if (k < n) xs[k] = v[u];
+    }
+    // entries beyond the first kStageU per thread (not on the shell's meshes)
+    if (n > nthreads * kStageU) {
+        for (int base = tid + nthreads * kStageU; base < n; base += nthreads * kStageU) {
+            int id[kStageU];
+#pragma unroll
+            for (int u = 0; u < kStageU; ++u) {
+                const int k = base + u * nthreads;
+                id[u] = k < n ? (idx ? idx[k] : k) : -1;
+            }
+            float4 w[kStageU];
+#pragma unroll
+            for (int u = 0; u < kStageU; ++u) w[u] = id[u] >= 0 ? x[id[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kStageU; ++u) {
+                const int k = base + u * nthreads;
+                if (k < n) xs[k] = w[u];
+            }
+        }
+    }
+}
+
 // three float planes x0/x1/x2[k] = x[idx ? idx[k] : k] for k < n_valid, 0 for n_valid <= k < n
 __device__ __forceinline__ void stage_planes(float* __restrict__ x0, float* __restrict__ x1, float* __restrict__ x2,
                                              int n_valid, int n, const float4* __restrict__ x,
@@ -408,8 +455,13 @@ __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_tma(const AxDesc*
         return;
     }
     // consumers (the producer streams the constant tile without waiting for the predecessor)
-    pdl_wait();
-    stage_f4(xs, D.K, B.x + D.x_off, D.bidx_off >= 0 ? B.bidx + D.bidx_off : nullptr, threadIdx.x, 32 * kAxtWarps);
+    {
+        const int* xi = D.bidx_off >= 0 ? B.bidx + D.bidx_off : nullptr;
+        StageIdx si;
+        stage_f4_indices(si, D.K, xi, threadIdx.x, 32 * kAxtWarps);   // constant: before the wait
+        pdl_wait();
+        stage_f4_values(xs, D.K, B.x + D.x_off, xi, si, threadIdx.x, 32 * kAxtWarps);
+    }
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kAxtWarps) : "memory");
     float acc[VN][3];
 #pragma unroll
@@ -606,8 +658,13 @@ __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_mma(const AxDesc*
         return;
     }
     // consumers: stage x, then the A operands of every k-block (hi rows 0..2, remainders 8..10)
-    pdl_wait();
-    stage_f4(xs, D.K, B.x + D.x_off, D.bidx_off >= 0 ? B.bidx + D.bidx_off : nullptr, threadIdx.x, 32 * kAxtWarps);
+    {
+        const int* xi = D.bidx_off >= 0 ? B.bidx + D.bidx_off : nullptr;
+        StageIdx si;
+        stage_f4_indices(si, D.K, xi, threadIdx.x, 32 * kAxtWarps);   // constant: before the wait
+        pdl_wait();
+        stage_f4_values(xs, D.K, B.x + D.x_off, xi, si, threadIdx.x, 32 * kAxtWarps);
+    }
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kAxtWarps) : "memory");
     if (TF32) {
         // a0 = (row g, k q), a1 = (row g + 8, k q), a2 = (row g, k q + 4), a3 = (row g + 8, k q + 4)
