@@ -1788,8 +1788,8 @@ void test_set_copy_extra(int bytes, cudaStream_t s) {
 
 // raise the dynamic shared-memory limit of the bulk-copy kernel (outside any capture)
 void ax_prepare_tma(int prec) {
-    if (prec == PD_PREC_BF16) (void)axm_smem_limit();
-    else (void)axt_smem_limit<float>();
+    if (prec == PD_PREC_BF16 || prec == PD_PREC_TF32) (void)axm_smem_limit();   // the tensor-core tile kernels
+    if (prec != PD_PREC_BF16) (void)axt_smem_limit<float>();
 }
 
 // Returns false when the largest interface vector does not fit in shared memory.
