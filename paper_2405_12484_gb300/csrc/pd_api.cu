@@ -350,6 +350,11 @@ pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tet
     m->n_dom = n_domains;
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     pdg::AllocStreamScope alloc_scope(m->stream);
+    {
+        int dev = 0;
+        PDG_CUDA(cudaGetDevice(&dev));
+        PDG_CUDA(cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, dev));
+    }
 
     // ---- validate tets, rest operators (Dm^-1, V_e); fix orientation
     std::vector<int32_t> T(tets, tets + 4 * (size_t)n_t);
@@ -1660,7 +1665,7 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
                 sb += (int64_t)D.K * D.ld * es + (int64_t)D.K * 16 + (int64_t)D.n_out * (D.akind >= 0 ? 32 : 16);
             m->phase_bytes[PH_SOLVE] = sb;
         }
-        int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (m->ax_blocks_int > 0 ? 1 : 0) +
+        int dd = (m->ax_blocks_cond > 0 ? 1 : 0) + (m->ax_blocks_int > 0 ? (m->ax_blocks_int > 3 * m->sms ? 2 : 1) : 0) +
                  (n_B > 0 ? (m->rows_coarse.n_blocks > 0 ? 2 : 3) : 0) + (m->ax_blocks_back > 0 ? 1 : 0);
         if (modal) dd += (m->ax_blocks_m1 > 0 ? 2 : 0) + (int)m->jacobi_omega.size();
         if (two)

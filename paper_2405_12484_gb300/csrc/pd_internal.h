@@ -484,6 +484,7 @@ struct pd_mesh {
     pdg::DBuf<float4> d_jx1, d_jx2;         // Jacobi iterates
     std::vector<float> jacobi_omega;        // Chebyshev weights of the sweeps
     bool batched_only = false;             // set by the serving loop: no streaming plans
+    int32_t sms = 1;                       // multiprocessors of the mesh's device
     pdg::StreamPlan st_solve;
     pdg::DBuf<int32_t> d_bidx2, d_gat2_ptr, d_gat2;
     pdg::DBuf<float4> d_tc2, d_cT;
