@@ -451,7 +451,9 @@ def time_leg(m, w, info, pins, n_iter, K, W, stream, local, world, phase_report=
         m.step(pins[n], w.gravity, n_iter)
     m.sync()
     warm = m.phase_times()
-    per_iter = {k: v for k, v in warm.items() if k not in ("inertia", "velocity") and v > 0}
+    # time per PD iteration: the mean per launch times the phase's launches per iteration
+    per_iter = {k: v * max(1, info.get("phase_launches", {}).get(k, 1)) for k, v in warm.items()
+                if k not in ("inertia", "velocity") and v > 0}
     t_max = max(per_iter.values())
     # near-ties (kernels that run side by side): the one streaming the most bytes
     dominant = max((k for k, v in per_iter.items() if v >= 0.9 * t_max), key=lambda k: info["phase_bytes"][k])
@@ -572,11 +574,14 @@ def main():
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
                 "traffic": traffic, "algorithmic_bytes": dom_bytes, "avg_launch_ms": dom_ms,
-                "launches_timed": K, "timed": f"CUDA events on the mesh stream, one launch per timed frame "
-                                             f"(PD iteration {leg['dom_sampled_iteration']})"}
+                "launches_timed": K * max(1, info["phase_launches"][dominant]),
+                "timed": f"CUDA events on the mesh stream around each launch of the kernel in PD iteration "
+                         f"{leg['dom_sampled_iteration']} of every timed frame ({info['phase_launches'][dominant]} "
+                         f"per iteration; bytes and time per launch)"}
     if dominant in ("dd_interior", "dd_interior2"):
         roofline["note"] = ("runs on a low-priority side stream beside the interface chain (off the critical "
-                            "path): its live duration includes the time it yields the GPU to that chain")
+                            "path): its live duration includes the time it yields the GPU to that chain; a large "
+                            "product goes out as two launches of half its tiles, each timed and counted alone")
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region;
     # the same captured frame as the timed region (with the dominant kernel's events)

@@ -121,6 +121,8 @@ typedef struct pd_mesh_info {
     int32_t n_groups;              /* domain groups of the two-level interface solve (0 = single level) */
     int32_t n_top_interface;       /* interface vertices shared by two or more groups */
     int32_t two_level;             /* 1 when the last pd_prefactor built the two-level interface solve */
+    int32_t phase_launches[24];    /* launches of each phase per PD iteration (per frame for the phases
+                                      outside the loop); phase_bytes and pd_phase_times are per launch */
 } pd_mesh_info;
 
 /*

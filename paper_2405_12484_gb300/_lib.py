@@ -46,7 +46,7 @@ class pd_mesh_info(C.Structure):
                 ("device_bytes", C.c_int64), ("prefactor_seconds", C.c_double),
                 ("launches_per_iter", C.c_int32), ("launches_per_frame", C.c_int32),
                 ("phase_bytes", C.c_int64 * 24), ("n_groups", C.c_int32), ("n_top_interface", C.c_int32),
-                ("two_level", C.c_int32)]
+                ("two_level", C.c_int32), ("phase_launches", C.c_int32 * 24)]
 
 
 class pd_fit_opts(C.Structure):

@@ -1647,17 +1647,18 @@ void dd_solve_impl(pd_mesh* m, const T* pool, const float4* b, float4* xout, con
                          AxBases{pool, w.pm, nullptr, nullptr, w.tc}, m->side[0]);
             phase_end(m, m->side[0]);
         } else {
-            phase_begin(m, PH_INTERIOR, m->side[0]);
             // In two launches when it has more than three blocks per SM: one launch of all its
             // tiles fills every SM with interior blocks, and the interface chain's blocks wait
             // for slots (measured on the 390K shell: 800 tiles in two launches 2.126 ms/frame,
             // one 2.197, three 2.236)
             const int nb = m->ax_blocks_int, parts = nb > 3 * m->sms ? 2 : 1, per = (nb + parts - 1) / parts;
-            for (int b0 = 0; b0 < nb; b0 += per)
+            for (int b0 = 0; b0 < nb; b0 += per) {
+                phase_begin(m, PH_INTERIOR, m->side[0]);   // (timed per launch)
                 launch_ax<T>(m->d_ax_desc_int.p, m->d_ax_blk_int.p + b0, std::min(per, nb - b0), m->ax_kmax_int,
                              AxBases{pool, b, nullptr, nullptr, w.tc}, m->side[0], m->ax_tiled ? m->d_err.p : nullptr,
                              m->ax_wmax_int, false, m->ax_tf32);
-            phase_end(m, m->side[0]);
+                phase_end(m, m->side[0]);
+            }
         }
         PDG_CUDA(cudaEventRecord(m->ev_join[0], m->side[0]));
     }

@@ -350,11 +350,6 @@ pd_status pd_create_mesh(const double* rest_xyz, int32_t n_v, const int32_t* tet
     m->n_dom = n_domains;
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     pdg::AllocStreamScope alloc_scope(m->stream);
-    {
-        int dev = 0;
-        PDG_CUDA(cudaGetDevice(&dev));
-        PDG_CUDA(cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, dev));
-    }
 
     // ---- validate tets, rest operators (Dm^-1, V_e); fix orientation
     std::vector<int32_t> T(tets, tets + 4 * (size_t)n_t);
@@ -729,6 +724,11 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = m->stream;
     m->prefactored = false;
+    {
+        int dev = 0;
+        PDG_CUDA(cudaGetDevice(&dev));
+        PDG_CUDA(cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, dev));
+    }
     for (auto& kv : m->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     m->graphs.clear();
@@ -1628,7 +1628,9 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
         m->phase_bytes[PH_ASSEMBLE] = 0;
         (void)ninc;
         m->phase_bytes[PH_CONDENSE] = mat_c + (int64_t)n_int * 16 + nbd_tot * 16;
-        m->phase_bytes[PH_INTERIOR] = mat_i + (int64_t)n_int * 32;
+        // (per launch: the interior product goes out in two launches when it has more than
+        // three tiles per SM, see the solve)
+        m->phase_bytes[PH_INTERIOR] = (mat_i + (int64_t)n_int * 32) / (m->ax_blocks_int > 3 * m->sms ? 2 : 1);
         if (modal) {
             int64_t mb = 0;
             for (int32_t d = 0; d < n_dom; ++d)
@@ -1673,6 +1675,9 @@ pd_status pd_prefactor(pd_mesh* m, double dt, const pd_solver_opts* opts) {
                   (m->rows_back2.n_blocks > 0 ? 1 : 0);
         if (m->use_stream) dd = 1;   // the fused solve
         m->launches_per_iter = 1 + (m->la_shared > 0 ? 1 : 0) + dd + (m->correction ? 1 : 0) + m->refine * (2 + dd);
+        for (int k = 0; k < 24; ++k) m->phase_launches[k] = m->phase_bytes[k] > 0 ? 1 : 0;
+        if (m->phase_bytes[PH_INTERIOR] > 0 && m->ax_blocks_int > 3 * m->sms) m->phase_launches[PH_INTERIOR] = 2;
+        if (m->phase_bytes[PH_RESIDUAL] > 0) m->phase_launches[PH_RESIDUAL] = m->refine;
     }
 
     // (the flag is read on the mesh's stream, never through the legacy default stream)
@@ -1888,6 +1893,7 @@ pd_status pd_get_info(pd_mesh* m, pd_mesh_info* out) {
     out->launches_per_iter = m->launches_per_iter;
     out->launches_per_frame = 3;   // pin copy (or hold), inertia, velocity
     for (int k = 0; k < 24; ++k) out->phase_bytes[k] = m->phase_bytes[k];
+    for (int k = 0; k < 24; ++k) out->phase_launches[k] = m->phase_launches[k];
     return PD_OK;
 }
 

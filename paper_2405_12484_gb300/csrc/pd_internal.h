@@ -519,6 +519,7 @@ struct pd_mesh {
     bool use_graphs = true;
     double prefactor_seconds = 0.0;
     int64_t phase_bytes[24] = {0};
+    int32_t phase_launches[24] = {0};   // launches of each phase per PD iteration (or per frame)
     int32_t launches_per_iter = 0;
 
     // per-phase timing: the event pairs recorded by one captured graph (or by

@@ -132,8 +132,9 @@ class Mesh:
     def info(self) -> dict:
         i = _lib.pd_mesh_info()
         _check(lib().pd_get_info(self._h, C.byref(i)), "pd_get_info")
-        d = {k: getattr(i, k) for k, _ in _lib.pd_mesh_info._fields_ if k != "phase_bytes"}
+        d = {k: getattr(i, k) for k, _ in _lib.pd_mesh_info._fields_ if k not in ("phase_bytes", "phase_launches")}
         d["phase_bytes"] = {PHASES[k]: int(i.phase_bytes[k]) for k in range(len(PHASES))}
+        d["phase_launches"] = {PHASES[k]: int(i.phase_launches[k]) for k in range(len(PHASES))}
         return d
 
     # -- diagnostics -------------------------------------------------------------
