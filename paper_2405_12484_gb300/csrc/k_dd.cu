@@ -538,12 +538,8 @@ __global__ void __launch_bounds__(32 * (kAxtWarps + 1)) k_axpy_tma(const AxDesc*
 // product carry x to about 16 bits while the matrix is BF16.  Output n of
 // right-hand side c is D[c][n] + D[c + 8][n].  The consumer warps own
 // disjoint output columns (no cross-warp reduction); the copy ring, the
-// producer lane and the bounded waits are those of k_axpy_tma.
-__host__ __device__ inline int64_t mma_frag_index(int r, int c_in_tile, int w) {
-    const int kb = r >> 4, kk = r & 15, nb = c_in_tile >> 3, n = c_in_tile & 7;
-    const int q = (kk & 7) >> 1, j = (kk & 1) + ((kk >> 3) << 1);
-    return ((int64_t)kb * (w >> 3) + nb) * 128 + (4 * n + q) * 4 + j;
-}
+// producer lane and the bounded waits are those of k_axpy_tma.  (The tiles
+// are written in this order by k_cast_frag16 at prefactorisation.)
 
 __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
@@ -1319,16 +1315,11 @@ __global__ void __launch_bounds__(32 * (kRowtWarps + 1)) k_rowdot_tma(const RowD
 // contiguous range), so one 16-byte shared load per lane feeds one mma.
 // The B operand is x: columns 0..2 hold x, y, z rounded to BF16, columns
 // 3..5 their BF16 remainders.  A CTA streams whole 16-row block-rows of its
-// unit range in stages of up to kRowtStageBytes with bulk copies; the 16-col
+// unit range in stages of up to kRowmStageBytes with bulk copies; the 16-col
 // blocks of a stage go to the consumer warps in turn, each warp accumulating
 // its own 16 x 8 tile, and the warps' tiles are added in warp order
-// (deterministic) before the 16 outputs of the block-row are written.
-__host__ __device__ inline int64_t rowfrag_index(int r, int c, int Kp) {
-    const int rb = r >> 4, kb = c >> 4, rr = r & 15, kk = c & 15;
-    const int g = rr & 7, rhi = rr >> 3, q = (kk & 7) >> 1, j = kk & 1, khi = kk >> 3;
-    return ((int64_t)rb * (Kp >> 4) + kb) * 256 + (4 * g + q) * 8 + (rhi + 2 * khi) * 2 + j;
-}
-
+// (deterministic) before the 16 outputs of the block-row are written.  The
+// blocks are written in this order by k_cast_rowfrag16 at prefactorisation.
 __device__ __forceinline__ void mma_bf16_rowform(float (&d)[4], const uint4& a, const uint2& b) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
