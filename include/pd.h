@@ -562,7 +562,10 @@ typedef struct pd_request {
  * iteration count of every frame.  Admission threads of the server build
  * and prefactor queued requests, each on its own stream of the device's
  * lowest priority, while the resident ones keep advancing; the first of them
- * also frees the meshes of retired requests.  The frames run on a stream of
+ * also frees the meshes of retired requests.  Requests are prefactored in
+ * FP32, with the two-level interface solve where pd_prefactor chooses it and
+ * every row of its row-form blocks fits one bulk-copy stage (else one
+ * level).  The frames run on a stream of
  * the server's own at the device's highest priority (ahead of admission work
  * whenever an SM frees up).  Requests and results are host arrays, so the
  * frames need no ordering with the caller's work; if cuda_stream is not
