@@ -439,6 +439,16 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+def dominant_phase(per_launch_ms: dict, phase_bytes: dict, phase_launches: dict) -> str:
+    """The kernel class with the largest time per PD iteration (mean time per
+    launch x launches per iteration); among near-ties (kernels that run side
+    by side) the one streaming the most bytes per launch."""
+    per_iter = {k: v * max(1, phase_launches.get(k, 1)) for k, v in per_launch_ms.items()
+                if k not in ("inertia", "velocity") and v > 0}
+    t_max = max(per_iter.values())
+    return max((k for k, v in per_iter.items() if v >= 0.9 * t_max), key=lambda k: phase_bytes.get(k, 0))
+
+
 def time_leg(m, w, info, pins, n_iter, K, W, stream, local, world, phase_report=True):
     """Warm-up with every phase timed (the phase with the largest time per
     frame is the dominant kernel), then K frames timed with CUDA events on the
@@ -451,12 +461,7 @@ def time_leg(m, w, info, pins, n_iter, K, W, stream, local, world, phase_report=
         m.step(pins[n], w.gravity, n_iter)
     m.sync()
     warm = m.phase_times()
-    # time per PD iteration: the mean per launch times the phase's launches per iteration
-    per_iter = {k: v * max(1, info.get("phase_launches", {}).get(k, 1)) for k, v in warm.items()
-                if k not in ("inertia", "velocity") and v > 0}
-    t_max = max(per_iter.values())
-    # near-ties (kernels that run side by side): the one streaming the most bytes
-    dominant = max((k for k, v in per_iter.items() if v >= 0.9 * t_max), key=lambda k: info["phase_bytes"][k])
+    dominant = dominant_phase(warm, info["phase_bytes"], info.get("phase_launches", {}))
     # events around the dominant kernel in one PD iteration of every frame (an event pair
     # in every iteration would add its own cost to the frame time)
     sample_it = n_iter // 2

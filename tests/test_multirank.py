@@ -38,3 +38,15 @@ def test_single_rank_needs_no_process_group():
     import bench
     value, t = bench.whole_job_rate(20, 10.0, 1)
     assert t == 10.0 and value == pytest.approx(2000.0)
+
+
+def test_dominant_phase_counts_every_launch_of_a_phase():
+    """The dominant kernel class is chosen by its time per PD iteration: a
+    phase split over two launches counts both; near-ties go to the larger
+    byte stream; the kernels outside the iteration loop are not candidates."""
+    import bench
+    times = {"dd_interior": 0.030, "dd_condense": 0.026, "local": 0.031, "inertia": 0.5, "velocity": 0.4}
+    nbytes = {"dd_interior": 71_000_000, "dd_condense": 48_000_000, "local": 44_000_000}
+    assert bench.dominant_phase(times, nbytes, {"dd_interior": 2, "dd_condense": 1, "local": 1}) == "dd_interior"
+    assert bench.dominant_phase(times, nbytes, {"dd_interior": 1, "dd_condense": 1, "local": 1}) == "dd_interior"
+    assert bench.dominant_phase({"local": 0.031, "dd_condense": 0.020}, nbytes, {}) == "local"
