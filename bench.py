@@ -73,6 +73,9 @@ def parse():
 # ("dd_interior", fp32, two levels): the ncu capture of the interior k_axpy_tma launch on the
 # 153,600-tet shell; the interior is one tile stream per domain, so the ratio carries over to the
 # full-size launch.
+# Thread instructions per tet and SIMT efficiency of the fused local step from its ncu capture
+# (profiles/k_local_assemble_shell153k_fp32.md): its roofline is the issue rate, not HBM.
+LOCAL_THREAD_INSTR_PER_TET, LOCAL_SIMT = 1052.0, 22.41
 TRAFFIC_RATIO = {("dd_interior", "fp32", "two"): 0.9931, ("dd_interior", "bf16", "two"): 0.991}
 
 
@@ -587,6 +590,28 @@ def main():
         roofline["note"] = ("runs on a low-priority side stream beside the interface chain (off the critical "
                             "path): its live duration includes the time it yields the GPU to that chain; a large "
                             "product goes out as two launches of half its tiles, each timed and counted alone")
+    # the same figures for the kernel class that takes the most time on the critical path (the
+    # side-stream products excluded), from the phase-report frames where every phase carries events
+    critical = None
+    ph = leg.get("phases", {})
+    cands = {k: v["ms"] * max(1, info["phase_launches"].get(k, 1)) for k, v in ph.items()
+             if k not in ("inertia", "velocity", "dd_interior", "dd_interior2") and v.get("bytes", 0) > 0}
+    if cands:
+        ck = max(cands, key=cands.get)
+        critical = {"kernel": ck, "achieved": ph[ck]["GB/s"], "peak": peak, "unit": "GB/s", "frac": ph[ck]["frac"],
+                    "algorithmic_bytes": ph[ck]["bytes"], "avg_launch_ms": ph[ck]["ms"],
+                    "timed": "phase-report frames after the timed region, every kernel class between CUDA events"}
+        if ck == "local" and not args.small:
+            # issue-rate roofline: warp instructions of the launch against 4 per SM and cycle at the SM clock
+            sm_hz = (leg["clocks"].get("sm_max_mhz") or 2070.0) * 1e6
+            warp_instr = w.n_t * LOCAL_THREAD_INSTR_PER_TET / LOCAL_SIMT
+            peak_issue = torch.cuda.get_device_properties(local).multi_processor_count * 4 * sm_hz
+            achieved_issue = warp_instr / (ph[ck]["ms"] * 1e-3)
+            critical["alu"] = {"bound": "alu", "warp_instructions": warp_instr, "achieved": achieved_issue,
+                               "peak": peak_issue, "unit": "warp instructions/s", "frac": achieved_issue / peak_issue,
+                               "source": "instructions per tet and SIMT efficiency of k_local_assemble from its ncu "
+                                         "capture over the phase's time (which includes k_assemble_shared); "
+                                         "peak = SMs x 4 schedulers x 1 instruction per cycle x SM clock"}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region;
     # the same captured frame as the timed region (with the dominant kernel's events)
@@ -682,6 +707,7 @@ def main():
             "frame_ms": {"p50": pct(leg["frame_ms"], 0.5), "p99": pct(leg["frame_ms"], 0.99),
                          "min": min(leg["frame_ms"]), "max": max(leg["frame_ms"])},
             "roofline": roofline,
+            "roofline_critical_path": critical,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pin_d.numel() * 4),
                     "d2h_bytes_per_step": int(w.n_v * 3 * 4), "ms_per_step": e2e_ms / K},
