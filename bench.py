@@ -166,10 +166,16 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
+        return self.summarize(self.path, getattr(self, "t0", None), getattr(self, "t1", None))
+
+    @staticmethod
+    def summarize(path, t0, t1):
+        """Median SM clock, max clock and the throttle reasons seen in the samples of
+        the timed window [t0, t1] (host wall time; all samples if none fall inside)."""
         import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         rows = []
-        for line in open(self.path):
+        for line in open(path):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 10:
                 continue
@@ -178,7 +184,6 @@ class ClockSampler:
                 rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-        t0, t1 = getattr(self, "t0", None), getattr(self, "t1", None)
         inside = [r for r in rows if t0 is not None and t1 is not None and t0 - 0.05 <= r[0] <= t1 + 0.05]
         use = inside or rows
         sm = [r[1] for r in use]

@@ -50,3 +50,24 @@ def test_dominant_phase_counts_every_launch_of_a_phase():
     assert bench.dominant_phase(times, nbytes, {"dd_interior": 2, "dd_condense": 1, "local": 1}) == "dd_interior"
     assert bench.dominant_phase(times, nbytes, {"dd_interior": 1, "dd_condense": 1, "local": 1}) == "dd_interior"
     assert bench.dominant_phase({"local": 0.031, "dd_condense": 0.020}, nbytes, {}) == "local"
+
+
+def test_clock_samples_are_read_inside_the_timed_window(tmp_path):
+    """nvidia-smi samples outside the timed window do not count; a throttle
+    reason active inside it is reported (such a run is re-measured)."""
+    import datetime
+    import bench
+    t0 = datetime.datetime(2026, 1, 1, 12, 0, 0).timestamp()
+    rows = []
+    for k, (mhz, hw) in enumerate([(1200.0, "Not Active"), (2070.0, "Not Active"), (2070.0, "Active"),
+                                   (2055.0, "Not Active"), (900.0, "Not Active")]):
+        ts = datetime.datetime.fromtimestamp(t0 + 0.3 * k).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        rows.append(f"{ts}, 0, {mhz}, 2070, 900.0, 0x0, {hw}, Not Active, Not Active, Not Active")
+    p = tmp_path / "clocks.csv"
+    p.write_text("\n".join(rows) + "\n")
+    out = bench.ClockSampler.summarize(str(p), t0 + 0.25, t0 + 0.95)   # samples 1, 2, 3
+    assert out["samples"] == 3 and out["in_timed_window"]
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["hw_slowdown"]
+    everything = bench.ClockSampler.summarize(str(p), None, None)
+    assert everything["samples"] == 5 and not everything["in_timed_window"]
