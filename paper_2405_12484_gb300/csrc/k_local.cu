@@ -27,6 +27,10 @@
 // cheapest candidate is kept; the face with d_3 clamped to 0.01 (d_1 d_2 = 100,
 // the same construction) is tried when the first face has no feasible point
 // or a - root under the clamp; failing both, d = (1e4, 0.01, 0.01).
+//
+// The serving loop runs the same block code over every resident request in
+// one launch (k_b_local_assemble, k_b_assemble_shared).
+
 #include <algorithm>
 
 #include "pd_internal.h"
